@@ -1,0 +1,175 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module holds geometry and random numbers only: phase maps (spheres,
+random sequential addition of spheres, laminates), material parameter tables
+and random deformation fields. It contains none of the homogenization
+method's arithmetic (no projection, no constitutive law, no solver), so both
+the CPU oracle and the CUDA path may take their inputs from here without
+sharing any computational code.
+
+Conventions
+-----------
+* A grid is ``(nx, ny, nz)``; voxel ``(i, j, k)`` has its centre at
+  ``((i + 1/2) h_x, (j + 1/2) h_y, (k + 1/2) h_z)`` in a periodic box of side
+  lengths ``L = (1, 1, 1)`` unless stated otherwise.
+* A phase map is a C-contiguous ``uint8`` array of shape ``(nx, ny, nz)``
+  (z fastest), value ``p`` selecting row ``p`` of a parameter table.
+* A parameter table is a float64 array of shape ``(n_phase, 2)`` holding the
+  Lame pair ``(lambda, mu)`` of each phase.
+* Tensor fields are float64 arrays of shape ``(9, nx, ny, nz)`` with component
+  index ``3*i + j`` for the entry ``F_ij`` (row-major 3x3).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "lame_from_bulk_shear",
+    "centered_sphere",
+    "random_spheres",
+    "laminate",
+    "two_phase_table",
+    "random_deformation",
+    "shear_macro",
+    "small_strain_config",
+    "neo_hookean_config",
+]
+
+
+def lame_from_bulk_shear(bulk: float, shear: float) -> tuple[float, float]:
+    """Lame pair (lambda, mu) of an isotropic solid from bulk and shear moduli."""
+    return bulk - 2.0 * shear / 3.0, shear
+
+
+def _periodic_sq_dist(n: int, c: float) -> np.ndarray:
+    """Squared periodic minimum-image distance (in voxels) of voxel centres to c."""
+    x = np.arange(n) + 0.5 - c
+    x = x - n * np.round(x / n)
+    return x * x
+
+
+def centered_sphere(n: tuple[int, int, int], radius_frac: float = 0.25,
+                    center_frac: tuple[float, float, float] = (0.5, 0.5, 0.5)) -> np.ndarray:
+    """Phase map of one sphere (phase 1) in a matrix (phase 0).
+
+    The sphere has radius ``radius_frac * nx`` voxels and its centre at
+    ``center_frac * n`` (in voxel units). A voxel is inside iff the periodic
+    minimum-image distance of its centre to the sphere centre is <= r.
+    """
+    nx, ny, nz = n
+    r = radius_frac * nx
+    d2 = (_periodic_sq_dist(nx, center_frac[0] * nx)[:, None, None]
+          + _periodic_sq_dist(ny, center_frac[1] * ny)[None, :, None]
+          + _periodic_sq_dist(nz, center_frac[2] * nz)[None, None, :])
+    return (d2 <= r * r).astype(np.uint8)
+
+
+def random_spheres(n: int, seed: int, r_min: float = 4.0, r_max: float = 10.0,
+                   target_fraction: float = 0.30, max_attempts: int = 200000) -> np.ndarray:
+    """Random sequential addition of non-overlapping spheres on an n^3 grid.
+
+    Radii are drawn uniformly in [r_min, r_max] voxels and centres uniformly in
+    the periodic box; a candidate is rejected when its periodic centre
+    distance to any accepted sphere is below the sum of the radii. Spheres are
+    added until the voxelised inclusion fraction first reaches
+    ``target_fraction``. Returns a uint8 phase map (1 = inclusion).
+    """
+    rng = np.random.default_rng(seed)
+    phase = np.zeros((n, n, n), dtype=np.uint8)
+    centres: list[np.ndarray] = []
+    radii: list[float] = []
+    filled = 0
+    target = target_fraction * n ** 3
+    for _ in range(max_attempts):
+        if filled >= target:
+            break
+        r = rng.uniform(r_min, r_max)
+        c = rng.uniform(0.0, n, size=3)
+        if centres:
+            d = np.asarray(centres) - c
+            d -= n * np.round(d / n)
+            if np.any(np.sqrt((d * d).sum(axis=1)) < np.asarray(radii) + r):
+                continue
+        centres.append(c)
+        radii.append(r)
+        lo = np.floor(c - r - 1).astype(int)
+        hi = np.ceil(c + r + 1).astype(int)
+        ix = np.arange(lo[0], hi[0] + 1)
+        iy = np.arange(lo[1], hi[1] + 1)
+        iz = np.arange(lo[2], hi[2] + 1)
+        dx = ix + 0.5 - c[0]
+        dy = iy + 0.5 - c[1]
+        dz = iz + 0.5 - c[2]
+        inside = (dx[:, None, None] ** 2 + dy[None, :, None] ** 2 + dz[None, None, :] ** 2) <= r * r
+        sub = phase[np.ix_(ix % n, iy % n, iz % n)]
+        filled += int(np.count_nonzero(inside & (sub == 0)))
+        sub[inside] = 1
+        phase[np.ix_(ix % n, iy % n, iz % n)] = sub
+    else:
+        raise RuntimeError("random_spheres: target fraction not reached")
+    return phase
+
+
+def laminate(n: tuple[int, int, int], thickness: int, axis: int = 0) -> np.ndarray:
+    """Two-phase laminate: phase 1 on the first ``thickness`` layers along ``axis``."""
+    phase = np.zeros(n, dtype=np.uint8)
+    idx = [slice(None)] * 3
+    idx[axis] = slice(0, thickness)
+    phase[tuple(idx)] = 1
+    return phase
+
+
+def two_phase_table(lam: float, mu: float, contrast: float) -> np.ndarray:
+    """Parameter table: phase 0 = (lam, mu), phase 1 = contrast * (lam, mu)."""
+    return np.array([[lam, mu], [contrast * lam, contrast * mu]], dtype=np.float64)
+
+
+def random_deformation(n_vox: int, seed: int, scale: float = 0.1,
+                       identity: bool = True) -> np.ndarray:
+    """Random 3x3 tensors as a (9, n_vox) float64 array: I + scale * U(-1, 1)."""
+    rng = np.random.default_rng(seed)
+    F = rng.uniform(-scale, scale, size=(9, n_vox))
+    if identity:
+        F[[0, 4, 8]] += 1.0
+    return F
+
+
+def shear_macro(gamma: float, finite: bool) -> np.ndarray:
+    """Macroscopic tensor with a simple shear gamma e_x (x) e_y (entry 01).
+
+    With ``finite`` it is the deformation gradient I + gamma e_x (x) e_y; else
+    the small-strain tensor with eps_xy = eps_yx = gamma.
+    """
+    F = np.zeros(9)
+    if finite:
+        F[[0, 4, 8]] = 1.0
+        F[1] = gamma
+    else:
+        F[1] = F[3] = gamma
+    return F
+
+
+def small_strain_config(n: int = 16):
+    """Two-phase linear elastic cube: centred sphere of radius 0.25 L.
+
+    Matrix bulk 0.833 and shear 0.386; the inclusion is 10x stiffer. The
+    macroscopic strain has only eps_xy = eps_yx = 0.01.
+    Returns (phase, params, Ebar).
+    """
+    lam, mu = lame_from_bulk_shear(0.833, 0.386)
+    phase = centered_sphere((n, n, n), 0.25)
+    params = np.array([[lam, mu], list(lame_from_bulk_shear(8.33, 3.86))], dtype=np.float64)
+    return phase, params, shear_macro(0.01, finite=False)
+
+
+def neo_hookean_config(n: int = 128, seed: int = 0):
+    """Random-sphere neo-Hookean cube: matrix mu=1, lambda=1.5, inclusions 10x.
+
+    Spheres of radius U[4, 10] voxels fill a volume fraction of 0.3. The
+    macroscopic deformation gradient is I + 0.05 e_x (x) e_y.
+    Returns (phase, params, Fbar).
+    """
+    phase = random_spheres(n, seed)
+    params = two_phase_table(1.5, 1.0, 10.0)
+    return phase, params, shear_macro(0.05, finite=True)
