@@ -1,0 +1,483 @@
+"""Benchmark: time-to-solve of the 128^3 neo-Hookean cell on the GB300 library.
+
+One step = one complete Newton-Krylov solve (Appendix A, Algorithm 1) of the
+128^3 random-sphere neo-Hookean cell: Fbar = I + 0.05 e_x (x) e_y reached in
+5 increments, Newton tolerance 1e-8 on ||dF||/(||Fbar|| sqrt(N)), CG
+tolerance 1e-10, every kernel of the path (AD constitutive evaluation, the
+five FFT/projection passes, CG and Newton updates) in the CUDA library.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle
+instead (the reference arm). Under torchrun every rank solves its own
+replica (seed = rank); nothing is exchanged between ranks but the barrier and
+the max of the timings.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 128
+N_INC = 5
+NEWTON_TOL = 1e-8
+GAMMA = 0.05
+METRIC = "time-to-solve @1e-8 residual (128³ neo-Hookean); CG matvec GB/s vs HBM peak"
+WORKLOAD = ("neo-Hookean 128^3, RSA spheres r~U[4,10] vox, f=0.30, contrast 10 (mu=1, lambda=1.5), "
+            "Fbar=I+0.05 e_x(x)e_y in 5 increments, Newton tol 1e-8, CG tol 1e-10, FP64")
+HBM_PEAK_FALLBACK = 6694.5
+FP64_PEAK_TFLOPS = 1.008       # in-repo DFMA probe (profiles/fp64_throughput_probe.md)
+FP64_NOMINAL_TFLOPS = 1.259    # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per launch of each kernel class (bytes moved at minimum,
+# FP64 flops with the conventional 5 L log2 L count per complex length-L FFT)
+# ---------------------------------------------------------------------------
+def algorithmic_work(cls: str, nx: int, ny: int, nz: int):
+    n = nx * ny * nz
+    h = nx * ny * (nz // 2 + 1)
+    c16 = 16  # bytes of a complex double
+    lg = math.log2
+    if cls == "fwd_z":        # read r, p, K(45); write p; write 9 half spectra
+        return (72 + 72 + 360 + 72) * n + 9 * c16 * h, (162 + 18) * n + 9 * 2.5 * n * lg(nz) + 3 * 2 * h
+    if cls == "fwd_y":        # read 9, write 6 spectral components
+        return (9 + 6) * c16 * h, 9 * 5 * h * lg(ny) + 3 * 4 * h
+    if cls == "x_ghat":       # read 6, write 6; 12 transforms + Ghat
+        return (6 + 6) * c16 * h, 12 * 5 * h * lg(nx) + 40 * h
+    if cls == "inv_y":        # read 6, write 9
+        return (6 + 9) * c16 * h, 9 * 5 * h * lg(ny) + 24 * h
+    if cls == "inv_z":        # read 9 spectra and p; write y
+        return 9 * c16 * h + (72 + 72) * n, 9 * 2.5 * n * lg(nz) + 18 * n
+    if cls == "cg_update":    # read x, r, p, y; write x, r
+        return 6 * 72 * n, 6 * 9 * n
+    return None, None
+
+
+def cg_iteration_bytes(nx, ny, nz):
+    return sum(algorithmic_work(c, nx, ny, nz)[0] for c in ("fwd_z", "fwd_y", "x_ghat", "inv_y", "inv_z",
+                                                           "cg_update"))
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2408_03804_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh_:
+            h.update(fh_.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel_class: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    ent = d.get("kernels", {}).get(kernel_class)
+    if not ent or ent.get("grid") != [N_GRID] * 3:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm, src = HBM_PEAK_FALLBACK, "fallback"
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        if "hbm_gbs" in d:
+            hbm, src = float(d["hbm_gbs"]), "measured"
+    return hbm, src
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (barrier and max only)
+# ---------------------------------------------------------------------------
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+
+
+def barrier(world, device=None):
+    if world > 1:
+        import torch.distributed as dist
+
+        if device is not None:
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(world, value, device):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def oracle_sample(phase, params, Fbar, n_cg_iters=6):
+    """Seconds per CG iteration and per Newton-step overhead of the oracle at full size.
+
+    The sample is one Newton iteration of the first increment with the CG
+    loop capped at n_cg_iters products, timed in two parts.
+    """
+    from oracle import materials as omat
+    from oracle import solver as osolver
+    from oracle import spectral
+
+    lam, mu = params[phase, 0], params[phase, 1]
+    F = np.broadcast_to(np.eye(3).reshape(9, 1, 1, 1), (9,) + phase.shape).copy()
+    F += ((Fbar - np.eye(3).reshape(9)) / N_INC).reshape(9, 1, 1, 1)
+    t0 = time.perf_counter()
+    P = omat.stress(1, F, lam, mu)
+    K = omat.tangent(1, F, lam, mu)
+    b = -spectral.project(P)
+    t1 = time.perf_counter()
+    x, it, _ = osolver.cg(lambda p: spectral.project(omat.apply_tangent(K, p)), b, 1e-30, n_cg_iters)
+    F += x
+    _ = float(np.linalg.norm(x))
+    t2 = time.perf_counter()
+    return (t2 - t1) / max(it, 1), t1 - t0, it
+
+
+def reference_counts():
+    path = os.path.join(ROOT, "tests", "golden", "neo_hookean_128_seed0.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    return d["n_newton"], d["n_cg"]
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle as it stands, on this host's cores."""
+    if rank != 0:
+        return
+    from rve_inputs import neo_hookean_config
+
+    counts = reference_counts()
+    if counts is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle Newton/CG counts for the 128^3 workload "
+                                                               "not generated (tests/golden)"}))
+        return
+    n_newton, n_cg = counts
+    phase, params, Fbar = neo_hookean_config(N_GRID, 0)
+    vals = []
+    for step in range(args.warmup + args.steps):
+        t_cg, t_newton, it = oracle_sample(phase, params, Fbar, n_cg_iters=3)
+        est = n_newton * t_newton + n_cg * t_cg
+        if step >= args.warmup:
+            vals.append(est)
+    v = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [N_GRID] * 3},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"per step: one Newton iteration at 128^3 with 3 CG products, extrapolated "
+                                   f"with the oracle's own counts ({n_newton} Newton, {n_cg} CG) of this workload"},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def cufft_matvec_ms(torch, K, p, reps=5):
+    """A cuFFT-based matrix-vector product (torch.fft) of the same workload, for comparison."""
+    n = p.shape[1]
+    k = torch.fft.fftfreq(n, d=1.0 / n, device=p.device, dtype=torch.float64)
+    k[n // 2] = 0.0
+    kz = torch.fft.rfftfreq(n, d=1.0 / n, device=p.device, dtype=torch.float64)
+    kz[-1] = 0.0
+    xi = torch.meshgrid(k, k, kz, indexing="ij")
+    xi2 = xi[0] ** 2 + xi[1] ** 2 + xi[2] ** 2
+    inv = torch.where(xi2 > 0, 1.0 / torch.where(xi2 > 0, xi2, torch.ones_like(xi2)), torch.zeros_like(xi2))
+    idx = torch.tensor([[min(a, b) * 9 - min(a, b) * (min(a, b) - 1) // 2 + abs(a - b) for b in range(9)]
+                        for a in range(9)], device=p.device)
+
+    def mv():
+        Kf = K[idx.reshape(-1)].reshape(9, 9, *p.shape[1:])
+        tau = torch.einsum("ab...,b...->a...", Kf, p)
+        A = torch.fft.rfftn(tau, dim=(1, 2, 3)).reshape(3, 3, *xi2.shape)
+        v = (A[:, 0] * xi[0] + A[:, 1] * xi[1] + A[:, 2] * xi[2]) * inv
+        out = torch.stack([v * xi[j] for j in range(3)], dim=1).reshape(9, *xi2.shape)
+        return torch.fft.irfftn(out, s=p.shape[1:], dim=(1, 2, 3))
+
+    for _ in range(2):
+        mv()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        mv()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    import paper_2408_03804_gb300 as fh
+    from paper_2408_03804_gb300 import build as fhbuild
+    from rve_inputs import neo_hookean_config
+
+    if rank == 0:
+        fhbuild.build()
+    barrier(world, local)
+    fhbuild.build()
+    fh.load()
+    dev = torch.device("cuda", local)
+    phase, params, Fbar = neo_hookean_config(N_GRID, seed=rank)
+    shape = phase.shape
+    n = phase.size
+    stream = torch.cuda.current_stream()
+    ctx = fh.Context(*shape, stream=stream.cuda_stream)
+    mat = fh.Material(fh.NEO_HOOKEAN, phase, params)
+    F = torch.empty((9,) + shape, dtype=torch.float64, device=dev)
+    opts = fh.default_options(newton_tol=NEWTON_TOL)
+
+    def step():
+        return ctx.fft_homog_solve(mat, Fbar, F, n_increments=N_INC, options=opts)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs ----
+    ctx.fh_profile_enable(True)
+    barrier(world, local)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            pbar, st, _ = step()
+            stats.append(st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    barrier(world, local)
+    prof = ctx.fh_profile_read()
+    ctx.fh_profile_enable(False)
+    elapsed_s = e0.elapsed_time(e1) / 1e3
+    elapsed_s = max_over_ranks(world, elapsed_s, dev)
+    per_step = elapsed_s / args.steps
+
+    # ---- end to end through the public API with host buffers ----
+    phase_host = torch.from_numpy(phase.copy()).pin_memory()
+    F_host = torch.empty((9,) + shape, dtype=torch.float64).pin_memory()
+    phase_dev = torch.empty(shape, dtype=torch.uint8, device=dev)
+    barrier(world, local)
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        phase_dev.copy_(phase_host, non_blocking=True)
+        mat_e = fh.Material(fh.NEO_HOOKEAN, phase_dev, params)
+        pbar_e, _, _ = ctx.fft_homog_solve(mat_e, Fbar, F, n_increments=N_INC, options=opts)
+        F_host.copy_(F, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(world, e2.elapsed_time(e3) / 1e3, dev) / args.steps
+
+    # ---- cuFFT comparison of one matrix-vector product ----
+    K = torch.empty((45,) + shape, dtype=torch.float64, device=dev)
+    ctx.fh_constitutive(mat, F, None, K, want_pbar=False)
+    p = torch.randn((9,) + shape, dtype=torch.float64, device=dev)
+    y = torch.empty_like(p)
+    for _ in range(2):
+        ctx.fh_matvec(p, y, K=K)
+    torch.cuda.synchronize()
+    e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e4.record(stream)
+    for _ in range(5):
+        ctx.fh_matvec(p, y, K=K)
+    e5.record(stream)
+    torch.cuda.synchronize()
+    ours_mv_ms = e4.elapsed_time(e5) / 5
+    cufft_ms = cufft_matvec_ms(torch, K, p)
+    del K, p, y
+
+    if rank != 0:
+        ctx.close()
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel ----
+    hbm_peak, hbm_src = peaks()
+    classes = {c: v for c, v in prof.items() if v[0] > 0}
+    dom = max(classes, key=lambda c: classes[c][1])
+    launches_dom, ms_dom = classes[dom]
+    avg_s = ms_dom / 1e3 / launches_dom
+    bytes_l, flops_l = algorithmic_work(dom, *shape)
+    fp64_ach = flops_l / avg_s / 1e12 if flops_l else None
+    roofline = {"bound": "alu", "kernel": dom, "achieved": fp64_ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": fp64_ach / FP64_PEAK_TFLOPS if fp64_ach else None,
+                "traffic": committed_traffic(dom),
+                "peak_source": "measured FP64 DFMA probe (MEASURED_PEAKS.json has no FP64 entry); nominal "
+                               f"{FP64_NOMINAL_TFLOPS} = 152 SM x 2 DFMA/clk x 2 x 2.07 GHz",
+                "avg_launch_ms": avg_s * 1e3, "launches": launches_dom,
+                "algorithmic_flops_per_launch": flops_l, "algorithmic_bytes_per_launch": bytes_l,
+                "hbm_gbs": bytes_l / avg_s / 1e9, "hbm_peak": hbm_peak, "hbm_peak_source": hbm_src,
+                "hbm_frac": bytes_l / avg_s / 1e9 / hbm_peak}
+    # CG iteration (matrix-vector product + vector update) effective bandwidth
+    cg_cls = ("fwd_z", "fwd_y", "x_ghat", "inv_y", "inv_z", "cg_update")
+    it_ms = sum(classes[c][1] / classes[c][0] for c in cg_cls if c in classes)
+    it_bytes = cg_iteration_bytes(*shape)
+    cg_iter = {"ms": it_ms, "algorithmic_bytes": it_bytes, "gbs": it_bytes / (it_ms / 1e3) / 1e9,
+               "hbm_frac": it_bytes / (it_ms / 1e3) / 1e9 / hbm_peak,
+               "matvec_ms_ours": ours_mv_ms, "matvec_ms_cufft_torch": cufft_ms}
+    kernels = {c: {"launches": v[0], "ms_total": v[1], "share": v[1] / sum(x[1] for x in classes.values())}
+               for c, v in classes.items()}
+
+    # ---- CPU oracle on a bounded sample (rank 0 only, at N = 1) ----
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        t_cg, t_newton, it = oracle_sample(phase, params, Fbar, n_cg_iters=6)
+        st = stats[-1]
+        est = st["n_newton"] * t_newton + st["n_cg"] * t_cg
+        cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one Newton iteration at 128^3 with {it} CG products on the host "
+                         f"({t_newton:.2f} s Newton overhead, {t_cg:.3f} s per CG iteration), extrapolated with "
+                         f"this run's counts ({st['n_newton']} Newton, {st['n_cg']} CG)"}
+
+    st = stats[-1]
+    line = {
+        "metric": METRIC, "value": per_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [N_GRID] * 3, "replicas": world,
+                   "l2": "working set ~1.6 GB per solve (inputs larger than L2), no explicit flush",
+                   "newton_iterations": st["n_newton"], "cg_iterations": st["n_cg"],
+                   "pbar": pbar.tolist()},
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(n), "d2h_bytes_per_step": int(9 * n * 8)},
+        "gpu_launches": int(sum(v[0] for v in prof.values())) // max(args.steps, 1) * args.steps,
+        "roofline": roofline,
+        "cg_iteration": cg_iter,
+        "kernels": kernels,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+        "wall_s_timed": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

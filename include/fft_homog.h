@@ -1,0 +1,200 @@
+/*
+ * fft_homog.h -- C-ABI of the GB300 Fourier-Galerkin homogenization library.
+ *
+ * The library solves the periodic cell problem of Pundir & Kammer,
+ * "Simplifying FFT-based methods for solid mechanics with automatic
+ * differentiation": a representative volume element under a prescribed
+ * macroscopic deformation gradient Fbar (Section 3), equilibrium in Fourier
+ * form  IFFT{ Ghat(xi) : FFT{P} } = 0  (Eq. 1), stress P = dW/dF (Eq. 2) and
+ * tangent K = dP/dF (Eq. 3) by forward-mode automatic differentiation of the
+ * stored energy W, a Newton-Krylov solve (Appendix A, Algorithm 1) and the
+ * homogenized stress Pbar = volume mean of P (Eq. 4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid        nx x ny x nz voxels, N = nx*ny*nz. Each extent must be a power
+ *             of two; nx, ny in [1, 256], nz in [2, 256]. Box side lengths
+ *             default to 1 (see fh_options.lengths).
+ * Fields      device float64 arrays in structure-of-arrays order
+ *             [9][nx][ny][nz] (z fastest); component c = 3*i + j holds the
+ *             tensor entry T_ij (row-major 3x3; F_ij = dx_i/dX_j).
+ * Tangents    device float64 arrays [45][nx][ny][nz]: the upper triangle of
+ *             the symmetric 9x9 matrix K[a][b] = dP_a/dF_b (a, b component
+ *             indices), row by row: slot s(a,b) = 9a - a(a-1)/2 + (b - a) for
+ *             a <= b. Hyperelastic tangents have this major symmetry.
+ * Phase map   device uint8 array [nx][ny][nz]; value p selects row p of the
+ *             host parameter table params[n_phase][2] = (lambda, mu).
+ * Ownership   the caller owns every pointer it passes; the context owns only
+ *             its own scratch (spectrum, CG vectors, tangent, partial sums),
+ *             allocated by fh_create and released by fh_destroy.
+ * Streams     all device work of a context runs on the stream given to
+ *             fh_create; every call has finished on that stream when it
+ *             returns.
+ * Errors      every int-returning call returns FH_OK (0) or one of the codes
+ *             below; fh_last_error_string() describes the last failure of the
+ *             calling thread. No C++ exception crosses this interface.
+ * Precision   all arithmetic of the solver is IEEE float64.
+ */
+#ifndef FFT_HOMOG_H
+#define FFT_HOMOG_H
+
+#if defined(__GNUC__)
+#define FH_API __attribute__((visibility("default")))
+#else
+#define FH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define FH_OK 0
+#define FH_ERR_ARG 1            /* invalid argument (size, pointer, option) */
+#define FH_ERR_CUDA 2           /* a CUDA runtime call failed */
+#define FH_ERR_NOT_CONVERGED 3  /* Newton or CG hit its iteration cap; outputs hold the last iterate */
+#define FH_ERR_NONPHYSICAL 4    /* det F <= 0 or a non-finite value in a voxel */
+#define FH_ERR_TIMEOUT 5        /* reserved: a bounded device-side wait ran out */
+#define FH_ERR_UNSUPPORTED 6    /* valid request this build does not implement */
+
+/* ---- material laws (energy densities differentiated in the kernels) ----
+ * FH_LINEAR_ELASTIC  small strain; the unknown is the displacement gradient
+ *                    H, eps = sym(H), W = lambda/2 tr(eps)^2 + mu eps:eps
+ *                    (Section 3.2; the paper omits the 1/2 on lambda).
+ * FH_NEO_HOOKEAN     W = mu/2 (tr F^T F - 3) - mu ln J + lambda/2 (ln J)^2.
+ * FH_SVK             St. Venant-Kirchhoff, W = lambda/2 tr(E)^2 + mu E:E with
+ *                    E = (F^T F - I)/2 (Eq. 6). */
+#define FH_LINEAR_ELASTIC 0
+#define FH_NEO_HOOKEAN 1
+#define FH_SVK 2
+
+/* ---- how the CG matrix-vector product gets K : dF (Section 3.2) ----
+ * FH_TANGENT_STORED  K is evaluated by AD once per Newton step and stored
+ *                    (45 doubles per voxel; Listing 2's explicit tangent).
+ * FH_TANGENT_JVP     K : dF is re-derived from F by AD inside every product
+ *                    (Listing 3's push-forward); nothing is stored. */
+#define FH_TANGENT_STORED 0
+#define FH_TANGENT_JVP 1
+
+/* ---- start state of a solve ----
+ * FH_INIT_REFERENCE  F starts at I (finite strain) or 0 (small strain).
+ * FH_INIT_GIVEN      F_dev holds the start field; its voxel mean is taken as
+ *                    the macroscopic tensor it is in equilibrium with. */
+#define FH_INIT_REFERENCE 0
+#define FH_INIT_GIVEN 1
+
+typedef struct fh_ctx fh_ctx;
+
+typedef struct fh_material {
+  int kind;                     /* FH_LINEAR_ELASTIC, FH_NEO_HOOKEAN or FH_SVK */
+  int n_phase;                  /* rows of params, 1..256 */
+  const unsigned char* phase;   /* device uint8[N], every value < n_phase */
+  const double* params;         /* host double[n_phase][2] = (lambda, mu) */
+} fh_material;
+
+typedef struct fh_options {
+  double newton_tol;    /* stop when ||dF||_2 / (||Fbar_n||_F sqrt(N)) < newton_tol (Alg. 1) */
+  double cg_tol;        /* CG stops when ||r|| <= cg_tol ||b||; <= 0 selects 1e-2 * newton_tol */
+  int max_newton;       /* Newton iterations per load increment */
+  int max_cg;           /* CG matrix-vector products per Newton iteration */
+  int init;             /* FH_INIT_REFERENCE or FH_INIT_GIVEN */
+  int tangent_mode;     /* FH_TANGENT_STORED or FH_TANGENT_JVP */
+  int check_every;      /* CG iterations queued between host convergence reads (>= 1) */
+  int reserved;
+  double lengths[3];    /* box side lengths L_x, L_y, L_z (> 0) */
+} fh_options;
+
+typedef struct fh_stats {
+  int n_newton;               /* Newton iterations over all increments */
+  int n_cg;                   /* CG matrix-vector products over all increments */
+  int capacity;               /* length of the two caller-owned arrays below (may be 0) */
+  int n_recorded;             /* entries written to them (min(n_newton, capacity)) */
+  double* newton_residuals;   /* host array: e after each Newton iteration, or NULL */
+  int* cg_iterations;         /* host array: CG products of each Newton iteration, or NULL */
+  double time_ms;             /* wall time of the call */
+} fh_stats;
+
+/* Fill *o with the defaults: newton_tol 1e-8, cg_tol 0 (= 1e-2 newton_tol),
+ * max_newton 50, max_cg 5000, FH_INIT_REFERENCE, FH_TANGENT_STORED,
+ * check_every 16, lengths (1, 1, 1). */
+FH_API void fh_default_options(fh_options* o);
+
+/* Create a context for an nx x ny x nz grid whose work runs on cuda_stream
+ * (a cudaStream_t; NULL = the legacy default stream) of the current device.
+ * Allocates the context's device scratch: about 650 bytes per voxel.
+ * Returns FH_ERR_ARG for unsupported extents, FH_ERR_CUDA if allocation
+ * fails; *out is set only on success. */
+FH_API int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream);
+
+/* Release a context and its scratch; NULL is accepted. */
+FH_API void fh_destroy(fh_ctx* ctx);
+
+/* Description of the last error on the calling thread ("" if none). */
+FH_API const char* fh_last_error_string(void);
+
+/* Stress and tangent of every voxel (Eqs. 2-3, Section 3.1-3.2), from the
+ * energy of mat->kind by forward-mode dual numbers of second order.
+ *   F_dev      in   [9][N] deformation gradient (H for small strain)
+ *   P_dev      out  [9][N] stress dW/dF, or NULL
+ *   K_dev      out  [45][N] packed tangent d2W/dF2, or NULL
+ *   Pbar_out   out  host double[9], volume mean of P (Eq. 4), or NULL
+ * Returns FH_ERR_NONPHYSICAL if any voxel has det F <= 0 or a non-finite
+ * result (outputs are still written). */
+FH_API int fh_constitutive(fh_ctx* ctx, const fh_material* mat, const double* F_dev,
+                    double* P_dev, double* K_dev, double Pbar_out[9]);
+
+/* out = scale * G(A): the compatibility projection of Eq. 1,
+ * IFFT{ Ghat(xi) : FFT{A} } with Ghat(xi)[Ahat] = (Ahat xi) (x) xi / |xi|^2
+ * and Ghat(0) = 0. On an even axis the Nyquist index has xi = 0.
+ *   A_dev    in   [9][N]     out_dev  out  [9][N] (may equal A_dev)
+ * lengths: box side lengths (NULL = unit box). */
+FH_API int fh_project(fh_ctx* ctx, const double* A_dev, double* out_dev, double scale,
+               const double lengths[3]);
+
+/* y = G(K : p), the CG matrix-vector product of the linearised Eq. 1.
+ * With K_dev != NULL the stored packed tangent [45][N] is applied; with
+ * K_dev == NULL, K : p is re-derived from F_dev and mat by AD (jvp form).
+ *   p_dev in [9][N], y_dev out [9][N] (must not alias p_dev). */
+FH_API int fh_matvec(fh_ctx* ctx, const fh_material* mat, const double* F_dev,
+              const double* K_dev, const double* p_dev, double* y_dev,
+              const double lengths[3]);
+
+/* Solve the cell under the macroscopic tensor Fbar (Appendix A, Algorithm 1;
+ * Listing 5's solve_microscale). The load goes from the start tensor to Fbar
+ * in n_increments equal additive steps; each step runs Newton iterations
+ *   P, K = AD(W)(F);  b = -G(P);  CG on G(K : dF) = b from dF = 0;  F += dF
+ * until ||dF||/(||Fbar_n|| sqrt(N)) < newton_tol.
+ *   F_dev      in/out [9][N]: start field if opt->init == FH_INIT_GIVEN;
+ *              the converged field on return (H for small strain)
+ *   Fbar       host double[9] macroscopic target
+ *   Pbar_out   host double[9] homogenized stress (Eq. 4), or NULL
+ *   stats      optional convergence record, or NULL
+ *   opt        NULL = defaults
+ * Returns FH_ERR_NOT_CONVERGED when an iteration cap is hit (F_dev and
+ * Pbar_out then hold the last iterate), FH_ERR_NONPHYSICAL on det F <= 0. */
+FH_API int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9],
+                    int n_increments, const fh_options* opt, double* F_dev,
+                    double Pbar_out[9], fh_stats* stats);
+
+/* ---- launch accounting and per-kernel device time ----
+ * Kernel classes, in slot order: 0 forward z pass (stress/tangent apply +
+ * real-to-complex), 1 forward y pass, 2 x pass with Ghat, 3 inverse y pass,
+ * 4 inverse z pass (complex-to-real + dot), 5 constitutive AD, 6 jvp tangent
+ * apply, 7 CG scalar kernels, 8 CG vector update, 9 Newton update,
+ * 10 fills and field sums, 11 partial-sum reductions. */
+#define FH_PROF_NCLASS 12
+
+/* Reset the context's launch counters and, with enable != 0, bracket every
+ * later launch with a pair of CUDA events on the context's stream (adds one
+ * event record before and after each kernel). */
+FH_API int fh_profile_enable(fh_ctx* ctx, int enable);
+
+/* Launches per class since the last fh_profile_enable, and the summed device
+ * time in milliseconds of those launched while events were enabled (0 when
+ * disabled). Waits for the context's stream. Either array may be NULL. */
+FH_API int fh_profile_read(fh_ctx* ctx, long long counts[FH_PROF_NCLASS], double ms[FH_PROF_NCLASS]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFT_HOMOG_H */

@@ -1,0 +1,242 @@
+"""ctypes binding of libfft_homog.so (argument marshalling only).
+
+Every computation runs in the CUDA library; this module only converts torch
+tensors to device pointers, host arrays to C arrays and return codes to
+exceptions. It fails loudly when the library has not been built: there is no
+CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_void_p
+
+import numpy as np
+
+from . import build as _build
+
+FH_OK = 0
+FH_ERR_ARG = 1
+FH_ERR_CUDA = 2
+FH_ERR_NOT_CONVERGED = 3
+FH_ERR_NONPHYSICAL = 4
+FH_ERR_TIMEOUT = 5
+FH_ERR_UNSUPPORTED = 6
+
+LINEAR_ELASTIC = 0
+NEO_HOOKEAN = 1
+SVK = 2
+
+TANGENT_STORED = 0
+TANGENT_JVP = 1
+
+INIT_REFERENCE = 0
+INIT_GIVEN = 1
+
+_ERR_NAMES = {1: "FH_ERR_ARG", 2: "FH_ERR_CUDA", 3: "FH_ERR_NOT_CONVERGED", 4: "FH_ERR_NONPHYSICAL",
+              5: "FH_ERR_TIMEOUT", 6: "FH_ERR_UNSUPPORTED"}
+
+# every symbol include/fft_homog.h declares
+EXPORTS = ["fh_default_options", "fh_create", "fh_destroy", "fh_last_error_string", "fh_constitutive",
+           "fh_project", "fh_matvec", "fft_homog_solve", "fh_profile_enable", "fh_profile_read"]
+
+PROF_NCLASS = 12
+PROF_CLASSES = ["fwd_z", "fwd_y", "x_ghat", "inv_y", "inv_z", "constitutive", "jvp", "cg_scalar", "cg_update",
+                "newton_update", "fill", "reduce"]
+
+
+class FhError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {message}")
+        self.code = code
+
+
+class FhMaterial(ctypes.Structure):
+    _fields_ = [("kind", c_int), ("n_phase", c_int), ("phase", c_void_p), ("params", POINTER(c_double))]
+
+
+class FhOptions(ctypes.Structure):
+    _fields_ = [("newton_tol", c_double), ("cg_tol", c_double), ("max_newton", c_int), ("max_cg", c_int),
+                ("init", c_int), ("tangent_mode", c_int), ("check_every", c_int), ("reserved", c_int),
+                ("lengths", c_double * 3)]
+
+
+class FhStats(ctypes.Structure):
+    _fields_ = [("n_newton", c_int), ("n_cg", c_int), ("capacity", c_int), ("n_recorded", c_int),
+                ("newton_residuals", POINTER(c_double)), ("cg_iterations", POINTER(c_int)),
+                ("time_ms", c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load the library (once). Raises if it is missing: build it first."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} is missing (run paper_2408_03804_gb300.build)")
+    lib = ctypes.CDLL(path)
+    lib.fh_default_options.argtypes = [POINTER(FhOptions)]
+    lib.fh_default_options.restype = None
+    lib.fh_create.argtypes = [POINTER(c_void_p), c_int, c_int, c_int, c_void_p]
+    lib.fh_create.restype = c_int
+    lib.fh_destroy.argtypes = [c_void_p]
+    lib.fh_destroy.restype = None
+    lib.fh_last_error_string.argtypes = []
+    lib.fh_last_error_string.restype = ctypes.c_char_p
+    lib.fh_constitutive.argtypes = [c_void_p, POINTER(FhMaterial), c_void_p, c_void_p, c_void_p, POINTER(c_double)]
+    lib.fh_constitutive.restype = c_int
+    lib.fh_project.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(c_double)]
+    lib.fh_project.restype = c_int
+    lib.fh_matvec.argtypes = [c_void_p, POINTER(FhMaterial), c_void_p, c_void_p, c_void_p, c_void_p,
+                              POINTER(c_double)]
+    lib.fh_matvec.restype = c_int
+    lib.fft_homog_solve.argtypes = [c_void_p, POINTER(FhMaterial), POINTER(c_double), c_int, POINTER(FhOptions),
+                                    c_void_p, POINTER(c_double), POINTER(FhStats)]
+    lib.fft_homog_solve.restype = c_int
+    lib.fh_profile_enable.argtypes = [c_void_p, c_int]
+    lib.fh_profile_enable.restype = c_int
+    lib.fh_profile_read.argtypes = [c_void_p, POINTER(ctypes.c_longlong), POINTER(c_double)]
+    lib.fh_profile_read.restype = c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, allow=()) -> int:
+    if rc != FH_OK and rc not in allow:
+        raise FhError(rc, load().fh_last_error_string().decode())
+    return rc
+
+
+def _ptr(t) -> int:
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _dvec(values, n=None):
+    a = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(-1))
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values")
+    return a, a.ctypes.data_as(POINTER(c_double))
+
+
+def default_options(**kw) -> FhOptions:
+    o = FhOptions()
+    load().fh_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "lengths":
+            for i in range(3):
+                o.lengths[i] = float(v[i])
+        else:
+            setattr(o, k, v)
+    return o
+
+
+class Material:
+    """A material description: kind, device phase map and host parameter table."""
+
+    def __init__(self, kind: int, phase, params):
+        import torch
+
+        self.kind = int(kind)
+        if not isinstance(phase, torch.Tensor):
+            phase = torch.as_tensor(np.ascontiguousarray(phase, dtype=np.uint8))
+        self.phase = phase.to(device="cuda", dtype=torch.uint8).contiguous()
+        self.params, _ = _dvec(params)
+        if self.params.size % 2:
+            raise ValueError("params must hold (lambda, mu) pairs")
+        self._c = FhMaterial(self.kind, self.params.size // 2, self.phase.data_ptr(),
+                             self.params.ctypes.data_as(POINTER(c_double)))
+
+    @property
+    def c(self):
+        return ctypes.byref(self._c)
+
+
+class Context:
+    """An fh_ctx bound to a grid and a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, stream=None):
+        import torch
+
+        lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.shape = (nx, ny, nz)
+        self.stream = stream
+        h = c_void_p()
+        _check(lib.fh_create(ctypes.byref(h), nx, ny, nz, c_void_p(stream)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().fh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- entry points (same names as the C-ABI) ----
+    def fh_constitutive(self, mat: Material, F, P=None, K=None, want_pbar=True, allow_nonphysical=False):
+        pbar = np.zeros(9)
+        rc = load().fh_constitutive(self._h, mat.c, _ptr(F), _ptr(P), _ptr(K),
+                                    pbar.ctypes.data_as(POINTER(c_double)) if want_pbar else None)
+        _check(rc, allow=(FH_ERR_NONPHYSICAL,) if allow_nonphysical else ())
+        return (pbar, rc) if allow_nonphysical else pbar
+
+    def fh_project(self, A, out, scale: float = 1.0, lengths=None):
+        La = _dvec(lengths, 3) if lengths is not None else (None, None)
+        _check(load().fh_project(self._h, _ptr(A), _ptr(out), float(scale), La[1]))
+
+    def fh_matvec(self, p, y, K=None, mat: Material | None = None, F=None, lengths=None):
+        La = _dvec(lengths, 3) if lengths is not None else (None, None)
+        _check(load().fh_matvec(self._h, mat.c if mat is not None else None, _ptr(F), _ptr(K), _ptr(p), _ptr(y),
+                                La[1]))
+
+    def fh_profile_enable(self, enable: bool = True):
+        _check(load().fh_profile_enable(self._h, 1 if enable else 0))
+
+    def fh_profile_read(self):
+        """{class name: (launches, device ms)} since the last fh_profile_enable."""
+        counts = (ctypes.c_longlong * PROF_NCLASS)()
+        ms = (c_double * PROF_NCLASS)()
+        _check(load().fh_profile_read(self._h, counts, ms))
+        return {PROF_CLASSES[i]: (int(counts[i]), float(ms[i])) for i in range(PROF_NCLASS)}
+
+    def fft_homog_solve(self, mat: Material, Fbar, F, n_increments: int = 1, options: FhOptions | None = None,
+                        capacity: int = 512, allow=()):
+        """Solve in place on F; returns (Pbar, stats dict, return code)."""
+        fb, fbp = _dvec(Fbar, 9)
+        pbar = np.zeros(9)
+        res = np.zeros(capacity)
+        cgi = np.zeros(capacity, dtype=np.int32)
+        st = FhStats(0, 0, capacity, 0, res.ctypes.data_as(POINTER(c_double)),
+                     cgi.ctypes.data_as(POINTER(c_int)), 0.0)
+        rc = load().fft_homog_solve(self._h, mat.c, fbp, int(n_increments),
+                                    ctypes.byref(options) if options is not None else None, _ptr(F),
+                                    pbar.ctypes.data_as(POINTER(c_double)), ctypes.byref(st))
+        _check(rc, allow=allow)
+        stats = {"n_newton": st.n_newton, "n_cg": st.n_cg, "time_ms": st.time_ms,
+                 "newton_residuals": res[:st.n_recorded].tolist(), "cg_iterations": cgi[:st.n_recorded].tolist()}
+        return pbar, stats, rc

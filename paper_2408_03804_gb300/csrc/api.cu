@@ -1,0 +1,544 @@
+// C-ABI entry points and the host-side Newton-Krylov driver (Appendix A,
+// Algorithm 1). The driver queues the kernels of kernels_pointwise.cu and
+// kernels_fft.cu on the context's stream; the CG scalars stay on the device
+// and the host reads them every `check_every` iterations, so a CG iteration
+// costs no host round trip. Kernels queued after convergence see the device
+// flag and return at once.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "fh_kernels.h"
+
+using namespace fh;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define FH_CUDA(call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) return fail(FH_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+// device scalars of a context
+struct DevScalars {
+  CgScalars cg;
+  double sums[16];
+  int flags;
+  int pad;
+};
+
+struct ProfPair {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+struct fh_ctx {
+  int dev = 0;
+  // launch accounting (fh_profile_enable / fh_profile_read)
+  long long counts[FH_PROF_NCLASS] = {};
+  double ms[FH_PROF_NCLASS] = {};
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<ProfPair> pending;
+  cudaStream_t stream = nullptr;
+  Grid g{};
+  Tiling tiling{};
+  double2* S = nullptr;       // spectrum [9][nx][ny][nzh]
+  double* x = nullptr;        // CG solution dF       [9][N]
+  double* r = nullptr;        // CG residual          [9][N]
+  double* p = nullptr;        // CG direction         [9][N]
+  double* y = nullptr;        // G(K : p)             [9][N]
+  double* P = nullptr;        // stress / jvp scratch [9][N]
+  double* K = nullptr;        // packed tangent       [45][N]
+  double* partials = nullptr;
+  long long n_partials = 0;
+  double* params = nullptr;   // [256][2]
+  double2* tw = nullptr;      // twiddle tables
+  DevScalars* sc = nullptr;
+};
+
+namespace {
+
+enum ProfClass : int {
+  kPFwdZ = 0, kPFwdY, kPXGhat, kPInvY, kPInvZ, kPConst, kPJvp, kPCgScalar, kPCgUpdate, kPNewton, kPFill, kPReduce
+};
+
+cudaEvent_t ev_get(fh_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// accumulate the timed pairs; call only when the stream is idle
+void prof_flush(fh_ctx* c) {
+  for (const ProfPair& q : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) c->ms[q.cls] += ms;
+    c->ev_pool.push_back(q.a);
+    c->ev_pool.push_back(q.b);
+  }
+  c->pending.clear();
+}
+
+template <class Fn>
+cudaError_t prof(fh_ctx* c, int cls, Fn&& fn) {
+  c->counts[cls]++;
+  if (!c->prof) return fn();
+  cudaEvent_t a = ev_get(c), b = ev_get(c);
+  cudaEventRecord(a, c->stream);
+  const cudaError_t e = fn();
+  cudaEventRecord(b, c->stream);
+  c->pending.push_back({cls, a, b});
+  return e;
+}
+
+void make_twiddles(std::vector<double2>& t) {
+  t.assign(kTwiddleTotal, make_double2(0.0, 0.0));
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  for (int L = 1; L <= kMaxN; L *= 2) {
+    for (int m = 0; m < L; ++m) {
+      const long double a = two_pi * (long double)m / (long double)L;
+      double c = (double)cosl(a), s = (double)-sinl(a);
+      // exact values at multiples of pi/2
+      if ((4 * m) % L == 0) {
+        const int q = (4 * m) / L;
+        c = (q == 0) ? 1.0 : (q == 2) ? -1.0 : 0.0;
+        s = (q == 1) ? -1.0 : (q == 3) ? 1.0 : 0.0;
+      }
+      t[twiddle_offset(L) + m] = make_double2(c, s);
+    }
+  }
+}
+
+Grid grid_with_lengths(const fh_ctx* ctx, const double* lengths) {
+  Grid g = ctx->g;
+  if (lengths) {
+    g.sx = 1.0 / lengths[0];
+    g.sy = 1.0 / lengths[1];
+    g.sz = 1.0 / lengths[2];
+  }
+  return g;
+}
+
+bool lengths_ok(const double* L) { return !L || (L[0] > 0 && L[1] > 0 && L[2] > 0 && std::isfinite(L[0]) && std::isfinite(L[1]) && std::isfinite(L[2])); }
+
+int check_material(const fh_material* m) {
+  if (!m) return fail(FH_ERR_ARG, "material is NULL");
+  if (m->kind < FH_LINEAR_ELASTIC || m->kind > FH_SVK) return fail(FH_ERR_ARG, "unknown material kind %d", m->kind);
+  if (m->n_phase < 1 || m->n_phase > 256) return fail(FH_ERR_ARG, "n_phase %d outside 1..256", m->n_phase);
+  if (!m->phase || !m->params) return fail(FH_ERR_ARG, "phase or params is NULL");
+  for (int i = 0; i < 2 * m->n_phase; ++i)
+    if (!std::isfinite(m->params[i])) return fail(FH_ERR_ARG, "non-finite material parameter");
+  return FH_OK;
+}
+
+// upload the parameter table; rows >= n_phase hold NaN so that an
+// out-of-range phase value surfaces as a non-physical state
+int upload_material(fh_ctx* ctx, const fh_material* m, MatView* mv) {
+  std::vector<double> tab(512, std::nan(""));
+  for (int i = 0; i < 2 * m->n_phase; ++i) tab[i] = m->params[i];
+  FH_CUDA(cudaMemcpyAsync(ctx->params, tab.data(), 512 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  FH_CUDA(cudaStreamSynchronize(ctx->stream));
+  prof_flush(ctx);
+  mv->kind = m->kind;
+  mv->phase = m->phase;
+  mv->params = ctx->params;
+  return FH_OK;
+}
+
+// G applied to src (tau = src, K : src, or the CG direction), result to out
+int run_projection(fh_ctx* ctx, const Grid& g, int zmode, const double* src, double* p, const double* K,
+                   double scale, int izmode, double* out, const double* pdot, CgScalars* cg) {
+  const Tiling& t = ctx->tiling;
+  cudaStream_t s = ctx->stream;
+  FH_CUDA(prof(ctx, kPFwdZ, [&] { return launch_fwd_z(g, t, zmode, src, p, K, cg, ctx->S, ctx->tw, s); }));
+  FH_CUDA(prof(ctx, kPFwdY, [&] { return launch_fwd_y(g, t, ctx->S, ctx->tw, cg, s); }));
+  FH_CUDA(prof(ctx, kPXGhat, [&] { return launch_x_ghat(g, t, ctx->S, ctx->tw, scale, cg, s); }));
+  FH_CUDA(prof(ctx, kPInvY, [&] { return launch_inv_y(g, t, ctx->S, ctx->tw, cg, s); }));
+  FH_CUDA(prof(ctx, kPInvZ, [&] { return launch_inv_z(g, t, izmode, ctx->S, out, pdot, ctx->partials, ctx->tw, cg, s); }));
+  return FH_OK;
+}
+
+int read_flags(fh_ctx* ctx, int* flags) {
+  FH_CUDA(cudaMemcpyAsync(flags, &ctx->sc->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  FH_CUDA(cudaStreamSynchronize(ctx->stream));
+  prof_flush(ctx);
+  return FH_OK;
+}
+
+int reduce9(fh_ctx* ctx, int n_parts, double out[9]) {
+  FH_CUDA(prof(ctx, kPReduce, [&] { return launch_sum_partials(ctx->partials, n_parts, 9, ctx->sc->sums, ctx->stream); }));
+  FH_CUDA(cudaMemcpyAsync(out, ctx->sc->sums, 9 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  FH_CUDA(cudaStreamSynchronize(ctx->stream));
+  prof_flush(ctx);
+  return FH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fh_default_options(fh_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->newton_tol = 1e-8;
+  o->cg_tol = 0.0;
+  o->max_newton = 50;
+  o->max_cg = 5000;
+  o->init = FH_INIT_REFERENCE;
+  o->tangent_mode = FH_TANGENT_STORED;
+  o->check_every = 16;
+  o->lengths[0] = o->lengths[1] = o->lengths[2] = 1.0;
+}
+
+const char* fh_last_error_string(void) { return g_err; }
+
+int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
+  g_err[0] = 0;
+  if (!out) return fail(FH_ERR_ARG, "out is NULL");
+  if (!pow2_in(nx, 1, kMaxN) || !pow2_in(ny, 1, kMaxN) || !pow2_in(nz, 2, kMaxN))
+    return fail(FH_ERR_ARG, "grid %dx%dx%d: extents must be powers of two, nx,ny in [1,256], nz in [2,256]", nx, ny,
+                nz);
+  fh_ctx* c = new fh_ctx();
+  FH_CUDA(cudaGetDevice(&c->dev));
+  c->stream = (cudaStream_t)cuda_stream;
+  Grid& g = c->g;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.nzh = nz / 2 + 1;
+  g.n = (long long)nx * ny * nz;
+  g.nspec = (long long)nx * ny * g.nzh;
+  g.sx = g.sy = g.sz = 1.0;
+  c->tiling = choose_tiling(g);
+  const size_t f9 = (size_t)9 * g.n * sizeof(double);
+  long long np = 9LL * constitutive_ctas(g);
+  np = std::max(np, z_pass_ctas(g, c->tiling));
+  np = std::max(np, cg_update_ctas(g));
+  np = std::max(np, newton_update_ctas(g));
+  c->n_partials = np;
+  auto cleanup = [&](int code) {
+    fh_destroy(c);
+    return code;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&c->S, (size_t)9 * g.nspec * sizeof(double2))) ||
+      (e = cudaMalloc(&c->x, f9)) || (e = cudaMalloc(&c->r, f9)) || (e = cudaMalloc(&c->p, f9)) ||
+      (e = cudaMalloc(&c->y, f9)) || (e = cudaMalloc(&c->P, f9)) ||
+      (e = cudaMalloc(&c->K, (size_t)45 * g.n * sizeof(double))) ||
+      (e = cudaMalloc(&c->partials, (size_t)np * sizeof(double))) ||
+      (e = cudaMalloc(&c->params, 512 * sizeof(double))) ||
+      (e = cudaMalloc(&c->tw, kTwiddleTotal * sizeof(double2))) || (e = cudaMalloc(&c->sc, sizeof(DevScalars)))) {
+    fail(FH_ERR_CUDA, "fh_create: allocation failed: %s", cudaGetErrorString(e));
+    return cleanup(FH_ERR_CUDA);
+  }
+  std::vector<double2> tw;
+  make_twiddles(tw);
+  if ((e = cudaMemcpy(c->tw, tw.data(), kTwiddleTotal * sizeof(double2), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemset(c->sc, 0, sizeof(DevScalars))) || (e = setup_fft_kernels(g, c->tiling))) {
+    fail(FH_ERR_CUDA, "fh_create: setup failed: %s", cudaGetErrorString(e));
+    return cleanup(FH_ERR_CUDA);
+  }
+  *out = c;
+  return FH_OK;
+}
+
+void fh_destroy(fh_ctx* c) {
+  if (!c) return;
+  DeviceGuard dg(c->dev);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  prof_flush(c);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  cudaFree(c->S);
+  cudaFree(c->x);
+  cudaFree(c->r);
+  cudaFree(c->p);
+  cudaFree(c->y);
+  cudaFree(c->P);
+  cudaFree(c->K);
+  cudaFree(c->partials);
+  cudaFree(c->params);
+  cudaFree(c->tw);
+  cudaFree(c->sc);
+  delete c;
+}
+
+int fh_constitutive(fh_ctx* ctx, const fh_material* mat, const double* F_dev, double* P_dev, double* K_dev,
+                    double Pbar_out[9]) {
+  g_err[0] = 0;
+  if (!ctx || !F_dev) return fail(FH_ERR_ARG, "context or F is NULL");
+  int rc = check_material(mat);
+  if (rc) return rc;
+  DeviceGuard dg(ctx->dev);
+  MatView mv;
+  if ((rc = upload_material(ctx, mat, &mv))) return rc;
+  FH_CUDA(cudaMemsetAsync(&ctx->sc->flags, 0, sizeof(int), ctx->stream));
+  FH_CUDA(prof(ctx, kPConst, [&] { return launch_constitutive(ctx->g, mv, F_dev, P_dev, K_dev, ctx->partials, &ctx->sc->flags, ctx->stream); }));
+  if (Pbar_out) {
+    double s[9];
+    if ((rc = reduce9(ctx, (int)constitutive_ctas(ctx->g), s))) return rc;
+    for (int c = 0; c < 9; ++c) Pbar_out[c] = s[c] / (double)ctx->g.n;
+  }
+  int flags = 0;
+  if ((rc = read_flags(ctx, &flags))) return rc;
+  if (flags & kFlagNonPhysical) return fail(FH_ERR_NONPHYSICAL, "det F <= 0 or non-finite value in some voxel");
+  return FH_OK;
+}
+
+int fh_project(fh_ctx* ctx, const double* A_dev, double* out_dev, double scale, const double lengths[3]) {
+  g_err[0] = 0;
+  if (!ctx || !A_dev || !out_dev) return fail(FH_ERR_ARG, "NULL argument");
+  if (!lengths_ok(lengths)) return fail(FH_ERR_ARG, "box lengths must be positive");
+  DeviceGuard dg(ctx->dev);
+  const Grid g = grid_with_lengths(ctx, lengths);
+  const double c = scale / (2.0 * (double)g.n);
+  int rc = run_projection(ctx, g, kZDirect, A_dev, nullptr, nullptr, c, kIZOut, out_dev, nullptr, nullptr);
+  if (rc) return rc;
+  FH_CUDA(cudaStreamSynchronize(ctx->stream));
+  prof_flush(ctx);
+  return FH_OK;
+}
+
+int fh_matvec(fh_ctx* ctx, const fh_material* mat, const double* F_dev, const double* K_dev, const double* p_dev,
+              double* y_dev, const double lengths[3]) {
+  g_err[0] = 0;
+  if (!ctx || !p_dev || !y_dev) return fail(FH_ERR_ARG, "NULL argument");
+  if (p_dev == y_dev) return fail(FH_ERR_ARG, "y must not alias p");
+  if (!lengths_ok(lengths)) return fail(FH_ERR_ARG, "box lengths must be positive");
+  DeviceGuard dg(ctx->dev);
+  const Grid g = grid_with_lengths(ctx, lengths);
+  const double c = 1.0 / (2.0 * (double)g.n);
+  int rc;
+  if (K_dev) {
+    rc = run_projection(ctx, g, kZKApply, p_dev, nullptr, K_dev, c, kIZOut, y_dev, nullptr, nullptr);
+    if (rc) return rc;
+  } else {
+    if (!F_dev) return fail(FH_ERR_ARG, "jvp form needs F");
+    if ((rc = check_material(mat))) return rc;
+    MatView mv;
+    if ((rc = upload_material(ctx, mat, &mv))) return rc;
+    FH_CUDA(cudaMemsetAsync(&ctx->sc->flags, 0, sizeof(int), ctx->stream));
+    FH_CUDA(prof(ctx, kPJvp, [&] { return launch_jvp(g, mv, F_dev, p_dev, nullptr, ctx->P, kZKApply, nullptr, &ctx->sc->flags, ctx->stream); }));
+    rc = run_projection(ctx, g, kZDirect, ctx->P, nullptr, nullptr, c, kIZOut, y_dev, nullptr, nullptr);
+    if (rc) return rc;
+    int flags = 0;
+    if ((rc = read_flags(ctx, &flags))) return rc;
+    if (flags & kFlagNonPhysical) return fail(FH_ERR_NONPHYSICAL, "det F <= 0 or non-finite value in some voxel");
+  }
+  FH_CUDA(cudaStreamSynchronize(ctx->stream));
+  prof_flush(ctx);
+  return FH_OK;
+}
+
+int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9], int n_increments,
+                    const fh_options* opt_in, double* F_dev, double Pbar_out[9], fh_stats* stats) {
+  g_err[0] = 0;
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!ctx || !F_dev || !Fbar) return fail(FH_ERR_ARG, "NULL argument");
+  int rc = check_material(mat);
+  if (rc) return rc;
+  fh_options opt;
+  if (opt_in) opt = *opt_in;
+  else fh_default_options(&opt);
+  if (n_increments < 1) return fail(FH_ERR_ARG, "n_increments must be >= 1");
+  if (!(opt.newton_tol > 0.0) || opt.max_newton < 1 || opt.max_cg < 0 || opt.check_every < 1)
+    return fail(FH_ERR_ARG, "invalid options");
+  if (opt.init != FH_INIT_REFERENCE && opt.init != FH_INIT_GIVEN) return fail(FH_ERR_ARG, "invalid init");
+  if (opt.tangent_mode != FH_TANGENT_STORED && opt.tangent_mode != FH_TANGENT_JVP)
+    return fail(FH_ERR_ARG, "invalid tangent_mode");
+  if (!lengths_ok(opt.lengths)) return fail(FH_ERR_ARG, "box lengths must be positive");
+  for (int c = 0; c < 9; ++c)
+    if (!std::isfinite(Fbar[c])) return fail(FH_ERR_ARG, "non-finite Fbar");
+  const double cg_tol = opt.cg_tol > 0.0 ? opt.cg_tol : 1e-2 * opt.newton_tol;
+  DeviceGuard dg(ctx->dev);
+  cudaStream_t s = ctx->stream;
+  const Grid g = grid_with_lengths(ctx, opt.lengths);
+  const double N = (double)g.n;
+  MatView mv;
+  if ((rc = upload_material(ctx, mat, &mv))) return rc;
+  FH_CUDA(cudaMemsetAsync(&ctx->sc->flags, 0, sizeof(int), s));
+  CgScalars* cg = &ctx->sc->cg;
+  const bool stored = opt.tangent_mode == FH_TANGENT_STORED;
+
+  // start tensor and load step (a1)
+  double start[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (opt.init == FH_INIT_REFERENCE) {
+    if (mat->kind != FH_LINEAR_ELASTIC) start[0] = start[4] = start[8] = 1.0;
+    FH_CUDA(prof(ctx, kPFill, [&] { return launch_fill(g, F_dev, start, 0, s); }));
+  } else {
+    FH_CUDA(prof(ctx, kPFill, [&] { return launch_field_sums(g, F_dev, ctx->partials, s); }));
+    if ((rc = reduce9(ctx, (int)constitutive_ctas(g), start))) return rc;
+    for (int c = 0; c < 9; ++c) start[c] /= N;
+  }
+  double dFbar[9];
+  for (int c = 0; c < 9; ++c) dFbar[c] = (Fbar[c] - start[c]) / n_increments;
+
+  const int n_iz = (int)z_pass_ctas(g, ctx->tiling);
+  const int n_upd = (int)cg_update_ctas(g);
+  const int n_nu = (int)newton_update_ctas(g);
+  const double c_rhs = -1.0 / (2.0 * N), c_mv = 1.0 / (2.0 * N);
+  int n_newton = 0, n_cg = 0, status = FH_OK;
+
+  for (int inc = 1; inc <= n_increments && status == FH_OK; ++inc) {
+    double Fn[9], nrm = 0.0;
+    for (int c = 0; c < 9; ++c) {
+      Fn[c] = start[c] + inc * dFbar[c];
+      nrm += Fn[c] * Fn[c];
+    }
+    const double denom = (nrm > 0.0 ? std::sqrt(nrm) : 1.0) * std::sqrt(N);
+    FH_CUDA(prof(ctx, kPFill, [&] { return launch_fill(g, F_dev, dFbar, 1, s); }));
+    bool inc_converged = false;
+    for (int it = 0; it < opt.max_newton; ++it) {
+      // stress and tangent by AD (a2)
+      FH_CUDA(prof(ctx, kPConst, [&] { return launch_constitutive(g, mv, F_dev, ctx->P, stored ? ctx->K : nullptr, ctx->partials,
+                                  &ctx->sc->flags, s); }));
+      int flags = 0;
+      if ((rc = read_flags(ctx, &flags))) return rc;
+      if (flags & kFlagNonPhysical) {
+        status = fail(FH_ERR_NONPHYSICAL, "det F <= 0 or non-finite value (increment %d, Newton iteration %d)", inc,
+                      it);
+        break;
+      }
+      // right-hand side b = -G(P) (a3), r = b
+      if ((rc = run_projection(ctx, g, kZDirect, ctx->P, nullptr, nullptr, c_rhs, kIZRhs, ctx->r, nullptr,
+                               nullptr)))
+        return rc;
+      FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_init(cg, ctx->partials, n_iz, cg_tol, opt.max_cg, s); }));
+      FH_CUDA(cudaMemsetAsync(ctx->x, 0, (size_t)9 * g.n * sizeof(double), s));
+      // CG on G(K : dF) = b (a4, a5); scalars stay on the device
+      CgScalars host_cg{};
+      int launched = 0;
+      while (true) {
+        for (int k = 0; k < opt.check_every; ++k, ++launched) {
+          const int zmode = launched == 0 ? kZCgFirst : kZCg;
+          if (stored) {
+            if ((rc = run_projection(ctx, g, zmode, ctx->r, ctx->p, ctx->K, c_mv, kIZDot, ctx->y, ctx->p, cg)))
+              return rc;
+          } else {
+            FH_CUDA(prof(ctx, kPJvp, [&] { return launch_jvp(g, mv, F_dev, ctx->r, ctx->p, ctx->P, zmode, cg, &ctx->sc->flags, s); }));
+            if ((rc = run_projection(ctx, g, kZDirect, ctx->P, nullptr, nullptr, c_mv, kIZDot, ctx->y, ctx->p, cg)))
+              return rc;
+          }
+          FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_alpha(cg, ctx->partials, n_iz, s); }));
+          FH_CUDA(prof(ctx, kPCgUpdate, [&] { return launch_cg_update(g, cg, ctx->x, ctx->r, ctx->p, ctx->y, ctx->partials, 0, s); }));
+          FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_beta(cg, ctx->partials, n_upd, s); }));
+        }
+        FH_CUDA(cudaMemcpyAsync(&host_cg, cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+        FH_CUDA(cudaStreamSynchronize(s));
+        prof_flush(ctx);
+        if (host_cg.done) break;
+        if (launched > opt.max_cg + 2 * opt.check_every)
+          return fail(FH_ERR_CUDA, "CG loop did not report completion");
+      }
+      // Newton update and convergence test (a6)
+      FH_CUDA(prof(ctx, kPNewton, [&] { return launch_newton_update(g, F_dev, ctx->x, ctx->partials, s); }));
+      FH_CUDA(prof(ctx, kPReduce, [&] { return launch_sum_partials(ctx->partials, n_nu, 1, ctx->sc->sums, s); }));
+      double dd = 0.0;
+      FH_CUDA(cudaMemcpyAsync(&dd, ctx->sc->sums, sizeof(double), cudaMemcpyDeviceToHost, s));
+      FH_CUDA(cudaStreamSynchronize(s));
+        prof_flush(ctx);
+      const double e = std::sqrt(dd) / denom;
+      if (stats && stats->newton_residuals && n_newton < stats->capacity) stats->newton_residuals[n_newton] = e;
+      if (stats && stats->cg_iterations && n_newton < stats->capacity) stats->cg_iterations[n_newton] = host_cg.it;
+      ++n_newton;
+      n_cg += host_cg.it;
+      if (host_cg.done != 1) {
+        status = fail(FH_ERR_NOT_CONVERGED, "CG %s after %d products (increment %d, Newton iteration %d)",
+                      host_cg.done == 2 ? "hit max_cg" : "broke down", host_cg.it, inc, it);
+        break;
+      }
+      if (!std::isfinite(e)) {
+        status = fail(FH_ERR_NONPHYSICAL, "non-finite Newton update");
+        break;
+      }
+      if (e < opt.newton_tol) {
+        inc_converged = true;
+        break;
+      }
+    }
+    if (status == FH_OK && !inc_converged)
+      status = fail(FH_ERR_NOT_CONVERGED, "Newton hit max_newton=%d in increment %d", opt.max_newton, inc);
+  }
+
+  // homogenized stress of the final state (a7, Eq. 4)
+  if (Pbar_out) {
+    FH_CUDA(prof(ctx, kPConst, [&] { return launch_constitutive(g, mv, F_dev, nullptr, nullptr, ctx->partials, &ctx->sc->flags, s); }));
+    double sums[9];
+    if ((rc = reduce9(ctx, (int)constitutive_ctas(g), sums))) return rc;
+    for (int c = 0; c < 9; ++c) Pbar_out[c] = sums[c] / N;
+  }
+  FH_CUDA(cudaStreamSynchronize(s));
+        prof_flush(ctx);
+  if (stats) {
+    stats->n_newton = n_newton;
+    stats->n_cg = n_cg;
+    stats->n_recorded = stats->capacity < n_newton ? stats->capacity : n_newton;
+    stats->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
+int fh_profile_enable(fh_ctx* ctx, int enable) {
+  g_err[0] = 0;
+  if (!ctx) return fail(FH_ERR_ARG, "context is NULL");
+  DeviceGuard dg(ctx->dev);
+  FH_CUDA(cudaStreamSynchronize(ctx->stream));
+  prof_flush(ctx);
+  for (int i = 0; i < FH_PROF_NCLASS; ++i) {
+    ctx->counts[i] = 0;
+    ctx->ms[i] = 0.0;
+  }
+  ctx->prof = enable != 0;
+  return FH_OK;
+}
+
+int fh_profile_read(fh_ctx* ctx, long long counts[FH_PROF_NCLASS], double ms[FH_PROF_NCLASS]) {
+  g_err[0] = 0;
+  if (!ctx) return fail(FH_ERR_ARG, "context is NULL");
+  DeviceGuard dg(ctx->dev);
+  FH_CUDA(cudaStreamSynchronize(ctx->stream));
+  prof_flush(ctx);
+  for (int i = 0; i < FH_PROF_NCLASS; ++i) {
+    if (counts) counts[i] = ctx->counts[i];
+    if (ms) ms[i] = ctx->ms[i];
+  }
+  return FH_OK;
+}
+
+}  // extern "C"

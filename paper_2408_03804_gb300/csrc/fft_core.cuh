@@ -1,0 +1,232 @@
+// Batched complex FFTs of power-of-two length on pencils held in shared
+// memory: the building block of the 3D transforms of Eq. 1.
+//
+// Each length-L transform is a Stockham auto-sort sequence of radix-R stages
+// (R in {2, 4, 8, 16}) that ping-pongs between two shared-memory buffers. A
+// stage with radix R and current sub-transform size Ns treats L/R butterflies;
+// butterfly j reads the R inputs j + r L/R, multiplies input r by the twiddle
+// w_L^(r (j mod Ns) L/(Ns R)), applies an R-point DFT in registers and writes
+// output r to (j div Ns) Ns R + (j mod Ns) + r Ns. The first stage (Ns = 1)
+// needs no twiddles. Twiddles w_L^m = exp(-2 pi i m / L) come from a table in
+// global memory (read through the L1 cache); the inverse uses their conjugates.
+//
+// The plans minimise FP64 instructions (FP64 issue is the bound of this path):
+// 32 = 8x4, 64 = 8x8, 128 = 16x8, 256 = 16x16, smaller lengths in one stage.
+#pragma once
+
+#include "fh_common.cuh"
+
+namespace fh {
+
+constexpr double kC8 = 0.70710678118654752440;   // cos(pi/4)
+constexpr double kC16 = 0.92387953251128675613;  // cos(pi/8)
+constexpr double kS16 = 0.38268343236508977173;  // sin(pi/8)
+
+// multiply by -i (forward, INV = false) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ double2 mul_mi(double2 a) {
+  return INV ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft2(double2* v) {
+  const double2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(double2& v0, double2& v1, double2& v2, double2& v3) {
+  const double2 t0 = cadd(v0, v2), t1 = csub(v0, v2);
+  const double2 t2 = cadd(v1, v3), t3 = mul_mi<INV>(csub(v1, v3));
+  v0 = cadd(t0, t2);
+  v2 = csub(t0, t2);
+  v1 = cadd(t1, t3);
+  v3 = csub(t1, t3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(double2* v) {
+  dft4<INV>(v[0], v[1], v[2], v[3]);
+}
+
+// e + w8^1 o and e - w8^1 o, fused (w8 = exp(-+ 2 pi i / 8))
+template <bool INV>
+__device__ __forceinline__ void bfly_w8_1(double2& e, double2& o) {
+  // forward: o (1 - i)/sqrt2 = ((x + y) + i (y - x))/sqrt2 ; inverse: ((x - y) + i (x + y))/sqrt2
+  const double s = INV ? o.x - o.y : o.x + o.y;
+  const double t = INV ? o.x + o.y : o.y - o.x;
+  const double2 a = e;
+  e = make_double2(fma(kC8, s, a.x), fma(kC8, t, a.y));
+  o = make_double2(fma(-kC8, s, a.x), fma(-kC8, t, a.y));
+}
+// e + w8^3 o and e - w8^3 o
+template <bool INV>
+__device__ __forceinline__ void bfly_w8_3(double2& e, double2& o) {
+  // forward: o (-1 - i)/sqrt2 = ((y - x) - i (x + y))/sqrt2 ; inverse: (-(x + y) + i (x - y))/sqrt2
+  const double s = INV ? -(o.x + o.y) : o.y - o.x;
+  const double t = INV ? o.x - o.y : -(o.x + o.y);
+  const double2 a = e;
+  e = make_double2(fma(kC8, s, a.x), fma(kC8, t, a.y));
+  o = make_double2(fma(-kC8, s, a.x), fma(-kC8, t, a.y));
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(double2* v) {
+  double2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  double2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  bfly_w8_1<INV>(e1, o1);
+  v[1] = e1;
+  v[5] = o1;
+  const double2 r2 = mul_mi<INV>(o2);
+  v[2] = cadd(e2, r2);
+  v[6] = csub(e2, r2);
+  bfly_w8_3<INV>(e3, o3);
+  v[3] = e3;
+  v[7] = o3;
+}
+
+// multiply by w16^m (forward exp(-2 pi i m/16), inverse its conjugate), m in 1..9
+template <bool INV, int M>
+__device__ __forceinline__ double2 rot16(double2 a) {
+  constexpr double sg = INV ? 1.0 : -1.0;  // sign of the imaginary part of the twiddle
+  if constexpr (M == 4) {
+    return mul_mi<INV>(a);
+  } else if constexpr (M == 2 || M == 6) {
+    // w = (c, sg c) for M = 2 ; (-c, sg c) for M = 6
+    constexpr double wr = (M == 2) ? kC8 : -kC8;
+    constexpr double wi = sg * kC8;
+    return make_double2(fma(a.x, wr, -a.y * wi), fma(a.x, wi, a.y * wr));
+  } else {
+    constexpr double wr = (M == 1) ? kC16 : (M == 3) ? kS16 : -kC16;  // M = 9: cos(9pi/8) = -c16
+    constexpr double wi = sg * ((M == 1) ? kS16 : (M == 3) ? kC16 : -kS16);
+    return make_double2(fma(a.x, wr, -a.y * wi), fma(a.x, wi, a.y * wr));
+  }
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16(double2* v) {
+  // 16 = 4 x 4: DFT-4 over stride-4 inputs, twiddles w16^(j k1), DFT-4 across
+  double2 a[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    a[j][0] = v[j];
+    a[j][1] = v[j + 4];
+    a[j][2] = v[j + 8];
+    a[j][3] = v[j + 12];
+    dft4<INV>(a[j][0], a[j][1], a[j][2], a[j][3]);
+  }
+  a[1][1] = rot16<INV, 1>(a[1][1]);
+  a[1][2] = rot16<INV, 2>(a[1][2]);
+  a[1][3] = rot16<INV, 3>(a[1][3]);
+  a[2][1] = rot16<INV, 2>(a[2][1]);
+  a[2][2] = rot16<INV, 4>(a[2][2]);
+  a[2][3] = rot16<INV, 6>(a[2][3]);
+  a[3][1] = rot16<INV, 3>(a[3][1]);
+  a[3][2] = rot16<INV, 6>(a[3][2]);
+  a[3][3] = rot16<INV, 9>(a[3][3]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    double2 b0 = a[0][k1], b1 = a[1][k1], b2 = a[2][k1], b3 = a[3][k1];
+    dft4<INV>(b0, b1, b2, b3);
+    v[k1] = b0;
+    v[k1 + 4] = b1;
+    v[k1 + 8] = b2;
+    v[k1 + 12] = b3;
+  }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_r(double2* v) {
+  if constexpr (R == 2) dft2<INV>(v);
+  else if constexpr (R == 4) dft4<INV>(v);
+  else if constexpr (R == 8) dft8<INV>(v);
+  else if constexpr (R == 16) dft16<INV>(v);
+}
+
+// ---- plans: radix of each stage for a length L --------------------------------
+template <int L>
+struct Plan;
+template <> struct Plan<1>   { static constexpr int n = 0; static constexpr int r[1] = {1}; };
+template <> struct Plan<2>   { static constexpr int n = 1; static constexpr int r[1] = {2}; };
+template <> struct Plan<4>   { static constexpr int n = 1; static constexpr int r[1] = {4}; };
+template <> struct Plan<8>   { static constexpr int n = 1; static constexpr int r[1] = {8}; };
+template <> struct Plan<16>  { static constexpr int n = 1; static constexpr int r[1] = {16}; };
+template <> struct Plan<32>  { static constexpr int n = 2; static constexpr int r[2] = {8, 4}; };
+template <> struct Plan<64>  { static constexpr int n = 2; static constexpr int r[2] = {8, 8}; };
+template <> struct Plan<128> { static constexpr int n = 2; static constexpr int r[2] = {16, 8}; };
+template <> struct Plan<256> { static constexpr int n = 2; static constexpr int r[2] = {16, 16}; };
+
+// Pencil addressing inside a shared buffer: element j of pencil q lives at
+// q_stride * q + j_stride * j (in double2 units). JFAST selects the mapping of
+// threads to (pencil, butterfly): butterfly index fastest when pencils are
+// contiguous (j_stride == 1), pencil index fastest otherwise, so that
+// neighbouring threads touch neighbouring addresses.
+struct PencilLayout {
+  int np;        // number of pencils
+  int q_stride;
+  int j_stride;
+};
+
+template <int L, int R, int NS, bool INV, bool JFAST>
+__device__ __forceinline__ void stockham_stage(const double2* __restrict__ src, double2* __restrict__ dst,
+                                               const PencilLayout& lay, const double2* __restrict__ tw) {
+  constexpr int NB = L / R;  // butterflies per pencil
+  const int total = lay.np * NB;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int q = JFAST ? t / NB : t % lay.np;
+    const int j = JFAST ? t % NB : t / lay.np;
+    const double2* s = src + q * lay.q_stride;
+    double2* d = dst + q * lay.q_stride;
+    double2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = s[(j + r * NB) * lay.j_stride];
+    if constexpr (NS > 1) {
+      const int k = j % NS;
+      constexpr int step = L / (NS * R);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const double2 w = __ldg(tw + r * k * step);
+        v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+      }
+    }
+    dft_r<R, INV>(v);
+    const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+    for (int r = 0; r < R; ++r) d[(base + r * NS) * lay.j_stride] = v[r];
+  }
+}
+
+// Transform all pencils of `a` (length L). Uses `b` as the ping-pong partner;
+// returns the buffer holding the result. Synchronises the CTA before each
+// stage and after the last one.
+template <int L, bool INV, bool JFAST>
+__device__ __forceinline__ double2* fft_pencils(double2* a, double2* b, const PencilLayout& lay,
+                                                const double2* __restrict__ tw_table) {
+  const double2* tw = tw_table + twiddle_offset(L);
+  if constexpr (Plan<L>::n == 0) {
+    __syncthreads();
+    return a;
+  } else if constexpr (Plan<L>::n == 1) {
+    __syncthreads();
+    stockham_stage<L, Plan<L>::r[0], 1, INV, JFAST>(a, b, lay, tw);
+    __syncthreads();
+    return b;
+  } else {
+    constexpr int R0 = Plan<L>::r[0];
+    constexpr int R1 = Plan<L>::r[1];
+    static_assert(R0 * R1 == L, "plan");
+    __syncthreads();
+    stockham_stage<L, R0, 1, INV, JFAST>(a, b, lay, tw);
+    __syncthreads();
+    stockham_stage<L, R1, R0, INV, JFAST>(b, a, lay, tw);
+    __syncthreads();
+    return a;
+  }
+}
+
+}  // namespace fh

@@ -1,0 +1,98 @@
+// Shared definitions of the CUDA library: complex helpers, index maps, error
+// plumbing and the launch interface between the host driver and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fft_homog.h"
+
+namespace fh {
+
+constexpr int kThreads = 256;          // threads per CTA of every kernel
+constexpr int kMaxN = 256;             // largest supported extent per axis
+constexpr int kTwiddleTotal = 2 * kMaxN;  // tables for L = 1..256 packed back to back
+
+// ---------------------------------------------------------------------------
+// complex helpers (double2 = re, im)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+// a * w with w a unit twiddle: 2 DMUL + 2 DFMA
+__device__ __forceinline__ double2 cmul(double2 a, double2 w) {
+  return make_double2(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
+}
+// a * conj(w)
+__device__ __forceinline__ double2 cmulc(double2 a, double2 w) {
+  return make_double2(fma(a.x, w.x, a.y * w.y), fma(a.y, w.x, -a.x * w.y));
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+
+// ---------------------------------------------------------------------------
+// symmetric 9x9 packing: slot of (a, b), a <= b, row by row
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int tri(int a, int b) { return 9 * a - a * (a - 1) / 2 + (b - a); }
+__host__ __device__ constexpr int sym_slot(int a, int b) { return a <= b ? tri(a, b) : tri(b, a); }
+
+// signed wave integer of index j on an n-point axis; the Nyquist index of an
+// even axis maps to 0 (first spectral derivative convention)
+__host__ __device__ __forceinline__ int wave_int(int j, int n) {
+  if (2 * j == n) return 0;
+  return (2 * j < n) ? j : j - n;
+}
+
+// offset of the twiddle table for length L (power of two) inside the packed
+// table: tables for L = 1, 2, 4, ... are stored back to back, table L at L - 1
+__host__ __device__ constexpr int twiddle_offset(int L) { return L - 1; }
+
+// ---------------------------------------------------------------------------
+// Grid description passed by value to kernels
+// ---------------------------------------------------------------------------
+struct Grid {
+  int nx, ny, nz, nzh;      // extents and half extent nz/2 + 1
+  long long n;              // voxels
+  long long nspec;          // complex entries per spectral component nx*ny*nzh
+  double sx, sy, sz;        // wave-vector scale 1/L_a (2 pi cancels in Ghat)
+};
+
+// Material tables passed by value (up to 256 phases live in a device buffer)
+struct MatView {
+  int kind;
+  const uint8_t* phase;      // device
+  const double* params;      // device [n_phase][2]
+};
+
+// ---------------------------------------------------------------------------
+// device flags written by kernels, read by the host after a solve step
+// ---------------------------------------------------------------------------
+enum : int {
+  kFlagNonPhysical = 1,
+};
+
+// ---------------------------------------------------------------------------
+// deterministic reductions: fixed shuffle tree inside a warp, then warp 0
+// adds the per-warp results in warp order
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Every thread of the CTA must call; the sum is valid in thread 0. `red`
+// points to at least 32 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0) {
+    t = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+}  // namespace fh

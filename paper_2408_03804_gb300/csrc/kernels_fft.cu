@@ -1,0 +1,481 @@
+// The five passes of one application of the compatibility projection G of
+// Eq. 1 to a nine-component real field, with the stages of the CG
+// matrix-vector product y = G(K : p) fused into the first and last pass.
+//
+// Spectral layout: one complex buffer S[9][nx][ny][nzh] (nzh = nz/2 + 1) that
+// every pass updates in place. Ghat(xi)[Ahat] = v (x) xi with
+// v = Ahat xi / |xi|^2, a rank structure that removes a third of the 1D
+// transforms of the two outer passes:
+//
+//   z  (forward, real-to-complex): tau = K : p (or P), transform along z,
+//      multiply the j = z column by xi_z                         9 transforms
+//   y  (forward): transform the i-th row (j = x, y, z) along y, keep
+//      T_ix and form W_i = xi_y T_iy + T_iz                      9 transforms
+//   x  (forward + Ghat + inverse): transform T_ix, W_i along x,
+//      v_i = s (xi_x T_ix + W_i), s = c / |xi|^2 (0 at xi = 0),
+//      inverse-transform A_i = xi_x v_i and B_i = v_i along x   6 + 6 transforms
+//   y  (inverse): y_ix <- A_i, y_iy <- xi_y B_i, y_iz <- B_i,
+//      inverse transform along y, multiply y_iz by xi_z         9 transforms
+//   z  (inverse, complex-to-real): back to the real field, optionally the
+//      CG dot product p . y in the same pass                     9 transforms
+//
+// All transforms are unnormalised; the real-to-complex step skips its usual
+// factor 1/2, so the constant c carries 1 / (2 N) together with the caller's
+// scale. Each CTA owns a disjoint region of S in every pass, so in-place
+// updates are race free.
+#include <cstdio>
+
+#include "fft_core.cuh"
+#include "fh_kernels.h"
+
+namespace fh {
+
+__device__ __forceinline__ bool cg_done(const CgScalars* cg) { return cg != nullptr && cg->done != 0; }
+
+// ---------------------------------------------------------------------------
+// forward z pass: real-to-complex along z of LB consecutive z lines
+// ---------------------------------------------------------------------------
+template <int M, int MODE>
+__global__ void __launch_bounds__(kThreads) k_fwd_z(Grid g, int LB, const double* __restrict__ src,
+                                                   double* __restrict__ p, const double* __restrict__ K,
+                                                   const CgScalars* __restrict__ cg, double2* __restrict__ S,
+                                                   const double2* __restrict__ tw) {
+  if (cg_done(cg)) return;
+  extern __shared__ double2 smem[];
+  constexpr int NZ = 2 * M;
+  double2* bufA = smem;
+  double2* bufB = smem + 9 * LB * M;
+  double* ra = reinterpret_cast<double*>(bufA);
+  const long long line0 = (long long)blockIdx.x * LB;
+  const long long v0 = line0 * NZ;
+  const long long n = g.n;
+  double beta = 0.0;
+  if constexpr (MODE == kZCg) beta = cg->beta;
+
+  for (int t = threadIdx.x; t < LB * NZ; t += blockDim.x) {
+    const long long gi = v0 + t;
+    const int line = t / NZ, z = t % NZ;
+    double tau[9];
+    if constexpr (MODE == kZDirect) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) tau[c] = src[c * n + gi];
+    } else {
+      double pv[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        if constexpr (MODE == kZKApply) {
+          pv[c] = src[c * n + gi];
+        } else if constexpr (MODE == kZCgFirst) {
+          pv[c] = src[c * n + gi];
+          p[c * n + gi] = pv[c];
+        } else {
+          pv[c] = fma(beta, p[c * n + gi], src[c * n + gi]);
+          p[c * n + gi] = pv[c];
+        }
+      }
+      double k[45];
+#pragma unroll
+      for (int s = 0; s < 45; ++s) k[s] = K[s * n + gi];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        double acc = k[sym_slot(a, 0)] * pv[0];
+#pragma unroll
+        for (int b = 1; b < 9; ++b) acc = fma(k[sym_slot(a, b)], pv[b], acc);
+        tau[a] = acc;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) ra[(c * LB + line) * NZ + z] = tau[c];
+  }
+
+  double2* R = fft_pencils<M, false, true>(bufA, bufB, PencilLayout{9 * LB, M, 1}, tw);
+
+  // unpack the half-length transform Z of z_m = x_2m + i x_2m+1 into
+  // 2 X_k = (Z_k + conj Z_{M-k}) - i w^k (Z_k - conj Z_{M-k}), k = 0..M
+  constexpr int KH = M / 2 + 1;
+  const double2* twn = tw + twiddle_offset(NZ);
+  for (int t = threadIdx.x; t < 9 * LB * KH; t += blockDim.x) {
+    const int q = t / KH, k = t % KH;
+    const int c = q / LB, line = q % LB;
+    const double2* Zq = R + q * M;
+    const double2 zk = Zq[k];
+    const double2 zm = Zq[(M - k) & (M - 1)];
+    const double2 e = make_double2(zk.x + zm.x, zk.y - zm.y);  // Z_k + conj Z_{M-k}
+    const double2 o = make_double2(zk.x - zm.x, zk.y + zm.y);  // Z_k - conj Z_{M-k}
+    const double2 wo = cmul(o, __ldg(twn + k));
+    const double2 tt = make_double2(wo.y, -wo.x);               // -i w^k o
+    double2 xk = cadd(e, tt);
+    double2 xm = make_double2(e.x - tt.x, tt.y - e.y);         // conj(e - tt)
+    double2* out = S + (long long)c * g.nspec + (line0 + line) * g.nzh;
+    if (c % 3 == 2) {
+      xk = cscale(xk, wave_int(k, NZ) * g.sz);
+      xm = cscale(xm, wave_int(M - k, NZ) * g.sz);
+    }
+    out[k] = xk;
+    if (M - k != k) out[M - k] = xm;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// forward y pass: row i, columns j = x, y, z along y; combine W_i
+// ---------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(kThreads) k_fwd_y(Grid g, int BK, double2* __restrict__ S,
+                                                   const double2* __restrict__ tw, const CgScalars* __restrict__ cg) {
+  if (cg_done(cg)) return;
+  extern __shared__ double2 smem[];
+  constexpr int QS = L + 1;
+  const int np = 3 * BK;
+  double2* bufA = smem;
+  double2* bufB = smem + np * QS;
+  const int NC = (g.nzh + BK - 1) / BK;
+  int b = blockIdx.x;
+  const int chunk = b % NC;
+  b /= NC;
+  const int i = b % 3;
+  const int x = b / 3;
+  const int kz0 = chunk * BK;
+  for (int t = threadIdx.x; t < 3 * L * BK; t += blockDim.x) {
+    const int kzl = t % BK, rest = t / BK;
+    const int y = rest % L, f = rest / L;
+    const int kz = kz0 + kzl;
+    double2 v = make_double2(0.0, 0.0);
+    if (kz < g.nzh) v = S[(3 * i + f) * g.nspec + ((long long)x * L + y) * g.nzh + kz];
+    bufA[(f * BK + kzl) * QS + y] = v;
+  }
+  double2* R = fft_pencils<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1}, tw);
+  for (int t = threadIdx.x; t < L * BK; t += blockDim.x) {
+    const int kzl = t % BK, y = t / BK;
+    const int kz = kz0 + kzl;
+    if (kz >= g.nzh) continue;
+    const double xi_y = wave_int(y, L) * g.sy;
+    const double2 tx = R[(0 * BK + kzl) * QS + y];
+    const double2 ty = R[(1 * BK + kzl) * QS + y];
+    const double2 tz = R[(2 * BK + kzl) * QS + y];
+    const long long o = ((long long)x * L + y) * g.nzh + kz;
+    S[(3 * i + 0) * g.nspec + o] = tx;
+    S[(3 * i + 1) * g.nspec + o] = make_double2(fma(xi_y, ty.x, tz.x), fma(xi_y, ty.y, tz.y));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// x pass: forward along x, Ghat, inverse along x
+// ---------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(kThreads) k_x_ghat(Grid g, int BK, double2* __restrict__ S,
+                                                    const double2* __restrict__ tw, double scale,
+                                                    const CgScalars* __restrict__ cg) {
+  if (cg_done(cg)) return;
+  extern __shared__ double2 smem[];
+  constexpr int QS = L + 1;
+  const int np = 6 * BK;
+  double2* bufA = smem;
+  double2* bufB = smem + np * QS;
+  const int NC = (g.nzh + BK - 1) / BK;
+  const int chunk = blockIdx.x % NC;
+  const int ky = blockIdx.x / NC;
+  const int kz0 = chunk * BK;
+  const long long row = (long long)g.ny * g.nzh;  // stride of x in S
+  for (int t = threadIdx.x; t < 6 * L * BK; t += blockDim.x) {
+    const int kzl = t % BK, rest = t / BK;
+    const int x = rest % L, f = rest / L;
+    const int kz = kz0 + kzl;
+    const int comp = 3 * (f >> 1) + (f & 1);
+    double2 v = make_double2(0.0, 0.0);
+    if (kz < g.nzh) v = S[comp * g.nspec + x * row + (long long)ky * g.nzh + kz];
+    bufA[(f * BK + kzl) * QS + x] = v;
+  }
+  double2* R = fft_pencils<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1}, tw);
+  const double xi_y = wave_int(ky, g.ny) * g.sy;
+  for (int t = threadIdx.x; t < L * BK; t += blockDim.x) {
+    const int kzl = t % BK, kx = t / BK;
+    const int kz = kz0 + kzl;
+    const double xi_x = wave_int(kx, L) * g.sx;
+    const double xi_z = wave_int(kz, g.nz) * g.sz;
+    const double d = fma(xi_x, xi_x, fma(xi_y, xi_y, xi_z * xi_z));
+    const double s = d > 0.0 ? scale / d : 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double2* pa = R + ((2 * i) * BK + kzl) * QS + kx;
+      double2* pb = R + ((2 * i + 1) * BK + kzl) * QS + kx;
+      const double2 X = *pa, W = *pb;
+      const double2 v = make_double2(s * fma(xi_x, X.x, W.x), s * fma(xi_x, X.y, W.y));
+      *pa = cscale(v, xi_x);
+      *pb = v;
+    }
+  }
+  double2* other = (R == bufA) ? bufB : bufA;
+  double2* R2 = fft_pencils<L, true, true>(R, other, PencilLayout{np, QS, 1}, tw);
+  for (int t = threadIdx.x; t < 6 * L * BK; t += blockDim.x) {
+    const int kzl = t % BK, rest = t / BK;
+    const int x = rest % L, f = rest / L;
+    const int kz = kz0 + kzl;
+    if (kz >= g.nzh) continue;
+    const int comp = 3 * (f >> 1) + (f & 1);
+    S[comp * g.nspec + x * row + (long long)ky * g.nzh + kz] = R2[(f * BK + kzl) * QS + x];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// inverse y pass: expand A_i, B_i to the three columns of row i
+// ---------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(kThreads) k_inv_y(Grid g, int BK, double2* __restrict__ S,
+                                                   const double2* __restrict__ tw, const CgScalars* __restrict__ cg) {
+  if (cg_done(cg)) return;
+  extern __shared__ double2 smem[];
+  constexpr int QS = L + 1;
+  const int np = 3 * BK;
+  double2* bufA = smem;
+  double2* bufB = smem + np * QS;
+  const int NC = (g.nzh + BK - 1) / BK;
+  int b = blockIdx.x;
+  const int chunk = b % NC;
+  b /= NC;
+  const int i = b % 3;
+  const int x = b / 3;
+  const int kz0 = chunk * BK;
+  for (int t = threadIdx.x; t < 2 * L * BK; t += blockDim.x) {
+    const int kzl = t % BK, rest = t / BK;
+    const int y = rest % L, h = rest / L;
+    const int kz = kz0 + kzl;
+    double2 v = make_double2(0.0, 0.0);
+    if (kz < g.nzh) v = S[(3 * i + h) * g.nspec + ((long long)x * L + y) * g.nzh + kz];
+    if (h == 0) {
+      bufA[(0 * BK + kzl) * QS + y] = v;
+    } else {
+      bufA[(1 * BK + kzl) * QS + y] = cscale(v, wave_int(y, L) * g.sy);
+      bufA[(2 * BK + kzl) * QS + y] = v;
+    }
+  }
+  double2* R = fft_pencils<L, true, true>(bufA, bufB, PencilLayout{np, QS, 1}, tw);
+  for (int t = threadIdx.x; t < L * BK; t += blockDim.x) {
+    const int kzl = t % BK, y = t / BK;
+    const int kz = kz0 + kzl;
+    if (kz >= g.nzh) continue;
+    const long long o = ((long long)x * L + y) * g.nzh + kz;
+    S[(3 * i + 0) * g.nspec + o] = R[(0 * BK + kzl) * QS + y];
+    S[(3 * i + 1) * g.nspec + o] = R[(1 * BK + kzl) * QS + y];
+    S[(3 * i + 2) * g.nspec + o] = cscale(R[(2 * BK + kzl) * QS + y], wave_int(kz, g.nz) * g.sz);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// inverse z pass: complex-to-real along z, optional dot-product epilogue
+// ---------------------------------------------------------------------------
+template <int M, int MODE>
+__global__ void __launch_bounds__(kThreads) k_inv_z(Grid g, int LB, const double2* __restrict__ S,
+                                                   double* __restrict__ out, const double* __restrict__ p,
+                                                   double* __restrict__ partials, const double2* __restrict__ tw,
+                                                   const CgScalars* __restrict__ cg) {
+  if (cg_done(cg)) return;
+  extern __shared__ double2 smem[];
+  __shared__ double red[32];
+  constexpr int NZ = 2 * M;
+  double2* bufA = smem;
+  double2* bufB = smem + 9 * LB * M;
+  const long long line0 = (long long)blockIdx.x * LB;
+  const long long n = g.n;
+  // pack Z_k = (X_k + conj X_{M-k}) + i w^-k (X_k - conj X_{M-k}); the
+  // imaginary parts of X_0 and X_M are dropped (complex-to-real semantics)
+  constexpr int KH = M / 2 + 1;
+  const double2* twn = tw + twiddle_offset(NZ);
+  for (int t = threadIdx.x; t < 9 * LB * KH; t += blockDim.x) {
+    const int q = t / KH, k = t % KH;
+    const int c = q / LB, line = q % LB;
+    const double2* in = S + (long long)c * g.nspec + (line0 + line) * g.nzh;
+    double2 xk = in[k], xm = in[M - k];
+    if (k == 0) {
+      xk.y = 0.0;
+      xm.y = 0.0;
+    }
+    const double2 a = make_double2(xk.x + xm.x, xk.y - xm.y);
+    const double2 bb = make_double2(xk.x - xm.x, xk.y + xm.y);
+    const double2 bw = cmulc(bb, __ldg(twn + k));
+    const double2 u = make_double2(-bw.y, bw.x);  // i w^-k b
+    bufA[q * M + k] = cadd(a, u);
+    if (k != 0 && M - k != k) bufA[q * M + (M - k)] = make_double2(a.x - u.x, u.y - a.y);
+  }
+  double2* R = fft_pencils<M, true, true>(bufA, bufB, PencilLayout{9 * LB, M, 1}, tw);
+  const double* rr = reinterpret_cast<const double*>(R);
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < LB * NZ; t += blockDim.x) {
+    const int line = t / NZ, z = t % NZ;
+    const long long gi = (line0 + line) * NZ + z;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const double yv = rr[(c * LB + line) * NZ + z];
+      out[c * n + gi] = yv;
+      if constexpr (MODE == kIZDot) acc = fma(p[c * n + gi], yv, acc);
+      if constexpr (MODE == kIZRhs) acc = fma(yv, yv, acc);
+    }
+  }
+  if constexpr (MODE != kIZOut) {
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side: tiling, dispatch on the compile-time lengths
+// ---------------------------------------------------------------------------
+static int ilog2(int v) {
+  int r = 0;
+  while ((1 << r) < v) ++r;
+  return r;
+}
+
+Tiling choose_tiling(const Grid& g) {
+  Tiling t;
+  const long long lines = (long long)g.nx * g.ny;
+  int lb = 512 / g.nz;
+  if (lb < 1) lb = 1;
+  if (lb > lines) lb = (int)lines;
+  t.lines_z = lb;
+  int by = 512 / g.ny;
+  if (by < 1) by = 1;
+  if (by > g.nzh) by = g.nzh;
+  t.bk_y = by;
+  int bx = 256 / g.nx;
+  if (bx < 1) bx = 1;
+  if (bx > g.nzh) bx = g.nzh;
+  t.bk_x = bx;
+  return t;
+}
+
+size_t z_pass_smem(const Grid& g, const Tiling& t) { return (size_t)9 * t.lines_z * g.nz * sizeof(double2); }
+long long z_pass_ctas(const Grid& g, const Tiling& t) { return (long long)g.nx * g.ny / t.lines_z; }
+static size_t y_smem(int L, int bk, int fields) { return (size_t)2 * fields * bk * (L + 1) * sizeof(double2); }
+
+#define FH_SWITCH_POW2(v, MACRO) \
+  switch (v) {                   \
+    MACRO(1)                     \
+    MACRO(2)                     \
+    MACRO(4)                     \
+    MACRO(8)                     \
+    MACRO(16)                    \
+    MACRO(32)                    \
+    MACRO(64)                    \
+    MACRO(128)                   \
+    MACRO(256)                   \
+    default:                     \
+      return cudaErrorInvalidValue; \
+  }
+
+template <class Kern>
+static cudaError_t allow_smem(Kern k, size_t bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t setup_fft_kernels(const Grid& g, const Tiling& t) {
+  cudaError_t e = cudaSuccess;
+  const size_t zs = z_pass_smem(g, t);
+  const int M = g.nz / 2;
+#define ZCASE(V)                                                      \
+  case V:                                                             \
+    if ((e = allow_smem(k_fwd_z<V, kZDirect>, zs))) return e;         \
+    if ((e = allow_smem(k_fwd_z<V, kZKApply>, zs))) return e;         \
+    if ((e = allow_smem(k_fwd_z<V, kZCg>, zs))) return e;             \
+    if ((e = allow_smem(k_fwd_z<V, kZCgFirst>, zs))) return e;        \
+    if ((e = allow_smem(k_inv_z<V, kIZOut>, zs))) return e;           \
+    if ((e = allow_smem(k_inv_z<V, kIZDot>, zs))) return e;           \
+    if ((e = allow_smem(k_inv_z<V, kIZRhs>, zs))) return e;           \
+    break;
+  FH_SWITCH_POW2(M, ZCASE)
+#undef ZCASE
+#define YCASE(V)                                                           \
+  case V:                                                                  \
+    if ((e = allow_smem(k_fwd_y<V>, y_smem(V, t.bk_y, 3)))) return e;      \
+    if ((e = allow_smem(k_inv_y<V>, y_smem(V, t.bk_y, 3)))) return e;      \
+    break;
+  FH_SWITCH_POW2(g.ny, YCASE)
+#undef YCASE
+#define XCASE(V)                                                           \
+  case V:                                                                  \
+    if ((e = allow_smem(k_x_ghat<V>, y_smem(V, t.bk_x, 6)))) return e;     \
+    break;
+  FH_SWITCH_POW2(g.nx, XCASE)
+#undef XCASE
+  (void)ilog2;
+  return cudaSuccess;
+}
+
+cudaError_t launch_fwd_z(const Grid& g, const Tiling& t, int mode, const double* src, double* p, const double* K,
+                         const CgScalars* cg, double2* S, const double2* tw, cudaStream_t s) {
+  const size_t smem = z_pass_smem(g, t);
+  const unsigned grid = (unsigned)z_pass_ctas(g, t);
+  const int M = g.nz / 2;
+#define ZL(V)                                                                                              \
+  case V:                                                                                                  \
+    switch (mode) {                                                                                        \
+      case kZDirect: k_fwd_z<V, kZDirect><<<grid, kThreads, smem, s>>>(g, t.lines_z, src, p, K, cg, S, tw); break; \
+      case kZKApply: k_fwd_z<V, kZKApply><<<grid, kThreads, smem, s>>>(g, t.lines_z, src, p, K, cg, S, tw); break; \
+      case kZCg: k_fwd_z<V, kZCg><<<grid, kThreads, smem, s>>>(g, t.lines_z, src, p, K, cg, S, tw); break;         \
+      case kZCgFirst: k_fwd_z<V, kZCgFirst><<<grid, kThreads, smem, s>>>(g, t.lines_z, src, p, K, cg, S, tw); break; \
+      default: return cudaErrorInvalidValue;                                                               \
+    }                                                                                                      \
+    break;
+  FH_SWITCH_POW2(M, ZL)
+#undef ZL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_y(const Grid& g, const Tiling& t, double2* S, const double2* tw, const CgScalars* cg,
+                         cudaStream_t s) {
+  const int NC = (g.nzh + t.bk_y - 1) / t.bk_y;
+  const unsigned grid = (unsigned)((long long)g.nx * 3 * NC);
+#define YL(V)                                                                               \
+  case V:                                                                                   \
+    k_fwd_y<V><<<grid, kThreads, y_smem(V, t.bk_y, 3), s>>>(g, t.bk_y, S, tw, cg);          \
+    break;
+  FH_SWITCH_POW2(g.ny, YL)
+#undef YL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_x_ghat(const Grid& g, const Tiling& t, double2* S, const double2* tw, double scale,
+                          const CgScalars* cg, cudaStream_t s) {
+  const int NC = (g.nzh + t.bk_x - 1) / t.bk_x;
+  const unsigned grid = (unsigned)((long long)g.ny * NC);
+#define XL(V)                                                                                      \
+  case V:                                                                                          \
+    k_x_ghat<V><<<grid, kThreads, y_smem(V, t.bk_x, 6), s>>>(g, t.bk_x, S, tw, scale, cg);         \
+    break;
+  FH_SWITCH_POW2(g.nx, XL)
+#undef XL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inv_y(const Grid& g, const Tiling& t, double2* S, const double2* tw, const CgScalars* cg,
+                         cudaStream_t s) {
+  const int NC = (g.nzh + t.bk_y - 1) / t.bk_y;
+  const unsigned grid = (unsigned)((long long)g.nx * 3 * NC);
+#define IYL(V)                                                                              \
+  case V:                                                                                   \
+    k_inv_y<V><<<grid, kThreads, y_smem(V, t.bk_y, 3), s>>>(g, t.bk_y, S, tw, cg);          \
+    break;
+  FH_SWITCH_POW2(g.ny, IYL)
+#undef IYL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inv_z(const Grid& g, const Tiling& t, int mode, const double2* S, double* out, const double* p,
+                         double* partials, const double2* tw, const CgScalars* cg, cudaStream_t s) {
+  const size_t smem = z_pass_smem(g, t);
+  const unsigned grid = (unsigned)z_pass_ctas(g, t);
+  const int M = g.nz / 2;
+#define IZL(V)                                                                                                  \
+  case V:                                                                                                       \
+    switch (mode) {                                                                                             \
+      case kIZOut: k_inv_z<V, kIZOut><<<grid, kThreads, smem, s>>>(g, t.lines_z, S, out, p, partials, tw, cg); break; \
+      case kIZDot: k_inv_z<V, kIZDot><<<grid, kThreads, smem, s>>>(g, t.lines_z, S, out, p, partials, tw, cg); break; \
+      case kIZRhs: k_inv_z<V, kIZRhs><<<grid, kThreads, smem, s>>>(g, t.lines_z, S, out, p, partials, tw, cg); break; \
+      default: return cudaErrorInvalidValue;                                                                    \
+    }                                                                                                           \
+    break;
+  FH_SWITCH_POW2(M, IZL)
+#undef IZL
+  return cudaGetLastError();
+}
+
+}  // namespace fh

@@ -1,0 +1,347 @@
+// Voxel-wise kernels of the Newton-Krylov solve (Appendix A, Algorithm 1):
+// the constitutive evaluation by automatic differentiation (Eqs. 2-3), the
+// homogenized-stress reduction (Eq. 4), the conjugate-gradient scalar and
+// vector updates, and the Newton update with its convergence norm.
+//
+// Every reduction is deterministic: each CTA writes one partial per output
+// (a fixed shuffle tree inside the CTA), and a single CTA adds the partials
+// in a fixed order, so repeated runs give bit-identical results.
+#include <math.h>
+
+#include "ad.cuh"
+#include "fh_kernels.h"
+
+namespace fh {
+
+constexpr int kPointwiseCtas = 4 * 152;  // grid of the grid-stride voxel kernels
+
+static unsigned pointwise_grid(const Grid& g) {
+  long long b = (g.n + kThreads - 1) / kThreads;
+  if (b > kPointwiseCtas) b = kPointwiseCtas;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+// ---------------------------------------------------------------------------
+// constitutive evaluation: P, packed K and per-CTA sums of P
+// ---------------------------------------------------------------------------
+template <class Law>
+__global__ void __launch_bounds__(kThreads) k_constitutive(Grid g, MatView m, const double* __restrict__ F,
+                                                          double* __restrict__ P, double* __restrict__ K,
+                                                          double* __restrict__ partials, int* __restrict__ flags) {
+  __shared__ double red[32];
+  double sum[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) sum[c] = 0.0;
+  bool bad = false;
+  const long long n = g.n;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    double f[9], pv[9], kv[45];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) f[c] = F[c * n + v];
+    const int ph = m.phase[v];
+    const double lam = m.params[2 * ph], mu = m.params[2 * ph + 1];
+    const double w = ad::energy_derivatives<Law>(f, lam, mu, pv, kv);
+    bool ok = isfinite(w);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      ok = ok && isfinite(pv[c]);
+      sum[c] += pv[c];
+      if (P) P[c * n + v] = pv[c];
+    }
+    if (K) {
+#pragma unroll
+      for (int s = 0; s < 45; ++s) {
+        ok = ok && isfinite(kv[s]);
+        K[s * n + v] = kv[s];
+      }
+    }
+    bad |= !ok;
+  }
+  if (bad) atomicOr(flags, kFlagNonPhysical);
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    const double s = block_sum(sum[c], red);
+    if (threadIdx.x == 0) partials[c * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+long long constitutive_ctas(const Grid& g) { return pointwise_grid(g); }
+
+cudaError_t launch_constitutive(const Grid& g, const MatView& m, const double* F, double* P, double* K,
+                                double* partials, int* flags, cudaStream_t s) {
+  const unsigned grid = pointwise_grid(g);
+  switch (m.kind) {
+    case FH_LINEAR_ELASTIC:
+      k_constitutive<LinearElasticLaw><<<grid, kThreads, 0, s>>>(g, m, F, P, K, partials, flags);
+      break;
+    case FH_NEO_HOOKEAN:
+      k_constitutive<NeoHookeanLaw><<<grid, kThreads, 0, s>>>(g, m, F, P, K, partials, flags);
+      break;
+    case FH_SVK:
+      k_constitutive<SVKLaw><<<grid, kThreads, 0, s>>>(g, m, F, P, K, partials, flags);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// jvp form of the tangent apply (Listing 3): tau = K(F) : p with K re-derived
+// by AD in every call. mode kZKApply: p = src ; kZCg: p = r + beta p ;
+// kZCgFirst: p = r (p written back in the CG modes).
+// ---------------------------------------------------------------------------
+template <class Law, int MODE>
+__global__ void __launch_bounds__(kThreads) k_jvp(Grid g, MatView m, const double* __restrict__ F,
+                                                 const double* __restrict__ src, double* __restrict__ p,
+                                                 double* __restrict__ tau, const CgScalars* __restrict__ cg,
+                                                 int* __restrict__ flags) {
+  if (cg != nullptr && cg->done) return;
+  const long long n = g.n;
+  double beta = 0.0;
+  if constexpr (MODE == kZCg) beta = cg->beta;
+  bool bad = false;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    double f[9], pv[9], kv[45], pd[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      f[c] = F[c * n + v];
+      if constexpr (MODE == kZKApply) {
+        pd[c] = src[c * n + v];
+      } else if constexpr (MODE == kZCgFirst) {
+        pd[c] = src[c * n + v];
+        p[c * n + v] = pd[c];
+      } else {
+        pd[c] = fma(beta, p[c * n + v], src[c * n + v]);
+        p[c * n + v] = pd[c];
+      }
+    }
+    const int ph = m.phase[v];
+    const double w = ad::energy_derivatives<Law>(f, m.params[2 * ph], m.params[2 * ph + 1], pv, kv);
+    bad |= !isfinite(w);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      double acc = kv[sym_slot(a, 0)] * pd[0];
+#pragma unroll
+      for (int b = 1; b < 9; ++b) acc = fma(kv[sym_slot(a, b)], pd[b], acc);
+      tau[a * n + v] = acc;
+    }
+  }
+  if (bad) atomicOr(flags, kFlagNonPhysical);
+}
+
+template <class Law>
+static void launch_jvp_law(unsigned grid, cudaStream_t s, const Grid& g, const MatView& m, const double* F,
+                           const double* src, double* p, double* tau, int mode, const CgScalars* cg, int* flags) {
+  switch (mode) {
+    case kZKApply: k_jvp<Law, kZKApply><<<grid, kThreads, 0, s>>>(g, m, F, src, p, tau, cg, flags); break;
+    case kZCg: k_jvp<Law, kZCg><<<grid, kThreads, 0, s>>>(g, m, F, src, p, tau, cg, flags); break;
+    default: k_jvp<Law, kZCgFirst><<<grid, kThreads, 0, s>>>(g, m, F, src, p, tau, cg, flags); break;
+  }
+}
+
+cudaError_t launch_jvp(const Grid& g, const MatView& m, const double* F, const double* src, double* p, double* tau,
+                       int mode, const CgScalars* cg, int* flags, cudaStream_t s) {
+  const unsigned grid = pointwise_grid(g);
+  switch (m.kind) {
+    case FH_LINEAR_ELASTIC: launch_jvp_law<LinearElasticLaw>(grid, s, g, m, F, src, p, tau, mode, cg, flags); break;
+    case FH_NEO_HOOKEAN: launch_jvp_law<NeoHookeanLaw>(grid, s, g, m, F, src, p, tau, mode, cg, flags); break;
+    case FH_SVK: launch_jvp_law<SVKLaw>(grid, s, g, m, F, src, p, tau, mode, cg, flags); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// single-CTA fixed-order sums of partials: out[w] = sum_b partials[w n_parts + b]
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double sum_fixed(const double* __restrict__ a, int n, double* red) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += a[i];
+  return block_sum(s, red);
+}
+
+__global__ void __launch_bounds__(kThreads) k_sum_partials(const double* __restrict__ partials, int n_parts,
+                                                          int width, double* __restrict__ out) {
+  __shared__ double red[32];
+  for (int w = 0; w < width; ++w) {
+    const double s = sum_fixed(partials + (long long)w * n_parts, n_parts, red);
+    if (threadIdx.x == 0) out[w] = s;
+  }
+}
+
+cudaError_t launch_sum_partials(const double* partials, int n_parts, int width, double* out, cudaStream_t s) {
+  k_sum_partials<<<1, kThreads, 0, s>>>(partials, n_parts, width, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// per-CTA sums of the nine components of a field (voxel mean of a start field)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_field_sums(Grid g, const double* __restrict__ F,
+                                                        double* __restrict__ partials) {
+  __shared__ double red[32];
+  const long long n = g.n;
+  for (int c = 0; c < 9; ++c) {
+    double acc = 0.0;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+      acc += F[c * n + v];
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[c * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+cudaError_t launch_field_sums(const Grid& g, const double* F, double* partials, cudaStream_t s) {
+  k_field_sums<<<pointwise_grid(g), kThreads, 0, s>>>(g, F, partials);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// F = value (add = 0) or F += value (add = 1) in every voxel (load increment)
+// ---------------------------------------------------------------------------
+struct Nine {
+  double v[9];
+};
+
+__global__ void __launch_bounds__(kThreads) k_fill(Grid g, double* __restrict__ F, Nine val, int add) {
+  const long long n = g.n;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) F[c * n + v] = add ? F[c * n + v] + val.v[c] : val.v[c];
+  }
+}
+
+cudaError_t launch_fill(const Grid& g, double* F, const double* value9, int add, cudaStream_t s) {
+  Nine val;
+  for (int c = 0; c < 9; ++c) val.v[c] = value9[c];
+  k_fill<<<pointwise_grid(g), kThreads, 0, s>>>(g, F, val, add);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// conjugate-gradient scalars (single CTA each)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_cg_init(CgScalars* cg, const double* __restrict__ partials, int n_parts,
+                                                     double tol, int max_it) {
+  __shared__ double red[32];
+  const double bb = sum_fixed(partials, n_parts, red);
+  if (threadIdx.x == 0) {
+    cg->bb = bb;
+    cg->rr = bb;
+    cg->alpha = 0.0;
+    cg->beta = 0.0;
+    cg->tol = tol;
+    cg->py = 0.0;
+    cg->it = 0;
+    cg->max_it = max_it;
+    // the test of the loop head with r = b (converged at once only if b = 0 or tol >= 1)
+    int done = 0;
+    if (!(bb == bb)) done = 3;
+    else if (sqrt(bb) <= tol * sqrt(bb)) done = 1;
+    else if (max_it <= 0) done = 2;
+    cg->done = done;
+  }
+}
+
+cudaError_t launch_cg_init(CgScalars* cg, const double* partials, int n_parts, double tol, int max_it,
+                           cudaStream_t s) {
+  k_cg_init<<<1, kThreads, 0, s>>>(cg, partials, n_parts, tol, max_it);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_alpha(CgScalars* cg, const double* __restrict__ partials,
+                                                      int n_parts) {
+  __shared__ double red[32];
+  if (cg->done) return;
+  const double py = sum_fixed(partials, n_parts, red);
+  if (threadIdx.x == 0) {
+    cg->py = py;
+    if (!(py > 0.0) || !isfinite(py)) {
+      cg->done = 3;
+      cg->alpha = 0.0;
+    } else {
+      cg->alpha = cg->rr / py;
+    }
+  }
+}
+
+cudaError_t launch_cg_alpha(CgScalars* cg, const double* partials, int n_parts, cudaStream_t s) {
+  k_cg_alpha<<<1, kThreads, 0, s>>>(cg, partials, n_parts);
+  return cudaGetLastError();
+}
+
+// x += alpha p (x = alpha p on the first iteration), r -= alpha y, partial r . r
+__global__ void __launch_bounds__(kThreads) k_cg_update(Grid g, const CgScalars* __restrict__ cg, double* __restrict__ x,
+                                                       double* __restrict__ r, const double* __restrict__ p,
+                                                       const double* __restrict__ y, double* __restrict__ partials,
+                                                       int first) {
+  __shared__ double red[32];
+  if (cg->done) return;
+  const double alpha = cg->alpha;
+  const long long n9 = 9 * g.n;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n9; i += (long long)gridDim.x * blockDim.x) {
+    const double pv = p[i];
+    x[i] = first ? alpha * pv : fma(alpha, pv, x[i]);
+    const double rv = fma(-alpha, y[i], r[i]);
+    r[i] = rv;
+    acc = fma(rv, rv, acc);
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+long long cg_update_ctas(const Grid& g) { return pointwise_grid(g); }
+
+cudaError_t launch_cg_update(const Grid& g, CgScalars* cg, double* x, double* r, const double* p, const double* y,
+                             double* partials, int first, cudaStream_t s) {
+  k_cg_update<<<pointwise_grid(g), kThreads, 0, s>>>(g, cg, x, r, p, y, partials, first);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_beta(CgScalars* cg, const double* __restrict__ partials,
+                                                     int n_parts) {
+  __shared__ double red[32];
+  if (cg->done) return;
+  const double rr = sum_fixed(partials, n_parts, red);
+  if (threadIdx.x == 0) {
+    const double rr_old = cg->rr;
+    cg->beta = rr / rr_old;
+    cg->rr = rr;
+    cg->it += 1;
+    if (!isfinite(rr)) cg->done = 3;
+    else if (sqrt(rr) <= cg->tol * sqrt(cg->bb)) cg->done = 1;
+    else if (cg->it >= cg->max_it) cg->done = 2;
+  }
+}
+
+cudaError_t launch_cg_beta(CgScalars* cg, const double* partials, int n_parts, cudaStream_t s) {
+  k_cg_beta<<<1, kThreads, 0, s>>>(cg, partials, n_parts);
+  return cudaGetLastError();
+}
+
+// F += dF and partial ||dF||^2 (Algorithm 1 update and convergence test)
+__global__ void __launch_bounds__(kThreads) k_newton_update(Grid g, double* __restrict__ F,
+                                                           const double* __restrict__ dF,
+                                                           double* __restrict__ partials) {
+  __shared__ double red[32];
+  const long long n9 = 9 * g.n;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n9; i += (long long)gridDim.x * blockDim.x) {
+    const double d = dF[i];
+    F[i] += d;
+    acc = fma(d, d, acc);
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+long long newton_update_ctas(const Grid& g) { return pointwise_grid(g); }
+
+cudaError_t launch_newton_update(const Grid& g, double* F, const double* dF, double* partials, cudaStream_t s) {
+  k_newton_update<<<pointwise_grid(g), kThreads, 0, s>>>(g, F, dF, partials);
+  return cudaGetLastError();
+}
+
+}  // namespace fh

@@ -1,0 +1,281 @@
+"""GPU path against the CPU oracle, element by element, through the C-ABI.
+
+Tolerances: homogenized stress relative 1e-9, voxel fields 1e-8 in the
+max-relative measure (max|a - b| / max|b| per component field); single
+operators (stress, tangent, projection, matrix-vector product) are compared
+at 1e-12, since both sides evaluate the same expression and differ only by
+rounding order (FFT sums of a few hundred terms, AD vs closed form).
+"""
+
+import numpy as np
+import pytest
+
+from gpu_helpers import dev, field_maxrel, host, pack_tangent, require_gpu
+from oracle import materials as omat
+from oracle import solver as osolver
+from oracle import spectral
+from rve_inputs import (centered_sphere, laminate, random_deformation, random_spheres, shear_macro,
+                        small_strain_config, two_phase_table)
+
+pytestmark = pytest.mark.gpu
+
+OP_TOL = 1e-12
+FIELD_TOL = 1e-8
+PBAR_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_gpu()
+
+
+@pytest.fixture(scope="module")
+def fh(torch):
+    import paper_2408_03804_gb300 as fh
+
+    return fh
+
+
+def _phase(shape, seed, n_phase=2):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, n_phase, size=shape).astype(np.uint8)
+
+
+# ---------------------------------------------------------------------------
+# a2: stress and tangent by AD
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(4, 8, 16), (2, 2, 2), (8, 1, 6 + 2)])
+def test_constitutive_matches_closed_form(fh, torch, kind, shape):
+    n = int(np.prod(shape))
+    F = random_deformation(n, seed=kind + 3, scale=0.2, identity=omat.FINITE_STRAIN[kind]).reshape((9,) + shape)
+    phase = _phase(shape, 1, 3)
+    params = np.array([[1.5, 1.0], [15.0, 10.0], [0.3, 0.7]])
+    lam, mu = params[phase, 0], params[phase, 1]
+    with fh.Context(*shape) as ctx:
+        mat = fh.Material(kind, phase, params)
+        Fd = dev(F)
+        P = torch.empty_like(Fd)
+        K = torch.empty((45,) + shape, dtype=torch.float64, device="cuda")
+        pbar = ctx.fh_constitutive(mat, Fd, P, K)
+    P_ref = omat.stress(kind, F, lam, mu)
+    K_ref = pack_tangent(omat.tangent(kind, F, lam, mu))
+    assert field_maxrel(host(P), P_ref) < OP_TOL
+    assert np.abs(host(K) - K_ref).max() < OP_TOL * np.abs(K_ref).max()
+    np.testing.assert_allclose(pbar, P_ref.reshape(9, -1).mean(axis=1), rtol=1e-12, atol=1e-14)
+
+
+def test_constitutive_reports_nonphysical_voxels(fh, torch):
+    shape = (4, 4, 4)
+    F = random_deformation(64, seed=1, scale=0.05).reshape((9,) + shape)
+    F[0, 1, 2, 3] = -1.0  # det F < 0 in one voxel
+    with fh.Context(*shape) as ctx:
+        mat = fh.Material(fh.NEO_HOOKEAN, np.zeros(shape, np.uint8), [[1.5, 1.0]])
+        _, rc = ctx.fh_constitutive(mat, dev(F), allow_nonphysical=True)
+    assert rc == fh.FH_ERR_NONPHYSICAL
+
+
+def test_out_of_range_phase_is_reported(fh, torch):
+    shape = (4, 4, 4)
+    F = random_deformation(64, seed=2, scale=0.05).reshape((9,) + shape)
+    phase = np.zeros(shape, np.uint8)
+    phase[0, 0, 0] = 5
+    with fh.Context(*shape) as ctx:
+        mat = fh.Material(fh.NEO_HOOKEAN, phase, [[1.5, 1.0], [3.0, 2.0]])
+        _, rc = ctx.fh_constitutive(mat, dev(F), allow_nonphysical=True)
+    assert rc == fh.FH_ERR_NONPHYSICAL
+
+
+# ---------------------------------------------------------------------------
+# a3/a4: projection and matrix-vector product
+# ---------------------------------------------------------------------------
+PROJ_SHAPES = [(8, 8, 8), (4, 8, 16), (16, 4, 2), (2, 2, 2), (1, 4, 8), (32, 16, 8), (8, 1, 32),
+               (256, 2, 2), (2, 256, 2), (2, 2, 256), (64, 32, 128)]
+
+
+@pytest.mark.parametrize("shape", PROJ_SHAPES)
+def test_projection_matches_oracle(fh, torch, shape):
+    rng = np.random.default_rng(sum(shape))
+    A = rng.standard_normal((9,) + shape)
+    lengths = (1.0, 2.0, 0.5) if shape[0] == 4 else (1.0, 1.0, 1.0)
+    with fh.Context(*shape) as ctx:
+        Ad = dev(A)
+        out = torch.empty_like(Ad)
+        ctx.fh_project(Ad, out, scale=-1.5, lengths=lengths)
+        inplace = Ad.clone()
+        ctx.fh_project(inplace, inplace, scale=1.0, lengths=lengths)
+    ref = spectral.project(A, lengths)
+    assert np.abs(host(out) + 1.5 * ref).max() < OP_TOL * 1.5 * np.abs(A).max()
+    assert np.abs(host(inplace) - ref).max() < OP_TOL * np.abs(A).max()
+
+
+@pytest.mark.parametrize("kind", [1, 2, 0])
+@pytest.mark.parametrize("shape", [(8, 8, 8), (4, 16, 32)])
+def test_matvec_matches_oracle_stored_and_jvp(fh, torch, kind, shape):
+    n = int(np.prod(shape))
+    F = random_deformation(n, seed=5, scale=0.1, identity=omat.FINITE_STRAIN[kind]).reshape((9,) + shape)
+    p = np.random.default_rng(6).standard_normal((9,) + shape)
+    phase = _phase(shape, 7)
+    params = two_phase_table(1.5, 1.0, 10.0)
+    lam, mu = params[phase, 0], params[phase, 1]
+    Kref = omat.tangent(kind, F, lam, mu)
+    ref = spectral.project(omat.apply_tangent(Kref, p))
+    with fh.Context(*shape) as ctx:
+        mat = fh.Material(kind, phase, params)
+        Fd, pd = dev(F), dev(p)
+        K = torch.empty((45,) + shape, dtype=torch.float64, device="cuda")
+        ctx.fh_constitutive(mat, Fd, None, K)
+        y1 = torch.empty_like(pd)
+        y2 = torch.empty_like(pd)
+        ctx.fh_matvec(pd, y1, K=K)
+        ctx.fh_matvec(pd, y2, mat=mat, F=Fd)
+    scale = np.abs(ref).max()
+    assert np.abs(host(y1) - ref).max() < OP_TOL * 10 * scale
+    assert np.abs(host(y2) - ref).max() < OP_TOL * 10 * scale
+
+
+# ---------------------------------------------------------------------------
+# a1-a7: the whole Newton-Krylov solve
+# ---------------------------------------------------------------------------
+def _solve_both(fh, torch, phase, params, kind, Fbar, n_inc, tol, cg_tol=None, tangent_mode=0,
+                lengths=(1.0, 1.0, 1.0), max_newton=50, max_cg=5000, allow=()):
+    shape = phase.shape
+    with fh.Context(*shape) as ctx:
+        mat = fh.Material(kind, phase, params)
+        F = torch.zeros((9,) + shape, dtype=torch.float64, device="cuda")
+        opts = fh.default_options(newton_tol=tol, cg_tol=cg_tol or 0.0, tangent_mode=tangent_mode,
+                                  lengths=lengths, max_newton=max_newton, max_cg=max_cg, check_every=4)
+        pbar, stats, rc = ctx.fft_homog_solve(mat, Fbar, F, n_increments=n_inc, options=opts, allow=allow)
+        Fg = host(F)
+    ref = osolver.solve(phase, params, kind, Fbar, n_increments=n_inc, newton_tol=tol, cg_tol=cg_tol,
+                        lengths=lengths, max_newton=max_newton, max_cg=max_cg, raise_on_failure=not allow)
+    return Fg, pbar, stats, rc, ref
+
+
+def test_small_strain_sphere_16_matches_oracle(fh, torch):
+    """Linear elastic 16^3 cube, centred sphere r = 0.25 L, eps_xy = 0.01, tol 1e-10."""
+    phase, params, Ebar = small_strain_config(16)
+    Fg, pbar, stats, _, ref = _solve_both(fh, torch, phase, params, 0, Ebar, 1, 1e-10)
+    assert stats["n_newton"] == len(ref.newton_residuals) == 2
+    assert all(abs(a - b) <= 1 for a, b in zip(stats["cg_iterations"], ref.cg_iterations))
+    np.testing.assert_allclose(pbar, ref.Pbar, rtol=PBAR_TOL, atol=PBAR_TOL * np.abs(ref.Pbar).max())
+    eps_g = osolver.strain_field(0, Fg)
+    eps_r = osolver.strain_field(0, ref.F)
+    assert field_maxrel(eps_g, eps_r) < FIELD_TOL
+
+
+def test_neo_hookean_random_spheres_matches_oracle(fh, torch):
+    n = 32
+    phase = random_spheres(n, seed=0, r_min=2.0, r_max=4.0)
+    params = two_phase_table(1.5, 1.0, 10.0)
+    Fbar = shear_macro(0.05, finite=True)
+    Fg, pbar, stats, _, ref = _solve_both(fh, torch, phase, params, 1, Fbar, 5, 1e-8)
+    assert stats["n_newton"] == len(ref.newton_residuals)
+    np.testing.assert_allclose(pbar, ref.Pbar, rtol=PBAR_TOL, atol=PBAR_TOL * np.abs(ref.Pbar).max())
+    assert field_maxrel(Fg - np.eye(3).reshape(9, 1, 1, 1), ref.F - np.eye(3).reshape(9, 1, 1, 1)) < FIELD_TOL
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_anisotropic_box_and_ragged_grid(fh, torch, kind):
+    shape = (8, 16, 4)
+    phase = _phase(shape, 11)
+    params = two_phase_table(1.5, 1.0, 5.0)
+    rng = np.random.default_rng(3)
+    Fbar = np.eye(3).reshape(9) + rng.uniform(-0.03, 0.03, 9)
+    Fg, pbar, stats, _, ref = _solve_both(fh, torch, phase, params, kind, Fbar, 2, 1e-10,
+                                          lengths=(1.0, 2.0, 0.5))
+    np.testing.assert_allclose(pbar, ref.Pbar, rtol=PBAR_TOL, atol=PBAR_TOL * np.abs(ref.Pbar).max())
+    assert np.abs(Fg - ref.F).max() < FIELD_TOL * np.abs(ref.F - Fbar.reshape(9, 1, 1, 1)).max()
+
+
+def test_jvp_mode_equals_stored_mode(fh, torch):
+    shape = (16, 8, 8)
+    phase = _phase(shape, 12)
+    params = two_phase_table(1.5, 1.0, 10.0)
+    Fbar = shear_macro(0.03, finite=True)
+    out = []
+    for mode in (0, 1):
+        with fh.Context(*shape) as ctx:
+            mat = fh.Material(1, phase, params)
+            F = torch.zeros((9,) + shape, dtype=torch.float64, device="cuda")
+            opts = fh.default_options(newton_tol=1e-10, tangent_mode=mode)
+            pbar, stats, _ = ctx.fft_homog_solve(mat, Fbar, F, n_increments=2, options=opts)
+            out.append((host(F), pbar, stats))
+    assert np.abs(out[0][0] - out[1][0]).max() < 1e-12
+    np.testing.assert_allclose(out[0][1], out[1][1], rtol=1e-12)
+
+
+def test_svk_laminate_matches_exact_solution(fh, torch):
+    from oracle import laminate as olam
+
+    shape = (8, 4, 4)
+    phase = laminate(shape, 2, axis=0)
+    params = two_phase_table(1.5, 1.0, 10.0)
+    Fbar = np.eye(3).reshape(9) + np.array([0.02, 0.03, -0.01, 0.01, -0.02, 0.0, 0.015, 0.0, 0.01])
+    with fh.Context(*shape) as ctx:
+        mat = fh.Material(2, phase, params)
+        F = torch.zeros((9,) + shape, dtype=torch.float64, device="cuda")
+        ctx.fft_homog_solve(mat, Fbar, F, n_increments=1, options=fh.default_options(newton_tol=1e-12))
+        Fg = host(F).reshape(9, -1)
+    FA, FB = olam.laminate_states(2, params, 0.25, Fbar)
+    ph = phase.reshape(-1)
+    assert np.abs(Fg[:, ph == 1] - FA[:, None]).max() < 1e-11
+    assert np.abs(Fg[:, ph == 0] - FB[:, None]).max() < 1e-11
+
+
+def test_homogeneous_and_degenerate_grids(fh, torch):
+    # homogeneous material: no fluctuation at all
+    shape = (8, 8, 8)
+    with fh.Context(*shape) as ctx:
+        mat = fh.Material(1, np.zeros(shape, np.uint8), [[1.5, 1.0]])
+        F = torch.zeros((9,) + shape, dtype=torch.float64, device="cuda")
+        Fbar = shear_macro(0.05, finite=True)
+        pbar, _, _ = ctx.fft_homog_solve(mat, Fbar, F, options=fh.default_options(newton_tol=1e-12))
+        assert np.abs(host(F) - Fbar.reshape(9, 1, 1, 1)).max() < 1e-14
+        np.testing.assert_allclose(pbar, omat.stress(1, Fbar.reshape(9, 1), 1.5, 1.0)[:, 0], rtol=1e-14, atol=1e-15)
+    # a 1 x 1 x 2 grid has no compatible fluctuation: F = Fbar in both voxels
+    with fh.Context(1, 1, 2) as ctx:
+        mat = fh.Material(1, np.array([[[0, 1]]], np.uint8), two_phase_table(1.5, 1.0, 10.0))
+        F = torch.zeros((9, 1, 1, 2), dtype=torch.float64, device="cuda")
+        ctx.fft_homog_solve(mat, Fbar, F)
+        assert np.abs(host(F) - Fbar.reshape(9, 1, 1, 1)).max() < 1e-15
+
+
+def test_iteration_caps_and_warm_start(fh, torch):
+    shape = (16, 16, 16)
+    phase = centered_sphere(shape, 0.25)
+    params = two_phase_table(1.5, 1.0, 10.0)
+    Fbar = shear_macro(0.05, finite=True)
+    with fh.Context(*shape) as ctx:
+        mat = fh.Material(1, phase, params)
+        F = torch.zeros((9,) + shape, dtype=torch.float64, device="cuda")
+        _, stats, rc = ctx.fft_homog_solve(mat, Fbar, F, options=fh.default_options(max_cg=3),
+                                           allow=(fh.FH_ERR_NOT_CONVERGED,))
+        assert rc == fh.FH_ERR_NOT_CONVERGED and stats["cg_iterations"] == [3]
+        assert torch.isfinite(F).all()
+        _, _, rc = ctx.fft_homog_solve(mat, Fbar, F, options=fh.default_options(max_newton=1),
+                                       allow=(fh.FH_ERR_NOT_CONVERGED,))
+        assert rc == fh.FH_ERR_NOT_CONVERGED
+        # cold solve to gamma = 0.02, then warm start to 0.05 equals a cold solve to 0.05
+        F1 = torch.zeros_like(F)
+        ctx.fft_homog_solve(mat, shear_macro(0.02, True), F1, options=fh.default_options(newton_tol=1e-11))
+        ctx.fft_homog_solve(mat, Fbar, F1, n_increments=3,
+                            options=fh.default_options(newton_tol=1e-11, init=fh.INIT_GIVEN))
+        F2 = torch.zeros_like(F)
+        ctx.fft_homog_solve(mat, Fbar, F2, n_increments=1, options=fh.default_options(newton_tol=1e-11))
+        assert (F1 - F2).abs().max().item() < 1e-10
+
+
+def test_solve_is_deterministic(fh, torch):
+    shape = (16, 16, 16)
+    phase = _phase(shape, 4)
+    params = two_phase_table(1.5, 1.0, 10.0)
+    res = []
+    for _ in range(2):
+        with fh.Context(*shape) as ctx:
+            F = torch.zeros((9,) + shape, dtype=torch.float64, device="cuda")
+            pbar, stats, _ = ctx.fft_homog_solve(fh.Material(1, phase, params), shear_macro(0.05, True), F,
+                                                 n_increments=2)
+            res.append((host(F), pbar, stats["cg_iterations"]))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert res[0][2] == res[1][2]
