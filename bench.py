@@ -38,8 +38,9 @@ METRIC = "time-to-solve @1e-8 residual (128³ neo-Hookean); CG matvec GB/s vs HB
 WORKLOAD = ("neo-Hookean 128^3, RSA spheres r~U[4,10] vox, f=0.30, contrast 10 (mu=1, lambda=1.5), "
             "Fbar=I+0.05 e_x(x)e_y in 5 increments, Newton tol 1e-8, CG tol 1e-10, FP64")
 HBM_PEAK_FALLBACK = 6694.5
-FP64_PEAK_TFLOPS = 1.008       # in-repo DFMA probe (profiles/fp64_throughput_probe.md)
-FP64_NOMINAL_TFLOPS = 1.259    # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+# FP64 peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA lanes per
+# clock x 2 flops x 2.07 GHz (MEASURED_PEAKS.json carries no FP64 figure)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 # ---------------------------------------------------------------------------
@@ -64,6 +65,37 @@ def algorithmic_work(cls: str, nx: int, ny: int, nz: int):
     if cls == "cg_update":    # read x, r, p, y; write x, r
         return 6 * 72 * n, 6 * 9 * n
     return None, None
+
+
+# FP64 lane operations (DADD, DMUL, DFMA each one) per launch, counted from the
+# kernels' code: complex length-L transform per point = FP64_FFT_OPS[L]
+FP64_FFT_OPS = {1: 0.0, 2: 2.0, 4: 4.0, 8: 6.5, 16: 10.0, 32: 13.5, 64: 16.5, 128: 20.0, 256: 23.75}
+FP64_LANE_PEAK = 152 * 2 * 2.07e9   # lane operations per second at the maximum SM clock
+
+
+def fp64_ops(cls: str, nx: int, ny: int, nz: int):
+    n = nx * ny * nz
+    h = nx * ny * (nz // 2 + 1)
+    m = nz // 2
+    r2c = 9 * (FP64_FFT_OPS[m] * m + 12 * (m // 2 + 1)) * nx * ny  # half-length FFT + unpack
+    if cls == "fwd_z":
+        return 90 * n + r2c + 3 * 4 * (m // 2 + 1) * nx * ny
+    if cls == "fwd_y":
+        return (9 * FP64_FFT_OPS[ny] + 12) * h
+    if cls == "x_ghat":
+        return (12 * FP64_FFT_OPS[nx] + 30) * h
+    if cls == "inv_y":
+        return (9 * FP64_FFT_OPS[ny] + 12) * h
+    if cls == "inv_z":
+        return 9 * n + r2c
+    if cls == "cg_update":
+        return 27 * n
+    return None
+
+
+def fp64_pipe_frac(cls, shape, avg_s):
+    ops = fp64_ops(cls, *shape)
+    return ops / avg_s / FP64_LANE_PEAK if ops else None
 
 
 def cg_iteration_bytes(nx, ny, nz):
@@ -308,6 +340,50 @@ def cufft_matvec_ms(torch, K, p, reps=5):
     return e0.elapsed_time(e1) / reps
 
 
+def run_e2e(args, world, ctx, fh, torch, phase, params, Fbar, F, opts, dev, stream):
+    """The same solve through the public API with host buffers: the phase map
+    goes host -> device and the converged field device -> host every step."""
+    shape = phase.shape
+    phase_host = torch.from_numpy(phase.copy()).pin_memory()
+    F_host = torch.empty((9,) + shape, dtype=torch.float64).pin_memory()
+    phase_dev = torch.empty(shape, dtype=torch.uint8, device=dev)
+    ctx.fh_profile_enable(True)
+    barrier(world, dev.index)
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        phase_dev.copy_(phase_host, non_blocking=True)
+        mat_e = fh.Material(fh.NEO_HOOKEAN, phase_dev, params)
+        ctx.fft_homog_solve(mat_e, Fbar, F, n_increments=N_INC, options=opts)
+        F_host.copy_(F, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ctx.fh_profile_enable(False)
+    return max_over_ranks(world, e2.elapsed_time(e3) / 1e3, dev) / args.steps
+
+
+def run_matvec_comparison(ctx, fh, torch, mat, F, shape, dev, stream):
+    K = torch.empty((45,) + shape, dtype=torch.float64, device=dev)
+    ctx.fh_constitutive(mat, F, None, K, want_pbar=False)
+    p = torch.randn((9,) + shape, dtype=torch.float64, device=dev)
+    y = torch.empty_like(p)
+    for _ in range(2):
+        ctx.fh_matvec(p, y, K=K)
+    torch.cuda.synchronize()
+    e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e4.record(stream)
+    for _ in range(5):
+        ctx.fh_matvec(p, y, K=K)
+    e5.record(stream)
+    torch.cuda.synchronize()
+    ours = e4.elapsed_time(e5) / 5
+    theirs = cufft_matvec_ms(torch, K, p)
+    del K, p, y
+    torch.cuda.empty_cache()
+    return ours, theirs
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -323,8 +399,8 @@ def run_ours(args, world, rank, local):
     fhbuild.build()
     fh.load()
     dev = torch.device("cuda", local)
-    phase, params, Fbar = neo_hookean_config(N_GRID, seed=rank)
-    shape = phase.shape
+    shape = tuple(args.shape)
+    phase, params, Fbar = neo_hookean_config(shape, seed=rank)
     n = phase.size
     stream = torch.cuda.current_stream()
     ctx = fh.Context(*shape, stream=stream.cuda_stream)
@@ -362,40 +438,14 @@ def run_ours(args, world, rank, local):
     per_step = elapsed_s / args.steps
 
     # ---- end to end through the public API with host buffers ----
-    phase_host = torch.from_numpy(phase.copy()).pin_memory()
-    F_host = torch.empty((9,) + shape, dtype=torch.float64).pin_memory()
-    phase_dev = torch.empty(shape, dtype=torch.uint8, device=dev)
-    barrier(world, local)
-    torch.cuda.synchronize()
-    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2.record(stream)
-    for _ in range(args.steps):
-        phase_dev.copy_(phase_host, non_blocking=True)
-        mat_e = fh.Material(fh.NEO_HOOKEAN, phase_dev, params)
-        pbar_e, _, _ = ctx.fft_homog_solve(mat_e, Fbar, F, n_increments=N_INC, options=opts)
-        F_host.copy_(F, non_blocking=True)
-    e3.record(stream)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(world, e2.elapsed_time(e3) / 1e3, dev) / args.steps
+    e2e_s = None
+    if not args.no_e2e:
+        e2e_s = run_e2e(args, world, ctx, fh, torch, phase, params, Fbar, F, opts, dev, stream)
 
     # ---- cuFFT comparison of one matrix-vector product ----
-    K = torch.empty((45,) + shape, dtype=torch.float64, device=dev)
-    ctx.fh_constitutive(mat, F, None, K, want_pbar=False)
-    p = torch.randn((9,) + shape, dtype=torch.float64, device=dev)
-    y = torch.empty_like(p)
-    for _ in range(2):
-        ctx.fh_matvec(p, y, K=K)
-    torch.cuda.synchronize()
-    e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e4.record(stream)
-    for _ in range(5):
-        ctx.fh_matvec(p, y, K=K)
-    e5.record(stream)
-    torch.cuda.synchronize()
-    ours_mv_ms = e4.elapsed_time(e5) / 5
-    cufft_ms = cufft_matvec_ms(torch, K, p)
-    del K, p, y
-
+    ours_mv_ms = cufft_ms = None
+    if not args.no_cufft:
+        ours_mv_ms, cufft_ms = run_matvec_comparison(ctx, fh, torch, mat, F, shape, dev, stream)
     if rank != 0:
         ctx.close()
         if world > 1:
@@ -415,8 +465,9 @@ def run_ours(args, world, rank, local):
     roofline = {"bound": "alu", "kernel": dom, "achieved": fp64_ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": fp64_ach / FP64_PEAK_TFLOPS if fp64_ach else None,
                 "traffic": committed_traffic(dom),
-                "peak_source": "measured FP64 DFMA probe (MEASURED_PEAKS.json has no FP64 entry); nominal "
-                               f"{FP64_NOMINAL_TFLOPS} = 152 SM x 2 DFMA/clk x 2 x 2.07 GHz",
+                "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (no FP64 entry in "
+                               "MEASURED_PEAKS.json); achieved counts flops the conventional way (5 L log2 L "
+                               "per complex length-L FFT)",
                 "avg_launch_ms": avg_s * 1e3, "launches": launches_dom,
                 "algorithmic_flops_per_launch": flops_l, "algorithmic_bytes_per_launch": bytes_l,
                 "hbm_gbs": bytes_l / avg_s / 1e9, "hbm_peak": hbm_peak, "hbm_peak_source": hbm_src,
@@ -428,12 +479,13 @@ def run_ours(args, world, rank, local):
     cg_iter = {"ms": it_ms, "algorithmic_bytes": it_bytes, "gbs": it_bytes / (it_ms / 1e3) / 1e9,
                "hbm_frac": it_bytes / (it_ms / 1e3) / 1e9 / hbm_peak,
                "matvec_ms_ours": ours_mv_ms, "matvec_ms_cufft_torch": cufft_ms}
+    roofline["fp64_pipe_frac"] = fp64_pipe_frac(dom, shape, avg_s)
     kernels = {c: {"launches": v[0], "ms_total": v[1], "share": v[1] / sum(x[1] for x in classes.values())}
                for c, v in classes.items()}
 
     # ---- CPU oracle on a bounded sample (rank 0 only, at N = 1) ----
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and shape == (N_GRID,) * 3:
         t_cg, t_newton, it = oracle_sample(phase, params, Fbar, n_cg_iters=6)
         st = stats[-1]
         est = st["n_newton"] * t_newton + st["n_cg"] * t_cg
@@ -447,12 +499,14 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": per_step, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [N_GRID] * 3, "replicas": world,
+        "config": {"workload": WORKLOAD if shape == (N_GRID,) * 3 else WORKLOAD.replace("128^3", "x".join(map(str, shape))),
+                   "grid": list(shape), "replicas": world,
                    "l2": "working set ~1.6 GB per solve (inputs larger than L2), no explicit flush",
                    "newton_iterations": st["n_newton"], "cg_iterations": st["n_cg"],
                    "pbar": pbar.tolist()},
-        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(n), "d2h_bytes_per_step": int(9 * n * 8)},
-        "gpu_launches": int(sum(v[0] for v in prof.values())) // max(args.steps, 1) * args.steps,
+        "e2e": ({"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(n), "d2h_bytes_per_step": int(9 * n * 8)}
+                if e2e_s is not None else None),
+        "gpu_launches": int(sum(v[0] for v in prof.values())),
         "roofline": roofline,
         "cg_iteration": cg_iter,
         "kernels": kernels,
@@ -471,6 +525,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true")
+    ap.add_argument("--shape", type=int, nargs=3, default=[N_GRID] * 3,
+                    help="grid of the solve (smaller cases are for profiling, not bench lines)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

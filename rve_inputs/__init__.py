@@ -34,6 +34,8 @@ __all__ = [
     "shear_macro",
     "small_strain_config",
     "neo_hookean_config",
+    "simp_density",
+    "simp_config",
 ]
 
 
@@ -65,30 +67,33 @@ def centered_sphere(n: tuple[int, int, int], radius_frac: float = 0.25,
     return (d2 <= r * r).astype(np.uint8)
 
 
-def random_spheres(n: int, seed: int, r_min: float = 4.0, r_max: float = 10.0,
+def random_spheres(n, seed: int, r_min: float = 4.0, r_max: float = 10.0,
                    target_fraction: float = 0.30, max_attempts: int = 200000) -> np.ndarray:
-    """Random sequential addition of non-overlapping spheres on an n^3 grid.
+    """Random sequential addition of non-overlapping spheres on a periodic grid.
 
-    Radii are drawn uniformly in [r_min, r_max] voxels and centres uniformly in
-    the periodic box; a candidate is rejected when its periodic centre
-    distance to any accepted sphere is below the sum of the radii. Spheres are
-    added until the voxelised inclusion fraction first reaches
+    ``n`` is an int (an n^3 cube) or a shape (nx, ny, nz), in voxels of unit
+    size. Radii are drawn uniformly in [r_min, r_max] voxels and centres
+    uniformly in the periodic box; a candidate is rejected when its periodic
+    centre distance to any accepted sphere is below the sum of the radii.
+    Spheres are added until the voxelised inclusion fraction first reaches
     ``target_fraction``. Returns a uint8 phase map (1 = inclusion).
     """
+    shape = (n, n, n) if np.isscalar(n) else tuple(int(v) for v in n)
+    box = np.asarray(shape, dtype=np.float64)
     rng = np.random.default_rng(seed)
-    phase = np.zeros((n, n, n), dtype=np.uint8)
+    phase = np.zeros(shape, dtype=np.uint8)
     centres: list[np.ndarray] = []
     radii: list[float] = []
     filled = 0
-    target = target_fraction * n ** 3
+    target = target_fraction * phase.size
     for _ in range(max_attempts):
         if filled >= target:
             break
         r = rng.uniform(r_min, r_max)
-        c = rng.uniform(0.0, n, size=3)
+        c = rng.uniform(0.0, 1.0, size=3) * box
         if centres:
             d = np.asarray(centres) - c
-            d -= n * np.round(d / n)
+            d -= box * np.round(d / box)
             if np.any(np.sqrt((d * d).sum(axis=1)) < np.asarray(radii) + r):
                 continue
         centres.append(c)
@@ -102,10 +107,15 @@ def random_spheres(n: int, seed: int, r_min: float = 4.0, r_max: float = 10.0,
         dy = iy + 0.5 - c[1]
         dz = iz + 0.5 - c[2]
         inside = (dx[:, None, None] ** 2 + dy[None, :, None] ** 2 + dz[None, None, :] ** 2) <= r * r
-        sub = phase[np.ix_(ix % n, iy % n, iz % n)]
-        filled += int(np.count_nonzero(inside & (sub == 0)))
+        sel = np.ix_(ix % shape[0], iy % shape[1], iz % shape[2])
+        sub = phase[sel]
+        # a sphere wider than a short axis may wrap onto itself: count each voxel once
+        keys = (ix % shape[0])[:, None, None] * (shape[1] * shape[2]) + \
+               (iy % shape[1])[None, :, None] * shape[2] + (iz % shape[2])[None, None, :]
+        new_vox = np.unique(keys[inside & (sub == 0)])
+        filled += int(new_vox.size)
         sub[inside] = 1
-        phase[np.ix_(ix % n, iy % n, iz % n)] = sub
+        phase[sel] = np.maximum(phase[sel], sub)
     else:
         raise RuntimeError("random_spheres: target fraction not reached")
     return phase
@@ -163,8 +173,10 @@ def small_strain_config(n: int = 16):
     return phase, params, shear_macro(0.01, finite=False)
 
 
-def neo_hookean_config(n: int = 128, seed: int = 0):
-    """Random-sphere neo-Hookean cube: matrix mu=1, lambda=1.5, inclusions 10x.
+def neo_hookean_config(n=128, seed: int = 0):
+    """Random-sphere neo-Hookean cell: matrix mu=1, lambda=1.5, inclusions 10x.
+
+    ``n`` is the cube edge in voxels or a shape (nx, ny, nz).
 
     Spheres of radius U[4, 10] voxels fill a volume fraction of 0.3. The
     macroscopic deformation gradient is I + 0.05 e_x (x) e_y.
@@ -173,3 +185,33 @@ def neo_hookean_config(n: int = 128, seed: int = 0):
     phase = random_spheres(n, seed)
     params = two_phase_table(1.5, 1.0, 10.0)
     return phase, params, shear_macro(0.05, finite=True)
+
+
+def simp_density(n, seed: int, sigma: float = 2.0, rho_min: float = 0.01) -> np.ndarray:
+    """Smoothed seeded noise rescaled to [rho_min, 1] (a SIMP density field).
+
+    Uniform noise on an n^3 (or (nx, ny, nz)) grid is smoothed by a periodic
+    Gaussian filter of standard deviation ``sigma`` voxels and min-max
+    rescaled to [rho_min, 1].
+    """
+    from scipy.ndimage import gaussian_filter
+
+    shape = (n, n, n) if np.isscalar(n) else tuple(int(v) for v in n)
+    rng = np.random.default_rng(seed)
+    t = gaussian_filter(rng.uniform(size=shape), sigma=sigma, mode="wrap")
+    t = (t - t.min()) / (t.max() - t.min())
+    return rho_min + (1.0 - rho_min) * t
+
+
+def simp_config(n: int = 64, seed: int = 0, penalty: float = 3.0, nu: float = 0.3):
+    """SIMP cell: one phase with E = 1, nu = 0.3, scaled per voxel by rho^penalty.
+
+    Returns (phase, params, rho, scale, dscale) with scale = rho^p and
+    dscale = p rho^(p-1) (the derivative of the modulus scale).
+    """
+    rho = simp_density(n, seed)
+    lam = nu / ((1 + nu) * (1 - 2 * nu))
+    mu = 1.0 / (2 * (1 + nu))
+    phase = np.zeros(rho.shape, dtype=np.uint8)
+    params = np.array([[lam, mu]], dtype=np.float64)
+    return phase, params, rho, rho ** penalty, penalty * rho ** (penalty - 1)
