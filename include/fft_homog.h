@@ -194,6 +194,29 @@ FH_API int fh_profile_enable(fh_ctx* ctx, int enable);
  * disabled). Waits for the context's stream. Either array may be NULL. */
 FH_API int fh_profile_read(fh_ctx* ctx, long long counts[FH_PROF_NCLASS], double ms[FH_PROF_NCLASS]);
 
+/* ---- projection without device allocation ----
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory, such as a plug-in inside an application that
+ * owns the GPU's memory, or a loop that must not allocate once it runs. It
+ * computes exactly what fh_project computes (out = scale * G(A)), with the
+ * same kernels, but needs no fh_ctx: its scratch is a static device array of
+ * 9 * 32768 complex doubles (4.5 MiB) plus 8 KiB of twiddle tables, which
+ * every GPU that loads this library holds until the process exits.
+ *   A_dev, out_dev  device [9][nx][ny][nz] fields (out may equal A)
+ *   nx, ny, nz      powers of two as for fh_create, nx*ny*nz <= 32768;
+ *                   larger grids return FH_ERR_ARG (use fh_project)
+ *   lengths         box side lengths, or NULL for the unit box
+ *   cuda_stream     stream to run on (NULL = legacy default stream)
+ * The first call on a device (with that device current) resolves the static
+ * arrays' device addresses and uploads the twiddle tables; make that first
+ * call before any stream capture. Every call on a device shares the one
+ * array and leaves its contents behind; no value carries over from one call
+ * to the next (each call overwrites all scratch it reads), but calls whose
+ * work overlaps on the GPU (for example on two streams) race on the array and
+ * must be serialised by the caller. Returns when the work has finished. */
+FH_API int fh_project_static(const double* A_dev, double* out_dev, int nx, int ny, int nz, double scale,
+                             const double lengths[3], void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

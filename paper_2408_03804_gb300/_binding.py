@@ -39,7 +39,7 @@ _ERR_NAMES = {1: "FH_ERR_ARG", 2: "FH_ERR_CUDA", 3: "FH_ERR_NOT_CONVERGED", 4: "
 
 # every symbol include/fft_homog.h declares
 EXPORTS = ["fh_default_options", "fh_create", "fh_destroy", "fh_last_error_string", "fh_constitutive",
-           "fh_project", "fh_matvec", "fft_homog_solve", "fh_profile_enable", "fh_profile_read"]
+           "fh_project", "fh_matvec", "fft_homog_solve", "fh_profile_enable", "fh_profile_read", "fh_project_static"]
 
 PROF_NCLASS = 12
 PROF_CLASSES = ["fwd_z", "fwd_y", "x_ghat", "inv_y", "inv_z", "constitutive", "jvp", "cg_scalar", "cg_update",
@@ -106,6 +106,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.fh_profile_enable.restype = c_int
     lib.fh_profile_read.argtypes = [c_void_p, POINTER(ctypes.c_longlong), POINTER(c_double)]
     lib.fh_profile_read.restype = c_int
+    lib.fh_project_static.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_double, POINTER(c_double),
+                                      c_void_p]
+    lib.fh_project_static.restype = c_int
     _lib = lib
     return lib
 
@@ -142,6 +145,21 @@ def default_options(**kw) -> FhOptions:
         else:
             setattr(o, k, v)
     return o
+
+
+def fh_project_static(A, out, scale: float = 1.0, lengths=None, stream=None):
+    """out = scale * G(A) without any device allocation (no fh_ctx needed).
+
+    For callers that may not allocate GPU memory; the grid must have at most
+    32768 voxels. A and out are contiguous CUDA float64 tensors (9, nx, ny, nz).
+    """
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    nx, ny, nz = A.shape[1:]
+    La = _dvec(lengths, 3) if lengths is not None else (None, None)
+    return _check(load().fh_project_static(_ptr(A), _ptr(out), nx, ny, nz, float(scale), La[1], c_void_p(stream)))
 
 
 class Material:

@@ -229,6 +229,11 @@ void fh_default_options(fh_options* o) {
 
 const char* fh_last_error_string(void) { return g_err; }
 
+// error text of entry points defined in other translation units (not exported)
+void fh_internal_set_error(const char* msg) {
+  snprintf(g_err, sizeof(g_err), "%s", msg ? msg : "");
+}
+
 int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
   g_err[0] = 0;
   if (!out) return fail(FH_ERR_ARG, "out is NULL");

@@ -1,0 +1,163 @@
+// fh_project_static: the compatibility projection of fh_project without any
+// device allocation.
+//
+// Some callers cannot allocate device memory: a plug-in hosted by another
+// application that owns the GPU's memory budget, or a loop that by policy
+// must not allocate after start-up (allocation can block, fragment a pool or
+// fail late). They cannot create an fh_ctx, whose scratch comes from
+// cudaMalloc. This entry point runs the same five projection kernels, but its
+// only scratch (the half spectrum, plus the twiddle tables) lives in the
+// file-scope arrays below, which every GPU that loads this library holds until
+// the process exits.
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+#include "fh_kernels.h"
+
+namespace fh {
+
+// largest grid the static scratch can serve: nx * ny * nz <= kStaticMaxVoxels
+constexpr long long kStaticMaxVoxels = 32768;
+// 9 half spectra of nx * ny * (nz/2 + 1) <= N complex entries each: 4.5 MiB
+constexpr long long kStaticSpectrum = 9 * kStaticMaxVoxels;
+
+static __device__ __align__(256) double2 g_static_spectrum[kStaticSpectrum];
+static __device__ __align__(256) double2 g_static_twiddles[kTwiddleTotal];
+
+namespace {
+
+struct StaticSlot {
+  bool ready = false;
+  double2* spectrum = nullptr;  // device address of g_static_spectrum on this device
+  double2* twiddles = nullptr;  // device address of g_static_twiddles on this device
+};
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+StaticSlot g_static_slots[kMaxDevices];
+
+void fill_twiddles(std::vector<double2>& t) {
+  t.assign(kTwiddleTotal, make_double2(0.0, 0.0));
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  for (int L = 1; L <= kMaxN; L *= 2) {
+    for (int m = 0; m < L; ++m) {
+      double c, s;
+      if ((4 * m) % L == 0) {
+        const int q = (4 * m) / L;
+        c = (q == 0) ? 1.0 : (q == 2) ? -1.0 : 0.0;
+        s = (q == 1) ? -1.0 : (q == 3) ? 1.0 : 0.0;
+      } else {
+        const long double a = two_pi * (long double)m / (long double)L;
+        c = (double)cosl(a);
+        s = (double)-sinl(a);
+      }
+      t[twiddle_offset(L) + m] = make_double2(c, s);
+    }
+  }
+}
+
+// One-time set-up of the calling thread's current device: resolve the device
+// addresses of the static arrays and write the twiddle tables into them.
+int static_setup(int dev, StaticSlot** out, char* msg, size_t len) {
+  if (dev < 0 || dev >= kMaxDevices) {
+    snprintf(msg, len, "fh_project_static: device %d outside 0..%d", dev, kMaxDevices - 1);
+    return FH_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  StaticSlot& s = g_static_slots[dev];
+  if (!s.ready) {
+    cudaError_t e = cudaGetSymbolAddress((void**)&s.spectrum, g_static_spectrum);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&s.twiddles, g_static_twiddles);
+    if (e != cudaSuccess) {
+      snprintf(msg, len, "fh_project_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return FH_ERR_CUDA;
+    }
+    std::vector<double2> tw;
+    fill_twiddles(tw);
+    e = cudaMemcpyToSymbol(g_static_twiddles, tw.data(), kTwiddleTotal * sizeof(double2));
+    if (e != cudaSuccess) {
+      snprintf(msg, len, "fh_project_static: twiddle upload failed: %s", cudaGetErrorString(e));
+      return FH_ERR_CUDA;
+    }
+    s.ready = true;
+  }
+  *out = &s;
+  return FH_OK;
+}
+
+bool is_pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+}  // namespace
+}  // namespace fh
+
+extern "C" void fh_internal_set_error(const char* msg);
+
+extern "C" int fh_project_static(const double* A_dev, double* out_dev, int nx, int ny, int nz, double scale,
+                                 const double lengths[3], void* cuda_stream) {
+  using namespace fh;
+  char msg[256];
+  auto fail = [&](int code) {
+    fh_internal_set_error(msg);
+    return code;
+  };
+  msg[0] = 0;
+  fh_internal_set_error("");
+  if (!A_dev || !out_dev) {
+    snprintf(msg, sizeof msg, "fh_project_static: NULL field pointer");
+    return fail(FH_ERR_ARG);
+  }
+  if (!is_pow2_in(nx, 1, kMaxN) || !is_pow2_in(ny, 1, kMaxN) || !is_pow2_in(nz, 2, kMaxN)) {
+    snprintf(msg, sizeof msg, "fh_project_static: grid %dx%dx%d: extents must be powers of two, nx,ny in [1,256], "
+             "nz in [2,256]", nx, ny, nz);
+    return fail(FH_ERR_ARG);
+  }
+  const long long n = (long long)nx * ny * nz;
+  if (n > kStaticMaxVoxels) {
+    snprintf(msg, sizeof msg, "fh_project_static: grid %dx%dx%d has %lld voxels, above the static scratch limit of "
+             "%lld voxels; use fh_project", nx, ny, nz, n, kStaticMaxVoxels);
+    return fail(FH_ERR_ARG);
+  }
+  if (lengths && !(lengths[0] > 0 && lengths[1] > 0 && lengths[2] > 0 && std::isfinite(lengths[0]) &&
+                   std::isfinite(lengths[1]) && std::isfinite(lengths[2]))) {
+    snprintf(msg, sizeof msg, "fh_project_static: box lengths must be positive");
+    return fail(FH_ERR_ARG);
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    snprintf(msg, sizeof msg, "fh_project_static: cudaGetDevice: %s", cudaGetErrorString(e));
+    return fail(FH_ERR_CUDA);
+  }
+  StaticSlot* slot = nullptr;
+  int rc = static_setup(dev, &slot, msg, sizeof msg);
+  if (rc) return fail(rc);
+
+  Grid g{};
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.nzh = nz / 2 + 1;
+  g.n = n;
+  g.nspec = (long long)nx * ny * g.nzh;
+  g.sx = lengths ? 1.0 / lengths[0] : 1.0;
+  g.sy = lengths ? 1.0 / lengths[1] : 1.0;
+  g.sz = lengths ? 1.0 / lengths[2] : 1.0;
+  const Tiling t = choose_tiling(g);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const double c = scale / (2.0 * (double)n);
+  if ((e = setup_fft_kernels(g, t)) != cudaSuccess ||
+      (e = launch_fwd_z(g, t, kZDirect, A_dev, nullptr, nullptr, nullptr, slot->spectrum, slot->twiddles, s)) !=
+          cudaSuccess ||
+      (e = launch_fwd_y(g, t, slot->spectrum, slot->twiddles, nullptr, s)) != cudaSuccess ||
+      (e = launch_x_ghat(g, t, slot->spectrum, slot->twiddles, c, nullptr, s)) != cudaSuccess ||
+      (e = launch_inv_y(g, t, slot->spectrum, slot->twiddles, nullptr, s)) != cudaSuccess ||
+      (e = launch_inv_z(g, t, kIZOut, slot->spectrum, out_dev, nullptr, nullptr, slot->twiddles, nullptr, s)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    snprintf(msg, sizeof msg, "fh_project_static: %s", cudaGetErrorString(e));
+    return fail(FH_ERR_CUDA);
+  }
+  return FH_OK;
+}
