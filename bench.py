@@ -411,6 +411,19 @@ def run_ours(args, world, rank, local):
     def step():
         return ctx.fft_homog_solve(mat, Fbar, F, n_increments=N_INC, options=opts)
 
+    if args.probe_newton:
+        # one Newton iteration of the first increment with 16 CG products: every
+        # kernel of the solve in its bench launch configuration, few launches
+        probe = fh.default_options(newton_tol=NEWTON_TOL, max_newton=1, max_cg=16)
+        for _ in range(2):
+            ctx.fft_homog_solve(mat, Fbar, F, n_increments=N_INC, options=probe,
+                                allow=(fh.FH_ERR_NOT_CONVERGED,))
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"probe_newton": "ok", "shape": list(shape)}), flush=True)
+        ctx.close()
+        return
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -526,6 +539,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--probe-newton", action="store_true",
+                    help="run one Newton iteration with 16 CG products (for ncu launch lists) and exit")
     ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--shape", type=int, nargs=3, default=[N_GRID] * 3,
                     help="grid of the solve (smaller cases are for profiling, not bench lines)")

@@ -90,6 +90,8 @@ typedef struct fh_material {
   int n_phase;                  /* rows of params, 1..256 */
   const unsigned char* phase;   /* device uint8[N], every value < n_phase */
   const double* params;         /* host double[n_phase][2] = (lambda, mu) */
+  const double* scale;          /* device double[N] multiplying both Lame parameters of each voxel
+                                   (a modulus field such as E = rho^p at fixed Poisson ratio), or NULL */
 } fh_material;
 
 typedef struct fh_options {
@@ -176,13 +178,39 @@ FH_API int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fba
                     int n_increments, const fh_options* opt, double* F_dev,
                     double Pbar_out[9], fh_stats* stats);
 
+/* Homogenized tangent Cbar = dPbar/dFbar at a converged state (Section 3.3,
+ * Eq. 4; the forward derivative of Listing 5's solve_microscale). For each of
+ * the nine unit macroscopic entries E_cd one conjugate-gradient solve gives
+ * the fluctuation d with G(K : (E_cd + d)) = 0, and column cd of Cbar is
+ * mean(K : (E_cd + d)), with K evaluated by AD at F_dev.
+ *   F_dev      in   [9][N] converged field (H for small strain)
+ *   opt        CG tolerance (cg_tol, or 1e-2 newton_tol), max_cg, lengths; NULL = defaults
+ *   Cbar_out   out  host double[81], Cbar[9*ab + cd] = dPbar_ab / dFbar_cd
+ * Returns FH_ERR_NOT_CONVERGED if a CG solve hits max_cg. */
+FH_API int fft_homog_tangent(fh_ctx* ctx, const fh_material* mat, const double* F_dev,
+                             const fh_options* opt, double Cbar_out[81]);
+
+/* Sensitivity of one homogenized modulus to a voxel density field
+ * (Section 4.4.2's topology-optimisation gradient), for small-strain linear
+ * elasticity with per-voxel moduli s(rho_v) * C0(phase_v) (mat->scale holds
+ * s). Because the cell problem is self-adjoint, no adjoint solve is needed:
+ *   dCbar_ab,cd / d rho_v = (1/N) (E_ab + d_ab)_v : C0_v : (E_cd + d_cd)_v * ds/drho_v
+ * with d_ab, d_cd the unit responses of fft_homog_tangent (one CG solve, two
+ * when ab != cd). ab = 3*i + j, cd = 3*k + l.
+ *   dscale_dev  in   device double[N], ds/drho per voxel
+ *   out_dev     out  device double[N], the sensitivity per voxel
+ * Returns FH_ERR_UNSUPPORTED for finite-strain laws. */
+FH_API int fft_homog_sensitivity(fh_ctx* ctx, const fh_material* mat, const fh_options* opt, int i, int j,
+                                 int k, int l, const double* dscale_dev, double* out_dev);
+
 /* ---- launch accounting and per-kernel device time ----
  * Kernel classes, in slot order: 0 forward z pass (stress/tangent apply +
  * real-to-complex), 1 forward y pass, 2 x pass with Ghat, 3 inverse y pass,
  * 4 inverse z pass (complex-to-real + dot), 5 constitutive AD, 6 jvp tangent
  * apply, 7 CG scalar kernels, 8 CG vector update, 9 Newton update,
- * 10 fills and field sums, 11 partial-sum reductions. */
-#define FH_PROF_NCLASS 12
+ * 10 fills and field sums, 11 partial-sum reductions, 12 tangent/sensitivity
+ * contractions. */
+#define FH_PROF_NCLASS 13
 
 /* Reset the context's launch counters and, with enable != 0, bracket every
  * later launch with a pair of CUDA events on the context's stream (adds one

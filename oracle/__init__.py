@@ -17,10 +17,11 @@ materials  closed-form energies, stresses and tangents (Eqs. 2-3)
 solver     Newton-Krylov solve with a conjugate-gradient inner loop (Alg. 1)
 laminate   exact laminate solutions (an independent pin of the solver)
 brute      dense energy minimisation on tiny grids (an independent pin)
+homogenize homogenized tangent (Eq. 4) and modulus sensitivities (Section 4.4.2)
 
 Readings of the paper taken here where it is silent or garbled are listed in
 each function's docstring; every function is pinned by a ``-m "not gpu"``
 test against something other than itself.
 """
 
-from . import spectral, materials, solver, laminate, brute  # noqa: F401
+from . import spectral, materials, solver, laminate, brute, homogenize  # noqa: F401

@@ -87,6 +87,16 @@ def cg(matvec, b: np.ndarray, tol: float, max_iter: int):
         p = r + beta * p
 
 
+def voxel_lame(phase, params, scale=None):
+    """Per-voxel (lambda, mu): the phase's row of params, times scale if given."""
+    lam = params[phase, 0]
+    mu = params[phase, 1]
+    if scale is not None:
+        lam = lam * scale
+        mu = mu * scale
+    return lam, mu
+
+
 def reference_tensor(kind: int) -> np.ndarray:
     """Start tensor of a cold solve: I for finite strain, 0 for small strain."""
     return np.eye(3).reshape(9) if mat.FINITE_STRAIN[kind] else np.zeros(9)
@@ -95,16 +105,17 @@ def reference_tensor(kind: int) -> np.ndarray:
 def solve(phase: np.ndarray, params: np.ndarray, kind: int, Fbar, n_increments: int = 1,
           newton_tol: float = 1e-10, cg_tol: float | None = None, max_newton: int = 50,
           max_cg: int = 5000, F_init: np.ndarray | None = None, lengths=(1.0, 1.0, 1.0),
-          raise_on_failure: bool = True) -> Result:
+          raise_on_failure: bool = True, scale: np.ndarray | None = None) -> Result:
     """Solve the periodic cell under the macroscopic tensor ``Fbar`` (Alg. 1).
 
     phase: uint8 (nx, ny, nz); params: (n_phase, 2) Lame pairs (lambda, mu);
-    Fbar: 9 entries (row-major); F_init: optional start field (9, nx, ny, nz).
+    Fbar: 9 entries (row-major); F_init: optional start field (9, nx, ny, nz);
+    scale: optional per-voxel multiplier of both Lame parameters (a modulus
+    field such as E = rho^3 at fixed Poisson ratio).
     """
     shape = phase.shape
     nvox = phase.size
-    lam = params[phase, 0]
-    mu = params[phase, 1]
+    lam, mu = voxel_lame(phase, params, scale)
     Fbar = np.asarray(Fbar, dtype=np.float64).reshape(9)
     if cg_tol is None:
         cg_tol = 1e-2 * newton_tol

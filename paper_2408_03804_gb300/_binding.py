@@ -39,11 +39,11 @@ _ERR_NAMES = {1: "FH_ERR_ARG", 2: "FH_ERR_CUDA", 3: "FH_ERR_NOT_CONVERGED", 4: "
 
 # every symbol include/fft_homog.h declares
 EXPORTS = ["fh_default_options", "fh_create", "fh_destroy", "fh_last_error_string", "fh_constitutive",
-           "fh_project", "fh_matvec", "fft_homog_solve", "fh_profile_enable", "fh_profile_read", "fh_project_static"]
+           "fh_project", "fh_matvec", "fft_homog_solve", "fh_profile_enable", "fh_profile_read", "fh_project_static", "fft_homog_tangent", "fft_homog_sensitivity"]
 
-PROF_NCLASS = 12
+PROF_NCLASS = 13
 PROF_CLASSES = ["fwd_z", "fwd_y", "x_ghat", "inv_y", "inv_z", "constitutive", "jvp", "cg_scalar", "cg_update",
-                "newton_update", "fill", "reduce"]
+                "newton_update", "fill", "reduce", "contract"]
 
 
 class FhError(RuntimeError):
@@ -53,7 +53,8 @@ class FhError(RuntimeError):
 
 
 class FhMaterial(ctypes.Structure):
-    _fields_ = [("kind", c_int), ("n_phase", c_int), ("phase", c_void_p), ("params", POINTER(c_double))]
+    _fields_ = [("kind", c_int), ("n_phase", c_int), ("phase", c_void_p), ("params", POINTER(c_double)),
+                ("scale", c_void_p)]
 
 
 class FhOptions(ctypes.Structure):
@@ -109,6 +110,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.fh_project_static.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_double, POINTER(c_double),
                                       c_void_p]
     lib.fh_project_static.restype = c_int
+    lib.fft_homog_tangent.argtypes = [c_void_p, POINTER(FhMaterial), c_void_p, POINTER(FhOptions),
+                                      POINTER(c_double)]
+    lib.fft_homog_tangent.restype = c_int
+    lib.fft_homog_sensitivity.argtypes = [c_void_p, POINTER(FhMaterial), POINTER(FhOptions), c_int, c_int, c_int,
+                                          c_int, c_void_p, c_void_p]
+    lib.fft_homog_sensitivity.restype = c_int
     _lib = lib
     return lib
 
@@ -165,7 +172,7 @@ def fh_project_static(A, out, scale: float = 1.0, lengths=None, stream=None):
 class Material:
     """A material description: kind, device phase map and host parameter table."""
 
-    def __init__(self, kind: int, phase, params):
+    def __init__(self, kind: int, phase, params, scale=None):
         import torch
 
         self.kind = int(kind)
@@ -175,8 +182,14 @@ class Material:
         self.params, _ = _dvec(params)
         if self.params.size % 2:
             raise ValueError("params must hold (lambda, mu) pairs")
+        self.scale = None
+        if scale is not None:
+            if not isinstance(scale, torch.Tensor):
+                scale = torch.as_tensor(np.ascontiguousarray(scale, dtype=np.float64))
+            self.scale = scale.to(device="cuda", dtype=torch.float64).contiguous()
         self._c = FhMaterial(self.kind, self.params.size // 2, self.phase.data_ptr(),
-                             self.params.ctypes.data_as(POINTER(c_double)))
+                             self.params.ctypes.data_as(POINTER(c_double)),
+                             self.scale.data_ptr() if self.scale is not None else None)
 
     @property
     def c(self):
@@ -241,6 +254,20 @@ class Context:
         ms = (c_double * PROF_NCLASS)()
         _check(load().fh_profile_read(self._h, counts, ms))
         return {PROF_CLASSES[i]: (int(counts[i]), float(ms[i])) for i in range(PROF_NCLASS)}
+
+    def fft_homog_tangent(self, mat: Material, F, options: FhOptions | None = None):
+        """Homogenized tangent as a 9x9 array, C[ab, cd] = dPbar_ab / dFbar_cd."""
+        C = np.zeros(81)
+        _check(load().fft_homog_tangent(self._h, mat.c, _ptr(F),
+                                        ctypes.byref(options) if options is not None else None,
+                                        C.ctypes.data_as(POINTER(c_double))))
+        return C.reshape(9, 9)
+
+    def fft_homog_sensitivity(self, mat: Material, ijkl, dscale, out, options: FhOptions | None = None):
+        """dCbar_ijkl / d rho per voxel into out (CUDA float64 tensor of the grid shape)."""
+        i, j, k, l = (int(v) for v in ijkl)
+        _check(load().fft_homog_sensitivity(self._h, mat.c, ctypes.byref(options) if options is not None else None,
+                                            i, j, k, l, _ptr(dscale), _ptr(out)))
 
     def fft_homog_solve(self, mat: Material, Fbar, F, n_increments: int = 1, options: FhOptions | None = None,
                         capacity: int = 512, allow=()):

@@ -91,7 +91,8 @@ struct fh_ctx {
 namespace {
 
 enum ProfClass : int {
-  kPFwdZ = 0, kPFwdY, kPXGhat, kPInvY, kPInvZ, kPConst, kPJvp, kPCgScalar, kPCgUpdate, kPNewton, kPFill, kPReduce
+  kPFwdZ = 0, kPFwdY, kPXGhat, kPInvY, kPInvZ, kPConst, kPJvp, kPCgScalar, kPCgUpdate, kPNewton, kPFill, kPReduce,
+  kPContract
 };
 
 cudaEvent_t ev_get(fh_ctx* c) {
@@ -179,6 +180,7 @@ int upload_material(fh_ctx* ctx, const fh_material* m, MatView* mv) {
   mv->kind = m->kind;
   mv->phase = m->phase;
   mv->params = ctx->params;
+  mv->scale = m->scale;
   return FH_OK;
 }
 
@@ -193,6 +195,46 @@ int run_projection(fh_ctx* ctx, const Grid& g, int zmode, const double* src, dou
   FH_CUDA(prof(ctx, kPInvY, [&] { return launch_inv_y(g, t, ctx->S, ctx->tw, cg, s); }));
   FH_CUDA(prof(ctx, kPInvZ, [&] { return launch_inv_z(g, t, izmode, ctx->S, out, pdot, ctx->partials, ctx->tw, cg, s); }));
   return FH_OK;
+}
+
+// Conjugate gradients on G(K : d) = b (Alg. 1 inner solve). On entry ctx->r
+// holds b and ctx->partials the per-CTA sums of b . b from the inverse z pass
+// that produced it; on return ctx->x holds d and *host_cg the final scalars.
+int run_cg(fh_ctx* ctx, const Grid& g, const MatView& mv, const double* F_dev, bool stored, double cg_tol,
+           int max_cg, int check_every, CgScalars* host_cg) {
+  cudaStream_t s = ctx->stream;
+  CgScalars* cg = &ctx->sc->cg;
+  const int n_iz = (int)z_pass_ctas(g, ctx->tiling);
+  const int n_upd = (int)cg_update_ctas(g);
+  const double c_mv = 1.0 / (2.0 * (double)g.n);
+  FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_init(cg, ctx->partials, n_iz, cg_tol, max_cg, s); }));
+  FH_CUDA(cudaMemsetAsync(ctx->x, 0, (size_t)9 * g.n * sizeof(double), s));
+  int launched = 0;
+  int rc;
+  while (true) {
+    for (int k = 0; k < check_every; ++k, ++launched) {
+      const int zmode = launched == 0 ? kZCgFirst : kZCg;
+      if (stored) {
+        if ((rc = run_projection(ctx, g, zmode, ctx->r, ctx->p, ctx->K, c_mv, kIZDot, ctx->y, ctx->p, cg))) return rc;
+      } else {
+        FH_CUDA(prof(ctx, kPJvp, [&] {
+          return launch_jvp(g, mv, F_dev, ctx->r, ctx->p, ctx->P, zmode, cg, &ctx->sc->flags, s);
+        }));
+        if ((rc = run_projection(ctx, g, kZDirect, ctx->P, nullptr, nullptr, c_mv, kIZDot, ctx->y, ctx->p, cg)))
+          return rc;
+      }
+      FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_alpha(cg, ctx->partials, n_iz, s); }));
+      FH_CUDA(prof(ctx, kPCgUpdate, [&] {
+        return launch_cg_update(g, cg, ctx->x, ctx->r, ctx->p, ctx->y, ctx->partials, 0, s);
+      }));
+      FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_beta(cg, ctx->partials, n_upd, s); }));
+    }
+    FH_CUDA(cudaMemcpyAsync(host_cg, cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    FH_CUDA(cudaStreamSynchronize(s));
+    prof_flush(ctx);
+    if (host_cg->done) return FH_OK;
+    if (launched > max_cg + 2 * check_every) return fail(FH_ERR_CUDA, "CG loop did not report completion");
+  }
 }
 
 int read_flags(fh_ctx* ctx, int* flags) {
@@ -398,7 +440,6 @@ int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9], i
   MatView mv;
   if ((rc = upload_material(ctx, mat, &mv))) return rc;
   FH_CUDA(cudaMemsetAsync(&ctx->sc->flags, 0, sizeof(int), s));
-  CgScalars* cg = &ctx->sc->cg;
   const bool stored = opt.tangent_mode == FH_TANGENT_STORED;
 
   // start tensor and load step (a1)
@@ -414,10 +455,8 @@ int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9], i
   double dFbar[9];
   for (int c = 0; c < 9; ++c) dFbar[c] = (Fbar[c] - start[c]) / n_increments;
 
-  const int n_iz = (int)z_pass_ctas(g, ctx->tiling);
-  const int n_upd = (int)cg_update_ctas(g);
   const int n_nu = (int)newton_update_ctas(g);
-  const double c_rhs = -1.0 / (2.0 * N), c_mv = 1.0 / (2.0 * N);
+  const double c_rhs = -1.0 / (2.0 * N);
   int n_newton = 0, n_cg = 0, status = FH_OK;
 
   for (int inc = 1; inc <= n_increments && status == FH_OK; ++inc) {
@@ -444,33 +483,9 @@ int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9], i
       if ((rc = run_projection(ctx, g, kZDirect, ctx->P, nullptr, nullptr, c_rhs, kIZRhs, ctx->r, nullptr,
                                nullptr)))
         return rc;
-      FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_init(cg, ctx->partials, n_iz, cg_tol, opt.max_cg, s); }));
-      FH_CUDA(cudaMemsetAsync(ctx->x, 0, (size_t)9 * g.n * sizeof(double), s));
       // CG on G(K : dF) = b (a4, a5); scalars stay on the device
       CgScalars host_cg{};
-      int launched = 0;
-      while (true) {
-        for (int k = 0; k < opt.check_every; ++k, ++launched) {
-          const int zmode = launched == 0 ? kZCgFirst : kZCg;
-          if (stored) {
-            if ((rc = run_projection(ctx, g, zmode, ctx->r, ctx->p, ctx->K, c_mv, kIZDot, ctx->y, ctx->p, cg)))
-              return rc;
-          } else {
-            FH_CUDA(prof(ctx, kPJvp, [&] { return launch_jvp(g, mv, F_dev, ctx->r, ctx->p, ctx->P, zmode, cg, &ctx->sc->flags, s); }));
-            if ((rc = run_projection(ctx, g, kZDirect, ctx->P, nullptr, nullptr, c_mv, kIZDot, ctx->y, ctx->p, cg)))
-              return rc;
-          }
-          FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_alpha(cg, ctx->partials, n_iz, s); }));
-          FH_CUDA(prof(ctx, kPCgUpdate, [&] { return launch_cg_update(g, cg, ctx->x, ctx->r, ctx->p, ctx->y, ctx->partials, 0, s); }));
-          FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_beta(cg, ctx->partials, n_upd, s); }));
-        }
-        FH_CUDA(cudaMemcpyAsync(&host_cg, cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
-        FH_CUDA(cudaStreamSynchronize(s));
-        prof_flush(ctx);
-        if (host_cg.done) break;
-        if (launched > opt.max_cg + 2 * opt.check_every)
-          return fail(FH_ERR_CUDA, "CG loop did not report completion");
-      }
+      if ((rc = run_cg(ctx, g, mv, F_dev, stored, cg_tol, opt.max_cg, opt.check_every, &host_cg))) return rc;
       // Newton update and convergence test (a6)
       FH_CUDA(prof(ctx, kPNewton, [&] { return launch_newton_update(g, F_dev, ctx->x, ctx->partials, s); }));
       FH_CUDA(prof(ctx, kPReduce, [&] { return launch_sum_partials(ctx->partials, n_nu, 1, ctx->sc->sums, s); }));
@@ -517,6 +532,113 @@ int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9], i
     stats->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return status;
+}
+
+namespace {
+
+int options_or_default(const fh_options* in, fh_options* o) {
+  if (in) *o = *in;
+  else fh_default_options(o);
+  if (!(o->newton_tol > 0.0) || o->max_cg < 0 || o->check_every < 1) return fail(FH_ERR_ARG, "invalid options");
+  if (!lengths_ok(o->lengths)) return fail(FH_ERR_ARG, "box lengths must be positive");
+  return FH_OK;
+}
+
+// unit response E_cd + d: b = -G(K : E_cd) into r, then CG; d in ctx->x
+int unit_response(fh_ctx* ctx, const Grid& g, const MatView& mv, int cd, double cg_tol, const fh_options& opt,
+                  CgScalars* host_cg) {
+  double e[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  e[cd] = 1.0;
+  FH_CUDA(prof(ctx, kPFill, [&] { return launch_fill(g, ctx->y, e, 0, ctx->stream); }));
+  int rc = run_projection(ctx, g, kZKApply, ctx->y, nullptr, ctx->K, -1.0 / (2.0 * (double)g.n), kIZRhs, ctx->r,
+                          nullptr, nullptr);
+  if (rc) return rc;
+  if ((rc = run_cg(ctx, g, mv, nullptr, true, cg_tol, opt.max_cg, opt.check_every, host_cg))) return rc;
+  if (host_cg->done != 1)
+    return fail(FH_ERR_NOT_CONVERGED, "tangent CG %s after %d products (column %d)",
+                host_cg->done == 2 ? "hit max_cg" : "broke down", host_cg->it, cd);
+  return FH_OK;
+}
+
+}  // namespace
+
+int fft_homog_tangent(fh_ctx* ctx, const fh_material* mat, const double* F_dev, const fh_options* opt_in,
+                      double Cbar_out[81]) {
+  g_err[0] = 0;
+  if (!ctx || !F_dev || !Cbar_out) return fail(FH_ERR_ARG, "NULL argument");
+  int rc = check_material(mat);
+  if (rc) return rc;
+  fh_options opt;
+  if ((rc = options_or_default(opt_in, &opt))) return rc;
+  const double cg_tol = opt.cg_tol > 0.0 ? opt.cg_tol : 1e-2 * opt.newton_tol;
+  DeviceGuard dg(ctx->dev);
+  cudaStream_t s = ctx->stream;
+  const Grid g = grid_with_lengths(ctx, opt.lengths);
+  MatView mv;
+  if ((rc = upload_material(ctx, mat, &mv))) return rc;
+  FH_CUDA(cudaMemsetAsync(&ctx->sc->flags, 0, sizeof(int), s));
+  FH_CUDA(prof(ctx, kPConst, [&] {
+    return launch_constitutive(g, mv, F_dev, nullptr, ctx->K, ctx->partials, &ctx->sc->flags, s);
+  }));
+  int flags = 0;
+  if ((rc = read_flags(ctx, &flags))) return rc;
+  if (flags & kFlagNonPhysical) return fail(FH_ERR_NONPHYSICAL, "det F <= 0 or non-finite value in some voxel");
+  const int n_k = (int)kapply_sums_ctas(g);
+  for (int cd = 0; cd < 9; ++cd) {
+    CgScalars host_cg{};
+    if ((rc = unit_response(ctx, g, mv, cd, cg_tol, opt, &host_cg))) return rc;
+    FH_CUDA(prof(ctx, kPContract, [&] { return launch_kapply_sums(g, ctx->K, ctx->x, cd, ctx->partials, s); }));
+    double col[9];
+    if ((rc = reduce9(ctx, n_k, col))) return rc;
+    for (int ab = 0; ab < 9; ++ab) Cbar_out[9 * ab + cd] = col[ab] / (double)g.n;
+  }
+  return FH_OK;
+}
+
+int fft_homog_sensitivity(fh_ctx* ctx, const fh_material* mat, const fh_options* opt_in, int i, int j, int k, int l,
+                          const double* dscale_dev, double* out_dev) {
+  g_err[0] = 0;
+  if (!ctx || !dscale_dev || !out_dev) return fail(FH_ERR_ARG, "NULL argument");
+  int rc = check_material(mat);
+  if (rc) return rc;
+  if (mat->kind != FH_LINEAR_ELASTIC)
+    return fail(FH_ERR_UNSUPPORTED, "sensitivities are implemented for small-strain linear elasticity only");
+  if (i < 0 || i > 2 || j < 0 || j > 2 || k < 0 || k > 2 || l < 0 || l > 2)
+    return fail(FH_ERR_ARG, "tensor indices must be 0, 1 or 2");
+  fh_options opt;
+  if ((rc = options_or_default(opt_in, &opt))) return rc;
+  const double cg_tol = opt.cg_tol > 0.0 ? opt.cg_tol : 1e-2 * opt.newton_tol;
+  DeviceGuard dg(ctx->dev);
+  cudaStream_t s = ctx->stream;
+  const Grid g = grid_with_lengths(ctx, opt.lengths);
+  MatView mv;
+  if ((rc = upload_material(ctx, mat, &mv))) return rc;
+  FH_CUDA(cudaMemsetAsync(&ctx->sc->flags, 0, sizeof(int), s));
+  // the linear tangent does not depend on the state: evaluate it at H = 0
+  FH_CUDA(cudaMemsetAsync(ctx->p, 0, (size_t)9 * g.n * sizeof(double), s));
+  FH_CUDA(prof(ctx, kPConst, [&] {
+    return launch_constitutive(g, mv, ctx->p, nullptr, ctx->K, ctx->partials, &ctx->sc->flags, s);
+  }));
+  int flags = 0;
+  if ((rc = read_flags(ctx, &flags))) return rc;
+  if (flags & kFlagNonPhysical) return fail(FH_ERR_NONPHYSICAL, "non-finite modulus in some voxel");
+  const int ab = 3 * i + j, cd = 3 * k + l;
+  CgScalars host_cg{};
+  if ((rc = unit_response(ctx, g, mv, ab, cg_tol, opt, &host_cg))) return rc;
+  const double* xa = ctx->x;
+  if (cd != ab) {
+    FH_CUDA(cudaMemcpyAsync(ctx->P, ctx->x, (size_t)9 * g.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    xa = ctx->P;
+    if ((rc = unit_response(ctx, g, mv, cd, cg_tol, opt, &host_cg))) return rc;
+  }
+  MatView base = mv;
+  base.scale = nullptr;
+  FH_CUDA(prof(ctx, kPContract, [&] {
+    return launch_sensitivity(g, base, xa, ab, ctx->x, cd, dscale_dev, out_dev, s);
+  }));
+  FH_CUDA(cudaStreamSynchronize(s));
+  prof_flush(ctx);
+  return FH_OK;
 }
 
 int fh_profile_enable(fh_ctx* ctx, int enable) {

@@ -60,7 +60,19 @@ struct MatView {
   int kind;
   const uint8_t* phase;      // device
   const double* params;      // device [n_phase][2]
+  const double* scale;       // device [N] modulus multiplier per voxel, or nullptr
 };
+
+__device__ __forceinline__ void voxel_lame(const MatView& m, long long v, double& lam, double& mu) {
+  const int ph = m.phase[v];
+  lam = m.params[2 * ph];
+  mu = m.params[2 * ph + 1];
+  if (m.scale) {
+    const double s = m.scale[v];
+    lam *= s;
+    mu *= s;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // device flags written by kernels, read by the host after a solve step

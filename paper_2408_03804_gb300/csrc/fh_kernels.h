@@ -74,5 +74,10 @@ cudaError_t launch_cg_update(const Grid& g, CgScalars* cg, double* x, double* r,
 cudaError_t launch_cg_beta(CgScalars* cg, const double* partials, int n_parts, cudaStream_t s);
 cudaError_t launch_newton_update(const Grid& g, double* F, const double* dF, double* partials, cudaStream_t s);
 long long newton_update_ctas(const Grid& g);
+long long kapply_sums_ctas(const Grid& g);
+cudaError_t launch_kapply_sums(const Grid& g, const double* K, const double* x, int cd, double* partials,
+                               cudaStream_t s);
+cudaError_t launch_sensitivity(const Grid& g, const MatView& m, const double* xa, int ab, const double* xc, int cd,
+                               const double* dscale, double* out, cudaStream_t s);
 
 }  // namespace fh

@@ -39,8 +39,8 @@ __global__ void __launch_bounds__(kThreads) k_constitutive(Grid g, MatView m, co
     double f[9], pv[9], kv[45];
 #pragma unroll
     for (int c = 0; c < 9; ++c) f[c] = F[c * n + v];
-    const int ph = m.phase[v];
-    const double lam = m.params[2 * ph], mu = m.params[2 * ph + 1];
+    double lam, mu;
+    voxel_lame(m, v, lam, mu);
     const double w = ad::energy_derivatives<Law>(f, lam, mu, pv, kv);
     bool ok = isfinite(w);
 #pragma unroll
@@ -117,8 +117,9 @@ __global__ void __launch_bounds__(kThreads) k_jvp(Grid g, MatView m, const doubl
         p[c * n + v] = pd[c];
       }
     }
-    const int ph = m.phase[v];
-    const double w = ad::energy_derivatives<Law>(f, m.params[2 * ph], m.params[2 * ph + 1], pv, kv);
+    double lam, mu;
+    voxel_lame(m, v, lam, mu);
+    const double w = ad::energy_derivatives<Law>(f, lam, mu, pv, kv);
     bad |= !isfinite(w);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
@@ -341,6 +342,83 @@ long long newton_update_ctas(const Grid& g) { return pointwise_grid(g); }
 
 cudaError_t launch_newton_update(const Grid& g, double* F, const double* dF, double* partials, cudaStream_t s) {
   k_newton_update<<<pointwise_grid(g), kThreads, 0, s>>>(g, F, dF, partials);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// homogenized tangent column: per-CTA sums of K : (E_cd + x) (Eq. 4)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_kapply_sums(Grid g, const double* __restrict__ K,
+                                                         const double* __restrict__ x, int cd,
+                                                         double* __restrict__ partials) {
+  __shared__ double red[32];
+  double sum[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) sum[a] = 0.0;
+  const long long n = g.n;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    double h[9];
+#pragma unroll
+    for (int b = 0; b < 9; ++b) h[b] = x[b * n + v] + (b == cd ? 1.0 : 0.0);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      double acc = 0.0;
+#pragma unroll
+      for (int b = 0; b < 9; ++b) acc = fma(K[sym_slot(a, b) * n + v], h[b], acc);
+      sum[a] += acc;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const double s = block_sum(sum[a], red);
+    if (threadIdx.x == 0) partials[a * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+long long kapply_sums_ctas(const Grid& g) { return pointwise_grid(g); }
+
+cudaError_t launch_kapply_sums(const Grid& g, const double* K, const double* x, int cd, double* partials,
+                               cudaStream_t s) {
+  k_kapply_sums<<<pointwise_grid(g), kThreads, 0, s>>>(g, K, x, cd, partials);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// voxel sensitivity of a homogenized linear modulus (self-adjoint form):
+// out_v = (E_ab + xa)_v : C0_v : (E_cd + xc)_v * dscale_v / N, with C0 the
+// tangent of the unscaled phase parameters, from the same AD as the solve
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_sensitivity(Grid g, MatView m, const double* __restrict__ xa, int ab,
+                                                         const double* __restrict__ xc, int cd,
+                                                         const double* __restrict__ dscale,
+                                                         double* __restrict__ out) {
+  const long long n = g.n;
+  const double inv_n = 1.0 / (double)n;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    double zero[9], pv[9], kv[45], ha[9], hc[9];
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+      zero[b] = 0.0;
+      ha[b] = xa[b * n + v] + (b == ab ? 1.0 : 0.0);
+      hc[b] = xc[b * n + v] + (b == cd ? 1.0 : 0.0);
+    }
+    const int ph = m.phase[v];
+    ad::energy_derivatives<LinearElasticLaw>(zero, m.params[2 * ph], m.params[2 * ph + 1], pv, kv);
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      double t = 0.0;
+#pragma unroll
+      for (int b = 0; b < 9; ++b) t = fma(kv[sym_slot(a, b)], hc[b], t);
+      acc = fma(ha[a], t, acc);
+    }
+    out[v] = acc * dscale[v] * inv_n;
+  }
+}
+
+cudaError_t launch_sensitivity(const Grid& g, const MatView& m, const double* xa, int ab, const double* xc, int cd,
+                               const double* dscale, double* out, cudaStream_t s) {
+  k_sensitivity<<<pointwise_grid(g), kThreads, 0, s>>>(g, m, xa, ab, xc, cd, dscale, out);
   return cudaGetLastError();
 }
 
