@@ -52,8 +52,8 @@ def algorithmic_work(cls: str, nx: int, ny: int, nz: int):
     h = nx * ny * (nz // 2 + 1)
     c16 = 16  # bytes of a complex double
     lg = math.log2
-    if cls == "fwd_z":        # read r, p, K(45); write p; write 9 half spectra
-        return (72 + 72 + 360 + 72) * n + 9 * c16 * h, (162 + 18) * n + 9 * 2.5 * n * lg(nz) + 3 * 2 * h
+    if cls == "fwd_z":        # read r, p, x, K(45); write p, x; write 9 half spectra
+        return (72 + 72 + 72 + 360 + 72 + 72) * n + 9 * c16 * h, (162 + 36) * n + 9 * 2.5 * n * lg(nz) + 3 * 2 * h
     if cls == "fwd_y":        # read 9, write 6 spectral components
         return (9 + 6) * c16 * h, 9 * 5 * h * lg(ny) + 3 * 4 * h
     if cls == "x_ghat":       # read 6, write 6; 12 transforms + Ghat
@@ -62,8 +62,8 @@ def algorithmic_work(cls: str, nx: int, ny: int, nz: int):
         return (6 + 9) * c16 * h, 9 * 5 * h * lg(ny) + 24 * h
     if cls == "inv_z":        # read 9 spectra and p; write y
         return 9 * c16 * h + (72 + 72) * n, 9 * 2.5 * n * lg(nz) + 18 * n
-    if cls == "cg_update":    # read x, r, p, y; write x, r
-        return 6 * 72 * n, 6 * 9 * n
+    if cls == "cg_update":    # read r, y; write r (x += alpha p is done by the next forward z pass)
+        return 3 * 72 * n, 4 * 9 * n
     return None, None
 
 
@@ -79,7 +79,7 @@ def fp64_ops(cls: str, nx: int, ny: int, nz: int):
     m = nz // 2
     r2c = 9 * (FP64_FFT_OPS[m] * m + 12 * (m // 2 + 1)) * nx * ny  # half-length FFT + unpack
     if cls == "fwd_z":
-        return 90 * n + r2c + 3 * 4 * (m // 2 + 1) * nx * ny
+        return 99 * n + r2c + 3 * 4 * (m // 2 + 1) * nx * ny
     if cls == "fwd_y":
         return (9 * FP64_FFT_OPS[ny] + 12) * h
     if cls == "x_ghat":
@@ -89,7 +89,7 @@ def fp64_ops(cls: str, nx: int, ny: int, nz: int):
     if cls == "inv_z":
         return 9 * n + r2c
     if cls == "cg_update":
-        return 27 * n
+        return 18 * n
     return None
 
 

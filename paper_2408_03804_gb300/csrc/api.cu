@@ -186,10 +186,10 @@ int upload_material(fh_ctx* ctx, const fh_material* m, MatView* mv) {
 
 // G applied to src (tau = src, K : src, or the CG direction), result to out
 int run_projection(fh_ctx* ctx, const Grid& g, int zmode, const double* src, double* p, const double* K,
-                   double scale, int izmode, double* out, const double* pdot, CgScalars* cg) {
+                   double scale, int izmode, double* out, const double* pdot, CgScalars* cg, double* x = nullptr) {
   const Tiling& t = ctx->tiling;
   cudaStream_t s = ctx->stream;
-  FH_CUDA(prof(ctx, kPFwdZ, [&] { return launch_fwd_z(g, t, zmode, src, p, K, cg, ctx->S, ctx->tw, s); }));
+  FH_CUDA(prof(ctx, kPFwdZ, [&] { return launch_fwd_z(g, t, zmode, src, p, x, K, cg, ctx->S, ctx->tw, s); }));
   FH_CUDA(prof(ctx, kPFwdY, [&] { return launch_fwd_y(g, t, ctx->S, ctx->tw, cg, s); }));
   FH_CUDA(prof(ctx, kPXGhat, [&] { return launch_x_ghat(g, t, ctx->S, ctx->tw, scale, cg, s); }));
   FH_CUDA(prof(ctx, kPInvY, [&] { return launch_inv_y(g, t, ctx->S, ctx->tw, cg, s); }));
@@ -215,24 +215,26 @@ int run_cg(fh_ctx* ctx, const Grid& g, const MatView& mv, const double* F_dev, b
     for (int k = 0; k < check_every; ++k, ++launched) {
       const int zmode = launched == 0 ? kZCgFirst : kZCg;
       if (stored) {
-        if ((rc = run_projection(ctx, g, zmode, ctx->r, ctx->p, ctx->K, c_mv, kIZDot, ctx->y, ctx->p, cg))) return rc;
+        if ((rc = run_projection(ctx, g, zmode, ctx->r, ctx->p, ctx->K, c_mv, kIZDot, ctx->y, ctx->p, cg, ctx->x)))
+          return rc;
       } else {
         FH_CUDA(prof(ctx, kPJvp, [&] {
-          return launch_jvp(g, mv, F_dev, ctx->r, ctx->p, ctx->P, zmode, cg, &ctx->sc->flags, s);
+          return launch_jvp(g, mv, F_dev, ctx->r, ctx->p, ctx->x, ctx->P, zmode, cg, &ctx->sc->flags, s);
         }));
         if ((rc = run_projection(ctx, g, kZDirect, ctx->P, nullptr, nullptr, c_mv, kIZDot, ctx->y, ctx->p, cg)))
           return rc;
       }
       FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_alpha(cg, ctx->partials, n_iz, s); }));
-      FH_CUDA(prof(ctx, kPCgUpdate, [&] {
-        return launch_cg_update(g, cg, ctx->x, ctx->r, ctx->p, ctx->y, ctx->partials, 0, s);
-      }));
+      FH_CUDA(prof(ctx, kPCgUpdate, [&] { return launch_cg_update(g, cg, ctx->r, ctx->y, ctx->partials, s); }));
       FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_beta(cg, ctx->partials, n_upd, s); }));
     }
     FH_CUDA(cudaMemcpyAsync(host_cg, cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
     FH_CUDA(cudaStreamSynchronize(s));
     prof_flush(ctx);
-    if (host_cg->done) return FH_OK;
+    if (host_cg->done) {
+      FH_CUDA(prof(ctx, kPCgUpdate, [&] { return launch_cg_finalize(g, cg, ctx->x, ctx->p, s); }));
+      return FH_OK;
+    }
     if (launched > max_cg + 2 * check_every) return fail(FH_ERR_CUDA, "CG loop did not report completion");
   }
 }
@@ -401,7 +403,7 @@ int fh_matvec(fh_ctx* ctx, const fh_material* mat, const double* F_dev, const do
     MatView mv;
     if ((rc = upload_material(ctx, mat, &mv))) return rc;
     FH_CUDA(cudaMemsetAsync(&ctx->sc->flags, 0, sizeof(int), ctx->stream));
-    FH_CUDA(prof(ctx, kPJvp, [&] { return launch_jvp(g, mv, F_dev, p_dev, nullptr, ctx->P, kZKApply, nullptr, &ctx->sc->flags, ctx->stream); }));
+    FH_CUDA(prof(ctx, kPJvp, [&] { return launch_jvp(g, mv, F_dev, p_dev, nullptr, nullptr, ctx->P, kZKApply, nullptr, &ctx->sc->flags, ctx->stream); }));
     rc = run_projection(ctx, g, kZDirect, ctx->P, nullptr, nullptr, c, kIZOut, y_dev, nullptr, nullptr);
     if (rc) return rc;
     int flags = 0;

@@ -7,8 +7,9 @@
 // butterfly j reads the R inputs j + r L/R, multiplies input r by the twiddle
 // w_L^(r (j mod Ns) L/(Ns R)), applies an R-point DFT in registers and writes
 // output r to (j div Ns) Ns R + (j mod Ns) + r Ns. The first stage (Ns = 1)
-// needs no twiddles. Twiddles w_L^m = exp(-2 pi i m / L) come from a table in
-// global memory (read through the L1 cache); the inverse uses their conjugates.
+// needs no twiddles. Twiddles w_L^m = exp(-2 pi i m / L) come from a table that
+// each CTA first copies from global to shared memory (reading them through the
+// texture path throttled the FP64 kernels); the inverse uses their conjugates.
 //
 // The plans minimise FP64 instructions (FP64 issue is the bound of this path):
 // 32 = 8x4, 64 = 8x8, 128 = 16x8, 256 = 16x16, smaller lengths in one stage.
@@ -162,24 +163,40 @@ template <> struct Plan<128> { static constexpr int n = 2; static constexpr int 
 template <> struct Plan<256> { static constexpr int n = 2; static constexpr int r[2] = {16, 16}; };
 
 // Pencil addressing inside a shared buffer: element j of pencil q lives at
-// q_stride * q + j_stride * j (in double2 units). JFAST selects the mapping of
+// q_stride * q + j_stride * j (in double2 units). Pencils come in groups of
+// `group`; only the first `valid` of each group hold data (the others pad a
+// ragged last chunk of columns and are skipped). JFAST selects the mapping of
 // threads to (pencil, butterfly): butterfly index fastest when pencils are
 // contiguous (j_stride == 1), pencil index fastest otherwise, so that
 // neighbouring threads touch neighbouring addresses.
 struct PencilLayout {
-  int np;        // number of pencils
+  int np;        // number of pencils (a multiple of group)
   int q_stride;
   int j_stride;
+  int group;
+  int valid;     // 1 <= valid <= group
 };
+
+__device__ __forceinline__ int pencil_of(int qv, const PencilLayout& lay) {
+  return lay.valid == lay.group ? qv : (qv / lay.valid) * lay.group + qv % lay.valid;
+}
+
+// copy the twiddle table of length L (first n entries) to shared memory;
+// the caller synchronises before use
+__device__ __forceinline__ void stage_twiddles(double2* dst, const double2* __restrict__ table, int L, int n) {
+  const double2* src = table + twiddle_offset(L);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
 
 template <int L, int R, int NS, bool INV, bool JFAST>
 __device__ __forceinline__ void stockham_stage(const double2* __restrict__ src, double2* __restrict__ dst,
                                                const PencilLayout& lay, const double2* __restrict__ tw) {
   constexpr int NB = L / R;  // butterflies per pencil
-  const int total = lay.np * NB;
+  const int nq = (lay.np / lay.group) * lay.valid;
+  const int total = nq * NB;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int q = JFAST ? t / NB : t % lay.np;
-    const int j = JFAST ? t % NB : t / lay.np;
+    const int q = pencil_of(JFAST ? t / NB : t % nq, lay);
+    const int j = JFAST ? t % NB : t / nq;
     const double2* s = src + q * lay.q_stride;
     double2* d = dst + q * lay.q_stride;
     double2 v[R];
@@ -190,7 +207,7 @@ __device__ __forceinline__ void stockham_stage(const double2* __restrict__ src, 
       constexpr int step = L / (NS * R);
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const double2 w = __ldg(tw + r * k * step);
+        const double2 w = tw[r * k * step];
         v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
       }
     }
@@ -202,12 +219,12 @@ __device__ __forceinline__ void stockham_stage(const double2* __restrict__ src, 
 }
 
 // Transform all pencils of `a` (length L). Uses `b` as the ping-pong partner;
-// returns the buffer holding the result. Synchronises the CTA before each
-// stage and after the last one.
+// `tw` is the length-L twiddle table (in shared memory). Returns the buffer
+// holding the result. Synchronises the CTA before each stage and after the
+// last one.
 template <int L, bool INV, bool JFAST>
 __device__ __forceinline__ double2* fft_pencils(double2* a, double2* b, const PencilLayout& lay,
-                                                const double2* __restrict__ tw_table) {
-  const double2* tw = tw_table + twiddle_offset(L);
+                                                const double2* tw) {
   if constexpr (Plan<L>::n == 0) {
     __syncthreads();
     return a;

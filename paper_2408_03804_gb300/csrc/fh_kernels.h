@@ -9,7 +9,7 @@ namespace fh {
 enum ZMode : int {
   kZDirect = 0,    // tau = src
   kZKApply = 1,    // tau = K : src            (src read only)
-  kZCg = 2,        // p = r + beta p ; tau = K : p   (src = r, p updated in place)
+  kZCg = 2,        // x += alpha p ; p = r + beta p ; tau = K : p   (src = r; x, p updated in place)
   kZCgFirst = 3,   // p = r ; tau = K : p
 };
 
@@ -45,8 +45,8 @@ size_t z_pass_smem(const Grid& g, const Tiling& t);
 long long z_pass_ctas(const Grid& g, const Tiling& t);
 
 cudaError_t setup_fft_kernels(const Grid& g, const Tiling& t);
-cudaError_t launch_fwd_z(const Grid& g, const Tiling& t, int mode, const double* src, double* p, const double* K,
-                         const CgScalars* cg, double2* S, const double2* tw, cudaStream_t s);
+cudaError_t launch_fwd_z(const Grid& g, const Tiling& t, int mode, const double* src, double* p, double* x,
+                         const double* K, const CgScalars* cg, double2* S, const double2* tw, cudaStream_t s);
 cudaError_t launch_fwd_y(const Grid& g, const Tiling& t, double2* S, const double2* tw, const CgScalars* cg,
                          cudaStream_t s);
 cudaError_t launch_x_ghat(const Grid& g, const Tiling& t, double2* S, const double2* tw, double scale,
@@ -60,8 +60,8 @@ cudaError_t launch_inv_z(const Grid& g, const Tiling& t, int mode, const double2
 long long constitutive_ctas(const Grid& g);
 cudaError_t launch_constitutive(const Grid& g, const MatView& m, const double* F, double* P, double* K,
                                 double* partials, int* flags, cudaStream_t s);
-cudaError_t launch_jvp(const Grid& g, const MatView& m, const double* F, const double* src, double* p, double* tau,
-                       int mode, const CgScalars* cg, int* flags, cudaStream_t s);
+cudaError_t launch_jvp(const Grid& g, const MatView& m, const double* F, const double* src, double* p, double* x,
+                       double* tau, int mode, const CgScalars* cg, int* flags, cudaStream_t s);
 cudaError_t launch_sum_partials(const double* partials, int n_parts, int width, double* out, cudaStream_t s);
 cudaError_t launch_field_sums(const Grid& g, const double* F, double* partials, cudaStream_t s);
 cudaError_t launch_fill(const Grid& g, double* F, const double* value9, int add, cudaStream_t s);
@@ -69,8 +69,9 @@ cudaError_t launch_cg_init(CgScalars* cg, const double* partials, int n_parts, d
                            cudaStream_t s);
 cudaError_t launch_cg_alpha(CgScalars* cg, const double* partials, int n_parts, cudaStream_t s);
 long long cg_update_ctas(const Grid& g);
-cudaError_t launch_cg_update(const Grid& g, CgScalars* cg, double* x, double* r, const double* p, const double* y,
-                             double* partials, int first, cudaStream_t s);
+cudaError_t launch_cg_update(const Grid& g, CgScalars* cg, double* r, const double* y, double* partials,
+                             cudaStream_t s);
+cudaError_t launch_cg_finalize(const Grid& g, const CgScalars* cg, double* x, const double* p, cudaStream_t s);
 cudaError_t launch_cg_beta(CgScalars* cg, const double* partials, int n_parts, cudaStream_t s);
 cudaError_t launch_newton_update(const Grid& g, double* F, const double* dF, double* partials, cudaStream_t s);
 long long newton_update_ctas(const Grid& g);

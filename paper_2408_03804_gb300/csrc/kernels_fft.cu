@@ -37,20 +37,27 @@ __device__ __forceinline__ bool cg_done(const CgScalars* cg) { return cg != null
 // ---------------------------------------------------------------------------
 template <int M, int MODE>
 __global__ void __launch_bounds__(kThreads) k_fwd_z(Grid g, int LB, const double* __restrict__ src,
-                                                   double* __restrict__ p, const double* __restrict__ K,
-                                                   const CgScalars* __restrict__ cg, double2* __restrict__ S,
-                                                   const double2* __restrict__ tw) {
+                                                   double* __restrict__ p, double* __restrict__ x,
+                                                   const double* __restrict__ K, const CgScalars* __restrict__ cg,
+                                                   double2* __restrict__ S, const double2* __restrict__ tw) {
   if (cg_done(cg)) return;
   extern __shared__ double2 smem[];
   constexpr int NZ = 2 * M;
   double2* bufA = smem;
   double2* bufB = smem + 9 * LB * M;
+  double2* twM = bufB + 9 * LB * M;   // length-M table (half-length FFT)
+  double2* twN = twM + M;              // first M/2 + 1 entries of the length-NZ table (unpack)
+  stage_twiddles(twM, tw, M, M);
+  stage_twiddles(twN, tw, NZ, M / 2 + 1);
   double* ra = reinterpret_cast<double*>(bufA);
   const long long line0 = (long long)blockIdx.x * LB;
   const long long v0 = line0 * NZ;
   const long long n = g.n;
-  double beta = 0.0;
-  if constexpr (MODE == kZCg) beta = cg->beta;
+  double beta = 0.0, alpha = 0.0;
+  if constexpr (MODE == kZCg) {
+    beta = cg->beta;
+    alpha = cg->alpha;
+  }
 
   for (int t = threadIdx.x; t < LB * NZ; t += blockDim.x) {
     const long long gi = v0 + t;
@@ -69,7 +76,10 @@ __global__ void __launch_bounds__(kThreads) k_fwd_z(Grid g, int LB, const double
           pv[c] = src[c * n + gi];
           p[c * n + gi] = pv[c];
         } else {
-          pv[c] = fma(beta, p[c * n + gi], src[c * n + gi]);
+          // the previous iteration's x += alpha p, then p = r + beta p
+          const double po = p[c * n + gi];
+          x[c * n + gi] = fma(alpha, po, x[c * n + gi]);
+          pv[c] = fma(beta, po, src[c * n + gi]);
           p[c * n + gi] = pv[c];
         }
       }
@@ -88,12 +98,11 @@ __global__ void __launch_bounds__(kThreads) k_fwd_z(Grid g, int LB, const double
     for (int c = 0; c < 9; ++c) ra[(c * LB + line) * NZ + z] = tau[c];
   }
 
-  double2* R = fft_pencils<M, false, true>(bufA, bufB, PencilLayout{9 * LB, M, 1}, tw);
+  double2* R = fft_pencils<M, false, true>(bufA, bufB, PencilLayout{9 * LB, M, 1, 1, 1}, twM);
 
   // unpack the half-length transform Z of z_m = x_2m + i x_2m+1 into
   // 2 X_k = (Z_k + conj Z_{M-k}) - i w^k (Z_k - conj Z_{M-k}), k = 0..M
   constexpr int KH = M / 2 + 1;
-  const double2* twn = tw + twiddle_offset(NZ);
   for (int t = threadIdx.x; t < 9 * LB * KH; t += blockDim.x) {
     const int q = t / KH, k = t % KH;
     const int c = q / LB, line = q % LB;
@@ -102,7 +111,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_z(Grid g, int LB, const double
     const double2 zm = Zq[(M - k) & (M - 1)];
     const double2 e = make_double2(zk.x + zm.x, zk.y - zm.y);  // Z_k + conj Z_{M-k}
     const double2 o = make_double2(zk.x - zm.x, zk.y + zm.y);  // Z_k - conj Z_{M-k}
-    const double2 wo = cmul(o, __ldg(twn + k));
+    const double2 wo = cmul(o, twN[k]);
     const double2 tt = make_double2(wo.y, -wo.x);               // -i w^k o
     double2 xk = cadd(e, tt);
     double2 xm = make_double2(e.x - tt.x, tt.y - e.y);         // conj(e - tt)
@@ -120,7 +129,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_z(Grid g, int LB, const double
 // forward y pass: row i, columns j = x, y, z along y; combine W_i
 // ---------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(kThreads) k_fwd_y(Grid g, int BK, double2* __restrict__ S,
+__global__ void __launch_bounds__(kThreads, 3) k_fwd_y(Grid g, int BK, double2* __restrict__ S,
                                                    const double2* __restrict__ tw, const CgScalars* __restrict__ cg) {
   if (cg_done(cg)) return;
   extern __shared__ double2 smem[];
@@ -128,6 +137,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd_y(Grid g, int BK, double2* __r
   const int np = 3 * BK;
   double2* bufA = smem;
   double2* bufB = smem + np * QS;
+  double2* twL = bufB + np * QS;
+  stage_twiddles(twL, tw, L, L);
   const int NC = (g.nzh + BK - 1) / BK;
   int b = blockIdx.x;
   const int chunk = b % NC;
@@ -135,6 +146,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_y(Grid g, int BK, double2* __r
   const int i = b % 3;
   const int x = b / 3;
   const int kz0 = chunk * BK;
+  const int valid = min(BK, g.nzh - kz0);
   for (int t = threadIdx.x; t < 3 * L * BK; t += blockDim.x) {
     const int kzl = t % BK, rest = t / BK;
     const int y = rest % L, f = rest / L;
@@ -143,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_y(Grid g, int BK, double2* __r
     if (kz < g.nzh) v = S[(3 * i + f) * g.nspec + ((long long)x * L + y) * g.nzh + kz];
     bufA[(f * BK + kzl) * QS + y] = v;
   }
-  double2* R = fft_pencils<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1}, tw);
+  double2* R = fft_pencils<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL);
   for (int t = threadIdx.x; t < L * BK; t += blockDim.x) {
     const int kzl = t % BK, y = t / BK;
     const int kz = kz0 + kzl;
@@ -162,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_y(Grid g, int BK, double2* __r
 // x pass: forward along x, Ghat, inverse along x
 // ---------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(kThreads) k_x_ghat(Grid g, int BK, double2* __restrict__ S,
+__global__ void __launch_bounds__(kThreads, 3) k_x_ghat(Grid g, int BK, double2* __restrict__ S,
                                                     const double2* __restrict__ tw, double scale,
                                                     const CgScalars* __restrict__ cg) {
   if (cg_done(cg)) return;
@@ -171,10 +183,13 @@ __global__ void __launch_bounds__(kThreads) k_x_ghat(Grid g, int BK, double2* __
   const int np = 6 * BK;
   double2* bufA = smem;
   double2* bufB = smem + np * QS;
+  double2* twL = bufB + np * QS;
+  stage_twiddles(twL, tw, L, L);
   const int NC = (g.nzh + BK - 1) / BK;
   const int chunk = blockIdx.x % NC;
   const int ky = blockIdx.x / NC;
   const int kz0 = chunk * BK;
+  const int valid = min(BK, g.nzh - kz0);
   const long long row = (long long)g.ny * g.nzh;  // stride of x in S
   for (int t = threadIdx.x; t < 6 * L * BK; t += blockDim.x) {
     const int kzl = t % BK, rest = t / BK;
@@ -185,11 +200,12 @@ __global__ void __launch_bounds__(kThreads) k_x_ghat(Grid g, int BK, double2* __
     if (kz < g.nzh) v = S[comp * g.nspec + x * row + (long long)ky * g.nzh + kz];
     bufA[(f * BK + kzl) * QS + x] = v;
   }
-  double2* R = fft_pencils<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1}, tw);
+  double2* R = fft_pencils<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL);
   const double xi_y = wave_int(ky, g.ny) * g.sy;
   for (int t = threadIdx.x; t < L * BK; t += blockDim.x) {
     const int kzl = t % BK, kx = t / BK;
     const int kz = kz0 + kzl;
+    if (kzl >= valid) continue;
     const double xi_x = wave_int(kx, L) * g.sx;
     const double xi_z = wave_int(kz, g.nz) * g.sz;
     const double d = fma(xi_x, xi_x, fma(xi_y, xi_y, xi_z * xi_z));
@@ -205,7 +221,7 @@ __global__ void __launch_bounds__(kThreads) k_x_ghat(Grid g, int BK, double2* __
     }
   }
   double2* other = (R == bufA) ? bufB : bufA;
-  double2* R2 = fft_pencils<L, true, true>(R, other, PencilLayout{np, QS, 1}, tw);
+  double2* R2 = fft_pencils<L, true, true>(R, other, PencilLayout{np, QS, 1, BK, valid}, twL);
   for (int t = threadIdx.x; t < 6 * L * BK; t += blockDim.x) {
     const int kzl = t % BK, rest = t / BK;
     const int x = rest % L, f = rest / L;
@@ -220,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) k_x_ghat(Grid g, int BK, double2* __
 // inverse y pass: expand A_i, B_i to the three columns of row i
 // ---------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(kThreads) k_inv_y(Grid g, int BK, double2* __restrict__ S,
+__global__ void __launch_bounds__(kThreads, 3) k_inv_y(Grid g, int BK, double2* __restrict__ S,
                                                    const double2* __restrict__ tw, const CgScalars* __restrict__ cg) {
   if (cg_done(cg)) return;
   extern __shared__ double2 smem[];
@@ -228,6 +244,8 @@ __global__ void __launch_bounds__(kThreads) k_inv_y(Grid g, int BK, double2* __r
   const int np = 3 * BK;
   double2* bufA = smem;
   double2* bufB = smem + np * QS;
+  double2* twL = bufB + np * QS;
+  stage_twiddles(twL, tw, L, L);
   const int NC = (g.nzh + BK - 1) / BK;
   int b = blockIdx.x;
   const int chunk = b % NC;
@@ -235,6 +253,7 @@ __global__ void __launch_bounds__(kThreads) k_inv_y(Grid g, int BK, double2* __r
   const int i = b % 3;
   const int x = b / 3;
   const int kz0 = chunk * BK;
+  const int valid = min(BK, g.nzh - kz0);
   for (int t = threadIdx.x; t < 2 * L * BK; t += blockDim.x) {
     const int kzl = t % BK, rest = t / BK;
     const int y = rest % L, h = rest / L;
@@ -248,7 +267,7 @@ __global__ void __launch_bounds__(kThreads) k_inv_y(Grid g, int BK, double2* __r
       bufA[(2 * BK + kzl) * QS + y] = v;
     }
   }
-  double2* R = fft_pencils<L, true, true>(bufA, bufB, PencilLayout{np, QS, 1}, tw);
+  double2* R = fft_pencils<L, true, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL);
   for (int t = threadIdx.x; t < L * BK; t += blockDim.x) {
     const int kzl = t % BK, y = t / BK;
     const int kz = kz0 + kzl;
@@ -274,12 +293,16 @@ __global__ void __launch_bounds__(kThreads) k_inv_z(Grid g, int LB, const double
   constexpr int NZ = 2 * M;
   double2* bufA = smem;
   double2* bufB = smem + 9 * LB * M;
+  double2* twM = bufB + 9 * LB * M;
+  double2* twN = twM + M;
+  stage_twiddles(twM, tw, M, M);
+  stage_twiddles(twN, tw, NZ, M / 2 + 1);
+  __syncthreads();
   const long long line0 = (long long)blockIdx.x * LB;
   const long long n = g.n;
   // pack Z_k = (X_k + conj X_{M-k}) + i w^-k (X_k - conj X_{M-k}); the
   // imaginary parts of X_0 and X_M are dropped (complex-to-real semantics)
   constexpr int KH = M / 2 + 1;
-  const double2* twn = tw + twiddle_offset(NZ);
   for (int t = threadIdx.x; t < 9 * LB * KH; t += blockDim.x) {
     const int q = t / KH, k = t % KH;
     const int c = q / LB, line = q % LB;
@@ -291,12 +314,12 @@ __global__ void __launch_bounds__(kThreads) k_inv_z(Grid g, int LB, const double
     }
     const double2 a = make_double2(xk.x + xm.x, xk.y - xm.y);
     const double2 bb = make_double2(xk.x - xm.x, xk.y + xm.y);
-    const double2 bw = cmulc(bb, __ldg(twn + k));
+    const double2 bw = cmulc(bb, twN[k]);
     const double2 u = make_double2(-bw.y, bw.x);  // i w^-k b
     bufA[q * M + k] = cadd(a, u);
     if (k != 0 && M - k != k) bufA[q * M + (M - k)] = make_double2(a.x - u.x, u.y - a.y);
   }
-  double2* R = fft_pencils<M, true, true>(bufA, bufB, PencilLayout{9 * LB, M, 1}, tw);
+  double2* R = fft_pencils<M, true, true>(bufA, bufB, PencilLayout{9 * LB, M, 1, 1, 1}, twM);
   const double* rr = reinterpret_cast<const double*>(R);
   double acc = 0.0;
   for (int t = threadIdx.x; t < LB * NZ; t += blockDim.x) {
@@ -343,9 +366,14 @@ Tiling choose_tiling(const Grid& g) {
   return t;
 }
 
-size_t z_pass_smem(const Grid& g, const Tiling& t) { return (size_t)9 * t.lines_z * g.nz * sizeof(double2); }
+size_t z_pass_smem(const Grid& g, const Tiling& t) {
+  const int M = g.nz / 2;
+  return ((size_t)9 * t.lines_z * g.nz + M + M / 2 + 1) * sizeof(double2);
+}
 long long z_pass_ctas(const Grid& g, const Tiling& t) { return (long long)g.nx * g.ny / t.lines_z; }
-static size_t y_smem(int L, int bk, int fields) { return (size_t)2 * fields * bk * (L + 1) * sizeof(double2); }
+static size_t y_smem(int L, int bk, int fields) {
+  return ((size_t)2 * fields * bk * (L + 1) + L) * sizeof(double2);
+}
 
 #define FH_SWITCH_POW2(v, MACRO) \
   switch (v) {                   \
@@ -400,18 +428,18 @@ cudaError_t setup_fft_kernels(const Grid& g, const Tiling& t) {
   return cudaSuccess;
 }
 
-cudaError_t launch_fwd_z(const Grid& g, const Tiling& t, int mode, const double* src, double* p, const double* K,
-                         const CgScalars* cg, double2* S, const double2* tw, cudaStream_t s) {
+cudaError_t launch_fwd_z(const Grid& g, const Tiling& t, int mode, const double* src, double* p, double* x,
+                         const double* K, const CgScalars* cg, double2* S, const double2* tw, cudaStream_t s) {
   const size_t smem = z_pass_smem(g, t);
   const unsigned grid = (unsigned)z_pass_ctas(g, t);
   const int M = g.nz / 2;
 #define ZL(V)                                                                                              \
   case V:                                                                                                  \
     switch (mode) {                                                                                        \
-      case kZDirect: k_fwd_z<V, kZDirect><<<grid, kThreads, smem, s>>>(g, t.lines_z, src, p, K, cg, S, tw); break; \
-      case kZKApply: k_fwd_z<V, kZKApply><<<grid, kThreads, smem, s>>>(g, t.lines_z, src, p, K, cg, S, tw); break; \
-      case kZCg: k_fwd_z<V, kZCg><<<grid, kThreads, smem, s>>>(g, t.lines_z, src, p, K, cg, S, tw); break;         \
-      case kZCgFirst: k_fwd_z<V, kZCgFirst><<<grid, kThreads, smem, s>>>(g, t.lines_z, src, p, K, cg, S, tw); break; \
+      case kZDirect: k_fwd_z<V, kZDirect><<<grid, kThreads, smem, s>>>(g, t.lines_z, src, p, x, K, cg, S, tw); break; \
+      case kZKApply: k_fwd_z<V, kZKApply><<<grid, kThreads, smem, s>>>(g, t.lines_z, src, p, x, K, cg, S, tw); break; \
+      case kZCg: k_fwd_z<V, kZCg><<<grid, kThreads, smem, s>>>(g, t.lines_z, src, p, x, K, cg, S, tw); break;         \
+      case kZCgFirst: k_fwd_z<V, kZCgFirst><<<grid, kThreads, smem, s>>>(g, t.lines_z, src, p, x, K, cg, S, tw); break; \
       default: return cudaErrorInvalidValue;                                                               \
     }                                                                                                      \
     break;

@@ -89,18 +89,21 @@ cudaError_t launch_constitutive(const Grid& g, const MatView& m, const double* F
 
 // ---------------------------------------------------------------------------
 // jvp form of the tangent apply (Listing 3): tau = K(F) : p with K re-derived
-// by AD in every call. mode kZKApply: p = src ; kZCg: p = r + beta p ;
-// kZCgFirst: p = r (p written back in the CG modes).
+// by AD in every call. mode kZKApply: p = src ; kZCg: x += alpha p, then
+// p = r + beta p ; kZCgFirst: p = r (p written back in the CG modes).
 // ---------------------------------------------------------------------------
 template <class Law, int MODE>
 __global__ void __launch_bounds__(kThreads) k_jvp(Grid g, MatView m, const double* __restrict__ F,
                                                  const double* __restrict__ src, double* __restrict__ p,
-                                                 double* __restrict__ tau, const CgScalars* __restrict__ cg,
-                                                 int* __restrict__ flags) {
+                                                 double* __restrict__ x, double* __restrict__ tau,
+                                                 const CgScalars* __restrict__ cg, int* __restrict__ flags) {
   if (cg != nullptr && cg->done) return;
   const long long n = g.n;
-  double beta = 0.0;
-  if constexpr (MODE == kZCg) beta = cg->beta;
+  double beta = 0.0, alpha = 0.0;
+  if constexpr (MODE == kZCg) {
+    beta = cg->beta;
+    alpha = cg->alpha;
+  }
   bool bad = false;
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
     double f[9], pv[9], kv[45], pd[9];
@@ -113,7 +116,9 @@ __global__ void __launch_bounds__(kThreads) k_jvp(Grid g, MatView m, const doubl
         pd[c] = src[c * n + v];
         p[c * n + v] = pd[c];
       } else {
-        pd[c] = fma(beta, p[c * n + v], src[c * n + v]);
+        const double po = p[c * n + v];
+        x[c * n + v] = fma(alpha, po, x[c * n + v]);
+        pd[c] = fma(beta, po, src[c * n + v]);
         p[c * n + v] = pd[c];
       }
     }
@@ -134,21 +139,24 @@ __global__ void __launch_bounds__(kThreads) k_jvp(Grid g, MatView m, const doubl
 
 template <class Law>
 static void launch_jvp_law(unsigned grid, cudaStream_t s, const Grid& g, const MatView& m, const double* F,
-                           const double* src, double* p, double* tau, int mode, const CgScalars* cg, int* flags) {
+                           const double* src, double* p, double* x, double* tau, int mode, const CgScalars* cg,
+                           int* flags) {
   switch (mode) {
-    case kZKApply: k_jvp<Law, kZKApply><<<grid, kThreads, 0, s>>>(g, m, F, src, p, tau, cg, flags); break;
-    case kZCg: k_jvp<Law, kZCg><<<grid, kThreads, 0, s>>>(g, m, F, src, p, tau, cg, flags); break;
-    default: k_jvp<Law, kZCgFirst><<<grid, kThreads, 0, s>>>(g, m, F, src, p, tau, cg, flags); break;
+    case kZKApply: k_jvp<Law, kZKApply><<<grid, kThreads, 0, s>>>(g, m, F, src, p, x, tau, cg, flags); break;
+    case kZCg: k_jvp<Law, kZCg><<<grid, kThreads, 0, s>>>(g, m, F, src, p, x, tau, cg, flags); break;
+    default: k_jvp<Law, kZCgFirst><<<grid, kThreads, 0, s>>>(g, m, F, src, p, x, tau, cg, flags); break;
   }
 }
 
-cudaError_t launch_jvp(const Grid& g, const MatView& m, const double* F, const double* src, double* p, double* tau,
-                       int mode, const CgScalars* cg, int* flags, cudaStream_t s) {
+cudaError_t launch_jvp(const Grid& g, const MatView& m, const double* F, const double* src, double* p, double* x,
+                       double* tau, int mode, const CgScalars* cg, int* flags, cudaStream_t s) {
   const unsigned grid = pointwise_grid(g);
   switch (m.kind) {
-    case FH_LINEAR_ELASTIC: launch_jvp_law<LinearElasticLaw>(grid, s, g, m, F, src, p, tau, mode, cg, flags); break;
-    case FH_NEO_HOOKEAN: launch_jvp_law<NeoHookeanLaw>(grid, s, g, m, F, src, p, tau, mode, cg, flags); break;
-    case FH_SVK: launch_jvp_law<SVKLaw>(grid, s, g, m, F, src, p, tau, mode, cg, flags); break;
+    case FH_LINEAR_ELASTIC:
+      launch_jvp_law<LinearElasticLaw>(grid, s, g, m, F, src, p, x, tau, mode, cg, flags);
+      break;
+    case FH_NEO_HOOKEAN: launch_jvp_law<NeoHookeanLaw>(grid, s, g, m, F, src, p, x, tau, mode, cg, flags); break;
+    case FH_SVK: launch_jvp_law<SVKLaw>(grid, s, g, m, F, src, p, x, tau, mode, cg, flags); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -272,19 +280,17 @@ cudaError_t launch_cg_alpha(CgScalars* cg, const double* partials, int n_parts, 
   return cudaGetLastError();
 }
 
-// x += alpha p (x = alpha p on the first iteration), r -= alpha y, partial r . r
-__global__ void __launch_bounds__(kThreads) k_cg_update(Grid g, const CgScalars* __restrict__ cg, double* __restrict__ x,
-                                                       double* __restrict__ r, const double* __restrict__ p,
-                                                       const double* __restrict__ y, double* __restrict__ partials,
-                                                       int first) {
+// r -= alpha y and partial r . r. The matching x += alpha p is deferred to the
+// next forward z pass (which reads p anyway) or to k_cg_finalize.
+__global__ void __launch_bounds__(kThreads) k_cg_update(Grid g, const CgScalars* __restrict__ cg,
+                                                       double* __restrict__ r, const double* __restrict__ y,
+                                                       double* __restrict__ partials) {
   __shared__ double red[32];
   if (cg->done) return;
   const double alpha = cg->alpha;
   const long long n9 = 9 * g.n;
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n9; i += (long long)gridDim.x * blockDim.x) {
-    const double pv = p[i];
-    x[i] = first ? alpha * pv : fma(alpha, pv, x[i]);
     const double rv = fma(-alpha, y[i], r[i]);
     r[i] = rv;
     acc = fma(rv, rv, acc);
@@ -295,9 +301,25 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(Grid g, const CgScalars*
 
 long long cg_update_ctas(const Grid& g) { return pointwise_grid(g); }
 
-cudaError_t launch_cg_update(const Grid& g, CgScalars* cg, double* x, double* r, const double* p, const double* y,
-                             double* partials, int first, cudaStream_t s) {
-  k_cg_update<<<pointwise_grid(g), kThreads, 0, s>>>(g, cg, x, r, p, y, partials, first);
+cudaError_t launch_cg_update(const Grid& g, CgScalars* cg, double* r, const double* y, double* partials,
+                             cudaStream_t s) {
+  k_cg_update<<<pointwise_grid(g), kThreads, 0, s>>>(g, cg, r, y, partials);
+  return cudaGetLastError();
+}
+
+// the last deferred x += alpha p once CG has stopped (nothing if no product ran;
+// alpha is 0 after a breakdown in k_cg_alpha)
+__global__ void __launch_bounds__(kThreads) k_cg_finalize(Grid g, const CgScalars* __restrict__ cg,
+                                                         double* __restrict__ x, const double* __restrict__ p) {
+  if (cg->it == 0) return;
+  const double alpha = cg->alpha;
+  const long long n9 = 9 * g.n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n9; i += (long long)gridDim.x * blockDim.x)
+    x[i] = fma(alpha, p[i], x[i]);
+}
+
+cudaError_t launch_cg_finalize(const Grid& g, const CgScalars* cg, double* x, const double* p, cudaStream_t s) {
+  k_cg_finalize<<<pointwise_grid(g), kThreads, 0, s>>>(g, cg, x, p);
   return cudaGetLastError();
 }
 

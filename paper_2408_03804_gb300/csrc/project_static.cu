@@ -148,7 +148,8 @@ extern "C" int fh_project_static(const double* A_dev, double* out_dev, int nx, i
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const double c = scale / (2.0 * (double)n);
   if ((e = setup_fft_kernels(g, t)) != cudaSuccess ||
-      (e = launch_fwd_z(g, t, kZDirect, A_dev, nullptr, nullptr, nullptr, slot->spectrum, slot->twiddles, s)) !=
+      (e = launch_fwd_z(g, t, kZDirect, A_dev, nullptr, nullptr, nullptr, nullptr, slot->spectrum,
+                        slot->twiddles, s)) !=
           cudaSuccess ||
       (e = launch_fwd_y(g, t, slot->spectrum, slot->twiddles, nullptr, s)) != cudaSuccess ||
       (e = launch_x_ghat(g, t, slot->spectrum, slot->twiddles, c, nullptr, s)) != cudaSuccess ||
