@@ -12,8 +12,9 @@
  *
  * Conventions shared by every entry point
  * ---------------------------------------
- * Grid        nx x ny x nz voxels, N = nx*ny*nz. Each extent must be a power
- *             of two; nx, ny in [1, 256], nz in [2, 256]. Box side lengths
+ * Grid        nx x ny x nz voxels, N = nx*ny*nz. Each extent is 2^a or
+ *             3*2^a and at most 256 (radix-2/4/8/16 and radix-3 transforms);
+ *             nz is even and nz/2 is of the same form. Box side lengths
  *             default to 1 (see fh_options.lengths).
  * Fields      device float64 arrays in structure-of-arrays order
  *             [9][nx][ny][nz] (z fastest); component c = 3*i + j holds the
@@ -231,7 +232,7 @@ FH_API int fh_profile_read(fh_ctx* ctx, long long counts[FH_PROF_NCLASS], double
  * 9 * 32768 complex doubles (4.5 MiB) plus 8 KiB of twiddle tables, which
  * every GPU that loads this library holds until the process exits.
  *   A_dev, out_dev  device [9][nx][ny][nz] fields (out may equal A)
- *   nx, ny, nz      powers of two as for fh_create, nx*ny*nz <= 32768;
+ *   nx, ny, nz      extents as for fh_create, nx*ny*nz <= 32768;
  *                   larger grids return FH_ERR_ARG (use fh_project)
  *   lengths         box side lengths, or NULL for the unit box
  *   cuda_stream     stream to run on (NULL = legacy default stream)

@@ -33,7 +33,6 @@ int fail(int code, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(FH_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
 
 struct DeviceGuard {
   int prev = -1;
@@ -132,7 +131,8 @@ cudaError_t prof(fh_ctx* c, int cls, Fn&& fn) {
 void make_twiddles(std::vector<double2>& t) {
   t.assign(kTwiddleTotal, make_double2(0.0, 0.0));
   const long double two_pi = 6.283185307179586476925286766559005768L;
-  for (int L = 1; L <= kMaxN; L *= 2) {
+  for (int L = 1; L <= kMaxN; ++L) {
+    if (!fft_length_ok(L)) continue;
     for (int m = 0; m < L; ++m) {
       const long double a = two_pi * (long double)m / (long double)L;
       double c = (double)cosl(a), s = (double)-sinl(a);
@@ -281,9 +281,10 @@ void fh_internal_set_error(const char* msg) {
 int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
   g_err[0] = 0;
   if (!out) return fail(FH_ERR_ARG, "out is NULL");
-  if (!pow2_in(nx, 1, kMaxN) || !pow2_in(ny, 1, kMaxN) || !pow2_in(nz, 2, kMaxN))
-    return fail(FH_ERR_ARG, "grid %dx%dx%d: extents must be powers of two, nx,ny in [1,256], nz in [2,256]", nx, ny,
-                nz);
+  if (!grid_extents_ok(nx, ny, nz))
+    return fail(FH_ERR_ARG,
+                "grid %dx%dx%d: each extent must be 2^a or 3*2^a up to 256, and nz even with nz/2 of that form",
+                nx, ny, nz);
   fh_ctx* c = new fh_ctx();
   FH_CUDA(cudaGetDevice(&c->dev));
   c->stream = (cudaStream_t)cuda_stream;

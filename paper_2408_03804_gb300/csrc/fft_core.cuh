@@ -2,7 +2,7 @@
 // memory: the building block of the 3D transforms of Eq. 1.
 //
 // Each length-L transform is a Stockham auto-sort sequence of radix-R stages
-// (R in {2, 4, 8, 16}) that ping-pongs between two shared-memory buffers. A
+// (R in {2, 3, 4, 8, 16}) that ping-pongs between two shared-memory buffers. A
 // stage with radix R and current sub-transform size Ns treats L/R butterflies;
 // butterfly j reads the R inputs j + r L/R, multiplies input r by the twiddle
 // w_L^(r (j mod Ns) L/(Ns R)), applies an R-point DFT in registers and writes
@@ -12,7 +12,8 @@
 // texture path throttled the FP64 kernels); the inverse uses their conjugates.
 //
 // The plans minimise FP64 instructions (FP64 issue is the bound of this path):
-// 32 = 8x4, 64 = 8x8, 128 = 16x8, 256 = 16x16, smaller lengths in one stage.
+// 32 = 8x4, 64 = 8x8, 128 = 16x8, 256 = 16x16, smaller powers of two in one
+// stage; lengths 3 * 2^a end with a radix-3 stage (48 = 16x3, 96 = 8x4x3).
 #pragma once
 
 #include "fh_common.cuh"
@@ -20,6 +21,7 @@
 namespace fh {
 
 constexpr double kC8 = 0.70710678118654752440;   // cos(pi/4)
+constexpr double kS3 = 0.86602540378443864676;   // sin(pi/3)
 constexpr double kC16 = 0.92387953251128675613;  // cos(pi/8)
 constexpr double kS16 = 0.38268343236508977173;  // sin(pi/8)
 
@@ -34,6 +36,19 @@ __device__ __forceinline__ void dft2(double2* v) {
   const double2 a = v[0], b = v[1];
   v[0] = cadd(a, b);
   v[1] = csub(a, b);
+}
+
+// X0 = a + b + c, X1,2 = a - (b + c)/2 -+ i sin(pi/3) (b - c) (forward; signs
+// of the sine term swap for the inverse)
+template <bool INV>
+__device__ __forceinline__ void dft3(double2* v) {
+  const double2 a = v[0];
+  const double2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+  const double2 m = make_double2(fma(-0.5, t1.x, a.x), fma(-0.5, t1.y, a.y));
+  v[0] = cadd(a, t1);
+  const double sx = INV ? -kS3 : kS3;
+  v[1] = make_double2(fma(sx, t2.y, m.x), fma(-sx, t2.x, m.y));
+  v[2] = make_double2(fma(-sx, t2.y, m.x), fma(sx, t2.x, m.y));
 }
 
 template <bool INV>
@@ -144,6 +159,7 @@ __device__ __forceinline__ void dft16(double2* v) {
 template <int R, bool INV>
 __device__ __forceinline__ void dft_r(double2* v) {
   if constexpr (R == 2) dft2<INV>(v);
+  else if constexpr (R == 3) dft3<INV>(v);
   else if constexpr (R == 4) dft4<INV>(v);
   else if constexpr (R == 8) dft8<INV>(v);
   else if constexpr (R == 16) dft16<INV>(v);
@@ -152,15 +168,22 @@ __device__ __forceinline__ void dft_r(double2* v) {
 // ---- plans: radix of each stage for a length L --------------------------------
 template <int L>
 struct Plan;
-template <> struct Plan<1>   { static constexpr int n = 0; static constexpr int r[1] = {1}; };
-template <> struct Plan<2>   { static constexpr int n = 1; static constexpr int r[1] = {2}; };
-template <> struct Plan<4>   { static constexpr int n = 1; static constexpr int r[1] = {4}; };
-template <> struct Plan<8>   { static constexpr int n = 1; static constexpr int r[1] = {8}; };
-template <> struct Plan<16>  { static constexpr int n = 1; static constexpr int r[1] = {16}; };
-template <> struct Plan<32>  { static constexpr int n = 2; static constexpr int r[2] = {8, 4}; };
-template <> struct Plan<64>  { static constexpr int n = 2; static constexpr int r[2] = {8, 8}; };
-template <> struct Plan<128> { static constexpr int n = 2; static constexpr int r[2] = {16, 8}; };
-template <> struct Plan<256> { static constexpr int n = 2; static constexpr int r[2] = {16, 16}; };
+template <> struct Plan<1>   { static constexpr int n = 0; static constexpr int r[3] = {1, 1, 1}; };
+template <> struct Plan<2>   { static constexpr int n = 1; static constexpr int r[3] = {2, 1, 1}; };
+template <> struct Plan<3>   { static constexpr int n = 1; static constexpr int r[3] = {3, 1, 1}; };
+template <> struct Plan<4>   { static constexpr int n = 1; static constexpr int r[3] = {4, 1, 1}; };
+template <> struct Plan<6>   { static constexpr int n = 2; static constexpr int r[3] = {2, 3, 1}; };
+template <> struct Plan<8>   { static constexpr int n = 1; static constexpr int r[3] = {8, 1, 1}; };
+template <> struct Plan<12>  { static constexpr int n = 2; static constexpr int r[3] = {4, 3, 1}; };
+template <> struct Plan<16>  { static constexpr int n = 1; static constexpr int r[3] = {16, 1, 1}; };
+template <> struct Plan<24>  { static constexpr int n = 2; static constexpr int r[3] = {8, 3, 1}; };
+template <> struct Plan<32>  { static constexpr int n = 2; static constexpr int r[3] = {8, 4, 1}; };
+template <> struct Plan<48>  { static constexpr int n = 2; static constexpr int r[3] = {16, 3, 1}; };
+template <> struct Plan<64>  { static constexpr int n = 2; static constexpr int r[3] = {8, 8, 1}; };
+template <> struct Plan<96>  { static constexpr int n = 3; static constexpr int r[3] = {8, 4, 3}; };
+template <> struct Plan<128> { static constexpr int n = 2; static constexpr int r[3] = {16, 8, 1}; };
+template <> struct Plan<192> { static constexpr int n = 3; static constexpr int r[3] = {16, 4, 3}; };
+template <> struct Plan<256> { static constexpr int n = 2; static constexpr int r[3] = {16, 16, 1}; };
 
 // Pencil addressing inside a shared buffer: element j of pencil q lives at
 // q_stride * q + j_stride * j (in double2 units). Pencils come in groups of
@@ -183,8 +206,10 @@ __device__ __forceinline__ int pencil_of(int qv, const PencilLayout& lay) {
 
 // copy the twiddle table of length L (first n entries) to shared memory;
 // the caller synchronises before use
-__device__ __forceinline__ void stage_twiddles(double2* dst, const double2* __restrict__ table, int L, int n) {
-  const double2* src = table + twiddle_offset(L);
+template <int L>
+__device__ __forceinline__ void stage_twiddles(double2* dst, const double2* __restrict__ table, int n) {
+  constexpr int off = twiddle_offset(L);
+  const double2* src = table + off;
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
@@ -218,6 +243,18 @@ __device__ __forceinline__ void stockham_stage(const double2* __restrict__ src, 
   }
 }
 
+template <int L, bool INV, bool JFAST, int S, int NS>
+__device__ __forceinline__ double2* run_stages(double2* a, double2* b, const PencilLayout& lay, const double2* tw) {
+  if constexpr (S == Plan<L>::n) {
+    return a;
+  } else {
+    constexpr int R = Plan<L>::r[S];
+    __syncthreads();
+    stockham_stage<L, R, NS, INV, JFAST>(a, b, lay, tw);
+    return run_stages<L, INV, JFAST, S + 1, NS * R>(b, a, lay, tw);
+  }
+}
+
 // Transform all pencils of `a` (length L). Uses `b` as the ping-pong partner;
 // `tw` is the length-L twiddle table (in shared memory). Returns the buffer
 // holding the result. Synchronises the CTA before each stage and after the
@@ -225,25 +262,10 @@ __device__ __forceinline__ void stockham_stage(const double2* __restrict__ src, 
 template <int L, bool INV, bool JFAST>
 __device__ __forceinline__ double2* fft_pencils(double2* a, double2* b, const PencilLayout& lay,
                                                 const double2* tw) {
-  if constexpr (Plan<L>::n == 0) {
-    __syncthreads();
-    return a;
-  } else if constexpr (Plan<L>::n == 1) {
-    __syncthreads();
-    stockham_stage<L, Plan<L>::r[0], 1, INV, JFAST>(a, b, lay, tw);
-    __syncthreads();
-    return b;
-  } else {
-    constexpr int R0 = Plan<L>::r[0];
-    constexpr int R1 = Plan<L>::r[1];
-    static_assert(R0 * R1 == L, "plan");
-    __syncthreads();
-    stockham_stage<L, R0, 1, INV, JFAST>(a, b, lay, tw);
-    __syncthreads();
-    stockham_stage<L, R1, R0, INV, JFAST>(b, a, lay, tw);
-    __syncthreads();
-    return a;
-  }
+  static_assert(L == 1 || Plan<L>::n > 0, "plan");
+  double2* out = run_stages<L, INV, JFAST, 0, 1>(a, b, lay, tw);
+  __syncthreads();
+  return out;
 }
 
 }  // namespace fh

@@ -11,7 +11,23 @@ namespace fh {
 
 constexpr int kThreads = 256;          // threads per CTA of every kernel
 constexpr int kMaxN = 256;             // largest supported extent per axis
-constexpr int kTwiddleTotal = 2 * kMaxN;  // tables for L = 1..256 packed back to back
+
+// transform lengths with a radix plan: 2^a and 3 * 2^a, up to 256
+__host__ __device__ constexpr bool fft_length_ok(int L) {
+  if (L < 1 || L > kMaxN) return false;
+  if (L % 3 == 0) L /= 3;
+  return (L & (L - 1)) == 0;
+}
+
+// offset of the twiddle table of length L: the tables of all supported lengths
+// are stored back to back in increasing order
+__host__ __device__ constexpr int twiddle_offset(int L) {
+  int off = 0;
+  for (int l = 1; l < L; ++l)
+    if (fft_length_ok(l)) off += l;
+  return off;
+}
+constexpr int kTwiddleTotal = twiddle_offset(kMaxN) + kMaxN;
 
 // ---------------------------------------------------------------------------
 // complex helpers (double2 = re, im)
@@ -41,9 +57,12 @@ __host__ __device__ __forceinline__ int wave_int(int j, int n) {
   return (2 * j < n) ? j : j - n;
 }
 
-// offset of the twiddle table for length L (power of two) inside the packed
-// table: tables for L = 1, 2, 4, ... are stored back to back, table L at L - 1
-__host__ __device__ constexpr int twiddle_offset(int L) { return L - 1; }
+// the extents a grid may have: nx, ny any supported length, nz an even one
+// whose half is supported too (the real-to-complex step transforms nz/2)
+__host__ __device__ constexpr bool grid_extents_ok(int nx, int ny, int nz) {
+  return fft_length_ok(nx) && fft_length_ok(ny) && nz >= 2 && nz % 2 == 0 && fft_length_ok(nz) &&
+         fft_length_ok(nz / 2);
+}
 
 // ---------------------------------------------------------------------------
 // Grid description passed by value to kernels

@@ -47,8 +47,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd_z(Grid g, int LB, const double
   double2* bufB = smem + 9 * LB * M;
   double2* twM = bufB + 9 * LB * M;   // length-M table (half-length FFT)
   double2* twN = twM + M;              // first M/2 + 1 entries of the length-NZ table (unpack)
-  stage_twiddles(twM, tw, M, M);
-  stage_twiddles(twN, tw, NZ, M / 2 + 1);
+  stage_twiddles<M>(twM, tw, M);
+  stage_twiddles<NZ>(twN, tw, M / 2 + 1);
   double* ra = reinterpret_cast<double*>(bufA);
   const long long line0 = (long long)blockIdx.x * LB;
   const long long v0 = line0 * NZ;
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_z(Grid g, int LB, const double
     const int c = q / LB, line = q % LB;
     const double2* Zq = R + q * M;
     const double2 zk = Zq[k];
-    const double2 zm = Zq[(M - k) & (M - 1)];
+    const double2 zm = Zq[k == 0 ? 0 : M - k];
     const double2 e = make_double2(zk.x + zm.x, zk.y - zm.y);  // Z_k + conj Z_{M-k}
     const double2 o = make_double2(zk.x - zm.x, zk.y + zm.y);  // Z_k - conj Z_{M-k}
     const double2 wo = cmul(o, twN[k]);
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_fwd_y(Grid g, int BK, double2* 
   double2* bufA = smem;
   double2* bufB = smem + np * QS;
   double2* twL = bufB + np * QS;
-  stage_twiddles(twL, tw, L, L);
+  stage_twiddles<L>(twL, tw, L);
   const int NC = (g.nzh + BK - 1) / BK;
   int b = blockIdx.x;
   const int chunk = b % NC;
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_x_ghat(Grid g, int BK, double2*
   double2* bufA = smem;
   double2* bufB = smem + np * QS;
   double2* twL = bufB + np * QS;
-  stage_twiddles(twL, tw, L, L);
+  stage_twiddles<L>(twL, tw, L);
   const int NC = (g.nzh + BK - 1) / BK;
   const int chunk = blockIdx.x % NC;
   const int ky = blockIdx.x / NC;
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_inv_y(Grid g, int BK, double2* 
   double2* bufA = smem;
   double2* bufB = smem + np * QS;
   double2* twL = bufB + np * QS;
-  stage_twiddles(twL, tw, L, L);
+  stage_twiddles<L>(twL, tw, L);
   const int NC = (g.nzh + BK - 1) / BK;
   int b = blockIdx.x;
   const int chunk = b % NC;
@@ -295,8 +295,8 @@ __global__ void __launch_bounds__(kThreads) k_inv_z(Grid g, int LB, const double
   double2* bufB = smem + 9 * LB * M;
   double2* twM = bufB + 9 * LB * M;
   double2* twN = twM + M;
-  stage_twiddles(twM, tw, M, M);
-  stage_twiddles(twN, tw, NZ, M / 2 + 1);
+  stage_twiddles<M>(twM, tw, M);
+  stage_twiddles<NZ>(twN, tw, M / 2 + 1);
   __syncthreads();
   const long long line0 = (long long)blockIdx.x * LB;
   const long long n = g.n;
@@ -342,18 +342,14 @@ __global__ void __launch_bounds__(kThreads) k_inv_z(Grid g, int LB, const double
 // ---------------------------------------------------------------------------
 // host side: tiling, dispatch on the compile-time lengths
 // ---------------------------------------------------------------------------
-static int ilog2(int v) {
-  int r = 0;
-  while ((1 << r) < v) ++r;
-  return r;
-}
-
 Tiling choose_tiling(const Grid& g) {
   Tiling t;
   const long long lines = (long long)g.nx * g.ny;
+  // z lines per CTA: the largest divisor of nx*ny not above 512 / nz
   int lb = 512 / g.nz;
   if (lb < 1) lb = 1;
   if (lb > lines) lb = (int)lines;
+  while (lines % lb) --lb;
   t.lines_z = lb;
   int by = 512 / g.ny;
   if (by < 1) by = 1;
@@ -375,17 +371,44 @@ static size_t y_smem(int L, int bk, int fields) {
   return ((size_t)2 * fields * bk * (L + 1) + L) * sizeof(double2);
 }
 
-#define FH_SWITCH_POW2(v, MACRO) \
+#define FH_SWITCH_LEN(v, MACRO) \
   switch (v) {                   \
     MACRO(1)                     \
     MACRO(2)                     \
+    MACRO(3)                     \
     MACRO(4)                     \
+    MACRO(6)                     \
     MACRO(8)                     \
+    MACRO(12)                    \
     MACRO(16)                    \
+    MACRO(24)                    \
     MACRO(32)                    \
+    MACRO(48)                    \
     MACRO(64)                    \
+    MACRO(96)                    \
     MACRO(128)                   \
+    MACRO(192)                   \
     MACRO(256)                   \
+    default:                     \
+      return cudaErrorInvalidValue; \
+  }
+// half lengths of the real-to-complex axis (nz/2 <= 128)
+#define FH_SWITCH_HALF(v, MACRO) \
+  switch (v) {                   \
+    MACRO(1)                     \
+    MACRO(2)                     \
+    MACRO(3)                     \
+    MACRO(4)                     \
+    MACRO(6)                     \
+    MACRO(8)                     \
+    MACRO(12)                    \
+    MACRO(16)                    \
+    MACRO(24)                    \
+    MACRO(32)                    \
+    MACRO(48)                    \
+    MACRO(64)                    \
+    MACRO(96)                    \
+    MACRO(128)                   \
     default:                     \
       return cudaErrorInvalidValue; \
   }
@@ -409,22 +432,21 @@ cudaError_t setup_fft_kernels(const Grid& g, const Tiling& t) {
     if ((e = allow_smem(k_inv_z<V, kIZDot>, zs))) return e;           \
     if ((e = allow_smem(k_inv_z<V, kIZRhs>, zs))) return e;           \
     break;
-  FH_SWITCH_POW2(M, ZCASE)
+  FH_SWITCH_HALF(M, ZCASE)
 #undef ZCASE
 #define YCASE(V)                                                           \
   case V:                                                                  \
     if ((e = allow_smem(k_fwd_y<V>, y_smem(V, t.bk_y, 3)))) return e;      \
     if ((e = allow_smem(k_inv_y<V>, y_smem(V, t.bk_y, 3)))) return e;      \
     break;
-  FH_SWITCH_POW2(g.ny, YCASE)
+  FH_SWITCH_LEN(g.ny, YCASE)
 #undef YCASE
 #define XCASE(V)                                                           \
   case V:                                                                  \
     if ((e = allow_smem(k_x_ghat<V>, y_smem(V, t.bk_x, 6)))) return e;     \
     break;
-  FH_SWITCH_POW2(g.nx, XCASE)
+  FH_SWITCH_LEN(g.nx, XCASE)
 #undef XCASE
-  (void)ilog2;
   return cudaSuccess;
 }
 
@@ -443,7 +465,7 @@ cudaError_t launch_fwd_z(const Grid& g, const Tiling& t, int mode, const double*
       default: return cudaErrorInvalidValue;                                                               \
     }                                                                                                      \
     break;
-  FH_SWITCH_POW2(M, ZL)
+  FH_SWITCH_HALF(M, ZL)
 #undef ZL
   return cudaGetLastError();
 }
@@ -456,7 +478,7 @@ cudaError_t launch_fwd_y(const Grid& g, const Tiling& t, double2* S, const doubl
   case V:                                                                                   \
     k_fwd_y<V><<<grid, kThreads, y_smem(V, t.bk_y, 3), s>>>(g, t.bk_y, S, tw, cg);          \
     break;
-  FH_SWITCH_POW2(g.ny, YL)
+  FH_SWITCH_LEN(g.ny, YL)
 #undef YL
   return cudaGetLastError();
 }
@@ -469,7 +491,7 @@ cudaError_t launch_x_ghat(const Grid& g, const Tiling& t, double2* S, const doub
   case V:                                                                                          \
     k_x_ghat<V><<<grid, kThreads, y_smem(V, t.bk_x, 6), s>>>(g, t.bk_x, S, tw, scale, cg);         \
     break;
-  FH_SWITCH_POW2(g.nx, XL)
+  FH_SWITCH_LEN(g.nx, XL)
 #undef XL
   return cudaGetLastError();
 }
@@ -482,7 +504,7 @@ cudaError_t launch_inv_y(const Grid& g, const Tiling& t, double2* S, const doubl
   case V:                                                                                   \
     k_inv_y<V><<<grid, kThreads, y_smem(V, t.bk_y, 3), s>>>(g, t.bk_y, S, tw, cg);          \
     break;
-  FH_SWITCH_POW2(g.ny, IYL)
+  FH_SWITCH_LEN(g.ny, IYL)
 #undef IYL
   return cudaGetLastError();
 }
@@ -501,7 +523,7 @@ cudaError_t launch_inv_z(const Grid& g, const Tiling& t, int mode, const double2
       default: return cudaErrorInvalidValue;                                                                    \
     }                                                                                                           \
     break;
-  FH_SWITCH_POW2(M, IZL)
+  FH_SWITCH_HALF(M, IZL)
 #undef IZL
   return cudaGetLastError();
 }

@@ -41,7 +41,8 @@ StaticSlot g_static_slots[kMaxDevices];
 void fill_twiddles(std::vector<double2>& t) {
   t.assign(kTwiddleTotal, make_double2(0.0, 0.0));
   const long double two_pi = 6.283185307179586476925286766559005768L;
-  for (int L = 1; L <= kMaxN; L *= 2) {
+  for (int L = 1; L <= kMaxN; ++L) {
+    if (!fft_length_ok(L)) continue;
     for (int m = 0; m < L; ++m) {
       double c, s;
       if ((4 * m) % L == 0) {
@@ -87,7 +88,6 @@ int static_setup(int dev, StaticSlot** out, char* msg, size_t len) {
   return FH_OK;
 }
 
-bool is_pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
 
 }  // namespace
 }  // namespace fh
@@ -108,9 +108,9 @@ extern "C" int fh_project_static(const double* A_dev, double* out_dev, int nx, i
     snprintf(msg, sizeof msg, "fh_project_static: NULL field pointer");
     return fail(FH_ERR_ARG);
   }
-  if (!is_pow2_in(nx, 1, kMaxN) || !is_pow2_in(ny, 1, kMaxN) || !is_pow2_in(nz, 2, kMaxN)) {
-    snprintf(msg, sizeof msg, "fh_project_static: grid %dx%dx%d: extents must be powers of two, nx,ny in [1,256], "
-             "nz in [2,256]", nx, ny, nz);
+  if (!grid_extents_ok(nx, ny, nz)) {
+    snprintf(msg, sizeof msg, "fh_project_static: grid %dx%dx%d: each extent must be 2^a or 3*2^a up to 256, and "
+             "nz even with nz/2 of that form", nx, ny, nz);
     return fail(FH_ERR_ARG);
   }
   const long long n = (long long)nx * ny * nz;

@@ -90,7 +90,10 @@ def test_out_of_range_phase_is_reported(fh, torch):
 # a3/a4: projection and matrix-vector product
 # ---------------------------------------------------------------------------
 PROJ_SHAPES = [(8, 8, 8), (4, 8, 16), (16, 4, 2), (2, 2, 2), (1, 4, 8), (32, 16, 8), (8, 1, 32),
-               (256, 2, 2), (2, 256, 2), (2, 2, 256), (64, 32, 128)]
+               (256, 2, 2), (2, 256, 2), (2, 2, 256), (64, 32, 128),
+               # radix-3 lengths (3 * 2^a), odd axes and odd half lengths
+               (48, 12, 6), (3, 6, 24), (96, 8, 4), (6, 3, 96), (24, 48, 12), (192, 2, 2), (2, 2, 192),
+               (12, 12, 12)]
 
 
 @pytest.mark.parametrize("shape", PROJ_SHAPES)
@@ -184,6 +187,17 @@ def test_anisotropic_box_and_ragged_grid(fh, torch, kind):
     Fbar = np.eye(3).reshape(9) + rng.uniform(-0.03, 0.03, 9)
     Fg, pbar, stats, _, ref = _solve_both(fh, torch, phase, params, kind, Fbar, 2, 1e-10,
                                           lengths=(1.0, 2.0, 0.5))
+    np.testing.assert_allclose(pbar, ref.Pbar, rtol=PBAR_TOL, atol=PBAR_TOL * np.abs(ref.Pbar).max())
+    assert np.abs(Fg - ref.F).max() < FIELD_TOL * np.abs(ref.F - Fbar.reshape(9, 1, 1, 1)).max()
+
+
+def test_radix3_grid_solve_matches_oracle(fh, torch):
+    shape = (12, 24, 12)
+    phase = random_spheres(shape, seed=4, r_min=1.5, r_max=3.0)
+    params = two_phase_table(1.5, 1.0, 10.0)
+    Fbar = shear_macro(0.05, finite=True)
+    Fg, pbar, stats, _, ref = _solve_both(fh, torch, phase, params, 1, Fbar, 2, 1e-10)
+    assert stats["n_newton"] == len(ref.newton_residuals)
     np.testing.assert_allclose(pbar, ref.Pbar, rtol=PBAR_TOL, atol=PBAR_TOL * np.abs(ref.Pbar).max())
     assert np.abs(Fg - ref.F).max() < FIELD_TOL * np.abs(ref.F - Fbar.reshape(9, 1, 1, 1)).max()
 

@@ -127,3 +127,23 @@ def test_simp_64_voigt_tangent_and_sensitivity_vs_finite_differences(fh):
             fd = (vals[0] - vals[1]) / (2 * h)
             errs.append(abs(fd - s[v]) / abs(s[v]))
         assert max(errs) < 1e-4, (max(errs), float(np.median(errs)))
+
+
+def test_eshelby_2d_mode_matches_oracle_and_table1(fh):
+    """2D plane strain as a z-invariant 192 x 192 x 2 cell (Section 4.2.1, Table 1)."""
+    import json
+    import os
+
+    from test_oracle_eshelby import GOLDEN, dilute_estimate, eshelby_cell
+
+    phase, f = eshelby_cell(192, nz=2)
+    params = np.array([[2.0, 1.0], [10.0, 5.0]])
+    zero = np.zeros((9,) + phase.shape)
+    C_ref = homogenize.tangent(phase, params, 0, zero, cg_tol=1e-12)
+    with fh.Context(*phase.shape) as ctx:
+        C = ctx.fft_homog_tangent(fh.Material(0, phase, params), dev(zero), options=fh.default_options(cg_tol=1e-12))
+    assert np.abs(C - C_ref).max() < TOL * np.abs(C_ref).max()
+    with open(GOLDEN) as fp:
+        num = json.load(fp)["numerical"]
+    np.testing.assert_allclose([C[0, 0], C[4, 4], C[1, 1]], [num["Cxxxx"], num["Cyyyy"], num["Cxyxy"]], rtol=3e-3)
+    np.testing.assert_allclose([C[0, 0], C[1, 1]], dilute_estimate(f), rtol=2e-4)

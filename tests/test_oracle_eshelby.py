@@ -1,0 +1,57 @@
+"""Eshelby validation of Section 4.2.1 (Table 1): a dilute circular inclusion in 2D.
+
+A 2D plane-strain cell is a z-invariant 3D cell: with one voxel along z
+(oracle) every wave vector has xi_z = 0. The homogenized tangent of the
+oracle is compared with
+* the values printed in Table 1 (tests/golden/eshelby_table1.json), loosely
+  (0.3 %): the paper's grid (199^2), its voxelisation and its analytical
+  formula are not stated in full;
+* the dilute estimate for a circular inclusion in plane strain, written out
+  here from the classical 2D Eshelby solution: with the plane bulk modulus
+  k = lambda + mu, the inclusion strain is A_k times the far-field volumetric
+  strain and A_mu times its deviatoric part,
+      A_k  = (k_m + mu_m) / (k_i + mu_m),
+      A_mu = (mu_m + eta) / (mu_i + eta),  eta = mu_m k_m / (k_m + 2 mu_m),
+  so that k_eff = k_m + f (k_i - k_m) A_k and mu_eff = mu_m + f (mu_i - mu_m) A_mu,
+  C_xxxx = k_eff + mu_eff, C_xyxy = mu_eff (dilute: error O(f^2)).
+"""
+
+import json
+import os
+
+import numpy as np
+
+from oracle import homogenize
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "eshelby_table1.json")
+
+
+def eshelby_cell(n, nz=1, fraction=0.007):
+    r = np.sqrt(fraction / np.pi) * n
+    x = np.arange(n) + 0.5 - n / 2
+    ph2 = ((x[:, None] ** 2 + x[None, :] ** 2) <= r * r).astype(np.uint8)
+    return np.repeat(ph2[:, :, None], nz, axis=2), float(ph2.mean())
+
+
+def dilute_estimate(f, lam_m=2.0, mu_m=1.0, lam_i=10.0, mu_i=5.0):
+    k_m, k_i = lam_m + mu_m, lam_i + mu_i
+    a_k = (k_m + mu_m) / (k_i + mu_m)
+    eta = mu_m * k_m / (k_m + 2 * mu_m)
+    a_mu = (mu_m + eta) / (mu_i + eta)
+    k = k_m + f * (k_i - k_m) * a_k
+    mu = mu_m + f * (mu_i - mu_m) * a_mu
+    return k + mu, mu
+
+
+def test_eshelby_table1_and_dilute_estimate():
+    with open(GOLDEN) as fh:
+        table = json.load(fh)
+    phase, f = eshelby_cell(99)
+    params = np.array([[2.0, 1.0], [10.0, 5.0]])
+    C = homogenize.tangent(phase, params, 0, np.zeros((9,) + phase.shape), cg_tol=1e-10)
+    cxxxx, cyyyy, cxyxy = C[0, 0], C[4, 4], C[1, 1]
+    np.testing.assert_allclose(cxxxx, cyyyy, rtol=1e-12)
+    num = table["numerical"]
+    np.testing.assert_allclose([cxxxx, cyyyy, cxyxy], [num["Cxxxx"], num["Cyyyy"], num["Cxyxy"]], rtol=3e-3)
+    d_xxxx, d_xyxy = dilute_estimate(f)
+    np.testing.assert_allclose([cxxxx, cxyxy], [d_xxxx, d_xyxy], rtol=2e-4)
