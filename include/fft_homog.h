@@ -204,6 +204,47 @@ FH_API int fft_homog_tangent(fh_ctx* ctx, const fh_material* mat, const double* 
 FH_API int fft_homog_sensitivity(fh_ctx* ctx, const fh_material* mat, const fh_options* opt, int i, int j,
                                  int k, int l, const double* dscale_dev, double* out_dev);
 
+/* Pick the tile shapes of the five projection passes for this context's grid
+ * by timing them: z lines per CTA in the z passes, kz columns per CTA in the
+ * y and x passes (a handful of candidates around the default, all within the
+ * per-CTA shared-memory limit), `reps` projections each. The fastest is kept
+ * for every later call on the context. Optional outputs: best_ms (time of
+ * one projection) and chosen[3] = (z lines, y columns, x columns). */
+FH_API int fh_autotune(fh_ctx* ctx, int reps, double* best_ms, int chosen[3]);
+
+/* ---- batched solves of many cells (Section 4.4.1's many-sample setting) ----
+ * A batch binds cells of possibly different grids; each keeps its own Newton
+ * and CG state (its own convergence), while every pass of the solve is one
+ * launch per group of equal grids and the CG iterations of the whole batch
+ * run as a captured CUDA graph. */
+typedef struct fh_batch fh_batch;
+
+typedef struct fh_cell {
+  int nx, ny, nz;               /* grid, as for fh_create */
+  const unsigned char* phase;   /* device uint8[N] */
+  const double* scale;          /* device double[N] modulus multiplier, or NULL */
+  double* F;                    /* device [9][N]: the cell's converged field on return */
+} fh_cell;
+
+/* Create a batch over n_cells cells whose device arrays the caller owns and
+ * keeps alive until fh_batch_destroy. Allocates each cell's scratch (about
+ * 700 bytes per voxel). cuda_stream NULL: the batch uses a stream of its own
+ * (CUDA graphs cannot be captured on the legacy stream). */
+FH_API int fh_batch_create(fh_batch** out, const fh_cell* cells, int n_cells, void* cuda_stream);
+FH_API void fh_batch_destroy(fh_batch* batch);
+
+/* Solve every cell of the batch under the same material law (kind, n_phase,
+ * host params[n_phase][2]), macroscopic tensor and options, as
+ * fft_homog_solve does for one cell (Algorithm 1), from the reference state,
+ * with the tangent stored and unit boxes. Per-cell outputs (host arrays of
+ * n_cells entries, each may be NULL): Pbar_out[9 * i + c], status_out[i]
+ * (FH_OK, FH_ERR_NOT_CONVERGED or FH_ERR_NONPHYSICAL), newton_out[i] and
+ * cg_out[i] (iteration totals). Returns FH_OK when every cell converged,
+ * else the first failing cell's status. */
+FH_API int fft_homog_solve_batched(fh_batch* batch, int kind, int n_phase, const double* params,
+                                   const double Fbar[9], int n_increments, const fh_options* opt,
+                                   double* Pbar_out, int* status_out, int* newton_out, int* cg_out);
+
 /* ---- launch accounting and per-kernel device time ----
  * Kernel classes, in slot order: 0 forward z pass (stress/tangent apply +
  * real-to-complex), 1 forward y pass, 2 x pass with Ghat, 3 inverse y pass,

@@ -39,7 +39,8 @@ _ERR_NAMES = {1: "FH_ERR_ARG", 2: "FH_ERR_CUDA", 3: "FH_ERR_NOT_CONVERGED", 4: "
 
 # every symbol include/fft_homog.h declares
 EXPORTS = ["fh_default_options", "fh_create", "fh_destroy", "fh_last_error_string", "fh_constitutive",
-           "fh_project", "fh_matvec", "fft_homog_solve", "fh_profile_enable", "fh_profile_read", "fh_project_static", "fft_homog_tangent", "fft_homog_sensitivity"]
+           "fh_project", "fh_matvec", "fft_homog_solve", "fh_profile_enable", "fh_profile_read", "fh_project_static", "fft_homog_tangent", "fft_homog_sensitivity",
+           "fh_batch_create", "fh_batch_destroy", "fft_homog_solve_batched", "fh_autotune"]
 
 PROF_NCLASS = 13
 PROF_CLASSES = ["fwd_z", "fwd_y", "x_ghat", "inv_y", "inv_z", "constitutive", "jvp", "cg_scalar", "cg_update",
@@ -61,6 +62,11 @@ class FhOptions(ctypes.Structure):
     _fields_ = [("newton_tol", c_double), ("cg_tol", c_double), ("max_newton", c_int), ("max_cg", c_int),
                 ("init", c_int), ("tangent_mode", c_int), ("check_every", c_int), ("reserved", c_int),
                 ("lengths", c_double * 3)]
+
+
+class FhCell(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int), ("phase", c_void_p), ("scale", c_void_p),
+                ("F", c_void_p)]
 
 
 class FhStats(ctypes.Structure):
@@ -116,6 +122,16 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.fft_homog_sensitivity.argtypes = [c_void_p, POINTER(FhMaterial), POINTER(FhOptions), c_int, c_int, c_int,
                                           c_int, c_void_p, c_void_p]
     lib.fft_homog_sensitivity.restype = c_int
+    lib.fh_batch_create.argtypes = [POINTER(c_void_p), POINTER(FhCell), c_int, c_void_p]
+    lib.fh_batch_create.restype = c_int
+    lib.fh_batch_destroy.argtypes = [c_void_p]
+    lib.fh_batch_destroy.restype = None
+    lib.fft_homog_solve_batched.argtypes = [c_void_p, c_int, c_int, POINTER(c_double), POINTER(c_double), c_int,
+                                            POINTER(FhOptions), POINTER(c_double), POINTER(c_int), POINTER(c_int),
+                                            POINTER(c_int)]
+    lib.fft_homog_solve_batched.restype = c_int
+    lib.fh_autotune.argtypes = [c_void_p, c_int, POINTER(c_double), POINTER(c_int)]
+    lib.fh_autotune.restype = c_int
     _lib = lib
     return lib
 
@@ -245,6 +261,16 @@ class Context:
         _check(load().fh_matvec(self._h, mat.c if mat is not None else None, _ptr(F), _ptr(K), _ptr(p), _ptr(y),
                                 La[1]))
 
+    def fh_autotune(self, reps: int = 3):
+        """Time candidate tile shapes of the projection passes and keep the fastest.
+
+        Returns (ms per projection, (z lines per CTA, y columns, x columns)).
+        """
+        ms = c_double()
+        ch = (c_int * 3)()
+        _check(load().fh_autotune(self._h, int(reps), ctypes.byref(ms), ch))
+        return ms.value, tuple(ch)
+
     def fh_profile_enable(self, enable: bool = True):
         _check(load().fh_profile_enable(self._h, 1 if enable else 0))
 
@@ -285,3 +311,72 @@ class Context:
         stats = {"n_newton": st.n_newton, "n_cg": st.n_cg, "time_ms": st.time_ms,
                  "newton_residuals": res[:st.n_recorded].tolist(), "cg_iterations": cgi[:st.n_recorded].tolist()}
         return pbar, stats, rc
+
+
+class Batch:
+    """An fh_batch: many cells of possibly different grids solved together.
+
+    cells: list of (phase, scale or None) with phase a uint8 array or CUDA
+    tensor of the cell's grid shape. The batch owns one CUDA float64 field per
+    cell (``self.F[i]``, shape (9, nx, ny, nz)).
+    """
+
+    def __init__(self, cells, stream=None):
+        import torch
+
+        lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.phase, self.scale, self.F = [], [], []
+        arr = (FhCell * len(cells))()
+        for i, (ph, sc) in enumerate(cells):
+            if not isinstance(ph, torch.Tensor):
+                ph = torch.as_tensor(np.ascontiguousarray(ph, dtype=np.uint8))
+            ph = ph.to(device="cuda", dtype=torch.uint8).contiguous()
+            if sc is not None:
+                if not isinstance(sc, torch.Tensor):
+                    sc = torch.as_tensor(np.ascontiguousarray(sc, dtype=np.float64))
+                sc = sc.to(device="cuda", dtype=torch.float64).contiguous()
+            F = torch.zeros((9,) + tuple(ph.shape), dtype=torch.float64, device="cuda")
+            self.phase.append(ph)
+            self.scale.append(sc)
+            self.F.append(F)
+            nx, ny, nz = ph.shape
+            arr[i] = FhCell(nx, ny, nz, ph.data_ptr(), sc.data_ptr() if sc is not None else None, F.data_ptr())
+        h = c_void_p()
+        _check(lib.fh_batch_create(ctypes.byref(h), arr, len(cells), c_void_p(stream)))
+        self._h = h
+        self.n = len(cells)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().fh_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def fft_homog_solve_batched(self, kind, params, Fbar, n_increments=1, options=None, allow=()):
+        """Returns (Pbar (n, 9), status (n,), newton (n,), cg (n,), return code)."""
+        pa, pp = _dvec(params)
+        fb, fbp = _dvec(Fbar, 9)
+        pbar = np.zeros((self.n, 9))
+        st = np.zeros(self.n, dtype=np.int32)
+        nw = np.zeros(self.n, dtype=np.int32)
+        cg = np.zeros(self.n, dtype=np.int32)
+        rc = load().fft_homog_solve_batched(self._h, int(kind), pa.size // 2, pp, fbp, int(n_increments),
+                                            ctypes.byref(options) if options is not None else None,
+                                            pbar.ctypes.data_as(POINTER(c_double)),
+                                            st.ctypes.data_as(POINTER(c_int)), nw.ctypes.data_as(POINTER(c_int)),
+                                            cg.ctypes.data_as(POINTER(c_int)))
+        _check(rc, allow=allow)
+        return pbar, st, nw, cg, rc

@@ -299,7 +299,7 @@ int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
   c->tiling = choose_tiling(g);
   const size_t f9 = (size_t)9 * g.n * sizeof(double);
   long long np = 9LL * constitutive_ctas(g);
-  np = std::max(np, z_pass_ctas(g, c->tiling));
+  np = std::max(np, (long long)nx * ny);  // z passes with one line per CTA (any autotuned tiling)
   np = std::max(np, cg_update_ctas(g));
   np = std::max(np, newton_update_ctas(g));
   c->n_partials = np;
@@ -641,6 +641,88 @@ int fft_homog_sensitivity(fh_ctx* ctx, const fh_material* mat, const fh_options*
   }));
   FH_CUDA(cudaStreamSynchronize(s));
   prof_flush(ctx);
+  return FH_OK;
+}
+
+namespace {
+
+// z lines per CTA must divide nx*ny; shared memory of a z pass must fit a CTA
+bool tiling_fits(const Grid& g, const Tiling& t) {
+  const long long lines = (long long)g.nx * g.ny;
+  if (t.lines_z < 1 || lines % t.lines_z) return false;
+  if (t.bk_y < 1 || t.bk_y > g.nzh || t.bk_x < 1 || t.bk_x > g.nzh) return false;
+  const size_t limit = 227 * 1024;
+  const size_t zs = ((size_t)9 * t.lines_z * g.nz + g.nz) * sizeof(double2);
+  const size_t ys = ((size_t)2 * 3 * t.bk_y * (g.ny + 1) + g.ny) * sizeof(double2);
+  const size_t xs = ((size_t)2 * 6 * t.bk_x * (g.nx + 1) + g.nx) * sizeof(double2);
+  return zs <= limit && ys <= limit && xs <= limit;
+}
+
+}  // namespace
+
+int fh_autotune(fh_ctx* ctx, int reps, double* best_ms, int chosen[3]) {
+  g_err[0] = 0;
+  if (!ctx) return fail(FH_ERR_ARG, "context is NULL");
+  if (reps < 1) reps = 3;
+  DeviceGuard dg(ctx->dev);
+  cudaStream_t s = ctx->stream;
+  const Grid& g = ctx->g;
+  const Tiling base = choose_tiling(g);
+  std::vector<Tiling> cand;
+  for (int fz : {1, 2, 4}) {
+    for (int fy : {1, 2}) {
+      for (int fx : {1, 2}) {
+        Tiling t = base;
+        t.lines_z = std::max(1, base.lines_z * fz / 2);
+        while ((long long)g.nx * g.ny % t.lines_z) --t.lines_z;
+        t.bk_y = std::min(g.nzh, std::max(1, base.bk_y * fy));
+        t.bk_x = std::min(g.nzh, std::max(1, base.bk_x * fx));
+        if (!tiling_fits(g, t)) continue;
+        bool dup = false;
+        for (const Tiling& u : cand) dup |= (u.lines_z == t.lines_z && u.bk_y == t.bk_y && u.bk_x == t.bk_x);
+        if (!dup) cand.push_back(t);
+      }
+    }
+  }
+  cudaEvent_t e0, e1;
+  FH_CUDA(cudaEventCreate(&e0));
+  FH_CUDA(cudaEventCreate(&e1));
+  FH_CUDA(cudaMemsetAsync(ctx->y, 0, (size_t)9 * g.n * sizeof(double), s));
+  const Tiling keep = ctx->tiling;
+  float best = 1e30f;
+  Tiling best_t = keep;
+  for (const Tiling& t : cand) {
+    ctx->tiling = t;
+    cudaError_t e = setup_fft_kernels(g, t);
+    if (e != cudaSuccess) continue;
+    int rc = run_projection(ctx, g, kZDirect, ctx->y, nullptr, nullptr, 1.0, kIZOut, ctx->p, nullptr, nullptr);
+    if (rc) continue;
+    FH_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r)
+      if ((rc = run_projection(ctx, g, kZDirect, ctx->y, nullptr, nullptr, 1.0, kIZOut, ctx->p, nullptr, nullptr)))
+        break;
+    FH_CUDA(cudaEventRecord(e1, s));
+    FH_CUDA(cudaEventSynchronize(e1));
+    if (rc) continue;
+    float ms = 0.f;
+    FH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    ms /= reps;
+    if (ms < best) {
+      best = ms;
+      best_t = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  prof_flush(ctx);
+  ctx->tiling = best_t;
+  FH_CUDA(setup_fft_kernels(g, best_t));
+  if (best_ms) *best_ms = best;
+  if (chosen) {
+    chosen[0] = best_t.lines_z;
+    chosen[1] = best_t.bk_y;
+    chosen[2] = best_t.bk_x;
+  }
   return FH_OK;
 }
 

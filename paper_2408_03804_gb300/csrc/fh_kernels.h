@@ -34,6 +34,40 @@ struct CgScalars {
   int pad;
 };
 
+// per-cell pointers of a batched launch (device array, one entry per cell of a
+// group of equal grids); `stop` is the cell's skip flag for this launch
+struct CellView {
+  const int* stop;          // skip the cell when *stop != 0 (its CG done flag, or its Newton flag)
+  const double* src;        // forward z pass input: P (right-hand side) or r (CG)
+  double* p;
+  double* x;
+  const double* K;
+  const CgScalars* cg;
+  double2* S;
+  double* out;              // inverse z pass output: r (right-hand side) or y (CG)
+  double* partials;         // this cell's partial sums
+};
+
+// per-cell state of a batched solve (device array, one entry per cell of a
+// group of equal grids)
+struct CellState {
+  double* F;
+  double* x;
+  double* r;
+  double* p;
+  double* y;
+  double* P;
+  double* K;
+  double2* S;
+  double* partials;
+  double* sums;             // 16 doubles: reductions read by the host
+  CgScalars* cg;
+  const uint8_t* phase;
+  const double* scale;
+  const int* newton_done;   // set once the cell's Newton loop has finished
+  int* flags;
+};
+
 struct Tiling {
   int lines_z;   // z lines per CTA in the z passes
   int bk_y;      // kz columns per CTA in the y passes
@@ -56,6 +90,17 @@ cudaError_t launch_inv_y(const Grid& g, const Tiling& t, double2* S, const doubl
 cudaError_t launch_inv_z(const Grid& g, const Tiling& t, int mode, const double2* S, double* out, const double* p,
                          double* partials, const double2* tw, const CgScalars* cg, cudaStream_t s);
 
+cudaError_t launch_fwd_z_batch(const Grid& g, const Tiling& t, int mode, const CellView* cells, int n_cells,
+                               const double2* tw, cudaStream_t s);
+cudaError_t launch_fwd_y_batch(const Grid& g, const Tiling& t, const CellView* cells, int n_cells,
+                               const double2* tw, cudaStream_t s);
+cudaError_t launch_x_ghat_batch(const Grid& g, const Tiling& t, const CellView* cells, int n_cells,
+                                const double2* tw, double scale, cudaStream_t s);
+cudaError_t launch_inv_y_batch(const Grid& g, const Tiling& t, const CellView* cells, int n_cells,
+                               const double2* tw, cudaStream_t s);
+cudaError_t launch_inv_z_batch(const Grid& g, const Tiling& t, int mode, const CellView* cells, int n_cells,
+                               const double2* tw, cudaStream_t s);
+
 // pointwise kernels (kernels_pointwise.cu)
 long long constitutive_ctas(const Grid& g);
 cudaError_t launch_constitutive(const Grid& g, const MatView& m, const double* F, double* P, double* K,
@@ -75,6 +120,18 @@ cudaError_t launch_cg_finalize(const Grid& g, const CgScalars* cg, double* x, co
 cudaError_t launch_cg_beta(CgScalars* cg, const double* partials, int n_parts, cudaStream_t s);
 cudaError_t launch_newton_update(const Grid& g, double* F, const double* dF, double* partials, cudaStream_t s);
 long long newton_update_ctas(const Grid& g);
+cudaError_t launch_constitutive_batch(const Grid& g, int kind, const double* params, const CellState* cells,
+                                      int n_cells, int store_K, cudaStream_t s);
+cudaError_t launch_cg_init_batch(const CellState* cells, int n_cells, int n_parts, double tol, int max_it,
+                                 cudaStream_t s);
+cudaError_t launch_cg_alpha_batch(const CellState* cells, int n_cells, int n_parts, cudaStream_t s);
+cudaError_t launch_cg_update_batch(const Grid& g, const CellState* cells, int n_cells, cudaStream_t s);
+cudaError_t launch_cg_beta_batch(const CellState* cells, int n_cells, int n_parts, cudaStream_t s);
+cudaError_t launch_cg_finalize_batch(const Grid& g, const CellState* cells, int n_cells, cudaStream_t s);
+cudaError_t launch_newton_update_batch(const Grid& g, const CellState* cells, int n_cells, cudaStream_t s);
+cudaError_t launch_sum_partials_batch(const CellState* cells, int n_cells, int n_parts, int width, cudaStream_t s);
+cudaError_t launch_fill_batch(const Grid& g, const CellState* cells, int n_cells, int field, const double* value9,
+                              int add, cudaStream_t s);
 long long kapply_sums_ctas(const Grid& g);
 cudaError_t launch_kapply_sums(const Grid& g, const double* K, const double* x, int cd, double* partials,
                                cudaStream_t s);

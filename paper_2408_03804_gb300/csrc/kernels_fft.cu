@@ -36,11 +36,10 @@ __device__ __forceinline__ bool cg_done(const CgScalars* cg) { return cg != null
 // forward z pass: real-to-complex along z of LB consecutive z lines
 // ---------------------------------------------------------------------------
 template <int M, int MODE>
-__global__ void __launch_bounds__(kThreads) k_fwd_z(Grid g, int LB, const double* __restrict__ src,
+__device__ __forceinline__ void fwd_z_body(int cta, Grid g, int LB, const double* __restrict__ src,
                                                    double* __restrict__ p, double* __restrict__ x,
                                                    const double* __restrict__ K, const CgScalars* __restrict__ cg,
                                                    double2* __restrict__ S, const double2* __restrict__ tw) {
-  if (cg_done(cg)) return;
   extern __shared__ double2 smem[];
   constexpr int NZ = 2 * M;
   double2* bufA = smem;
@@ -50,7 +49,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_z(Grid g, int LB, const double
   stage_twiddles<M>(twM, tw, M);
   stage_twiddles<NZ>(twN, tw, M / 2 + 1);
   double* ra = reinterpret_cast<double*>(bufA);
-  const long long line0 = (long long)blockIdx.x * LB;
+  const long long line0 = (long long)cta * LB;
   const long long v0 = line0 * NZ;
   const long long n = g.n;
   double beta = 0.0, alpha = 0.0;
@@ -129,9 +128,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd_z(Grid g, int LB, const double
 // forward y pass: row i, columns j = x, y, z along y; combine W_i
 // ---------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(kThreads, 3) k_fwd_y(Grid g, int BK, double2* __restrict__ S,
+__device__ __forceinline__ void fwd_y_body(int cta, Grid g, int BK, double2* __restrict__ S,
                                                    const double2* __restrict__ tw, const CgScalars* __restrict__ cg) {
-  if (cg_done(cg)) return;
   extern __shared__ double2 smem[];
   constexpr int QS = L + 1;
   const int np = 3 * BK;
@@ -140,7 +138,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_fwd_y(Grid g, int BK, double2* 
   double2* twL = bufB + np * QS;
   stage_twiddles<L>(twL, tw, L);
   const int NC = (g.nzh + BK - 1) / BK;
-  int b = blockIdx.x;
+  int b = cta;
   const int chunk = b % NC;
   b /= NC;
   const int i = b % 3;
@@ -174,10 +172,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_fwd_y(Grid g, int BK, double2* 
 // x pass: forward along x, Ghat, inverse along x
 // ---------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(kThreads, 3) k_x_ghat(Grid g, int BK, double2* __restrict__ S,
+__device__ __forceinline__ void x_ghat_body(int cta, Grid g, int BK, double2* __restrict__ S,
                                                     const double2* __restrict__ tw, double scale,
                                                     const CgScalars* __restrict__ cg) {
-  if (cg_done(cg)) return;
   extern __shared__ double2 smem[];
   constexpr int QS = L + 1;
   const int np = 6 * BK;
@@ -186,8 +183,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_x_ghat(Grid g, int BK, double2*
   double2* twL = bufB + np * QS;
   stage_twiddles<L>(twL, tw, L);
   const int NC = (g.nzh + BK - 1) / BK;
-  const int chunk = blockIdx.x % NC;
-  const int ky = blockIdx.x / NC;
+  const int chunk = cta % NC;
+  const int ky = cta / NC;
   const int kz0 = chunk * BK;
   const int valid = min(BK, g.nzh - kz0);
   const long long row = (long long)g.ny * g.nzh;  // stride of x in S
@@ -236,9 +233,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_x_ghat(Grid g, int BK, double2*
 // inverse y pass: expand A_i, B_i to the three columns of row i
 // ---------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(kThreads, 3) k_inv_y(Grid g, int BK, double2* __restrict__ S,
+__device__ __forceinline__ void inv_y_body(int cta, Grid g, int BK, double2* __restrict__ S,
                                                    const double2* __restrict__ tw, const CgScalars* __restrict__ cg) {
-  if (cg_done(cg)) return;
   extern __shared__ double2 smem[];
   constexpr int QS = L + 1;
   const int np = 3 * BK;
@@ -247,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_inv_y(Grid g, int BK, double2* 
   double2* twL = bufB + np * QS;
   stage_twiddles<L>(twL, tw, L);
   const int NC = (g.nzh + BK - 1) / BK;
-  int b = blockIdx.x;
+  int b = cta;
   const int chunk = b % NC;
   b /= NC;
   const int i = b % 3;
@@ -283,11 +279,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_inv_y(Grid g, int BK, double2* 
 // inverse z pass: complex-to-real along z, optional dot-product epilogue
 // ---------------------------------------------------------------------------
 template <int M, int MODE>
-__global__ void __launch_bounds__(kThreads) k_inv_z(Grid g, int LB, const double2* __restrict__ S,
+__device__ __forceinline__ void inv_z_body(int cta, Grid g, int LB, const double2* __restrict__ S,
                                                    double* __restrict__ out, const double* __restrict__ p,
                                                    double* __restrict__ partials, const double2* __restrict__ tw,
                                                    const CgScalars* __restrict__ cg) {
-  if (cg_done(cg)) return;
   extern __shared__ double2 smem[];
   __shared__ double red[32];
   constexpr int NZ = 2 * M;
@@ -298,7 +293,7 @@ __global__ void __launch_bounds__(kThreads) k_inv_z(Grid g, int LB, const double
   stage_twiddles<M>(twM, tw, M);
   stage_twiddles<NZ>(twN, tw, M / 2 + 1);
   __syncthreads();
-  const long long line0 = (long long)blockIdx.x * LB;
+  const long long line0 = (long long)cta * LB;
   const long long n = g.n;
   // pack Z_k = (X_k + conj X_{M-k}) + i w^-k (X_k - conj X_{M-k}); the
   // imaginary parts of X_0 and X_M are dropped (complex-to-real semantics)
@@ -335,8 +330,85 @@ __global__ void __launch_bounds__(kThreads) k_inv_z(Grid g, int LB, const double
   }
   if constexpr (MODE != kIZOut) {
     const double s = block_sum(acc, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (threadIdx.x == 0) partials[cta] = s;
   }
+}
+
+// ---------------------------------------------------------------------------
+// kernels: one cell (blockIdx.x = CTA of the pass) ...
+// ---------------------------------------------------------------------------
+template <int M, int MODE>
+__global__ void __launch_bounds__(kThreads) k_fwd_z(Grid g, int LB, const double* __restrict__ src,
+                                                   double* __restrict__ p, double* __restrict__ x,
+                                                   const double* __restrict__ K, const CgScalars* __restrict__ cg,
+                                                   double2* __restrict__ S, const double2* __restrict__ tw) {
+  if (cg_done(cg)) return;
+  fwd_z_body<M, MODE>(blockIdx.x, g, LB, src, p, x, K, cg, S, tw);
+}
+template <int L>
+__global__ void __launch_bounds__(kThreads, 3) k_fwd_y(Grid g, int BK, double2* __restrict__ S,
+                                                      const double2* __restrict__ tw, const CgScalars* __restrict__ cg) {
+  if (cg_done(cg)) return;
+  fwd_y_body<L>(blockIdx.x, g, BK, S, tw, cg);
+}
+template <int L>
+__global__ void __launch_bounds__(kThreads, 3) k_x_ghat(Grid g, int BK, double2* __restrict__ S,
+                                                       const double2* __restrict__ tw, double scale,
+                                                       const CgScalars* __restrict__ cg) {
+  if (cg_done(cg)) return;
+  x_ghat_body<L>(blockIdx.x, g, BK, S, tw, scale, cg);
+}
+template <int L>
+__global__ void __launch_bounds__(kThreads, 3) k_inv_y(Grid g, int BK, double2* __restrict__ S,
+                                                      const double2* __restrict__ tw, const CgScalars* __restrict__ cg) {
+  if (cg_done(cg)) return;
+  inv_y_body<L>(blockIdx.x, g, BK, S, tw, cg);
+}
+template <int M, int MODE>
+__global__ void __launch_bounds__(kThreads) k_inv_z(Grid g, int LB, const double2* __restrict__ S,
+                                                   double* __restrict__ out, const double* __restrict__ p,
+                                                   double* __restrict__ partials, const double2* __restrict__ tw,
+                                                   const CgScalars* __restrict__ cg) {
+  if (cg_done(cg)) return;
+  inv_z_body<M, MODE>(blockIdx.x, g, LB, S, out, p, partials, tw, cg);
+}
+
+// ... and a group of cells of one grid shape (blockIdx.y = cell); a cell whose
+// stop flag is set skips the launch
+template <int M, int MODE>
+__global__ void __launch_bounds__(kThreads) k_fwd_z_b(Grid g, int LB, const CellView* __restrict__ cells,
+                                                     const double2* __restrict__ tw) {
+  const CellView& c = cells[blockIdx.y];
+  if (*c.stop) return;
+  fwd_z_body<M, MODE>(blockIdx.x, g, LB, c.src, c.p, c.x, c.K, c.cg, c.S, tw);
+}
+template <int L>
+__global__ void __launch_bounds__(kThreads, 3) k_fwd_y_b(Grid g, int BK, const CellView* __restrict__ cells,
+                                                        const double2* __restrict__ tw) {
+  const CellView& c = cells[blockIdx.y];
+  if (*c.stop) return;
+  fwd_y_body<L>(blockIdx.x, g, BK, c.S, tw, c.cg);
+}
+template <int L>
+__global__ void __launch_bounds__(kThreads, 3) k_x_ghat_b(Grid g, int BK, const CellView* __restrict__ cells,
+                                                         const double2* __restrict__ tw, double scale) {
+  const CellView& c = cells[blockIdx.y];
+  if (*c.stop) return;
+  x_ghat_body<L>(blockIdx.x, g, BK, c.S, tw, scale, c.cg);
+}
+template <int L>
+__global__ void __launch_bounds__(kThreads, 3) k_inv_y_b(Grid g, int BK, const CellView* __restrict__ cells,
+                                                        const double2* __restrict__ tw) {
+  const CellView& c = cells[blockIdx.y];
+  if (*c.stop) return;
+  inv_y_body<L>(blockIdx.x, g, BK, c.S, tw, c.cg);
+}
+template <int M, int MODE>
+__global__ void __launch_bounds__(kThreads) k_inv_z_b(Grid g, int LB, const CellView* __restrict__ cells,
+                                                     const double2* __restrict__ tw) {
+  const CellView& c = cells[blockIdx.y];
+  if (*c.stop) return;
+  inv_z_body<M, MODE>(blockIdx.x, g, LB, c.S, c.out, c.p, c.partials, tw, c.cg);
 }
 
 // ---------------------------------------------------------------------------
@@ -431,6 +503,11 @@ cudaError_t setup_fft_kernels(const Grid& g, const Tiling& t) {
     if ((e = allow_smem(k_inv_z<V, kIZOut>, zs))) return e;           \
     if ((e = allow_smem(k_inv_z<V, kIZDot>, zs))) return e;           \
     if ((e = allow_smem(k_inv_z<V, kIZRhs>, zs))) return e;           \
+    if ((e = allow_smem(k_fwd_z_b<V, kZDirect>, zs))) return e;       \
+    if ((e = allow_smem(k_fwd_z_b<V, kZCg>, zs))) return e;           \
+    if ((e = allow_smem(k_fwd_z_b<V, kZCgFirst>, zs))) return e;      \
+    if ((e = allow_smem(k_inv_z_b<V, kIZDot>, zs))) return e;         \
+    if ((e = allow_smem(k_inv_z_b<V, kIZRhs>, zs))) return e;         \
     break;
   FH_SWITCH_HALF(M, ZCASE)
 #undef ZCASE
@@ -438,12 +515,15 @@ cudaError_t setup_fft_kernels(const Grid& g, const Tiling& t) {
   case V:                                                                  \
     if ((e = allow_smem(k_fwd_y<V>, y_smem(V, t.bk_y, 3)))) return e;      \
     if ((e = allow_smem(k_inv_y<V>, y_smem(V, t.bk_y, 3)))) return e;      \
+    if ((e = allow_smem(k_fwd_y_b<V>, y_smem(V, t.bk_y, 3)))) return e;    \
+    if ((e = allow_smem(k_inv_y_b<V>, y_smem(V, t.bk_y, 3)))) return e;    \
     break;
   FH_SWITCH_LEN(g.ny, YCASE)
 #undef YCASE
 #define XCASE(V)                                                           \
   case V:                                                                  \
     if ((e = allow_smem(k_x_ghat<V>, y_smem(V, t.bk_x, 6)))) return e;     \
+    if ((e = allow_smem(k_x_ghat_b<V>, y_smem(V, t.bk_x, 6)))) return e;   \
     break;
   FH_SWITCH_LEN(g.nx, XCASE)
 #undef XCASE
@@ -525,6 +605,85 @@ cudaError_t launch_inv_z(const Grid& g, const Tiling& t, int mode, const double2
     break;
   FH_SWITCH_HALF(M, IZL)
 #undef IZL
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// batched launches: one pass over every cell of a group of equal grids
+// ---------------------------------------------------------------------------
+cudaError_t launch_fwd_z_batch(const Grid& g, const Tiling& t, int mode, const CellView* cells, int n_cells,
+                               const double2* tw, cudaStream_t s) {
+  const size_t smem = z_pass_smem(g, t);
+  const dim3 grid((unsigned)z_pass_ctas(g, t), (unsigned)n_cells);
+  const int M = g.nz / 2;
+#define ZB(V)                                                                                          \
+  case V:                                                                                              \
+    switch (mode) {                                                                                    \
+      case kZDirect: k_fwd_z_b<V, kZDirect><<<grid, kThreads, smem, s>>>(g, t.lines_z, cells, tw); break; \
+      case kZCg: k_fwd_z_b<V, kZCg><<<grid, kThreads, smem, s>>>(g, t.lines_z, cells, tw); break;         \
+      case kZCgFirst: k_fwd_z_b<V, kZCgFirst><<<grid, kThreads, smem, s>>>(g, t.lines_z, cells, tw); break; \
+      default: return cudaErrorInvalidValue;                                                           \
+    }                                                                                                  \
+    break;
+  FH_SWITCH_HALF(M, ZB)
+#undef ZB
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_y_batch(const Grid& g, const Tiling& t, const CellView* cells, int n_cells,
+                               const double2* tw, cudaStream_t s) {
+  const int NC = (g.nzh + t.bk_y - 1) / t.bk_y;
+  const dim3 grid((unsigned)((long long)g.nx * 3 * NC), (unsigned)n_cells);
+#define YB(V)                                                                         \
+  case V:                                                                             \
+    k_fwd_y_b<V><<<grid, kThreads, y_smem(V, t.bk_y, 3), s>>>(g, t.bk_y, cells, tw);  \
+    break;
+  FH_SWITCH_LEN(g.ny, YB)
+#undef YB
+  return cudaGetLastError();
+}
+
+cudaError_t launch_x_ghat_batch(const Grid& g, const Tiling& t, const CellView* cells, int n_cells,
+                                const double2* tw, double scale, cudaStream_t s) {
+  const int NC = (g.nzh + t.bk_x - 1) / t.bk_x;
+  const dim3 grid((unsigned)((long long)g.ny * NC), (unsigned)n_cells);
+#define XB(V)                                                                                \
+  case V:                                                                                    \
+    k_x_ghat_b<V><<<grid, kThreads, y_smem(V, t.bk_x, 6), s>>>(g, t.bk_x, cells, tw, scale); \
+    break;
+  FH_SWITCH_LEN(g.nx, XB)
+#undef XB
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inv_y_batch(const Grid& g, const Tiling& t, const CellView* cells, int n_cells,
+                               const double2* tw, cudaStream_t s) {
+  const int NC = (g.nzh + t.bk_y - 1) / t.bk_y;
+  const dim3 grid((unsigned)((long long)g.nx * 3 * NC), (unsigned)n_cells);
+#define IYB(V)                                                                        \
+  case V:                                                                             \
+    k_inv_y_b<V><<<grid, kThreads, y_smem(V, t.bk_y, 3), s>>>(g, t.bk_y, cells, tw);  \
+    break;
+  FH_SWITCH_LEN(g.ny, IYB)
+#undef IYB
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inv_z_batch(const Grid& g, const Tiling& t, int mode, const CellView* cells, int n_cells,
+                               const double2* tw, cudaStream_t s) {
+  const size_t smem = z_pass_smem(g, t);
+  const dim3 grid((unsigned)z_pass_ctas(g, t), (unsigned)n_cells);
+  const int M = g.nz / 2;
+#define IZB(V)                                                                                      \
+  case V:                                                                                           \
+    switch (mode) {                                                                                 \
+      case kIZDot: k_inv_z_b<V, kIZDot><<<grid, kThreads, smem, s>>>(g, t.lines_z, cells, tw); break; \
+      case kIZRhs: k_inv_z_b<V, kIZRhs><<<grid, kThreads, smem, s>>>(g, t.lines_z, cells, tw); break; \
+      default: return cudaErrorInvalidValue;                                                        \
+    }                                                                                               \
+    break;
+  FH_SWITCH_HALF(M, IZB)
+#undef IZB
   return cudaGetLastError();
 }
 

@@ -26,7 +26,7 @@ static unsigned pointwise_grid(const Grid& g) {
 // constitutive evaluation: P, packed K and per-CTA sums of P
 // ---------------------------------------------------------------------------
 template <class Law>
-__global__ void __launch_bounds__(kThreads) k_constitutive(Grid g, MatView m, const double* __restrict__ F,
+__device__ __forceinline__ void constitutive_body(Grid g, MatView m, const double* __restrict__ F,
                                                           double* __restrict__ P, double* __restrict__ K,
                                                           double* __restrict__ partials, int* __restrict__ flags) {
   __shared__ double red[32];
@@ -66,7 +66,39 @@ __global__ void __launch_bounds__(kThreads) k_constitutive(Grid g, MatView m, co
   }
 }
 
+template <class Law>
+__global__ void __launch_bounds__(kThreads) k_constitutive(Grid g, MatView m, const double* __restrict__ F,
+                                                          double* __restrict__ P, double* __restrict__ K,
+                                                          double* __restrict__ partials, int* __restrict__ flags) {
+  constitutive_body<Law>(g, m, F, P, K, partials, flags);
+}
+
+template <class Law>
+__global__ void __launch_bounds__(kThreads) k_constitutive_b(Grid g, int kind, const double* __restrict__ params,
+                                                            const CellState* __restrict__ cells, int store_K) {
+  const CellState& c = cells[blockIdx.y];
+  if (*c.newton_done) return;
+  const MatView m{kind, c.phase, params, c.scale};
+  constitutive_body<Law>(g, m, c.F, c.P, store_K ? c.K : nullptr, c.partials, c.flags);
+}
+
 long long constitutive_ctas(const Grid& g) { return pointwise_grid(g); }
+
+cudaError_t launch_constitutive_batch(const Grid& g, int kind, const double* params, const CellState* cells,
+                                      int n_cells, int store_K, cudaStream_t s) {
+  const dim3 grid(pointwise_grid(g), (unsigned)n_cells);
+  switch (kind) {
+    case FH_LINEAR_ELASTIC:
+      k_constitutive_b<LinearElasticLaw><<<grid, kThreads, 0, s>>>(g, kind, params, cells, store_K);
+      break;
+    case FH_NEO_HOOKEAN:
+      k_constitutive_b<NeoHookeanLaw><<<grid, kThreads, 0, s>>>(g, kind, params, cells, store_K);
+      break;
+    case FH_SVK: k_constitutive_b<SVKLaw><<<grid, kThreads, 0, s>>>(g, kind, params, cells, store_K); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_constitutive(const Grid& g, const MatView& m, const double* F, double* P, double* K,
                                 double* partials, int* flags, cudaStream_t s) {
@@ -185,6 +217,22 @@ cudaError_t launch_sum_partials(const double* partials, int n_parts, int width, 
   return cudaGetLastError();
 }
 
+// one CTA per cell: the cell's partials to its sums
+__global__ void __launch_bounds__(kThreads) k_sum_partials_b(const CellState* __restrict__ cells, int n_parts,
+                                                            int width) {
+  __shared__ double red[32];
+  const CellState& c = cells[blockIdx.x];
+  for (int w = 0; w < width; ++w) {
+    const double s = sum_fixed(c.partials + (long long)w * n_parts, n_parts, red);
+    if (threadIdx.x == 0) c.sums[w] = s;
+  }
+}
+
+cudaError_t launch_sum_partials_batch(const CellState* cells, int n_cells, int n_parts, int width, cudaStream_t s) {
+  k_sum_partials_b<<<n_cells, kThreads, 0, s>>>(cells, n_parts, width);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // per-CTA sums of the nine components of a field (voxel mean of a start field)
 // ---------------------------------------------------------------------------
@@ -221,6 +269,26 @@ __global__ void __launch_bounds__(kThreads) k_fill(Grid g, double* __restrict__ 
   }
 }
 
+// per cell: F (field 0) or the CG solution x (field 1) set to / incremented by val
+__global__ void __launch_bounds__(kThreads) k_fill_b(Grid g, const CellState* __restrict__ cells, int field, Nine val,
+                                                    int add) {
+  const CellState& c = cells[blockIdx.y];
+  double* F = field == 0 ? c.F : c.x;
+  const long long n = g.n;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F[k * n + v] = add ? F[k * n + v] + val.v[k] : val.v[k];
+  }
+}
+
+cudaError_t launch_fill_batch(const Grid& g, const CellState* cells, int n_cells, int field, const double* value9,
+                              int add, cudaStream_t s) {
+  Nine val;
+  for (int c = 0; c < 9; ++c) val.v[c] = value9[c];
+  k_fill_b<<<dim3(pointwise_grid(g), n_cells), kThreads, 0, s>>>(g, cells, field, val, add);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fill(const Grid& g, double* F, const double* value9, int add, cudaStream_t s) {
   Nine val;
   for (int c = 0; c < 9; ++c) val.v[c] = value9[c];
@@ -231,7 +299,7 @@ cudaError_t launch_fill(const Grid& g, double* F, const double* value9, int add,
 // ---------------------------------------------------------------------------
 // conjugate-gradient scalars (single CTA each)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_cg_init(CgScalars* cg, const double* __restrict__ partials, int n_parts,
+__device__ __forceinline__ void cg_init_body(CgScalars* cg, const double* __restrict__ partials, int n_parts,
                                                      double tol, int max_it) {
   __shared__ double red[32];
   const double bb = sum_fixed(partials, n_parts, red);
@@ -253,13 +321,38 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(CgScalars* cg, const doubl
   }
 }
 
+__global__ void __launch_bounds__(kThreads) k_cg_init(CgScalars* cg, const double* __restrict__ partials,
+                                                     int n_parts, double tol, int max_it) {
+  cg_init_body(cg, partials, n_parts, tol, max_it);
+}
+
+// one CTA per cell; a cell whose Newton loop has finished gets done = 1
+__global__ void __launch_bounds__(kThreads) k_cg_init_b(const CellState* __restrict__ cells, int n_parts, double tol,
+                                                       int max_it) {
+  const CellState& c = cells[blockIdx.x];
+  if (*c.newton_done) {
+    if (threadIdx.x == 0) {
+      c.cg->done = 1;
+      c.cg->it = 0;
+    }
+    return;
+  }
+  cg_init_body(c.cg, c.partials, n_parts, tol, max_it);
+}
+
 cudaError_t launch_cg_init(CgScalars* cg, const double* partials, int n_parts, double tol, int max_it,
                            cudaStream_t s) {
   k_cg_init<<<1, kThreads, 0, s>>>(cg, partials, n_parts, tol, max_it);
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(kThreads) k_cg_alpha(CgScalars* cg, const double* __restrict__ partials,
+cudaError_t launch_cg_init_batch(const CellState* cells, int n_cells, int n_parts, double tol, int max_it,
+                                 cudaStream_t s) {
+  k_cg_init_b<<<n_cells, kThreads, 0, s>>>(cells, n_parts, tol, max_it);
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ void cg_alpha_body(CgScalars* cg, const double* __restrict__ partials,
                                                       int n_parts) {
   __shared__ double red[32];
   if (cg->done) return;
@@ -275,14 +368,27 @@ __global__ void __launch_bounds__(kThreads) k_cg_alpha(CgScalars* cg, const doub
   }
 }
 
+__global__ void __launch_bounds__(kThreads) k_cg_alpha(CgScalars* cg, const double* __restrict__ partials,
+                                                      int n_parts) {
+  cg_alpha_body(cg, partials, n_parts);
+}
+__global__ void __launch_bounds__(kThreads) k_cg_alpha_b(const CellState* __restrict__ cells, int n_parts) {
+  const CellState& c = cells[blockIdx.x];
+  cg_alpha_body(c.cg, c.partials, n_parts);
+}
+
 cudaError_t launch_cg_alpha(CgScalars* cg, const double* partials, int n_parts, cudaStream_t s) {
   k_cg_alpha<<<1, kThreads, 0, s>>>(cg, partials, n_parts);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_alpha_batch(const CellState* cells, int n_cells, int n_parts, cudaStream_t s) {
+  k_cg_alpha_b<<<n_cells, kThreads, 0, s>>>(cells, n_parts);
   return cudaGetLastError();
 }
 
 // r -= alpha y and partial r . r. The matching x += alpha p is deferred to the
 // next forward z pass (which reads p anyway) or to k_cg_finalize.
-__global__ void __launch_bounds__(kThreads) k_cg_update(Grid g, const CgScalars* __restrict__ cg,
+__device__ __forceinline__ void cg_update_body(Grid g, const CgScalars* __restrict__ cg,
                                                        double* __restrict__ r, const double* __restrict__ y,
                                                        double* __restrict__ partials) {
   __shared__ double red[32];
@@ -299,6 +405,16 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(Grid g, const CgScalars*
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+__global__ void __launch_bounds__(kThreads) k_cg_update(Grid g, const CgScalars* __restrict__ cg,
+                                                       double* __restrict__ r, const double* __restrict__ y,
+                                                       double* __restrict__ partials) {
+  cg_update_body(g, cg, r, y, partials);
+}
+__global__ void __launch_bounds__(kThreads) k_cg_update_b(Grid g, const CellState* __restrict__ cells) {
+  const CellState& c = cells[blockIdx.y];
+  cg_update_body(g, c.cg, c.r, c.y, c.partials);
+}
+
 long long cg_update_ctas(const Grid& g) { return pointwise_grid(g); }
 
 cudaError_t launch_cg_update(const Grid& g, CgScalars* cg, double* r, const double* y, double* partials,
@@ -306,10 +422,14 @@ cudaError_t launch_cg_update(const Grid& g, CgScalars* cg, double* r, const doub
   k_cg_update<<<pointwise_grid(g), kThreads, 0, s>>>(g, cg, r, y, partials);
   return cudaGetLastError();
 }
+cudaError_t launch_cg_update_batch(const Grid& g, const CellState* cells, int n_cells, cudaStream_t s) {
+  k_cg_update_b<<<dim3(pointwise_grid(g), n_cells), kThreads, 0, s>>>(g, cells);
+  return cudaGetLastError();
+}
 
 // the last deferred x += alpha p once CG has stopped (nothing if no product ran;
 // alpha is 0 after a breakdown in k_cg_alpha)
-__global__ void __launch_bounds__(kThreads) k_cg_finalize(Grid g, const CgScalars* __restrict__ cg,
+__device__ __forceinline__ void cg_finalize_body(Grid g, const CgScalars* __restrict__ cg,
                                                          double* __restrict__ x, const double* __restrict__ p) {
   if (cg->it == 0) return;
   const double alpha = cg->alpha;
@@ -318,12 +438,25 @@ __global__ void __launch_bounds__(kThreads) k_cg_finalize(Grid g, const CgScalar
     x[i] = fma(alpha, p[i], x[i]);
 }
 
+__global__ void __launch_bounds__(kThreads) k_cg_finalize(Grid g, const CgScalars* __restrict__ cg,
+                                                         double* __restrict__ x, const double* __restrict__ p) {
+  cg_finalize_body(g, cg, x, p);
+}
+__global__ void __launch_bounds__(kThreads) k_cg_finalize_b(Grid g, const CellState* __restrict__ cells) {
+  const CellState& c = cells[blockIdx.y];
+  cg_finalize_body(g, c.cg, c.x, c.p);
+}
+
 cudaError_t launch_cg_finalize(const Grid& g, const CgScalars* cg, double* x, const double* p, cudaStream_t s) {
   k_cg_finalize<<<pointwise_grid(g), kThreads, 0, s>>>(g, cg, x, p);
   return cudaGetLastError();
 }
+cudaError_t launch_cg_finalize_batch(const Grid& g, const CellState* cells, int n_cells, cudaStream_t s) {
+  k_cg_finalize_b<<<dim3(pointwise_grid(g), n_cells), kThreads, 0, s>>>(g, cells);
+  return cudaGetLastError();
+}
 
-__global__ void __launch_bounds__(kThreads) k_cg_beta(CgScalars* cg, const double* __restrict__ partials,
+__device__ __forceinline__ void cg_beta_body(CgScalars* cg, const double* __restrict__ partials,
                                                      int n_parts) {
   __shared__ double red[32];
   if (cg->done) return;
@@ -339,13 +472,26 @@ __global__ void __launch_bounds__(kThreads) k_cg_beta(CgScalars* cg, const doubl
   }
 }
 
+__global__ void __launch_bounds__(kThreads) k_cg_beta(CgScalars* cg, const double* __restrict__ partials,
+                                                     int n_parts) {
+  cg_beta_body(cg, partials, n_parts);
+}
+__global__ void __launch_bounds__(kThreads) k_cg_beta_b(const CellState* __restrict__ cells, int n_parts) {
+  const CellState& c = cells[blockIdx.x];
+  cg_beta_body(c.cg, c.partials, n_parts);
+}
+
 cudaError_t launch_cg_beta(CgScalars* cg, const double* partials, int n_parts, cudaStream_t s) {
   k_cg_beta<<<1, kThreads, 0, s>>>(cg, partials, n_parts);
   return cudaGetLastError();
 }
+cudaError_t launch_cg_beta_batch(const CellState* cells, int n_cells, int n_parts, cudaStream_t s) {
+  k_cg_beta_b<<<n_cells, kThreads, 0, s>>>(cells, n_parts);
+  return cudaGetLastError();
+}
 
 // F += dF and partial ||dF||^2 (Algorithm 1 update and convergence test)
-__global__ void __launch_bounds__(kThreads) k_newton_update(Grid g, double* __restrict__ F,
+__device__ __forceinline__ void newton_update_body(Grid g, double* __restrict__ F,
                                                            const double* __restrict__ dF,
                                                            double* __restrict__ partials) {
   __shared__ double red[32];
@@ -358,6 +504,21 @@ __global__ void __launch_bounds__(kThreads) k_newton_update(Grid g, double* __re
   }
   const double s = block_sum(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_newton_update(Grid g, double* __restrict__ F,
+                                                           const double* __restrict__ dF,
+                                                           double* __restrict__ partials) {
+  newton_update_body(g, F, dF, partials);
+}
+__global__ void __launch_bounds__(kThreads) k_newton_update_b(Grid g, const CellState* __restrict__ cells) {
+  const CellState& c = cells[blockIdx.y];
+  if (*c.newton_done) return;
+  newton_update_body(g, c.F, c.x, c.partials);
+}
+cudaError_t launch_newton_update_batch(const Grid& g, const CellState* cells, int n_cells, cudaStream_t s) {
+  k_newton_update_b<<<dim3(pointwise_grid(g), n_cells), kThreads, 0, s>>>(g, cells);
+  return cudaGetLastError();
 }
 
 long long newton_update_ctas(const Grid& g) { return pointwise_grid(g); }

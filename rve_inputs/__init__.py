@@ -36,6 +36,8 @@ __all__ = [
     "neo_hookean_config",
     "simp_density",
     "simp_config",
+    "lognormal_modulus",
+    "batch_config",
 ]
 
 
@@ -215,3 +217,50 @@ def simp_config(n: int = 64, seed: int = 0, penalty: float = 3.0, nu: float = 0.
     phase = np.zeros(rho.shape, dtype=np.uint8)
     params = np.array([[lam, mu]], dtype=np.float64)
     return phase, params, rho, rho ** penalty, penalty * rho ** (penalty - 1)
+
+
+def lognormal_modulus(n, seed: int, corr: float = 0.1, sigma_log: float = 0.3) -> np.ndarray:
+    """Log-normal modulus field E = exp(sigma_log * g) about a median of 1.
+
+    g is a unit-variance Gaussian random field on the periodic grid with the
+    covariance exp(-r^2 / (2 l^2)), l = corr * (box edge): white noise filtered
+    in Fourier space by the square root of the covariance's spectrum, then
+    scaled to unit sample variance.
+    """
+    shape = (n, n, n) if np.isscalar(n) else tuple(int(v) for v in n)
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal(shape)
+    d2 = np.zeros(shape)
+    for a, m in enumerate(shape):
+        x = np.arange(m, dtype=np.float64)
+        x = np.minimum(x, m - x) / m  # periodic distance in box units
+        sh = [1, 1, 1]
+        sh[a] = m
+        d2 = d2 + (x ** 2).reshape(sh)
+    cov = np.exp(-d2 / (2.0 * corr ** 2))
+    spec = np.maximum(np.fft.rfftn(cov).real, 0.0)
+    g = np.fft.irfftn(np.fft.rfftn(w) * np.sqrt(spec), s=shape, axes=(0, 1, 2))
+    g = (g - g.mean()) / g.std()
+    return np.exp(sigma_log * g)
+
+
+def batch_config(n_cells: int = 256, seed: int = 0, sizes=(32, 48, 64, 96), nu: float = 0.3):
+    """Cells of uneven cubic grids with log-normal Young's modulus fields.
+
+    Sizes are drawn uniformly from ``sizes`` (seeded); cell i has the modulus
+    field lognormal_modulus(n_i, seed + 1 + i). All cells are linear elastic
+    with E = 1 (median), nu = 0.3, and share the macroscopic strain
+    eps_xx = 0.01. Returns (list of (phase, scale) per cell, params, Ebar).
+    """
+    rng = np.random.default_rng(seed)
+    ns = rng.choice(np.asarray(sizes), size=n_cells)
+    lam = nu / ((1 + nu) * (1 - 2 * nu))
+    mu = 1.0 / (2 * (1 + nu))
+    params = np.array([[lam, mu]], dtype=np.float64)
+    cells = []
+    for i, n in enumerate(ns):
+        E = lognormal_modulus(int(n), seed + 1 + i)
+        cells.append((np.zeros(E.shape, dtype=np.uint8), E))
+    Ebar = np.zeros(9)
+    Ebar[0] = 0.01
+    return cells, params, Ebar
