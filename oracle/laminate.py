@@ -27,21 +27,37 @@ def laminate_states(kind: int, params: np.ndarray, f_A: float, Fbar, axis: int =
 
     ``f_A`` is the volume fraction of phase A (row 1, the layered phase).
     """
-    Fbar = np.asarray(Fbar, dtype=np.float64).reshape(9)
-    f_B = 1.0 - f_A
     lA, mA = params[1]
     lB, mB = params[0]
+    return laminate_states_law(
+        lambda F: mat.stress(kind, F[:, None], lA, mA)[:, 0],
+        lambda F: mat.tangent(kind, F[:, None], lA, mA)[:, :, 0],
+        lambda F: mat.stress(kind, F[:, None], lB, mB)[:, 0],
+        lambda F: mat.tangent(kind, F[:, None], lB, mB)[:, :, 0],
+        f_A, Fbar, axis, tol, max_iter)
+
+
+def laminate_states_law(stress_A, tangent_A, stress_B, tangent_B, f_A: float, Fbar, axis: int = 0,
+                        tol: float = 1e-15, max_iter: int = 50):
+    """Laminate states for any pair of stress laws given as callables.
+
+    ``stress_X(F)`` returns the 9 stress entries of one voxel state F (9,),
+    ``tangent_X(F)`` the 9x9 derivative. Used for path-dependent laws, whose
+    callables close over the layer's history.
+    """
+    Fbar = np.asarray(Fbar, dtype=np.float64).reshape(9)
+    f_B = 1.0 - f_A
     e = np.zeros(3)
     e[axis] = 1.0
     c = np.zeros(3)
     for _ in range(max_iter):
         FA = Fbar + f_B * np.outer(c, e).reshape(9)
         FB = Fbar - f_A * np.outer(c, e).reshape(9)
-        PA = mat.stress(kind, FA[:, None], lA, mA)[:, 0].reshape(3, 3)
-        PB = mat.stress(kind, FB[:, None], lB, mB)[:, 0].reshape(3, 3)
+        PA = stress_A(FA).reshape(3, 3)
+        PB = stress_B(FB).reshape(3, 3)
         R = PA[:, axis] - PB[:, axis]
-        KA = mat.tangent(kind, FA[:, None], lA, mA)[:, :, 0].reshape(3, 3, 3, 3)
-        KB = mat.tangent(kind, FB[:, None], lB, mB)[:, :, 0].reshape(3, 3, 3, 3)
+        KA = tangent_A(FA).reshape(3, 3, 3, 3)
+        KB = tangent_B(FB).reshape(3, 3, 3, 3)
         Jac = f_B * KA[:, axis, :, axis] + f_A * KB[:, axis, :, axis]
         dc = np.linalg.solve(Jac, -R)
         c += dc

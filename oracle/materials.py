@@ -27,7 +27,8 @@ import numpy as np
 LINEAR_ELASTIC = 0
 NEO_HOOKEAN = 1
 SVK = 2
-FINITE_STRAIN = {LINEAR_ELASTIC: False, NEO_HOOKEAN: True, SVK: True}
+J2 = 3  # small-strain J2 plasticity; stress and tangent in ``plasticity`` (no energy)
+FINITE_STRAIN = {LINEAR_ELASTIC: False, NEO_HOOKEAN: True, SVK: True, J2: False}
 
 
 class NonPhysicalState(ValueError):

@@ -27,7 +27,12 @@ Readings where the paper is silent or garbled:
   outer one in both of the paper's examples);
 * a zero right-hand side gives dF = 0 without iterating;
 * load increments are equal additive steps from the start tensor (I for a
-  finite-strain law, 0 for small strain, or the mean of a given start field).
+  finite-strain law, 0 for small strain, or the mean of a given start field);
+* for J2 plasticity (Section 4.1.2) the stress and tangent of every Newton
+  iteration come from the history of the last converged increment, and the
+  history advances once the increment has converged (the incremental scheme
+  of Appendix B); the reported stress is the return-map stress at the final
+  strain from the history before its last update.
 """
 
 from __future__ import annotations
@@ -38,6 +43,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import materials as mat
+from . import plasticity
 from .spectral import project
 
 
@@ -53,6 +59,7 @@ class Result:
     newton_residuals: list = field(default_factory=list)
     cg_iterations: list = field(default_factory=list)
     converged: bool = True
+    history: np.ndarray | None = None  # J2: (10, ...) plastic strain and cumulative plastic strain
 
 
 def cg(matvec, b: np.ndarray, tol: float, max_iter: int):
@@ -105,17 +112,38 @@ def reference_tensor(kind: int) -> np.ndarray:
 def solve(phase: np.ndarray, params: np.ndarray, kind: int, Fbar, n_increments: int = 1,
           newton_tol: float = 1e-10, cg_tol: float | None = None, max_newton: int = 50,
           max_cg: int = 5000, F_init: np.ndarray | None = None, lengths=(1.0, 1.0, 1.0),
-          raise_on_failure: bool = True, scale: np.ndarray | None = None) -> Result:
+          raise_on_failure: bool = True, scale: np.ndarray | None = None,
+          plastic: np.ndarray | None = None, history: np.ndarray | None = None) -> Result:
     """Solve the periodic cell under the macroscopic tensor ``Fbar`` (Alg. 1).
 
     phase: uint8 (nx, ny, nz); params: (n_phase, 2) Lame pairs (lambda, mu);
     Fbar: 9 entries (row-major); F_init: optional start field (9, nx, ny, nz);
     scale: optional per-voxel multiplier of both Lame parameters (a modulus
     field such as E = rho^3 at fixed Poisson ratio).
+    J2 only: plastic (n_phase, 2) = (yield stress, hardening modulus) per
+    phase; history (10, nx, ny, nz) start plastic strain and cumulative
+    plastic strain (zero when None). The advanced history is returned in
+    ``Result.history``; the input array is not modified.
     """
     shape = phase.shape
     nvox = phase.size
     lam, mu = voxel_lame(phase, params, scale)
+    j2 = kind == mat.J2
+    if j2:
+        plastic = np.asarray(plastic, dtype=np.float64).reshape(-1, 2)
+        sy, hh = plastic[phase, 0], plastic[phase, 1]
+        hist = np.zeros((10,) + shape) if history is None else np.array(history, dtype=np.float64)
+
+    def stress_of(F):
+        if j2:
+            return plasticity.stress(F, hist[:9], hist[9], lam, mu, sy, hh)
+        return mat.stress(kind, F, lam, mu)
+
+    def tangent_of(F):
+        if j2:
+            return plasticity.tangent(F, hist[:9], hist[9], lam, mu, sy, hh)
+        return mat.tangent(kind, F, lam, mu)
+
     Fbar = np.asarray(Fbar, dtype=np.float64).reshape(9)
     if cg_tol is None:
         cg_tol = 1e-2 * newton_tol
@@ -134,8 +162,8 @@ def solve(phase: np.ndarray, params: np.ndarray, kind: int, Fbar, n_increments: 
             denom = math.sqrt(nvox)
         F += dFbar.reshape(9, 1, 1, 1)
         for _ in range(max_newton):
-            P = mat.stress(kind, F, lam, mu)
-            K = mat.tangent(kind, F, lam, mu)
+            P = stress_of(F)
+            K = tangent_of(F)
             b = -project(P, lengths)
             dF, ncg, ok = cg(lambda p: project(mat.apply_tangent(K, p), lengths), b, cg_tol, max_cg)
             F += dF
@@ -153,8 +181,15 @@ def solve(phase: np.ndarray, params: np.ndarray, kind: int, Fbar, n_increments: 
             res.converged = False
             if raise_on_failure:
                 raise NotConverged("Newton did not converge")
+        if j2 and res.converged:
+            res.P = stress_of(F)
+            eps_p, pc = plasticity.update(F, hist[:9], hist[9], lam, mu, sy, hh)
+            hist = np.concatenate([eps_p, pc[None]], axis=0)
     res.F = F
-    res.P = mat.stress(kind, F, lam, mu)
+    if not j2 or res.P is None:
+        res.P = stress_of(F)
+    if j2:
+        res.history = hist
     res.Pbar = res.P.reshape(9, -1).mean(axis=1)
     return res
 

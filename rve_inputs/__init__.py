@@ -38,6 +38,8 @@ __all__ = [
     "simp_config",
     "lognormal_modulus",
     "batch_config",
+    "random_disks",
+    "j2_config",
 ]
 
 
@@ -264,3 +266,61 @@ def batch_config(n_cells: int = 256, seed: int = 0, sizes=(32, 48, 64, 96), nu: 
     Ebar = np.zeros(9)
     Ebar[0] = 0.01
     return cells, params, Ebar
+
+
+def random_disks(n: int, seed: int, nz: int = 1, r_min: float = 6.0, r_max: float = 14.0,
+                 target_fraction: float = 0.25, max_attempts: int = 200000) -> np.ndarray:
+    """Random sequential addition of non-overlapping disks on an n x n periodic grid.
+
+    The same rule as ``random_spheres`` in the (x, y) plane; the map is
+    repeated ``nz`` times along z, so the cell is invariant along z (a 2D
+    cell; nz = 1 for the oracle, nz = 2 for the GPU's even-z layout).
+    Returns a uint8 phase map (n, n, nz), 1 = inclusion.
+    """
+    rng = np.random.default_rng(seed)
+    phase = np.zeros((n, n), dtype=np.uint8)
+    centres: list[np.ndarray] = []
+    radii: list[float] = []
+    x = np.arange(n) + 0.5
+    target = target_fraction * phase.size
+    for _ in range(max_attempts):
+        if int(phase.sum()) >= target:
+            break
+        r = rng.uniform(r_min, r_max)
+        c = rng.uniform(0.0, n, size=2)
+        if centres:
+            d = np.asarray(centres) - c
+            d -= n * np.round(d / n)
+            if np.any(np.sqrt((d * d).sum(axis=1)) < np.asarray(radii) + r):
+                continue
+        centres.append(c)
+        radii.append(r)
+        dx = x - c[0]
+        dx -= n * np.round(dx / n)
+        dy = x - c[1]
+        dy -= n * np.round(dy / n)
+        phase[(dx[:, None] ** 2 + dy[None, :] ** 2) <= r * r] = 1
+    else:
+        raise RuntimeError("random_disks: target fraction not reached")
+    return np.repeat(phase[:, :, None], nz, axis=2).copy()
+
+
+def j2_config(n: int = 192, seed: int = 0, nz: int = 1, nu: float = 0.3):
+    """Two-phase J2 elastoplastic cell with hard circular inclusions.
+
+    Disks of radius U[6, 14] * n / 192 voxels fill an area fraction of 0.25
+    in an elastic matrix of the same stiffness (E = 1, nu = 0.3 in both
+    phases). Matrix yield stress 2e-3 and hardening modulus 0.05; the
+    inclusions have twice both (a yield and hardening contrast of 2). The
+    load is the biaxial small strain eps_xx = eps_yy = 0.01 (plane strain,
+    eps_zz = 0). Returns (phase, params, plastic, Ebar).
+    """
+    k = n / 192.0
+    phase = random_disks(n, seed, nz=nz, r_min=6.0 * k, r_max=14.0 * k)
+    lam = nu / ((1 + nu) * (1 - 2 * nu))
+    mu = 1.0 / (2 * (1 + nu))
+    params = np.array([[lam, mu], [lam, mu]], dtype=np.float64)
+    plastic = np.array([[2e-3, 0.05], [4e-3, 0.10]], dtype=np.float64)
+    Ebar = np.zeros(9)
+    Ebar[0] = Ebar[4] = 0.01
+    return phase, params, plastic, Ebar
