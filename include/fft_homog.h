@@ -64,10 +64,17 @@ extern "C" {
  *                    (Section 3.2; the paper omits the 1/2 on lambda).
  * FH_NEO_HOOKEAN     W = mu/2 (tr F^T F - 3) - mu ln J + lambda/2 (ln J)^2.
  * FH_SVK             St. Venant-Kirchhoff, W = lambda/2 tr(E)^2 + mu E:E with
- *                    E = (F^T F - I)/2 (Eq. 6). */
+ *                    E = (F^T F - I)/2 (Eq. 6).
+ * FH_J2              small-strain J2 plasticity with linear isotropic hardening
+ *                    (Section 4.1.2, Appendix B): elastic predictor from the
+ *                    plastic strain of the last converged increment, von Mises
+ *                    yield check, radial return; the stress is the return map
+ *                    itself (no energy) and K its AD derivative. Needs
+ *                    fh_material.plastic and .history. */
 #define FH_LINEAR_ELASTIC 0
 #define FH_NEO_HOOKEAN 1
 #define FH_SVK 2
+#define FH_J2 3
 
 /* ---- how the CG matrix-vector product gets K : dF (Section 3.2) ----
  * FH_TANGENT_STORED  K is evaluated by AD once per Newton step and stored
@@ -87,12 +94,17 @@ extern "C" {
 typedef struct fh_ctx fh_ctx;
 
 typedef struct fh_material {
-  int kind;                     /* FH_LINEAR_ELASTIC, FH_NEO_HOOKEAN or FH_SVK */
+  int kind;                     /* FH_LINEAR_ELASTIC, FH_NEO_HOOKEAN, FH_SVK or FH_J2 */
   int n_phase;                  /* rows of params, 1..256 */
   const unsigned char* phase;   /* device uint8[N], every value < n_phase */
   const double* params;         /* host double[n_phase][2] = (lambda, mu) */
   const double* scale;          /* device double[N] multiplying both Lame parameters of each voxel
                                    (a modulus field such as E = rho^p at fixed Poisson ratio), or NULL */
+  const double* plastic;        /* FH_J2: host double[n_phase][2] = (yield stress, hardening modulus) */
+  double* history;              /* FH_J2: device double[10][N], the plastic strain (9 components,
+                                   symmetric) and the cumulative plastic strain; zero for a virgin
+                                   material; fft_homog_solve updates it after each converged
+                                   increment, the other entry points only read it */
 } fh_material;
 
 typedef struct fh_options {
@@ -136,7 +148,9 @@ FH_API void fh_destroy(fh_ctx* ctx);
 FH_API const char* fh_last_error_string(void);
 
 /* Stress and tangent of every voxel (Eqs. 2-3, Section 3.1-3.2), from the
- * energy of mat->kind by forward-mode dual numbers of second order.
+ * energy of mat->kind by forward-mode dual numbers of second order; for
+ * FH_J2, the return-mapped stress from mat->history and its first-order AD
+ * derivative (Section 4.1.2). The history is only read.
  *   F_dev      in   [9][N] deformation gradient (H for small strain)
  *   P_dev      out  [9][N] stress dW/dF, or NULL
  *   K_dev      out  [45][N] packed tangent d2W/dF2, or NULL
@@ -173,6 +187,10 @@ FH_API int fh_matvec(fh_ctx* ctx, const fh_material* mat, const double* F_dev,
  *   Pbar_out   host double[9] homogenized stress (Eq. 4), or NULL
  *   stats      optional convergence record, or NULL
  *   opt        NULL = defaults
+ * FH_J2: every Newton iteration of an increment starts its return map from
+ * mat->history, which is advanced in place once the increment has converged
+ * (a failed increment leaves it at the last converged one); a second call
+ * with opt->init = FH_INIT_GIVEN continues the loading path.
  * Returns FH_ERR_NOT_CONVERGED when an iteration cap is hit (F_dev and
  * Pbar_out then hold the last iterate), FH_ERR_NONPHYSICAL on det F <= 0. */
 FH_API int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9],
@@ -187,7 +205,8 @@ FH_API int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fba
  *   F_dev      in   [9][N] converged field (H for small strain)
  *   opt        CG tolerance (cg_tol, or 1e-2 newton_tol), max_cg, lengths; NULL = defaults
  *   Cbar_out   out  host double[81], Cbar[9*ab + cd] = dPbar_ab / dFbar_cd
- * Returns FH_ERR_NOT_CONVERGED if a CG solve hits max_cg. */
+ * Returns FH_ERR_NOT_CONVERGED if a CG solve hits max_cg, FH_ERR_UNSUPPORTED
+ * for FH_J2. */
 FH_API int fft_homog_tangent(fh_ctx* ctx, const fh_material* mat, const double* F_dev,
                              const fh_options* opt, double Cbar_out[81]);
 
@@ -200,7 +219,7 @@ FH_API int fft_homog_tangent(fh_ctx* ctx, const fh_material* mat, const double* 
  * when ab != cd). ab = 3*i + j, cd = 3*k + l.
  *   dscale_dev  in   device double[N], ds/drho per voxel
  *   out_dev     out  device double[N], the sensitivity per voxel
- * Returns FH_ERR_UNSUPPORTED for finite-strain laws. */
+ * Returns FH_ERR_UNSUPPORTED for finite-strain laws and FH_J2. */
 FH_API int fft_homog_sensitivity(fh_ctx* ctx, const fh_material* mat, const fh_options* opt, int i, int j,
                                  int k, int l, const double* dscale_dev, double* out_dev);
 
@@ -240,7 +259,8 @@ FH_API void fh_batch_destroy(fh_batch* batch);
  * n_cells entries, each may be NULL): Pbar_out[9 * i + c], status_out[i]
  * (FH_OK, FH_ERR_NOT_CONVERGED or FH_ERR_NONPHYSICAL), newton_out[i] and
  * cg_out[i] (iteration totals). Returns FH_OK when every cell converged,
- * else the first failing cell's status. */
+ * else the first failing cell's status; FH_ERR_UNSUPPORTED for FH_J2 (no
+ * per-cell history). */
 FH_API int fft_homog_solve_batched(fh_batch* batch, int kind, int n_phase, const double* params,
                                    const double Fbar[9], int n_increments, const fh_options* opt,
                                    double* Pbar_out, int* status_out, int* newton_out, int* cg_out);

@@ -27,6 +27,7 @@ FH_ERR_UNSUPPORTED = 6
 LINEAR_ELASTIC = 0
 NEO_HOOKEAN = 1
 SVK = 2
+J2 = 3
 
 TANGENT_STORED = 0
 TANGENT_JVP = 1
@@ -55,7 +56,7 @@ class FhError(RuntimeError):
 
 class FhMaterial(ctypes.Structure):
     _fields_ = [("kind", c_int), ("n_phase", c_int), ("phase", c_void_p), ("params", POINTER(c_double)),
-                ("scale", c_void_p)]
+                ("scale", c_void_p), ("plastic", POINTER(c_double)), ("history", c_void_p)]
 
 
 class FhOptions(ctypes.Structure):
@@ -188,7 +189,7 @@ def fh_project_static(A, out, scale: float = 1.0, lengths=None, stream=None):
 class Material:
     """A material description: kind, device phase map and host parameter table."""
 
-    def __init__(self, kind: int, phase, params, scale=None):
+    def __init__(self, kind: int, phase, params, scale=None, plastic=None, history=None):
         import torch
 
         self.kind = int(kind)
@@ -203,9 +204,15 @@ class Material:
             if not isinstance(scale, torch.Tensor):
                 scale = torch.as_tensor(np.ascontiguousarray(scale, dtype=np.float64))
             self.scale = scale.to(device="cuda", dtype=torch.float64).contiguous()
+        self.plastic = None
+        if plastic is not None:
+            self.plastic, _ = _dvec(plastic)
+        self.history = history  # CUDA float64 tensor (10, nx, ny, nz) for J2, updated in place by solves
         self._c = FhMaterial(self.kind, self.params.size // 2, self.phase.data_ptr(),
                              self.params.ctypes.data_as(POINTER(c_double)),
-                             self.scale.data_ptr() if self.scale is not None else None)
+                             self.scale.data_ptr() if self.scale is not None else None,
+                             self.plastic.ctypes.data_as(POINTER(c_double)) if self.plastic is not None else None,
+                             _ptr(history) if history is not None else None)
 
     @property
     def c(self):

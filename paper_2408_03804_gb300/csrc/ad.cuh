@@ -18,6 +18,8 @@
 
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "fh_common.cuh"
 
 namespace fh {
@@ -251,6 +253,25 @@ __device__ __forceinline__ auto square(const T2<G, H>& a) {
   return unary(a, a.v * a.v, 2.0 * a.v, 2.0);
 }
 template <uint32_t G, uint64_t H>
+__device__ __forceinline__ auto sqrt(const T2<G, H>& a) {
+  const double r = ::sqrt(a.v);
+  const double d1 = 0.5 / r;
+  return unary(a, r, d1, -0.5 * d1 / a.v);
+}
+// every entry of a set to zero (a branch that contributes nothing)
+template <uint32_t G, uint64_t H>
+__device__ __forceinline__ void zero_out(T2<G, H>& a) {
+  a.v = 0.0;
+  static_for<0, 9>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr ((G >> i) & 1u) a.g[i] = 0.0;
+  });
+  static_for<0, 45>([&](auto Kk) {
+    constexpr int k = decltype(Kk)::value;
+    if constexpr ((H >> k) & 1ull) a.h[k] = 0.0;
+  });
+}
+template <uint32_t G, uint64_t H>
 __device__ __forceinline__ auto recip(const T2<G, H>& a) {
   const double inv = 1.0 / a.v;
   return unary(a, inv, -inv * inv, 2.0 * inv * inv * inv);
@@ -295,6 +316,26 @@ __device__ __forceinline__ double energy_derivatives(const double F[9], double l
     else K[k] = 0.0;
   });
   return w.v;
+}
+
+// Evaluate the stress function of a Law that returns the stress itself (laws
+// whose stress is not the derivative of a stored energy, such as a return
+// map); write P and the packed tangent K = dP/dF (the upper triangle of the
+// Jacobian; the laws used here have symmetric Jacobians). Law::stress calls
+// emit(IC<a>{}, sigma_a) once for every component a.
+template <class Law, class State>
+__device__ __forceinline__ void stress_derivatives(const double F[9], const State& st, double P[9], double K[45]) {
+  Law::stress(seed<0>(F[0]), seed<1>(F[1]), seed<2>(F[2]), seed<3>(F[3]), seed<4>(F[4]), seed<5>(F[5]),
+              seed<6>(F[6]), seed<7>(F[7]), seed<8>(F[8]), st, [&](auto A, const auto& sig) {
+                constexpr int a = decltype(A)::value;
+                using S = typename std::remove_cv<typename std::remove_reference<decltype(sig)>::type>::type;
+                P[a] = sig.v;
+                static_for<a, 9>([&](auto B) {
+                  constexpr int b = decltype(B)::value;
+                  if constexpr ((S::gm >> b) & 1u) K[tri(a, b)] = sig.g[b];
+                  else K[tri(a, b)] = 0.0;
+                });
+              });
 }
 
 }  // namespace ad
@@ -352,6 +393,67 @@ struct SVKLaw {
     const auto trE = E00 + E11 + E22;
     const auto EE = square(E00) + square(E11) + square(E22) + 2.0 * (square(E01) + square(E02) + square(E12));
     return (0.5 * lam) * square(trE) + mu * EE;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Small-strain J2 plasticity with linear isotropic hardening (Section 4.1.2,
+// Appendix B): elastic predictor from the plastic strain of the last
+// converged increment, von Mises check, radial return. The branch is chosen
+// on the value; both branches share one expression (the return factor is
+// zeroed in the elastic branch), so AD differentiates the active one.
+// ---------------------------------------------------------------------------
+struct J2State {
+  double ep[9];     // plastic strain of the last converged increment
+  double p;         // cumulative plastic strain
+  double lam, mu;   // Lame parameters
+  double sy, h;     // yield stress and hardening modulus
+};
+
+struct J2Law {
+  template <class A0, class A1, class A2, class A3, class A4, class A5, class A6, class A7, class A8, class Emit>
+  __device__ static void stress(const A0& H00, const A1& H01, const A2& H02, const A3& H10, const A4& H11,
+                                const A5& H12, const A6& H20, const A7& H21, const A8& H22, const J2State& st,
+                                Emit&& emit) {
+    using ad::IC;
+    using ad::square;
+    const double mu2 = 2.0 * st.mu;
+    const auto e00 = H00 - st.ep[0];
+    const auto e11 = H11 - st.ep[4];
+    const auto e22 = H22 - st.ep[8];
+    const auto e01 = 0.5 * (H01 + H10) - st.ep[1];
+    const auto e02 = 0.5 * (H02 + H20) - st.ep[2];
+    const auto e12 = 0.5 * (H12 + H21) - st.ep[5];
+    const auto tr = e00 + e11 + e22;
+    const auto third = tr * (1.0 / 3.0);
+    const auto d00 = mu2 * (e00 - third);     // deviatoric trial stress
+    const auto d11 = mu2 * (e11 - third);
+    const auto d22 = mu2 * (e22 - third);
+    const auto d01 = mu2 * e01;
+    const auto d02 = mu2 * e02;
+    const auto d12 = mu2 * e12;
+    auto ss = square(d00) + square(d11) + square(d22) + 2.0 * (square(d01) + square(d02) + square(d12));
+    ss.v += (ss.v > 0.0) ? 0.0 : 1.0;  // a stress-free deviator is elastic: keep sqrt finite
+    const auto q = ad::sqrt(1.5 * ss);
+    const auto phi = q - (st.sy + st.h * st.p);
+    auto kappa = (3.0 * st.mu / (3.0 * st.mu + st.h)) * (phi / q);  // 3 mu dp / q
+    if (!(phi.v > 0.0)) ad::zero_out(kappa);
+    const auto vol = (st.lam + mu2 / 3.0) * tr;  // bulk part, unchanged by the return
+    const auto s00 = vol + (d00 - kappa * d00);
+    const auto s11 = vol + (d11 - kappa * d11);
+    const auto s22 = vol + (d22 - kappa * d22);
+    const auto s01 = d01 - kappa * d01;
+    const auto s02 = d02 - kappa * d02;
+    const auto s12 = d12 - kappa * d12;
+    emit(IC<0>{}, s00);
+    emit(IC<1>{}, s01);
+    emit(IC<2>{}, s02);
+    emit(IC<3>{}, s01);
+    emit(IC<4>{}, s11);
+    emit(IC<5>{}, s12);
+    emit(IC<6>{}, s02);
+    emit(IC<7>{}, s12);
+    emit(IC<8>{}, s22);
   }
 };
 

@@ -82,7 +82,7 @@ struct fh_ctx {
   double* K = nullptr;        // packed tangent       [45][N]
   double* partials = nullptr;
   long long n_partials = 0;
-  double* params = nullptr;   // [256][2]
+  double* params = nullptr;   // [256][2] Lame pairs, then [256][2] J2 (yield stress, hardening)
   double2* tw = nullptr;      // twiddle tables
   DevScalars* sc = nullptr;
 };
@@ -161,26 +161,36 @@ bool lengths_ok(const double* L) { return !L || (L[0] > 0 && L[1] > 0 && L[2] > 
 
 int check_material(const fh_material* m) {
   if (!m) return fail(FH_ERR_ARG, "material is NULL");
-  if (m->kind < FH_LINEAR_ELASTIC || m->kind > FH_SVK) return fail(FH_ERR_ARG, "unknown material kind %d", m->kind);
+  if (m->kind < FH_LINEAR_ELASTIC || m->kind > FH_J2) return fail(FH_ERR_ARG, "unknown material kind %d", m->kind);
   if (m->n_phase < 1 || m->n_phase > 256) return fail(FH_ERR_ARG, "n_phase %d outside 1..256", m->n_phase);
   if (!m->phase || !m->params) return fail(FH_ERR_ARG, "phase or params is NULL");
   for (int i = 0; i < 2 * m->n_phase; ++i)
     if (!std::isfinite(m->params[i])) return fail(FH_ERR_ARG, "non-finite material parameter");
+  if (m->kind == FH_J2) {
+    if (!m->plastic || !m->history) return fail(FH_ERR_ARG, "J2 needs the plastic parameters and the history array");
+    for (int i = 0; i < 2 * m->n_phase; ++i)
+      if (!std::isfinite(m->plastic[i]) || m->plastic[i] < 0.0)
+        return fail(FH_ERR_ARG, "J2 yield stress and hardening modulus must be finite and >= 0");
+  }
   return FH_OK;
 }
 
 // upload the parameter table; rows >= n_phase hold NaN so that an
 // out-of-range phase value surfaces as a non-physical state
 int upload_material(fh_ctx* ctx, const fh_material* m, MatView* mv) {
-  std::vector<double> tab(512, std::nan(""));
+  std::vector<double> tab(1024, std::nan(""));
   for (int i = 0; i < 2 * m->n_phase; ++i) tab[i] = m->params[i];
-  FH_CUDA(cudaMemcpyAsync(ctx->params, tab.data(), 512 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  if (m->kind == FH_J2)
+    for (int i = 0; i < 2 * m->n_phase; ++i) tab[512 + i] = m->plastic[i];
+  FH_CUDA(cudaMemcpyAsync(ctx->params, tab.data(), 1024 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   FH_CUDA(cudaStreamSynchronize(ctx->stream));
   prof_flush(ctx);
   mv->kind = m->kind;
   mv->phase = m->phase;
   mv->params = ctx->params;
   mv->scale = m->scale;
+  mv->plastic = m->kind == FH_J2 ? ctx->params + 512 : nullptr;
+  mv->history = m->kind == FH_J2 ? m->history : nullptr;
   return FH_OK;
 }
 
@@ -313,7 +323,7 @@ int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
       (e = cudaMalloc(&c->y, f9)) || (e = cudaMalloc(&c->P, f9)) ||
       (e = cudaMalloc(&c->K, (size_t)45 * g.n * sizeof(double))) ||
       (e = cudaMalloc(&c->partials, (size_t)np * sizeof(double))) ||
-      (e = cudaMalloc(&c->params, 512 * sizeof(double))) ||
+      (e = cudaMalloc(&c->params, 1024 * sizeof(double))) ||
       (e = cudaMalloc(&c->tw, kTwiddleTotal * sizeof(double2))) || (e = cudaMalloc(&c->sc, sizeof(DevScalars)))) {
     fail(FH_ERR_CUDA, "fh_create: allocation failed: %s", cudaGetErrorString(e));
     return cleanup(FH_ERR_CUDA);
@@ -448,7 +458,7 @@ int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9], i
   // start tensor and load step (a1)
   double start[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (opt.init == FH_INIT_REFERENCE) {
-    if (mat->kind != FH_LINEAR_ELASTIC) start[0] = start[4] = start[8] = 1.0;
+    if (mat->kind != FH_LINEAR_ELASTIC && mat->kind != FH_J2) start[0] = start[4] = start[8] = 1.0;
     FH_CUDA(prof(ctx, kPFill, [&] { return launch_fill(g, F_dev, start, 0, s); }));
   } else {
     FH_CUDA(prof(ctx, kPFill, [&] { return launch_field_sums(g, F_dev, ctx->partials, s); }));
@@ -515,6 +525,10 @@ int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9], i
         break;
       }
     }
+    if (inc_converged && mat->kind == FH_J2) {
+      // plastic strain and cumulative plastic strain of the converged increment
+      FH_CUDA(prof(ctx, kPConst, [&] { return launch_j2_update(g, mv, F_dev, mat->history, s); }));
+    }
     if (status == FH_OK && !inc_converged)
       status = fail(FH_ERR_NOT_CONVERGED, "Newton hit max_newton=%d in increment %d", opt.max_newton, inc);
   }
@@ -571,6 +585,8 @@ int fft_homog_tangent(fh_ctx* ctx, const fh_material* mat, const double* F_dev, 
   if (!ctx || !F_dev || !Cbar_out) return fail(FH_ERR_ARG, "NULL argument");
   int rc = check_material(mat);
   if (rc) return rc;
+  if (mat->kind == FH_J2)
+    return fail(FH_ERR_UNSUPPORTED, "the homogenized tangent is implemented for hyperelastic laws");
   fh_options opt;
   if ((rc = options_or_default(opt_in, &opt))) return rc;
   const double cg_tol = opt.cg_tol > 0.0 ? opt.cg_tol : 1e-2 * opt.newton_tol;

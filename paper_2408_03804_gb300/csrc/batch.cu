@@ -257,7 +257,9 @@ int fft_homog_solve_batched(fh_batch* b, int kind, int n_phase, const double* pa
   const auto t0 = std::chrono::steady_clock::now();
   (void)t0;
   if (!b || !params || !Fbar) return bfail(FH_ERR_ARG, "fft_homog_solve_batched: NULL argument");
-  if (kind < FH_LINEAR_ELASTIC || kind > FH_SVK) return bfail(FH_ERR_ARG, "unknown material kind %d", kind);
+  if (kind < FH_LINEAR_ELASTIC || kind > FH_SVK)
+    return bfail(kind == FH_J2 ? FH_ERR_UNSUPPORTED : FH_ERR_ARG, "material kind %d not available in batched solves",
+                 kind);
   if (n_phase < 1 || n_phase > 256) return bfail(FH_ERR_ARG, "n_phase %d outside 1..256", n_phase);
   if (n_increments < 1) return bfail(FH_ERR_ARG, "n_increments must be >= 1");
   fh_options opt;

@@ -80,6 +80,8 @@ struct MatView {
   const uint8_t* phase;      // device
   const double* params;      // device [n_phase][2]
   const double* scale;       // device [N] modulus multiplier per voxel, or nullptr
+  const double* plastic;     // device [n_phase][2] (yield stress, hardening modulus), J2 only
+  const double* history;     // device [10][N] plastic strain and cumulative plastic strain, J2 only
 };
 
 __device__ __forceinline__ void voxel_lame(const MatView& m, long long v, double& lam, double& mu) {

@@ -133,6 +133,7 @@ cudaError_t launch_sum_partials_batch(const CellState* cells, int n_cells, int n
 cudaError_t launch_fill_batch(const Grid& g, const CellState* cells, int n_cells, int field, const double* value9,
                               int add, cudaStream_t s);
 long long kapply_sums_ctas(const Grid& g);
+cudaError_t launch_j2_update(const Grid& g, const MatView& m, const double* H, double* history, cudaStream_t s);
 cudaError_t launch_kapply_sums(const Grid& g, const double* K, const double* x, int cd, double* partials,
                                cudaStream_t s);
 cudaError_t launch_sensitivity(const Grid& g, const MatView& m, const double* xa, int ab, const double* xc, int cd,

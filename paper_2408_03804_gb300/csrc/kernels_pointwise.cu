@@ -15,6 +15,30 @@ namespace fh {
 
 constexpr int kPointwiseCtas = 4 * 152;  // grid of the grid-stride voxel kernels
 
+// P and packed K of one voxel for any law: energy laws by second-order AD of W,
+// the J2 return map by first-order AD of the stress, from the voxel's history
+template <class Law>
+__device__ __forceinline__ double material_derivatives(const MatView& m, long long v, long long n, const double f[9],
+                                                       double P[9], double K[45]) {
+  double lam, mu;
+  voxel_lame(m, v, lam, mu);
+  if constexpr (std::is_same<Law, J2Law>::value) {
+    J2State st;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) st.ep[c] = m.history[c * n + v];
+    st.p = m.history[9 * n + v];
+    st.lam = lam;
+    st.mu = mu;
+    const int ph = m.phase[v];
+    st.sy = m.plastic[2 * ph];
+    st.h = m.plastic[2 * ph + 1];
+    ad::stress_derivatives<J2Law>(f, st, P, K);
+    return 0.0;
+  } else {
+    return ad::energy_derivatives<Law>(f, lam, mu, P, K);
+  }
+}
+
 static unsigned pointwise_grid(const Grid& g) {
   long long b = (g.n + kThreads - 1) / kThreads;
   if (b > kPointwiseCtas) b = kPointwiseCtas;
@@ -39,9 +63,7 @@ __device__ __forceinline__ void constitutive_body(Grid g, MatView m, const doubl
     double f[9], pv[9], kv[45];
 #pragma unroll
     for (int c = 0; c < 9; ++c) f[c] = F[c * n + v];
-    double lam, mu;
-    voxel_lame(m, v, lam, mu);
-    const double w = ad::energy_derivatives<Law>(f, lam, mu, pv, kv);
+    const double w = material_derivatives<Law>(m, v, n, f, pv, kv);
     bool ok = isfinite(w);
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
@@ -78,7 +100,7 @@ __global__ void __launch_bounds__(kThreads) k_constitutive_b(Grid g, int kind, c
                                                             const CellState* __restrict__ cells, int store_K) {
   const CellState& c = cells[blockIdx.y];
   if (*c.newton_done) return;
-  const MatView m{kind, c.phase, params, c.scale};
+  const MatView m{kind, c.phase, params, c.scale, nullptr, nullptr};
   constitutive_body<Law>(g, m, c.F, c.P, store_K ? c.K : nullptr, c.partials, c.flags);
 }
 
@@ -112,6 +134,9 @@ cudaError_t launch_constitutive(const Grid& g, const MatView& m, const double* F
       break;
     case FH_SVK:
       k_constitutive<SVKLaw><<<grid, kThreads, 0, s>>>(g, m, F, P, K, partials, flags);
+      break;
+    case FH_J2:
+      k_constitutive<J2Law><<<grid, kThreads, 0, s>>>(g, m, F, P, K, partials, flags);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -154,9 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_jvp(Grid g, MatView m, const doubl
         p[c * n + v] = pd[c];
       }
     }
-    double lam, mu;
-    voxel_lame(m, v, lam, mu);
-    const double w = ad::energy_derivatives<Law>(f, lam, mu, pv, kv);
+    const double w = material_derivatives<Law>(m, v, n, f, pv, kv);
     bad |= !isfinite(w);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
@@ -189,6 +212,7 @@ cudaError_t launch_jvp(const Grid& g, const MatView& m, const double* F, const d
       break;
     case FH_NEO_HOOKEAN: launch_jvp_law<NeoHookeanLaw>(grid, s, g, m, F, src, p, x, tau, mode, cg, flags); break;
     case FH_SVK: launch_jvp_law<SVKLaw>(grid, s, g, m, F, src, p, x, tau, mode, cg, flags); break;
+    case FH_J2: launch_jvp_law<J2Law>(grid, s, g, m, F, src, p, x, tau, mode, cg, flags); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -602,6 +626,52 @@ __global__ void __launch_bounds__(kThreads) k_sensitivity(Grid g, MatView m, con
 cudaError_t launch_sensitivity(const Grid& g, const MatView& m, const double* xa, int ab, const double* xc, int cd,
                                const double* dscale, double* out, cudaStream_t s) {
   k_sensitivity<<<pointwise_grid(g), kThreads, 0, s>>>(g, m, xa, ab, xc, cd, dscale, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// J2 history after a converged increment: plastic strain and cumulative
+// plastic strain of the return map at the converged total strain
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_j2_update(Grid g, MatView m, const double* __restrict__ H,
+                                                       double* __restrict__ history) {
+  const long long n = g.n;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    double lam, mu;
+    voxel_lame(m, v, lam, mu);
+    const int ph = m.phase[v];
+    const double sy = m.plastic[2 * ph], h = m.plastic[2 * ph + 1];
+    double e[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) e[c] = H[c * n + v];
+    const double p = history[9 * n + v];
+    // symmetric elastic trial strain, stored as a full 3x3
+    double ee[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) ee[3 * i + j] = 0.5 * (e[3 * i + j] + e[3 * j + i]) - history[(3 * i + j) * n + v];
+    const double tr = ee[0] + ee[4] + ee[8];
+    double d[9], ss = 0.0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      d[c] = 2.0 * mu * (ee[c] - ((c % 4 == 0) ? tr / 3.0 : 0.0));
+      ss = fma(d[c], d[c], ss);
+    }
+    const double q = ::sqrt(1.5 * ss);
+    const double phi = q - (sy + h * p);
+    if (phi > 0.0) {
+      const double dp = phi / (3.0 * mu + h);
+      const double f = 1.5 * dp / q;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) history[c * n + v] += f * d[c];
+      history[9 * n + v] = p + dp;
+    }
+  }
+}
+
+cudaError_t launch_j2_update(const Grid& g, const MatView& m, const double* H, double* history, cudaStream_t s) {
+  k_j2_update<<<pointwise_grid(g), kThreads, 0, s>>>(g, m, H, history);
   return cudaGetLastError();
 }
 
