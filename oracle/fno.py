@@ -126,3 +126,19 @@ def predict(theta, phi, Fbar):
     """Predicted fluctuation F - Fbar (B, 9, nx, ny, nz)."""
     q, s = forward(theta, phi, Fbar)
     return q * s[:, None, None, None, None]
+
+
+def adam_step(theta, g, m, v, t: int, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8,
+              wd: float = 0.0):
+    """One Adam step (Kingma and Ba, Algorithm 1) with decoupled weight decay.
+
+    Returns the new (theta, m, v); arrays are float64 numpy arrays.
+    """
+    import numpy as np
+
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mhat = m / (1.0 - b1 ** t)
+    vhat = v / (1.0 - b2 ** t)
+    theta = theta - lr * (mhat / (np.sqrt(vhat) + eps) + wd * theta)
+    return theta, m, v

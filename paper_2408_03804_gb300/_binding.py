@@ -41,7 +41,9 @@ _ERR_NAMES = {1: "FH_ERR_ARG", 2: "FH_ERR_CUDA", 3: "FH_ERR_NOT_CONVERGED", 4: "
 # every symbol include/fft_homog.h declares
 EXPORTS = ["fh_default_options", "fh_create", "fh_destroy", "fh_last_error_string", "fh_constitutive",
            "fh_project", "fh_matvec", "fft_homog_solve", "fh_profile_enable", "fh_profile_read", "fh_project_static", "fft_homog_tangent", "fft_homog_sensitivity",
-           "fh_batch_create", "fh_batch_destroy", "fft_homog_solve_batched", "fh_autotune"]
+           "fh_batch_create", "fh_batch_destroy", "fft_homog_solve_batched", "fh_autotune",
+           "fh_fno_param_count", "fh_fno_create", "fh_fno_destroy", "fh_fno_set_params", "fh_fno_forward",
+           "fh_fno_loss_grad", "fh_fno_adam", "fh_fno_make_target", "fh_fno_warm_start"]
 
 PROF_NCLASS = 13
 PROF_CLASSES = ["fwd_z", "fwd_y", "x_ghat", "inv_y", "inv_z", "constitutive", "jvp", "cg_scalar", "cg_update",
@@ -133,6 +135,25 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.fft_homog_solve_batched.restype = c_int
     lib.fh_autotune.argtypes = [c_void_p, c_int, POINTER(c_double), POINTER(c_int)]
     lib.fh_autotune.restype = c_int
+    lib.fh_fno_param_count.argtypes = []
+    lib.fh_fno_param_count.restype = ctypes.c_longlong
+    lib.fh_fno_create.argtypes = [POINTER(c_void_p), c_int, c_int, c_int, c_int, c_int, c_void_p]
+    lib.fh_fno_create.restype = c_int
+    lib.fh_fno_destroy.argtypes = [c_void_p]
+    lib.fh_fno_destroy.restype = None
+    lib.fh_fno_set_params.argtypes = [c_void_p, c_void_p]
+    lib.fh_fno_set_params.restype = c_int
+    lib.fh_fno_forward.argtypes = [c_void_p, c_int, POINTER(c_void_p), POINTER(c_double), POINTER(c_void_p)]
+    lib.fh_fno_forward.restype = c_int
+    lib.fh_fno_loss_grad.argtypes = [c_void_p, POINTER(c_void_p), POINTER(c_double), c_void_p]
+    lib.fh_fno_loss_grad.restype = c_int
+    lib.fh_fno_adam.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float,
+                                ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+    lib.fh_fno_adam.restype = c_int
+    lib.fh_fno_make_target.argtypes = [c_void_p, c_void_p, POINTER(c_double), c_void_p]
+    lib.fh_fno_make_target.restype = c_int
+    lib.fh_fno_warm_start.argtypes = [c_void_p, c_void_p, c_void_p, POINTER(c_double), c_void_p]
+    lib.fh_fno_warm_start.restype = c_int
     _lib = lib
     return lib
 
@@ -387,3 +408,78 @@ class Batch:
                                             cg.ctypes.data_as(POINTER(c_int)))
         _check(rc, allow=allow)
         return pbar, st, nw, cg, rc
+
+
+def _ptr_array(tensors):
+    arr = (c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = _ptr(t)
+    return arr
+
+
+class Fno:
+    """An fh_fno: the learned warm-start network (include/fh_fno.h).
+
+    Grids are nx x ny x nz with every extent >= 24; batches hold up to
+    ``max_batch`` cells. Phase maps are CUDA uint8 tensors of the grid shape,
+    predictions and targets CUDA float32 tensors (9, nx, ny, nz), parameter
+    vectors CUDA float32 tensors of ``n_params`` entries.
+    """
+
+    def __init__(self, nx: int, ny: int, nz: int, max_batch: int = 1, train: bool = False, stream=None):
+        import torch
+
+        lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.shape = (nx, ny, nz)
+        self.n_params = int(lib.fh_fno_param_count())
+        h = c_void_p()
+        _check(lib.fh_fno_create(ctypes.byref(h), nx, ny, nz, int(max_batch), 1 if train else 0, c_void_p(stream)))
+        self._h = h
+
+    def set_params(self, theta):
+        _check(load().fh_fno_set_params(self._h, _ptr(theta)))
+
+    def forward(self, phases, Fbar, q=None):
+        """phases: list of B uint8 maps; Fbar: (B, 9); q: list of B outputs or None."""
+        fb, fbp = _dvec(Fbar, 9 * len(phases))
+        qa = _ptr_array(q) if q is not None else None
+        _check(load().fh_fno_forward(self._h, len(phases), _ptr_array(phases), fbp, qa))
+
+    def loss_grad(self, targets, grad=None) -> float:
+        """Loss of the last forward pass; the parameter gradient into ``grad`` if given."""
+        L = c_double()
+        _check(load().fh_fno_loss_grad(self._h, _ptr_array(targets), ctypes.byref(L), _ptr(grad)))
+        return L.value
+
+    def adam(self, theta, grad, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+             eps: float = 1e-8, wd: float = 0.0):
+        _check(load().fh_fno_adam(self._h, _ptr(theta), _ptr(grad), _ptr(m), _ptr(v), int(t), float(lr),
+                                  float(beta1), float(beta2), float(eps), float(wd)))
+
+    def make_target(self, F, Fbar, target):
+        fb, fbp = _dvec(Fbar, 9)
+        _check(load().fh_fno_make_target(self._h, _ptr(F), fbp, _ptr(target)))
+
+    def warm_start(self, ctx: "Context", phase, Fbar, F):
+        """F = Fbar + G(s q): the start field for fft_homog_solve with init = INIT_GIVEN."""
+        fb, fbp = _dvec(Fbar, 9)
+        _check(load().fh_fno_warm_start(self._h, ctx._h, _ptr(phase), fbp, _ptr(F)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fh_fno_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB_NAME = "libfft_homog.so"
-SOURCES = ["kernels_fft.cu", "kernels_pointwise.cu", "api.cu", "project_static.cu", "batch.cu"]
+SOURCES = ["kernels_fft.cu", "kernels_pointwise.cu", "api.cu", "project_static.cu", "batch.cu", "fno.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-fvisibility=hidden"]
@@ -54,6 +54,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     out = lib_path()
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     deps.append(os.path.join(HERE, "..", "include", "fft_homog.h"))
+    deps.append(os.path.join(HERE, "..", "include", "fh_fno.h"))
     if not force and os.path.exists(out):
         t = os.path.getmtime(out)
         if all(os.path.getmtime(d) <= t for d in deps):

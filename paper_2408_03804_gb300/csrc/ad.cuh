@@ -433,11 +433,12 @@ struct J2Law {
     const auto d02 = mu2 * e02;
     const auto d12 = mu2 * e12;
     auto ss = square(d00) + square(d11) + square(d22) + 2.0 * (square(d01) + square(d02) + square(d12));
-    ss.v += (ss.v > 0.0) ? 0.0 : 1.0;  // a stress-free deviator is elastic: keep sqrt finite
+    const bool stress_free = !(ss.v > 0.0);  // a stress-free deviator is elastic
+    ss.v += stress_free ? 1.0 : 0.0;         // keeps sqrt and the quotient below finite
     const auto q = ad::sqrt(1.5 * ss);
     const auto phi = q - (st.sy + st.h * st.p);
     auto kappa = (3.0 * st.mu / (3.0 * st.mu + st.h)) * (phi / q);  // 3 mu dp / q
-    if (!(phi.v > 0.0)) ad::zero_out(kappa);
+    if (stress_free || !(phi.v > 0.0)) ad::zero_out(kappa);
     const auto vol = (st.lam + mu2 / 3.0) * tr;  // bulk part, unchanged by the return
     const auto s00 = vol + (d00 - kappa * d00);
     const auto s11 = vol + (d11 - kappa * d11);

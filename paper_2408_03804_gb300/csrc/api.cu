@@ -288,6 +288,13 @@ void fh_internal_set_error(const char* msg) {
   snprintf(g_err, sizeof(g_err), "%s", msg ? msg : "");
 }
 
+// grid of a context, for entry points of other translation units (not exported)
+void fh_internal_ctx_grid(const fh_ctx* ctx, int* nx, int* ny, int* nz) {
+  *nx = ctx->g.nx;
+  *ny = ctx->g.ny;
+  *nz = ctx->g.nz;
+}
+
 int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
   g_err[0] = 0;
   if (!out) return fail(FH_ERR_ARG, "out is NULL");

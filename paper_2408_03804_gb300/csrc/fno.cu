@@ -1,0 +1,1199 @@
+// Learned warm start: forward, backward and Adam kernels of the factorized
+// Fourier neural operator declared in include/fh_fno.h.
+//
+// Activations are stored channels-last, [sample][x][y][z][32 channels], so
+// that a line of voxels along any axis is a run of 128-byte channel vectors:
+// one warp handles one line with lane = channel, and every global access of
+// the spectral kernels is a coalesced 128-byte row whatever the axis. The
+// truncated real DFT along a line keeps 12 modes, so it is computed as a
+// direct sum against precomputed twiddles (24 cosines/sines per position)
+// rather than by an FFT. All arithmetic is float32 on the CUDA cores with
+// bfloat16 weights; every reduction over voxels (weight gradients, loss)
+// runs in a fixed order through per-block partials, so a training step is
+// deterministic.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/fh_fno.h"
+
+extern "C" void fh_internal_set_error(const char* msg);
+extern "C" void fh_internal_ctx_grid(const fh_ctx* ctx, int* nx, int* ny, int* nz);
+
+namespace fh {
+namespace fno {
+
+constexpr int kC = 32;       // width
+constexpr int kLayers = 4;
+constexpr int kModes = 12;
+constexpr int kJ = 2 * kModes;  // real coefficients per channel and line
+constexpr int kHid = 128;
+constexpr int kOut = 9;
+constexpr int kMinN = 2 * kModes;  // retained modes stay below the Nyquist index
+
+constexpr long long kLift = kC + kC * 9 + kC;                       // 352
+constexpr long long kWSize = 3LL * kModes * 2 * kC * kC;           // 73728
+constexpr long long kWAxis = (long long)kModes * 2 * kC * kC;       // 24576
+constexpr long long kLayer = kWSize + kC * kC + kC;                 // 74784
+constexpr long long kOffA = 0, kOffB = kC, kOffB0 = kC + kC * 9;
+__host__ __device__ constexpr long long off_W(int l) { return kLift + l * kLayer; }
+__host__ __device__ constexpr long long off_M(int l) { return off_W(l) + kWSize; }
+__host__ __device__ constexpr long long off_m(int l) { return off_M(l) + kC * kC; }
+constexpr long long kOffP1 = kLift + kLayers * kLayer;
+constexpr long long kOffp1 = kOffP1 + kHid * kC;
+constexpr long long kOffP2 = kOffp1 + kHid;
+constexpr long long kOffp2 = kOffP2 + kOut * kHid;
+constexpr long long kNParam = kOffp2 + kOut;                        // 304873
+constexpr int kProjLen = (int)(kNParam - kOffP1);                   // 5385
+constexpr int kPointLen = kC * kC + kC;                             // 1056
+constexpr long long kSpecW = (long long)kLayers * 3 * kModes * kC * kC;  // complex spectral weights
+static_assert(kNParam == 304873, "parameter layout");
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kTileProj = 64;
+constexpr size_t kPointBwdSmem = 2 * (size_t)kWarps * 32 * kC * sizeof(float);  // 64 KiB      // voxels per tile of the projection weight gradient
+constexpr int kLinesPerChunk = 128;  // lines per block of the spectral weight gradient
+constexpr long long kLiftChunk = 4096;  // voxels per block of the lifting gradient
+constexpr double kPi = 3.14159265358979323846;
+
+struct Geom {
+  int nx, ny, nz;
+  long long N;  // voxels per sample
+};
+
+// first voxel (global index over samples) and voxel stride of line li along axis ax
+__device__ __forceinline__ void line_of(const Geom& g, int ax, long long li, long long& base, long long& stride) {
+  if (ax == 0) {
+    const long long per = (long long)g.ny * g.nz;
+    const long long b = li / per, r = li - b * per;
+    base = b * g.N + r;
+    stride = per;
+  } else if (ax == 1) {
+    const long long per = (long long)g.nx * g.nz;
+    const long long b = li / per, r = li - b * per;
+    const long long x = r / g.nz, z = r - x * g.nz;
+    base = b * g.N + x * g.ny * g.nz + z;
+    stride = g.nz;
+  } else {
+    const long long per = (long long)g.nx * g.ny;
+    const long long b = li / per, r = li - b * per;
+    base = b * g.N + r * g.nz;
+    stride = 1;
+  }
+}
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+__device__ __forceinline__ float bf(const __nv_bfloat16* p, long long i) { return __bfloat162float(p[i]); }
+
+// ---------------------------------------------------------------------------
+// parameters: bfloat16 copies, spectral weights also as (re, im) pairs in the
+// two transposed orders the forward ([k][c][o]) and backward ([k][o][c])
+// passes read with lane-contiguous addresses
+// ---------------------------------------------------------------------------
+__global__ void k_prepare(const float* __restrict__ theta, __nv_bfloat16* __restrict__ wq,
+                          __nv_bfloat162* __restrict__ wf, __nv_bfloat162* __restrict__ wb) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < kNParam; i += stride)
+    wq[i] = __float2bfloat16_rn(theta[i]);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < kSpecW; e += stride) {
+    const int c = (int)(e % kC);
+    const int o = (int)((e / kC) % kC);
+    const long long lak = e / (kC * kC);  // (l * 3 + ax) * kModes + k
+    const int k = (int)(lak % kModes);
+    const long long la = lak / kModes;
+    const int ax = (int)(la % 3);
+    const int l = (int)(la / 3);
+    const long long src = off_W(l) + ((long long)(ax * kModes + k) * 2) * kC * kC + (long long)o * kC + c;
+    const __nv_bfloat162 w = __floats2bfloat162_rn(theta[src], theta[src + kC * kC]);
+    wf[lak * kC * kC + (long long)c * kC + o] = w;
+    wb[lak * kC * kC + (long long)o * kC + c] = w;
+  }
+}
+
+// s = |Fbar - I|_F and u = (Fbar - I)/s per sample (u = 0 when s = 0)
+__global__ void k_load_dir(const double* __restrict__ Fbar, int B, float* __restrict__ su) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double d[9], s2 = 0.0;
+  for (int c = 0; c < 9; ++c) {
+    d[c] = Fbar[9 * b + c] - ((c % 4 == 0) ? 1.0 : 0.0);
+    s2 += d[c] * d[c];
+  }
+  const double s = sqrt(s2);
+  su[10 * b] = (float)s;
+  for (int c = 0; c < 9; ++c) su[10 * b + 1 + c] = s > 0.0 ? (float)(d[c] / s) : 0.0f;
+}
+
+// h0 = a phi + B u + b0
+__global__ void k_lift(const uint8_t* const* __restrict__ phase, const float* __restrict__ su,
+                       const __nv_bfloat16* __restrict__ wq, long long N, int B, float* __restrict__ h0) {
+  const long long total = (long long)B * N * kC;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e & (kC - 1));
+    const long long vox = e >> 5;
+    const int b = (int)(vox / N);
+    const long long v = vox - (long long)b * N;
+    float bias = bf(wq, kOffB0 + c);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) bias = fmaf(bf(wq, kOffB + c * 9 + j), su[10 * b + 1 + j], bias);
+    const float phi = phase[b][v] != 0 ? 1.0f : 0.0f;
+    h0[e] = fmaf(bf(wq, kOffA + c), phi, bias);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// spectral convolution along one axis, forward: out (=/+=) S_ax(h)
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr size_t spec_smem(int n) {
+  return (size_t)kModes * kC * kC * sizeof(__nv_bfloat162) + 2 * (size_t)n * kJ * sizeof(float) +
+         (size_t)kWarps * kJ * kC * sizeof(float);
+}
+
+template <bool ACCUM>
+__global__ void __launch_bounds__(kThreads) k_spec_fwd(const float* __restrict__ h, float* __restrict__ out,
+                                                       const __nv_bfloat162* __restrict__ W,
+                                                       const float* __restrict__ tw, const float* __restrict__ itw,
+                                                       Geom g, int ax, int n, long long n_lines) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __nv_bfloat162* sW = reinterpret_cast<__nv_bfloat162*>(smem);
+  float* stw = reinterpret_cast<float*>(smem + (size_t)kModes * kC * kC * sizeof(__nv_bfloat162));
+  float* sitw = stw + n * kJ;
+  float* sX = sitw + n * kJ;
+  for (int i = threadIdx.x; i < kModes * kC * kC; i += blockDim.x) sW[i] = W[i];
+  for (int i = threadIdx.x; i < n * kJ; i += blockDim.x) {
+    stw[i] = tw[i];
+    sitw[i] = itw[i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* X = sX + warp * kJ * kC;
+  for (long long li = (long long)blockIdx.x * kWarps + warp; li < n_lines; li += (long long)gridDim.x * kWarps) {
+    long long base, stride;
+    line_of(g, ax, li, base, stride);
+    const float* src = h + base * kC + lane;
+    const long long step = stride * kC;
+    // truncated DFT of this lane's channel: X[2k] = sum h cos, X[2k+1] = -sum h sin
+    float a[kJ];
+#pragma unroll
+    for (int j = 0; j < kJ; ++j) a[j] = 0.0f;
+#pragma unroll 4
+    for (int x = 0; x < n; ++x) {
+      const float v = src[x * step];
+      const float4* t4 = reinterpret_cast<const float4*>(stw + x * kJ);
+#pragma unroll
+      for (int q = 0; q < kJ / 4; ++q) {
+        const float4 t = t4[q];
+        a[4 * q] = fmaf(v, t.x, a[4 * q]);
+        a[4 * q + 1] = fmaf(v, t.y, a[4 * q + 1]);
+        a[4 * q + 2] = fmaf(v, t.z, a[4 * q + 2]);
+        a[4 * q + 3] = fmaf(v, t.w, a[4 * q + 3]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kJ; ++j) X[j * kC + lane] = a[j];
+    __syncwarp();
+    // channel mixing per mode (lane = output channel): Y_k = W_k X_k
+    float y[kJ];
+#pragma unroll
+    for (int j = 0; j < kJ; ++j) y[j] = 0.0f;
+    for (int c = 0; c < kC; ++c) {
+#pragma unroll
+      for (int k = 0; k < kModes; ++k) {
+        const float2 w = __bfloat1622float2(sW[(k * kC + c) * kC + lane]);
+        const float xr = X[(2 * k) * kC + c], xi = X[(2 * k + 1) * kC + c];
+        y[2 * k] = fmaf(w.x, xr, fmaf(-w.y, xi, y[2 * k]));
+        y[2 * k + 1] = fmaf(w.x, xi, fmaf(w.y, xr, y[2 * k + 1]));
+      }
+    }
+    __syncwarp();
+    // truncated real inverse DFT: S[x] = sum_j y[j] itw[x][j]
+    float* dst = out + base * kC + lane;
+#pragma unroll 2
+    for (int x = 0; x < n; ++x) {
+      const float4* t4 = reinterpret_cast<const float4*>(sitw + x * kJ);
+      float s = 0.0f;
+#pragma unroll
+      for (int q = 0; q < kJ / 4; ++q) {
+        const float4 t = t4[q];
+        s = fmaf(y[4 * q], t.x, s);
+        s = fmaf(y[4 * q + 1], t.y, s);
+        s = fmaf(y[4 * q + 2], t.z, s);
+        s = fmaf(y[4 * q + 3], t.w, s);
+      }
+      if (ACCUM)
+        dst[x * step] += s;
+      else
+        dst[x * step] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// spectral convolution along one axis, backward: gh += S_ax^T(gz); stores the
+// forward coefficients X of h and the coefficient gradient gY of every line
+// for the weight gradient
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_spec_bwd(const float* __restrict__ h, const float* __restrict__ gz,
+                                                       float* __restrict__ gh, float* __restrict__ xs,
+                                                       float* __restrict__ gys, const __nv_bfloat162* __restrict__ W,
+                                                       const float* __restrict__ tw, const float* __restrict__ itw,
+                                                       Geom g, int ax, int n, long long n_lines) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __nv_bfloat162* sW = reinterpret_cast<__nv_bfloat162*>(smem);
+  float* stw = reinterpret_cast<float*>(smem + (size_t)kModes * kC * kC * sizeof(__nv_bfloat162));
+  float* sitw = stw + n * kJ;
+  float* sG = sitw + n * kJ;
+  for (int i = threadIdx.x; i < kModes * kC * kC; i += blockDim.x) sW[i] = W[i];
+  for (int i = threadIdx.x; i < n * kJ; i += blockDim.x) {
+    stw[i] = tw[i];
+    sitw[i] = itw[i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* G = sG + warp * kJ * kC;
+  for (long long li = (long long)blockIdx.x * kWarps + warp; li < n_lines; li += (long long)gridDim.x * kWarps) {
+    long long base, stride;
+    line_of(g, ax, li, base, stride);
+    const long long step = stride * kC;
+    const float* hs = h + base * kC + lane;
+    const float* gs = gz + base * kC + lane;
+    float a[kJ], b[kJ];
+#pragma unroll
+    for (int j = 0; j < kJ; ++j) a[j] = b[j] = 0.0f;
+#pragma unroll 2
+    for (int x = 0; x < n; ++x) {
+      const float v = hs[x * step], w = gs[x * step];
+      const float4* t4 = reinterpret_cast<const float4*>(stw + x * kJ);
+      const float4* u4 = reinterpret_cast<const float4*>(sitw + x * kJ);
+#pragma unroll
+      for (int q = 0; q < kJ / 4; ++q) {
+        const float4 t = t4[q], u = u4[q];
+        a[4 * q] = fmaf(v, t.x, a[4 * q]);
+        a[4 * q + 1] = fmaf(v, t.y, a[4 * q + 1]);
+        a[4 * q + 2] = fmaf(v, t.z, a[4 * q + 2]);
+        a[4 * q + 3] = fmaf(v, t.w, a[4 * q + 3]);
+        b[4 * q] = fmaf(w, u.x, b[4 * q]);
+        b[4 * q + 1] = fmaf(w, u.y, b[4 * q + 1]);
+        b[4 * q + 2] = fmaf(w, u.z, b[4 * q + 2]);
+        b[4 * q + 3] = fmaf(w, u.w, b[4 * q + 3]);
+      }
+    }
+    float* xo = xs + li * (kJ * kC) + lane;
+    float* go = gys + li * (kJ * kC) + lane;
+#pragma unroll
+    for (int j = 0; j < kJ; ++j) {
+      xo[j * kC] = a[j];
+      go[j * kC] = b[j];
+      G[j * kC + lane] = b[j];
+    }
+    __syncwarp();
+    // gX = W^T gY (lane = input channel c)
+    float gx[kJ];
+#pragma unroll
+    for (int j = 0; j < kJ; ++j) gx[j] = 0.0f;
+    for (int o = 0; o < kC; ++o) {
+#pragma unroll
+      for (int k = 0; k < kModes; ++k) {
+        const float2 w = __bfloat1622float2(sW[(k * kC + o) * kC + lane]);
+        const float yr = G[(2 * k) * kC + o], yi = G[(2 * k + 1) * kC + o];
+        gx[2 * k] = fmaf(yr, w.x, fmaf(yi, w.y, gx[2 * k]));
+        gx[2 * k + 1] = fmaf(yi, w.x, fmaf(-yr, w.y, gx[2 * k + 1]));
+      }
+    }
+    __syncwarp();
+    float* dst = gh + base * kC + lane;
+#pragma unroll 2
+    for (int x = 0; x < n; ++x) {
+      const float4* t4 = reinterpret_cast<const float4*>(stw + x * kJ);
+      float s = 0.0f;
+#pragma unroll
+      for (int q = 0; q < kJ / 4; ++q) {
+        const float4 t = t4[q];
+        s = fmaf(gx[4 * q], t.x, s);
+        s = fmaf(gx[4 * q + 1], t.y, s);
+        s = fmaf(gx[4 * q + 2], t.z, s);
+        s = fmaf(gx[4 * q + 3], t.w, s);
+      }
+      dst[x * step] += s;
+    }
+  }
+}
+
+// spectral weight gradient of one axis: per block (chunk of lines, mode k),
+// gWr[o][c] = sum gYr[o] Xr[c] + gYi[o] Xi[c], gWi[o][c] = sum gYi[o] Xr[c] - gYr[o] Xi[c]
+__global__ void __launch_bounds__(kThreads) k_wgrad(const float* __restrict__ xs, const float* __restrict__ gys,
+                                                    long long n_lines, float* __restrict__ partial) {
+  const int k = blockIdx.y;
+  const int o = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
+  float ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
+  const long long l0 = (long long)blockIdx.x * kLinesPerChunk;
+  const long long l1 = l0 + kLinesPerChunk < n_lines ? l0 + kLinesPerChunk : n_lines;
+  for (long long li = l0; li < l1; ++li) {
+    const float* X = xs + li * (kJ * kC);
+    const float* Gy = gys + li * (kJ * kC);
+    const float yr = Gy[(2 * k) * kC + o], yi = Gy[(2 * k + 1) * kC + o];
+    const float4 xr = *reinterpret_cast<const float4*>(X + (2 * k) * kC + c0);
+    const float4 xi = *reinterpret_cast<const float4*>(X + (2 * k + 1) * kC + c0);
+    const float r4[4] = {xr.x, xr.y, xr.z, xr.w}, i4[4] = {xi.x, xi.y, xi.z, xi.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ar[q] = fmaf(yr, r4[q], fmaf(yi, i4[q], ar[q]));
+      ai[q] = fmaf(yi, r4[q], fmaf(-yr, i4[q], ai[q]));
+    }
+  }
+  float* p = partial + ((long long)blockIdx.x * kModes + k) * 2 * kC * kC;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    p[o * kC + c0 + q] = ar[q];
+    p[kC * kC + o * kC + c0 + q] = ai[q];
+  }
+}
+
+// out[i] = sum over p of partial[p][i], in order of p (double accumulator)
+__global__ void k_reduce(const float* __restrict__ partial, int n_part, int len, float* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < n_part; ++p) s += (double)partial[(long long)p * len + i];
+    out[i] = (float)s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pointwise part of a layer: z = acc + M h + m, h_next = gelu(z) (or z)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_point_fwd(const float* __restrict__ h, const float* __restrict__ acc,
+                                                        const __nv_bfloat16* __restrict__ wq, int layer,
+                                                        float* __restrict__ z, float* __restrict__ hn,
+                                                        long long nvox, int act) {
+  __shared__ __align__(16) float sh[kWarps][32 * kC];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float Mr[kC];
+#pragma unroll
+  for (int c = 0; c < kC; ++c) Mr[c] = bf(wq, off_M(layer) + lane * kC + c);
+  const float mb = bf(wq, off_m(layer) + lane);
+  const long long tiles = (nvox + 31) / 32;
+  for (long long t = (long long)blockIdx.x * kWarps + warp; t < tiles; t += (long long)gridDim.x * kWarps) {
+    const long long v0 = t * 32;
+    for (int i = 0; i < 32; ++i) sh[warp][i * kC + lane] = v0 + i < nvox ? h[(v0 + i) * kC + lane] : 0.0f;
+    __syncwarp();
+    for (int i = 0; i < 32 && v0 + i < nvox; ++i) {
+      const long long e = (v0 + i) * kC + lane;
+      float s = mb + acc[e];
+      const float4* r = reinterpret_cast<const float4*>(&sh[warp][i * kC]);
+#pragma unroll
+      for (int q = 0; q < kC / 4; ++q) {
+        const float4 hv = r[q];
+        s = fmaf(Mr[4 * q], hv.x, s);
+        s = fmaf(Mr[4 * q + 1], hv.y, s);
+        s = fmaf(Mr[4 * q + 2], hv.z, s);
+        s = fmaf(Mr[4 * q + 3], hv.w, s);
+      }
+      if (z) z[e] = s;
+      hn[e] = act ? gelu(s) : s;
+    }
+    __syncwarp();
+  }
+}
+
+// pointwise part, backward: gz = gn * gelu'(z) (or gn), gh = M^T gz, and the
+// per-warp partial sums gM[o][c] = sum gz[o] h[c], gm[o] = sum gz[o]
+__global__ void __launch_bounds__(kThreads) k_point_bwd(const float* __restrict__ gn, const float* __restrict__ z,
+                                                        const float* __restrict__ h,
+                                                        const __nv_bfloat16* __restrict__ wq, int layer,
+                                                        float* __restrict__ gz, float* __restrict__ gh,
+                                                        float* __restrict__ partial, long long nvox) {
+  extern __shared__ __align__(16) unsigned char psmem[];
+  float(*sg)[32 * kC] = reinterpret_cast<float(*)[32 * kC]>(psmem);
+  float(*sh)[32 * kC] = reinterpret_cast<float(*)[32 * kC]>(psmem + (size_t)kWarps * 32 * kC * sizeof(float));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float Mc[kC], gM[kC];
+  float gm = 0.0f;
+#pragma unroll
+  for (int o = 0; o < kC; ++o) {
+    Mc[o] = bf(wq, off_M(layer) + o * kC + lane);
+    gM[o] = 0.0f;
+  }
+  const long long tiles = (nvox + 31) / 32;
+  for (long long t = (long long)blockIdx.x * kWarps + warp; t < tiles; t += (long long)gridDim.x * kWarps) {
+    const long long v0 = t * 32;
+    for (int i = 0; i < 32; ++i) {
+      float gv = 0.0f, hv = 0.0f;
+      if (v0 + i < nvox) {
+        const long long e = (v0 + i) * kC + lane;
+        gv = gn[e];
+        if (z) gv *= gelu_d(z[e]);
+        gz[e] = gv;
+        hv = h[e];
+      }
+      sg[warp][i * kC + lane] = gv;
+      sh[warp][i * kC + lane] = hv;
+    }
+    __syncwarp();
+    for (int i = 0; i < 32; ++i) {
+      const float4* gr = reinterpret_cast<const float4*>(&sg[warp][i * kC]);
+      const float4* hr = reinterpret_cast<const float4*>(&sh[warp][i * kC]);
+      // lane = input channel c: gh[c] = sum_o M[o][c] gz[o]
+      float s = 0.0f;
+#pragma unroll
+      for (int q = 0; q < kC / 4; ++q) {
+        const float4 gv = gr[q];
+        s = fmaf(Mc[4 * q], gv.x, s);
+        s = fmaf(Mc[4 * q + 1], gv.y, s);
+        s = fmaf(Mc[4 * q + 2], gv.z, s);
+        s = fmaf(Mc[4 * q + 3], gv.w, s);
+      }
+      if (v0 + i < nvox) gh[(v0 + i) * kC + lane] = s;
+      // lane = output channel o: gM[o][c] += gz[o] h[c]
+      const float go = sg[warp][i * kC + lane];
+      gm += go;
+#pragma unroll
+      for (int q = 0; q < kC / 4; ++q) {
+        const float4 hv = hr[q];
+        gM[4 * q] = fmaf(go, hv.x, gM[4 * q]);
+        gM[4 * q + 1] = fmaf(go, hv.y, gM[4 * q + 1]);
+        gM[4 * q + 2] = fmaf(go, hv.z, gM[4 * q + 2]);
+        gM[4 * q + 3] = fmaf(go, hv.w, gM[4 * q + 3]);
+      }
+    }
+    __syncwarp();
+  }
+  float* p = partial + ((long long)blockIdx.x * kWarps + warp) * kPointLen;
+#pragma unroll
+  for (int c = 0; c < kC; ++c) p[lane * kC + c] = gM[c];
+  p[kC * kC + lane] = gm;
+}
+
+// ---------------------------------------------------------------------------
+// projection: q = P2 gelu(P1 h4 + p1) + p2, written [9][N] per sample; with
+// targets, the per-block partial sums of (q - target)^2
+// ---------------------------------------------------------------------------
+struct ProjSmem {
+  float P1[kHid * kC];
+  float p1[kHid];
+  float P2[kOut * kHid];
+  float p2[kOut];
+};
+
+__device__ __forceinline__ void load_proj(ProjSmem& s, const __nv_bfloat16* wq) {
+  for (int i = threadIdx.x; i < kHid * kC; i += blockDim.x) s.P1[i] = bf(wq, kOffP1 + i);
+  for (int i = threadIdx.x; i < kHid; i += blockDim.x) s.p1[i] = bf(wq, kOffp1 + i);
+  for (int i = threadIdx.x; i < kOut * kHid; i += blockDim.x) s.P2[i] = bf(wq, kOffP2 + i);
+  for (int i = threadIdx.x; i < kOut; i += blockDim.x) s.p2[i] = bf(wq, kOffp2 + i);
+  __syncthreads();
+}
+
+__device__ __forceinline__ float hidden_pre(const ProjSmem& s, int j, const float hv[kC]) {
+  float pre = s.p1[j];
+  const float4* r = reinterpret_cast<const float4*>(&s.P1[j * kC]);
+#pragma unroll
+  for (int q = 0; q < kC / 4; ++q) {
+    const float4 w = r[q];
+    pre = fmaf(w.x, hv[4 * q], pre);
+    pre = fmaf(w.y, hv[4 * q + 1], pre);
+    pre = fmaf(w.z, hv[4 * q + 2], pre);
+    pre = fmaf(w.w, hv[4 * q + 3], pre);
+  }
+  return pre;
+}
+
+__device__ __forceinline__ void load_h(const float* h4, long long vox, float hv[kC]) {
+  const float4* r = reinterpret_cast<const float4*>(h4 + vox * kC);
+#pragma unroll
+  for (int q = 0; q < kC / 4; ++q) {
+    const float4 v = r[q];
+    hv[4 * q] = v.x;
+    hv[4 * q + 1] = v.y;
+    hv[4 * q + 2] = v.z;
+    hv[4 * q + 3] = v.w;
+  }
+}
+
+__device__ __forceinline__ double block_sum_d(double v) {
+  __shared__ double red[kWarps];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kWarps; ++w) s += red[w];
+  return s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_proj_fwd(const float* __restrict__ h4,
+                                                       const __nv_bfloat16* __restrict__ wq,
+                                                       float* const* __restrict__ qtab,
+                                                       const float* const* __restrict__ ttab, long long N, int B,
+                                                       double* __restrict__ loss_part) {
+  __shared__ __align__(16) ProjSmem s;
+  load_proj(s, wq);
+  double loss = 0.0;
+  const long long nvox = (long long)B * N;
+  for (long long vox = (long long)blockIdx.x * blockDim.x + threadIdx.x; vox < nvox;
+       vox += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(vox / N);
+    const long long v = vox - (long long)b * N;
+    float hv[kC];
+    load_h(h4, vox, hv);
+    float q[kOut];
+#pragma unroll
+    for (int i = 0; i < kOut; ++i) q[i] = s.p2[i];
+    for (int j = 0; j < kHid; ++j) {
+      const float t = gelu(hidden_pre(s, j, hv));
+#pragma unroll
+      for (int i = 0; i < kOut; ++i) q[i] = fmaf(s.P2[i * kHid + j], t, q[i]);
+    }
+    if (qtab && qtab[b])
+#pragma unroll
+      for (int i = 0; i < kOut; ++i) qtab[b][i * N + v] = q[i];
+    if (ttab)
+#pragma unroll
+      for (int i = 0; i < kOut; ++i) {
+        const double d = (double)q[i] - (double)ttab[b][i * N + v];
+        loss += d * d;
+      }
+  }
+  if (loss_part) {
+    const double t = block_sum_d(loss);
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = t;
+  }
+}
+
+// projection backward, per voxel: gq = (2/count)(q - target) (kept [vox][9]),
+// gh4 = P1^T (gelu'(pre) . P2^T gq), and the loss partial sums
+__global__ void __launch_bounds__(kThreads) k_proj_bwd_a(const float* __restrict__ h4,
+                                                         const __nv_bfloat16* __restrict__ wq,
+                                                         const float* const* __restrict__ ttab, long long N, int B,
+                                                         float scale, float* __restrict__ gq_out,
+                                                         float* __restrict__ gh4, double* __restrict__ loss_part) {
+  __shared__ __align__(16) ProjSmem s;
+  load_proj(s, wq);
+  double loss = 0.0;
+  const long long nvox = (long long)B * N;
+  for (long long vox = (long long)blockIdx.x * blockDim.x + threadIdx.x; vox < nvox;
+       vox += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(vox / N);
+    const long long v = vox - (long long)b * N;
+    float hv[kC];
+    load_h(h4, vox, hv);
+    float q[kOut];
+#pragma unroll
+    for (int i = 0; i < kOut; ++i) q[i] = s.p2[i];
+    for (int j = 0; j < kHid; ++j) {
+      const float t = gelu(hidden_pre(s, j, hv));
+#pragma unroll
+      for (int i = 0; i < kOut; ++i) q[i] = fmaf(s.P2[i * kHid + j], t, q[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < kOut; ++i) {
+      const float d = q[i] - ttab[b][i * N + v];
+      loss += (double)d * (double)d;
+      q[i] = scale * d;  // now gq
+      gq_out[vox * kOut + i] = q[i];
+    }
+    float g[kC];
+#pragma unroll
+    for (int c = 0; c < kC; ++c) g[c] = 0.0f;
+    for (int j = 0; j < kHid; ++j) {
+      const float pre = hidden_pre(s, j, hv);
+      float gt = 0.0f;
+#pragma unroll
+      for (int i = 0; i < kOut; ++i) gt = fmaf(s.P2[i * kHid + j], q[i], gt);
+      const float gp = gt * gelu_d(pre);
+      const float4* r = reinterpret_cast<const float4*>(&s.P1[j * kC]);
+#pragma unroll
+      for (int qq = 0; qq < kC / 4; ++qq) {
+        const float4 w = r[qq];
+        g[4 * qq] = fmaf(w.x, gp, g[4 * qq]);
+        g[4 * qq + 1] = fmaf(w.y, gp, g[4 * qq + 1]);
+        g[4 * qq + 2] = fmaf(w.z, gp, g[4 * qq + 2]);
+        g[4 * qq + 3] = fmaf(w.w, gp, g[4 * qq + 3]);
+      }
+    }
+    float4* o = reinterpret_cast<float4*>(gh4 + vox * kC);
+#pragma unroll
+    for (int qq = 0; qq < kC / 4; ++qq) o[qq] = make_float4(g[4 * qq], g[4 * qq + 1], g[4 * qq + 2], g[4 * qq + 3]);
+  }
+  const double t = block_sum_d(loss);
+  if (threadIdx.x == 0) loss_part[blockIdx.x] = t;
+}
+
+// projection weight gradient: thread (hidden unit j, half of the channels)
+// accumulates gP1[j][16 channels]; the first half also gp1[j] and gP2[.][j];
+// threads 0..8 also gp2. Per-block partials in parameter order from P1 on.
+__global__ void __launch_bounds__(kThreads) k_proj_bwd_b(const float* __restrict__ h4, const float* __restrict__ gq,
+                                                         const __nv_bfloat16* __restrict__ wq, long long nvox,
+                                                         float* __restrict__ partial) {
+  __shared__ __align__(16) float sH[kTileProj * kC];
+  __shared__ float sQ[kTileProj * kOut];
+  const int j = threadIdx.x & (kHid - 1), half = threadIdx.x >> 7, c0 = half * 16;
+  float P1j[kC], P2j[kOut];
+#pragma unroll
+  for (int c = 0; c < kC; ++c) P1j[c] = bf(wq, kOffP1 + j * kC + c);
+#pragma unroll
+  for (int i = 0; i < kOut; ++i) P2j[i] = bf(wq, kOffP2 + i * kHid + j);
+  const float p1j = bf(wq, kOffp1 + j);
+  float a1[16], a2[kOut];
+  float ap1 = 0.0f, ap2 = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) a1[k] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < kOut; ++i) a2[i] = 0.0f;
+  const long long tiles = (nvox + kTileProj - 1) / kTileProj;
+  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const long long v0 = t * kTileProj;
+    for (int e = threadIdx.x; e < kTileProj * kC; e += blockDim.x)
+      sH[e] = v0 + e / kC < nvox ? h4[v0 * kC + e] : 0.0f;
+    for (int e = threadIdx.x; e < kTileProj * kOut; e += blockDim.x)
+      sQ[e] = v0 + e / kOut < nvox ? gq[v0 * kOut + e] : 0.0f;
+    __syncthreads();
+    const int nv = (int)(nvox - v0 < kTileProj ? nvox - v0 : kTileProj);
+    for (int v = 0; v < nv; ++v) {
+      const float* hr = &sH[v * kC];
+      float pre = p1j;
+#pragma unroll
+      for (int c = 0; c < kC; ++c) pre = fmaf(P1j[c], hr[c], pre);
+      const float* qr = &sQ[v * kOut];
+      float gt = 0.0f;
+#pragma unroll
+      for (int i = 0; i < kOut; ++i) gt = fmaf(P2j[i], qr[i], gt);
+      const float gp = gt * gelu_d(pre);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) a1[k] = fmaf(gp, hr[c0 + k], a1[k]);
+      if (half == 0) {
+        const float tt = gelu(pre);
+        ap1 += gp;
+#pragma unroll
+        for (int i = 0; i < kOut; ++i) a2[i] = fmaf(qr[i], tt, a2[i]);
+      }
+      if (threadIdx.x < kOut) ap2 += qr[threadIdx.x];
+    }
+    __syncthreads();
+  }
+  float* p = partial + (long long)blockIdx.x * kProjLen;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) p[j * kC + c0 + k] = a1[k];
+  if (half == 0) {
+    p[kHid * kC + j] = ap1;
+#pragma unroll
+    for (int i = 0; i < kOut; ++i) p[kHid * kC + kHid + i * kHid + j] = a2[i];
+  }
+  if (threadIdx.x < kOut) p[kHid * kC + kHid + kOut * kHid + threadIdx.x] = ap2;
+}
+
+// lifting backward: per (sample, chunk) sums of gh0 and of gh0 phi per channel
+__global__ void __launch_bounds__(kThreads) k_lift_bwd(const float* __restrict__ g0,
+                                                       const uint8_t* const* __restrict__ phase, long long N,
+                                                       long long chunk_vox, float* __restrict__ partial) {
+  __shared__ float red[kWarps][2 * kC];
+  const int b = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long v0 = (long long)blockIdx.x * chunk_vox;
+  const long long v1 = v0 + chunk_vox < N ? v0 + chunk_vox : N;
+  float s = 0.0f, sp = 0.0f;
+  for (long long v = v0 + warp; v < v1; v += kWarps) {
+    const float g = g0[((long long)b * N + v) * kC + lane];
+    s += g;
+    if (phase[b][v] != 0) sp += g;
+  }
+  red[warp][lane] = s;
+  red[warp][kC + lane] = sp;
+  __syncthreads();
+  if (warp == 0) {
+    float a = 0.0f, ap = 0.0f;
+    for (int w = 0; w < kWarps; ++w) {
+      a += red[w][lane];
+      ap += red[w][kC + lane];
+    }
+    float* p = partial + ((long long)b * gridDim.x + blockIdx.x) * 2 * kC;
+    p[lane] = a;
+    p[kC + lane] = ap;
+  }
+}
+
+__global__ void k_lift_finish(const float* __restrict__ partial, int B, int n_chunks, const float* __restrict__ su,
+                              float* __restrict__ grad) {
+  const int c = threadIdx.x;
+  if (c >= kC) return;
+  double ga = 0.0, gb0 = 0.0, gB[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < B; ++b) {
+    double S = 0.0, Sp = 0.0;
+    for (int k = 0; k < n_chunks; ++k) {
+      S += partial[((long long)b * n_chunks + k) * 2 * kC + c];
+      Sp += partial[((long long)b * n_chunks + k) * 2 * kC + kC + c];
+    }
+    ga += Sp;
+    gb0 += S;
+    for (int j = 0; j < 9; ++j) gB[j] += (double)su[10 * b + 1 + j] * S;
+  }
+  grad[kOffA + c] = (float)ga;
+  grad[kOffB0 + c] = (float)gb0;
+  for (int j = 0; j < 9; ++j) grad[kOffB + c * 9 + j] = (float)gB[j];
+}
+
+__global__ void k_adam(float* __restrict__ theta, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long long n, int t, float lr, float b1, float b2, float eps, float wd) {
+  const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    theta[i] -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * theta[i]);
+  }
+}
+
+__global__ void k_make_target(const double* __restrict__ F, const double* __restrict__ Fbar, long long N,
+                              float* __restrict__ target) {
+  double s2 = 0.0;
+  for (int c = 0; c < 9; ++c) {
+    const double d = Fbar[c] - ((c % 4 == 0) ? 1.0 : 0.0);
+    s2 += d * d;
+  }
+  const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < 9 * N;
+       e += (long long)gridDim.x * blockDim.x)
+    target[e] = (float)((F[e] - Fbar[e / N]) * inv);
+}
+
+// fluctuation s q of sample 0 as float64 [9][N]
+__global__ void k_scale_q(const float* __restrict__ q, const float* __restrict__ su, long long N,
+                          double* __restrict__ F) {
+  const double s = su[0];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < 9 * N;
+       e += (long long)gridDim.x * blockDim.x)
+    F[e] = s * (double)q[e];
+}
+
+__global__ void k_add_fbar(const double* __restrict__ Fbar, long long N, double* __restrict__ F) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < 9 * N;
+       e += (long long)gridDim.x * blockDim.x)
+    F[e] += Fbar[e / N];
+}
+
+}  // namespace fno
+}  // namespace fh
+
+using namespace fh::fno;
+
+struct fh_fno {
+  int dev = 0;
+  int nx = 0, ny = 0, nz = 0, max_batch = 0, train = 0, sms = 0;
+  long long N = 0;
+  cudaStream_t stream = nullptr;
+  __nv_bfloat16* wq = nullptr;
+  __nv_bfloat162* wf = nullptr;
+  __nv_bfloat162* wb = nullptr;
+  float* tw[3] = {nullptr, nullptr, nullptr};
+  float* itw[3] = {nullptr, nullptr, nullptr};
+  float* h[5] = {};
+  float* z[3] = {};
+  float* acc = nullptr;
+  float* gz = nullptr;
+  float* gn = nullptr;
+  float* gh = nullptr;
+  float* xs = nullptr;
+  float* gys = nullptr;
+  float* partial = nullptr;
+  long long n_partial = 0;
+  double* loss_part = nullptr;
+  int n_loss_part = 0;
+  double* fbar = nullptr;   // [max_batch][9]
+  float* su = nullptr;      // [max_batch][10]
+  const uint8_t** phase_tab = nullptr;
+  float** q_tab = nullptr;
+  const float** t_tab = nullptr;
+  float* qtmp = nullptr;    // [9][N] for the warm start
+  std::vector<const uint8_t*> last_phase;
+  int last_B = 0;
+  bool params_set = false;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+int ffail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  fh_internal_set_error(buf);
+  return code;
+}
+
+#define FN_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return ffail(FH_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+struct DevGuard {
+  int old = -1;
+  explicit DevGuard(int d) {
+    cudaGetDevice(&old);
+    if (old != d) cudaSetDevice(d);
+  }
+  ~DevGuard() {
+    if (old >= 0) cudaSetDevice(old);
+  }
+};
+
+template <class T>
+cudaError_t nalloc(fh_fno* net, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e == cudaSuccess) {
+    net->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+  }
+  return e;
+}
+
+void free_all(fh_fno* net) {
+  for (void* p : net->allocs) cudaFree(p);
+  net->allocs.clear();
+}
+
+Geom geom(const fh_fno* net) { return Geom{net->nx, net->ny, net->nz, net->N}; }
+int axis_len(const fh_fno* net, int ax) { return ax == 0 ? net->nx : (ax == 1 ? net->ny : net->nz); }
+
+unsigned grid_for(long long work, int per_block, int cap) {
+  long long b = (work + per_block - 1) / per_block;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+int spec_fwd(fh_fno* net, int B, int l, int ax, bool accum, const float* h, float* out) {
+  const int n = axis_len(net, ax);
+  const long long lines = (long long)B * (net->N / n);
+  const unsigned grid = grid_for(lines, kWarps, 2 * net->sms);
+  const __nv_bfloat162* W = net->wf + (long long)(l * 3 + ax) * kModes * kC * kC;
+  const size_t sm = spec_smem(n);
+  if (accum)
+    k_spec_fwd<true><<<grid, kThreads, sm, net->stream>>>(h, out, W, net->tw[ax], net->itw[ax], geom(net), ax, n, lines);
+  else
+    k_spec_fwd<false><<<grid, kThreads, sm, net->stream>>>(h, out, W, net->tw[ax], net->itw[ax], geom(net), ax, n, lines);
+  FN_CUDA(cudaGetLastError());
+  return FH_OK;
+}
+
+int reduce_into(fh_fno* net, int n_part, int len, float* out) {
+  k_reduce<<<grid_for(len, kThreads, 4 * net->sms), kThreads, 0, net->stream>>>(net->partial, n_part, len, out);
+  FN_CUDA(cudaGetLastError());
+  return FH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+long long fh_fno_param_count(void) { return kNParam; }
+
+int fh_fno_create(fh_fno** out, int nx, int ny, int nz, int max_batch, int train, void* cuda_stream) {
+  fh_internal_set_error("");
+  if (!out) return ffail(FH_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (nx < kMinN || ny < kMinN || nz < kMinN)
+    return ffail(FH_ERR_ARG, "every extent must be >= %d (got %d x %d x %d)", kMinN, nx, ny, nz);
+  if (nx > 4096 || ny > 4096 || nz > 4096) return ffail(FH_ERR_ARG, "extent above 4096");
+  if (max_batch < 1 || max_batch > 1024) return ffail(FH_ERR_ARG, "max_batch %d outside 1..1024", max_batch);
+  fh_fno* net = new fh_fno();
+  cudaGetDevice(&net->dev);
+  net->nx = nx;
+  net->ny = ny;
+  net->nz = nz;
+  net->N = (long long)nx * ny * nz;
+  net->max_batch = max_batch;
+  net->train = train ? 1 : 0;
+  net->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaDeviceGetAttribute(&net->sms, cudaDevAttrMultiProcessorCount, net->dev);
+  if (net->sms < 1) net->sms = 1;
+  const long long act = (long long)max_batch * net->N * kC;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](auto** p, size_t count) {
+    if (e == cudaSuccess) e = nalloc(net, p, count);
+  };
+  A(&net->wq, (size_t)kNParam);
+  A(&net->wf, (size_t)kSpecW);
+  A(&net->wb, (size_t)kSpecW);
+  for (int ax = 0; ax < 3; ++ax) {
+    A(&net->tw[ax], (size_t)axis_len(net, ax) * kJ);
+    A(&net->itw[ax], (size_t)axis_len(net, ax) * kJ);
+  }
+  A(&net->acc, (size_t)act);
+  if (net->train) {
+    for (int i = 0; i < 5; ++i) A(&net->h[i], (size_t)act);
+    for (int i = 0; i < 3; ++i) A(&net->z[i], (size_t)act);
+    A(&net->gz, (size_t)act);
+    A(&net->gn, (size_t)act);
+    A(&net->gh, (size_t)act);
+    // per-line coefficients of the shortest axis bound every axis
+    const int nmin = nx < ny ? (nx < nz ? nx : nz) : (ny < nz ? ny : nz);
+    const long long coef = (long long)max_batch * (net->N / nmin) * kJ * kC;
+    const long long gq = (long long)max_batch * net->N * kOut;
+    A(&net->xs, (size_t)(coef > gq ? coef : gq));
+    A(&net->gys, (size_t)coef);
+    // partial sums: spectral weight gradient chunks, warps of the pointwise
+    // backward, blocks of the projection backward, lifting chunks
+    const long long lines_max = (long long)max_batch * (net->N / nmin);
+    const long long n_chunks = (lines_max + kLinesPerChunk - 1) / kLinesPerChunk;
+    long long np = n_chunks * kModes * 2 * kC * kC;
+    np = np > (long long)4 * net->sms * kWarps * kPointLen ? np : (long long)4 * net->sms * kWarps * kPointLen;
+    np = np > (long long)2 * net->sms * kProjLen ? np : (long long)2 * net->sms * kProjLen;
+    const long long lift = (long long)max_batch * ((net->N + kLiftChunk - 1) / kLiftChunk) * 2 * kC;
+    np = np > lift ? np : lift;
+    net->n_partial = np;
+    A(&net->partial, (size_t)np);
+  } else {
+    A(&net->h[0], (size_t)act);
+    A(&net->h[1], (size_t)act);
+  }
+  net->n_loss_part = 4 * net->sms;
+  A(&net->loss_part, (size_t)net->n_loss_part);
+  A(&net->fbar, (size_t)max_batch * 9);
+  A(&net->su, (size_t)max_batch * 10);
+  A(&net->phase_tab, (size_t)max_batch);
+  A(&net->q_tab, (size_t)max_batch);
+  A(&net->t_tab, (size_t)max_batch);
+  A(&net->qtmp, (size_t)9 * net->N);
+  if (e != cudaSuccess) {
+    free_all(net);
+    delete net;
+    return ffail(FH_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(e));
+  }
+  // twiddles: tw[x][2k] = cos(2 pi k x / n), tw[x][2k+1] = -sin(.);
+  // itw = (c_k / n) tw with c_0 = 1 and c_k = 2 (the real inverse DFT)
+  for (int ax = 0; ax < 3; ++ax) {
+    const int n = axis_len(net, ax);
+    std::vector<float> t((size_t)n * kJ), it((size_t)n * kJ);
+    for (int x = 0; x < n; ++x)
+      for (int k = 0; k < kModes; ++k) {
+        const double ang = 2.0 * kPi * (double)(((long long)k * x) % n) / (double)n;
+        const double ck = (k == 0 ? 1.0 : 2.0) / (double)n;
+        t[(size_t)x * kJ + 2 * k] = (float)std::cos(ang);
+        t[(size_t)x * kJ + 2 * k + 1] = (float)(-std::sin(ang));
+        it[(size_t)x * kJ + 2 * k] = (float)(ck * std::cos(ang));
+        it[(size_t)x * kJ + 2 * k + 1] = (float)(-ck * std::sin(ang));
+      }
+    e = cudaMemcpy(net->tw[ax], t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(net->itw[ax], it.data(), it.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) break;
+  }
+  const int nmax = nx > ny ? (nx > nz ? nx : nz) : (ny > nz ? ny : nz);
+  const size_t sm = spec_smem(nmax);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_point_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPointBwdSmem);
+  if (e != cudaSuccess) {
+    free_all(net);
+    delete net;
+    return ffail(FH_ERR_CUDA, "set-up failed: %s", cudaGetErrorString(e));
+  }
+  *out = net;
+  return FH_OK;
+}
+
+void fh_fno_destroy(fh_fno* net) {
+  if (!net) return;
+  DevGuard dg(net->dev);
+  cudaStreamSynchronize(net->stream);
+  free_all(net);
+  delete net;
+}
+
+int fh_fno_set_params(fh_fno* net, const float* theta_dev) {
+  fh_internal_set_error("");
+  if (!net || !theta_dev) return ffail(FH_ERR_ARG, "NULL argument");
+  DevGuard dg(net->dev);
+  k_prepare<<<grid_for(kNParam, kThreads, 4 * net->sms), kThreads, 0, net->stream>>>(theta_dev, net->wq, net->wf,
+                                                                                     net->wb);
+  FN_CUDA(cudaGetLastError());
+  FN_CUDA(cudaStreamSynchronize(net->stream));
+  net->params_set = true;
+  return FH_OK;
+}
+
+int fh_fno_forward(fh_fno* net, int B, const unsigned char* const* phase_ptrs, const double* Fbar,
+                   float* const* q_ptrs) {
+  fh_internal_set_error("");
+  if (!net || !phase_ptrs || !Fbar) return ffail(FH_ERR_ARG, "NULL argument");
+  if (B < 1 || B > net->max_batch) return ffail(FH_ERR_ARG, "batch %d outside 1..%d", B, net->max_batch);
+  if (!net->params_set) return ffail(FH_ERR_ARG, "parameters not set (fh_fno_set_params)");
+  for (int b = 0; b < B; ++b) {
+    if (!phase_ptrs[b]) return ffail(FH_ERR_ARG, "phase pointer %d is NULL", b);
+    for (int c = 0; c < 9; ++c)
+      if (!std::isfinite(Fbar[9 * b + c])) return ffail(FH_ERR_ARG, "non-finite Fbar of sample %d", b);
+  }
+  DevGuard dg(net->dev);
+  cudaStream_t s = net->stream;
+  std::vector<float*> qp((size_t)B, nullptr);
+  if (q_ptrs)
+    for (int b = 0; b < B; ++b) qp[b] = q_ptrs[b];
+  net->last_phase.assign(phase_ptrs, phase_ptrs + B);
+  FN_CUDA(cudaMemcpyAsync(net->phase_tab, phase_ptrs, B * sizeof(void*), cudaMemcpyHostToDevice, s));
+  FN_CUDA(cudaMemcpyAsync(net->q_tab, qp.data(), B * sizeof(void*), cudaMemcpyHostToDevice, s));
+  FN_CUDA(cudaMemcpyAsync(net->fbar, Fbar, (size_t)B * 9 * sizeof(double), cudaMemcpyHostToDevice, s));
+  k_load_dir<<<(B + 63) / 64, 64, 0, s>>>(net->fbar, B, net->su);
+  FN_CUDA(cudaGetLastError());
+  const long long nvox = (long long)B * net->N;
+  auto H = [&](int l) { return net->train ? net->h[l] : net->h[l & 1]; };
+  k_lift<<<grid_for(nvox * kC, kThreads, 8 * net->sms), kThreads, 0, s>>>(net->phase_tab, net->su, net->wq, net->N, B,
+                                                                        H(0));
+  FN_CUDA(cudaGetLastError());
+  for (int l = 0; l < kLayers; ++l) {
+    int rc;
+    if ((rc = spec_fwd(net, B, l, 2, false, H(l), net->acc))) return rc;
+    if ((rc = spec_fwd(net, B, l, 1, true, H(l), net->acc))) return rc;
+    if ((rc = spec_fwd(net, B, l, 0, true, H(l), net->acc))) return rc;
+    float* z = (net->train && l < kLayers - 1) ? net->z[l] : nullptr;
+    k_point_fwd<<<grid_for((nvox + 31) / 32, kWarps, 4 * net->sms), kThreads, 0, s>>>(
+        H(l), net->acc, net->wq, l, z, H(l + 1), nvox, l < kLayers - 1 ? 1 : 0);
+    FN_CUDA(cudaGetLastError());
+  }
+  k_proj_fwd<<<grid_for(nvox, kThreads, 4 * net->sms), kThreads, 0, s>>>(H(kLayers), net->wq, net->q_tab, nullptr,
+                                                                        net->N, B, nullptr);
+  FN_CUDA(cudaGetLastError());
+  FN_CUDA(cudaStreamSynchronize(s));
+  net->last_B = B;
+  return FH_OK;
+}
+
+int fh_fno_loss_grad(fh_fno* net, const float* const* target_ptrs, double* loss_out, float* grad_dev) {
+  fh_internal_set_error("");
+  if (!net || !target_ptrs) return ffail(FH_ERR_ARG, "NULL argument");
+  if (!net->train) return ffail(FH_ERR_ARG, "network created without training buffers");
+  const int B = net->last_B;
+  if (B < 1) return ffail(FH_ERR_ARG, "no forward pass to differentiate");
+  for (int b = 0; b < B; ++b)
+    if (!target_ptrs[b]) return ffail(FH_ERR_ARG, "target pointer %d is NULL", b);
+  DevGuard dg(net->dev);
+  cudaStream_t s = net->stream;
+  FN_CUDA(cudaMemcpyAsync(net->t_tab, target_ptrs, B * sizeof(void*), cudaMemcpyHostToDevice, s));
+  const long long nvox = (long long)B * net->N;
+  const double count = (double)nvox * kOut;
+  const unsigned gl = (unsigned)net->n_loss_part;
+  if (!grad_dev) {
+    k_proj_fwd<<<gl, kThreads, 0, s>>>(net->h[kLayers], net->wq, nullptr, net->t_tab, net->N, B, net->loss_part);
+    FN_CUDA(cudaGetLastError());
+  } else {
+    int rc;
+    // projection
+    k_proj_bwd_a<<<gl, kThreads, 0, s>>>(net->h[kLayers], net->wq, net->t_tab, net->N, B, (float)(2.0 / count),
+                                         net->xs, net->gn, net->loss_part);
+    FN_CUDA(cudaGetLastError());
+    const unsigned gp = (unsigned)(2 * net->sms);
+    k_proj_bwd_b<<<gp, kThreads, 0, s>>>(net->h[kLayers], net->xs, net->wq, nvox, net->partial);
+    FN_CUDA(cudaGetLastError());
+    if ((rc = reduce_into(net, (int)gp, kProjLen, grad_dev + kOffP1))) return rc;
+    // layers, last to first
+    for (int l = kLayers - 1; l >= 0; --l) {
+      const unsigned gpw = grid_for((nvox + 31) / 32, kWarps, 4 * net->sms);
+      k_point_bwd<<<gpw, kThreads, kPointBwdSmem, s>>>(net->gn, l < kLayers - 1 ? net->z[l] : nullptr, net->h[l], net->wq, l,
+                                           net->gz, net->gh, net->partial, nvox);
+      FN_CUDA(cudaGetLastError());
+      if ((rc = reduce_into(net, (int)(gpw * kWarps), kPointLen, grad_dev + off_M(l)))) return rc;
+      for (int ax = 0; ax < 3; ++ax) {
+        const int n = axis_len(net, ax);
+        const long long lines = (long long)B * (net->N / n);
+        const __nv_bfloat162* W = net->wb + (long long)(l * 3 + ax) * kModes * kC * kC;
+        k_spec_bwd<<<grid_for(lines, kWarps, 2 * net->sms), kThreads, spec_smem(n), s>>>(
+            net->h[l], net->gz, net->gh, net->xs, net->gys, W, net->tw[ax], net->itw[ax], geom(net), ax, n, lines);
+        FN_CUDA(cudaGetLastError());
+        const unsigned chunks = (unsigned)((lines + kLinesPerChunk - 1) / kLinesPerChunk);
+        k_wgrad<<<dim3(chunks, kModes), kThreads, 0, s>>>(net->xs, net->gys, lines, net->partial);
+        FN_CUDA(cudaGetLastError());
+        if ((rc = reduce_into(net, (int)chunks, (int)kWAxis, grad_dev + off_W(l) + ax * kWAxis))) return rc;
+      }
+      float* t = net->gn;
+      net->gn = net->gh;
+      net->gh = t;
+    }
+    // lifting: gn now holds the gradient with respect to h0
+    const long long chunk_vox = kLiftChunk;
+    const unsigned nch = (unsigned)((net->N + chunk_vox - 1) / chunk_vox);
+    FN_CUDA(cudaMemcpyAsync(net->phase_tab, net->last_phase.data(), B * sizeof(void*), cudaMemcpyHostToDevice, s));
+    k_lift_bwd<<<dim3(nch, B), kThreads, 0, s>>>(net->gn, net->phase_tab, net->N, chunk_vox, net->partial);
+    FN_CUDA(cudaGetLastError());
+    k_lift_finish<<<1, 32, 0, s>>>(net->partial, B, (int)nch, net->su, grad_dev);
+    FN_CUDA(cudaGetLastError());
+  }
+  std::vector<double> lp((size_t)gl);
+  FN_CUDA(cudaMemcpyAsync(lp.data(), net->loss_part, gl * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FN_CUDA(cudaStreamSynchronize(s));
+  double L = 0.0;
+  for (double v : lp) L += v;
+  if (loss_out) *loss_out = L / count;
+  return FH_OK;
+}
+
+int fh_fno_adam(fh_fno* net, float* theta_dev, const float* grad_dev, float* m_dev, float* v_dev, int t, float lr,
+                float beta1, float beta2, float eps, float wd) {
+  fh_internal_set_error("");
+  if (!net || !theta_dev || !grad_dev || !m_dev || !v_dev) return ffail(FH_ERR_ARG, "NULL argument");
+  if (t < 1) return ffail(FH_ERR_ARG, "Adam step number must be >= 1");
+  if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps > 0.0f && lr >= 0.0f && wd >= 0.0f))
+    return ffail(FH_ERR_ARG, "invalid Adam hyper-parameters");
+  DevGuard dg(net->dev);
+  k_adam<<<grid_for(kNParam, kThreads, 4 * net->sms), kThreads, 0, net->stream>>>(theta_dev, grad_dev, m_dev, v_dev,
+                                                                                 kNParam, t, lr, beta1, beta2, eps,
+                                                                                 wd);
+  FN_CUDA(cudaGetLastError());
+  FN_CUDA(cudaStreamSynchronize(net->stream));
+  return FH_OK;
+}
+
+int fh_fno_make_target(fh_fno* net, const double* F_dev, const double Fbar[9], float* target_dev) {
+  fh_internal_set_error("");
+  if (!net || !F_dev || !Fbar || !target_dev) return ffail(FH_ERR_ARG, "NULL argument");
+  DevGuard dg(net->dev);
+  FN_CUDA(cudaMemcpyAsync(net->fbar, Fbar, 9 * sizeof(double), cudaMemcpyHostToDevice, net->stream));
+  k_make_target<<<grid_for(9 * net->N, kThreads, 4 * net->sms), kThreads, 0, net->stream>>>(F_dev, net->fbar, net->N,
+                                                                                           target_dev);
+  FN_CUDA(cudaGetLastError());
+  FN_CUDA(cudaStreamSynchronize(net->stream));
+  return FH_OK;
+}
+
+int fh_fno_warm_start(fh_fno* net, fh_ctx* ctx, const unsigned char* phase_dev, const double Fbar[9],
+                      double* F_dev) {
+  fh_internal_set_error("");
+  if (!net || !ctx || !phase_dev || !Fbar || !F_dev) return ffail(FH_ERR_ARG, "NULL argument");
+  int cx, cy, cz;
+  fh_internal_ctx_grid(ctx, &cx, &cy, &cz);
+  if (cx != net->nx || cy != net->ny || cz != net->nz)
+    return ffail(FH_ERR_ARG, "context grid %dx%dx%d differs from the network grid %dx%dx%d", cx, cy, cz, net->nx,
+                 net->ny, net->nz);
+  const unsigned char* pp[1] = {phase_dev};
+  float* qp[1] = {net->qtmp};
+  int rc = fh_fno_forward(net, 1, pp, Fbar, qp);
+  if (rc) return rc;
+  {
+    DevGuard dg(net->dev);
+    k_scale_q<<<grid_for(9 * net->N, kThreads, 4 * net->sms), kThreads, 0, net->stream>>>(net->qtmp, net->su, net->N,
+                                                                                         F_dev);
+    FN_CUDA(cudaGetLastError());
+    FN_CUDA(cudaStreamSynchronize(net->stream));
+  }
+  if ((rc = fh_project(ctx, F_dev, F_dev, 1.0, nullptr))) return rc;
+  DevGuard dg(net->dev);
+  FN_CUDA(cudaMemcpyAsync(net->fbar, Fbar, 9 * sizeof(double), cudaMemcpyHostToDevice, net->stream));
+  k_add_fbar<<<grid_for(9 * net->N, kThreads, 4 * net->sms), kThreads, 0, net->stream>>>(net->fbar, net->N, F_dev);
+  FN_CUDA(cudaGetLastError());
+  FN_CUDA(cudaStreamSynchronize(net->stream));
+  return FH_OK;
+}
+
+}  // extern "C"

@@ -120,3 +120,19 @@ def test_loss_gradient_matches_finite_differences():
         tm = th.clone(); tm[i] -= h
         fd = (float(fno.loss(tp, phi, Fbar, target)) - float(fno.loss(tm, phi, Fbar, target))) / (2 * h)
         assert abs(fd - float(g[i])) <= 1e-8 * max(1.0, abs(fd)), (i, fd, float(g[i]))
+
+
+def test_adam_first_step_closed_form():
+    """At t = 1 the bias-corrected moments are g and g^2: the step is lr g / (|g| + eps) (+ lr wd theta)."""
+    rng = np.random.default_rng(8)
+    th = rng.normal(size=50)
+    g = rng.normal(size=50) * 1e-3
+    z = np.zeros(50)
+    lr, eps, wd = 1e-3, 1e-8, 0.01
+    t1, m1, v1 = fno.adam_step(th, g, z, z, 1, lr, eps=eps, wd=wd)
+    np.testing.assert_allclose(t1, th - lr * (g / (np.abs(g) + eps) + wd * th), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(m1, 0.1 * g, rtol=1e-15)
+    np.testing.assert_allclose(v1, 0.001 * g * g, rtol=1e-12)
+    # a constant gradient keeps the bias-corrected moments at g and g^2 at every step
+    t2, m2, v2 = fno.adam_step(t1, g, m1, v1, 2, lr, eps=eps)
+    np.testing.assert_allclose(t2, t1 - lr * g / (np.abs(g) + eps), rtol=1e-10, atol=1e-15)
