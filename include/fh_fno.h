@@ -15,7 +15,8 @@
  *   h0(x)  = a phi(x) + B u + b0                   width 32, phi = (phase != 0)
  *   z_l    = sum_{d = x, y, z} S_{l,d}(h_l) + M_l h_l + m_l,   l = 0..3
  *   h_l+1  = gelu(z_l) (l < 3),  h_4 = z_3         gelu(z) = z Phi(z), exact erf form
- *   q(x)   = P2 gelu(P1 h_4 + p1) + p2             hidden 128, 9 outputs
+ *   R(x)   = P2 gelu(P1 h_4 + p1) + p2             hidden 128, 81 outputs R_ij
+ *   q_i(x) = sum_j R_ij(x) u_j                     (a response per load direction)
  *   predicted fluctuation F - Fbar = s q(x)
  * S_{l,d} acts along axis d alone: the real DFT of each channel along d,
  * the 12 lowest modes k = 0..11 multiplied by a complex 32x32 matrix
@@ -23,10 +24,10 @@
  * the real inverse DFT (1/n, the imaginary part of the k = 0 term dropped).
  * Every axis of the grid must have at least 24 voxels.
  *
- * Parameter vector (float32, n = fh_fno_param_count() = 304873), in order:
+ * Parameter vector (float32, n = fh_fno_param_count() = 314161), in order:
  *   a[32], B[32][9], b0[32];
  *   for l = 0..3: W_l[3 axes x,y,z][12 modes][2 re,im][32 o][32 c], M_l[32 o][32 c], m_l[32];
- *   P1[128][32], p1[128], P2[9][128], p2[9].
+ *   P1[128][32], p1[128], P2[81][128] (row 9i + j), p2[81].
  * The forward and backward passes use a bfloat16 copy of every parameter
  * (made by fh_fno_set_params); activations, accumulations and gradients are
  * float32.
@@ -49,7 +50,7 @@ extern "C" {
 
 typedef struct fh_fno fh_fno;
 
-/* Number of float32 entries of the parameter vector (304873). */
+/* Number of float32 entries of the parameter vector (314161). */
 FH_API long long fh_fno_param_count(void);
 
 /* Network scratch for batches of up to max_batch cells of nx x ny x nz voxels

@@ -15,7 +15,8 @@ along z; a full 12^3-mode kernel would have ~7M complex weights per layer):
     h0(x)  = a phi(x) + B u + b0                          (lifting, width 32)
     z_l    = sum_{d in x,y,z} S_{l,d}(h_l) + M_l h_l + m_l,  l = 0..3
     h_l+1  = gelu(z_l) for l < 3,  h_4 = z_3
-    q(x)   = P2 gelu(P1 h_4 + p1) + p2                    (projection, 9 outputs)
+    R(x)   = P2 gelu(P1 h_4 + p1) + p2                    (projection, 81 outputs R_ij)
+    q_i(x) = sum_j R_ij(x) u_j                            (response to the load direction)
     F - Fbar ~ s q(x)
 
     S_{l,d}(h) = irfft_d( W_{l,d}[k] rfft_d(h)[k] for k < 12, zero above ),
@@ -23,7 +24,9 @@ along z; a full 12^3-mode kernel would have ~7M complex weights per layer):
 with rfft/irfft along axis d alone (unnormalised forward, 1/n inverse, the
 imaginary part of the k = 0 term dropped as irfft does) and
 W_{l,d}[k] a complex 32x32 matrix acting on the channel vector. gelu is the
-exact form z Phi(z). The loss is the mean squared error against the solver's
+exact form z Phi(z). The head predicts a 9x9 response per voxel and applies
+it to u, so the prediction is linear in the load direction for a given
+microstructure, as the cell response is to first order in |Fbar - I|. The loss is the mean squared error against the solver's
 normalised fluctuation (F - Fbar)/s over samples, components and voxels.
 
 Parameters live in one flat vector (float64 here, the GPU stores float32
@@ -45,6 +48,7 @@ LAYERS = 4
 MODES = 12
 HIDDEN = 128
 N_OUT = 9
+N_HEAD = N_OUT * 9
 
 
 def layout():
@@ -52,7 +56,7 @@ def layout():
     items = [("a", (WIDTH,)), ("B", (WIDTH, 9)), ("b0", (WIDTH,))]
     for l in range(LAYERS):
         items += [(f"W{l}", (3, MODES, 2, WIDTH, WIDTH)), (f"M{l}", (WIDTH, WIDTH)), (f"m{l}", (WIDTH,))]
-    items += [("P1", (HIDDEN, WIDTH)), ("p1", (HIDDEN,)), ("P2", (N_OUT, HIDDEN)), ("p2", (N_OUT,))]
+    items += [("P1", (HIDDEN, WIDTH)), ("p1", (HIDDEN,)), ("P2", (N_HEAD, HIDDEN)), ("p2", (N_HEAD,))]
     return items
 
 
@@ -105,7 +109,9 @@ def forward(theta: torch.Tensor, phi: torch.Tensor, Fbar: torch.Tensor, return_a
         z = z + torch.einsum("oc,bcxyz->boxyz", p[f"M{l}"], h) + p[f"m{l}"][None, :, None, None, None]
         h = gelu(z) if l < LAYERS - 1 else z
     t = gelu(torch.einsum("oc,bcxyz->boxyz", p["P1"], h) + p["p1"][None, :, None, None, None])
-    q = torch.einsum("oc,bcxyz->boxyz", p["P2"], t) + p["p2"][None, :, None, None, None]
+    R = torch.einsum("oc,bcxyz->boxyz", p["P2"], t) + p["p2"][None, :, None, None, None]
+    R = R.reshape((R.shape[0], N_OUT, 9) + R.shape[2:])
+    q = torch.einsum("bijxyz,bj->bixyz", R, u)
     return q, s
 
 

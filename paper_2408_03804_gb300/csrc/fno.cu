@@ -34,6 +34,7 @@ constexpr int kModes = 12;
 constexpr int kJ = 2 * kModes;  // real coefficients per channel and line
 constexpr int kHid = 128;
 constexpr int kOut = 9;
+constexpr int kHead = kOut * 9;  // per-voxel 9x9 response R_ij, applied to the load direction u
 constexpr int kMinN = 2 * kModes;  // retained modes stay below the Nyquist index
 
 constexpr long long kLift = kC + kC * 9 + kC;                       // 352
@@ -47,12 +48,17 @@ __host__ __device__ constexpr long long off_m(int l) { return off_M(l) + kC * kC
 constexpr long long kOffP1 = kLift + kLayers * kLayer;
 constexpr long long kOffp1 = kOffP1 + kHid * kC;
 constexpr long long kOffP2 = kOffp1 + kHid;
-constexpr long long kOffp2 = kOffP2 + kOut * kHid;
-constexpr long long kNParam = kOffp2 + kOut;                        // 304873
-constexpr int kProjLen = (int)(kNParam - kOffP1);                   // 5385
+constexpr long long kOffp2 = kOffP2 + kHead * kHid;
+constexpr long long kNParam = kOffp2 + kHead;                       // 314161
+// per-sample effective head: P2u[i][k] = sum_j P2[9i + j][k] u_j, p2u[i] = sum_j p2[9i + j] u_j
+constexpr int kHeadEff = kOut * kHid + kOut;                        // 1161
+// row of the projection weight-gradient partials: P1, p1, then the
+// per-sample sums G[i][k] = sum gq_i t_k and Gp[i] = sum gq_i
+constexpr int kProjRow = kHid * kC + kHid + kHeadEff;               // 5385
+constexpr int kProjShared = kHid * kC + kHid;                       // 4224
 constexpr int kPointLen = kC * kC + kC;                             // 1056
 constexpr long long kSpecW = (long long)kLayers * 3 * kModes * kC * kC;  // complex spectral weights
-static_assert(kNParam == 304873, "parameter layout");
+static_assert(kNParam == 314161, "parameter layout");
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
@@ -359,12 +365,54 @@ __global__ void __launch_bounds__(kThreads) k_wgrad(const float* __restrict__ xs
   }
 }
 
-// out[i] = sum over p of partial[p][i], in order of p (double accumulator)
-__global__ void k_reduce(const float* __restrict__ partial, int n_part, int len, float* __restrict__ out) {
+// out[i] = sum over p of partial[p * stride + i], in order of p (double accumulator)
+__global__ void k_reduce(const float* __restrict__ partial, int n_part, int len, int stride, float* __restrict__ out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int p = 0; p < n_part; ++p) s += (double)partial[(long long)p * len + i];
+    for (int p = 0; p < n_part; ++p) s += (double)partial[(long long)p * stride + i];
     out[i] = (float)s;
+  }
+}
+
+// effective head of every sample from P2, p2 and the sample's load direction u
+__global__ void k_head(const __nv_bfloat16* __restrict__ wq, const float* __restrict__ su, int B,
+                       float* __restrict__ head) {
+  const int total = B * kHeadEff;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int b = e / kHeadEff, r = e - b * kHeadEff;
+    const float* u = su + 10 * b + 1;
+    float acc = 0.0f;
+    if (r < kOut * kHid) {
+      const int i = r / kHid, k = r - i * kHid;
+#pragma unroll
+      for (int j = 0; j < 9; ++j) acc = fmaf(bf(wq, kOffP2 + (long long)(9 * i + j) * kHid + k), u[j], acc);
+    } else {
+      const int i = r - kOut * kHid;
+#pragma unroll
+      for (int j = 0; j < 9; ++j) acc = fmaf(bf(wq, kOffp2 + 9 * i + j), u[j], acc);
+    }
+    head[e] = acc;
+  }
+}
+
+// head gradient from the per-sample sums: gP2[9i + j][k] = sum_b u_bj G_b[i][k], gp2[9i + j] = sum_b u_bj Gp_b[i]
+__global__ void k_head_grad(const float* __restrict__ G, const float* __restrict__ su, int B,
+                            float* __restrict__ grad) {
+  const int total = kHead * kHid + kHead;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    int src, j;
+    if (e < kHead * kHid) {
+      const int row = e / kHid, k = e - row * kHid;
+      j = row % 9;
+      src = (row / 9) * kHid + k;
+    } else {
+      const int row = e - kHead * kHid;
+      j = row % 9;
+      src = kOut * kHid + row / 9;
+    }
+    double acc = 0.0;
+    for (int b = 0; b < B; ++b) acc += (double)su[10 * b + 1 + j] * (double)G[(long long)b * kHeadEff + src];
+    grad[kOffP2 + e] = (float)acc;
   }
 }
 
@@ -484,11 +532,11 @@ struct ProjSmem {
   float p2[kOut];
 };
 
-__device__ __forceinline__ void load_proj(ProjSmem& s, const __nv_bfloat16* wq) {
+__device__ __forceinline__ void load_proj(ProjSmem& s, const __nv_bfloat16* wq, const float* head) {
   for (int i = threadIdx.x; i < kHid * kC; i += blockDim.x) s.P1[i] = bf(wq, kOffP1 + i);
   for (int i = threadIdx.x; i < kHid; i += blockDim.x) s.p1[i] = bf(wq, kOffp1 + i);
-  for (int i = threadIdx.x; i < kOut * kHid; i += blockDim.x) s.P2[i] = bf(wq, kOffP2 + i);
-  for (int i = threadIdx.x; i < kOut; i += blockDim.x) s.p2[i] = bf(wq, kOffp2 + i);
+  for (int i = threadIdx.x; i < kOut * kHid; i += blockDim.x) s.P2[i] = head[i];
+  for (int i = threadIdx.x; i < kOut; i += blockDim.x) s.p2[i] = head[kOut * kHid + i];
   __syncthreads();
 }
 
@@ -531,19 +579,15 @@ __device__ __forceinline__ double block_sum_d(double v) {
 
 __global__ void __launch_bounds__(kThreads) k_proj_fwd(const float* __restrict__ h4,
                                                        const __nv_bfloat16* __restrict__ wq,
-                                                       float* const* __restrict__ qtab,
-                                                       const float* const* __restrict__ ttab, long long N, int B,
+                                                       const float* __restrict__ head, float* __restrict__ qo,
+                                                       const float* __restrict__ target, long long N,
                                                        double* __restrict__ loss_part) {
   __shared__ __align__(16) ProjSmem s;
-  load_proj(s, wq);
+  load_proj(s, wq, head);
   double loss = 0.0;
-  const long long nvox = (long long)B * N;
-  for (long long vox = (long long)blockIdx.x * blockDim.x + threadIdx.x; vox < nvox;
-       vox += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(vox / N);
-    const long long v = vox - (long long)b * N;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (long long)gridDim.x * blockDim.x) {
     float hv[kC];
-    load_h(h4, vox, hv);
+    load_h(h4, v, hv);
     float q[kOut];
 #pragma unroll
     for (int i = 0; i < kOut; ++i) q[i] = s.p2[i];
@@ -552,13 +596,13 @@ __global__ void __launch_bounds__(kThreads) k_proj_fwd(const float* __restrict__
 #pragma unroll
       for (int i = 0; i < kOut; ++i) q[i] = fmaf(s.P2[i * kHid + j], t, q[i]);
     }
-    if (qtab && qtab[b])
+    if (qo)
 #pragma unroll
-      for (int i = 0; i < kOut; ++i) qtab[b][i * N + v] = q[i];
-    if (ttab)
+      for (int i = 0; i < kOut; ++i) qo[i * N + v] = q[i];
+    if (target)
 #pragma unroll
       for (int i = 0; i < kOut; ++i) {
-        const double d = (double)q[i] - (double)ttab[b][i * N + v];
+        const double d = (double)q[i] - (double)target[i * N + v];
         loss += d * d;
       }
   }
@@ -572,17 +616,15 @@ __global__ void __launch_bounds__(kThreads) k_proj_fwd(const float* __restrict__
 // gh4 = P1^T (gelu'(pre) . P2^T gq), and the loss partial sums
 __global__ void __launch_bounds__(kThreads) k_proj_bwd_a(const float* __restrict__ h4,
                                                          const __nv_bfloat16* __restrict__ wq,
-                                                         const float* const* __restrict__ ttab, long long N, int B,
-                                                         float scale, float* __restrict__ gq_out,
-                                                         float* __restrict__ gh4, double* __restrict__ loss_part) {
+                                                         const float* __restrict__ head,
+                                                         const float* __restrict__ target, long long N, float scale,
+                                                         float* __restrict__ gq_out, float* __restrict__ gh4,
+                                                         double* __restrict__ loss_part) {
   __shared__ __align__(16) ProjSmem s;
-  load_proj(s, wq);
+  load_proj(s, wq, head);
   double loss = 0.0;
-  const long long nvox = (long long)B * N;
-  for (long long vox = (long long)blockIdx.x * blockDim.x + threadIdx.x; vox < nvox;
-       vox += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(vox / N);
-    const long long v = vox - (long long)b * N;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (long long)gridDim.x * blockDim.x) {
+    const long long vox = v;
     float hv[kC];
     load_h(h4, vox, hv);
     float q[kOut];
@@ -595,12 +637,12 @@ __global__ void __launch_bounds__(kThreads) k_proj_bwd_a(const float* __restrict
     }
 #pragma unroll
     for (int i = 0; i < kOut; ++i) {
-      const float d = q[i] - ttab[b][i * N + v];
+      const float d = q[i] - target[i * N + v];
       loss += (double)d * (double)d;
       q[i] = scale * d;  // now gq
       gq_out[vox * kOut + i] = q[i];
     }
-    float g[kC];
+  float g[kC];
 #pragma unroll
     for (int c = 0; c < kC; ++c) g[c] = 0.0f;
     for (int j = 0; j < kHid; ++j) {
@@ -627,11 +669,13 @@ __global__ void __launch_bounds__(kThreads) k_proj_bwd_a(const float* __restrict
   if (threadIdx.x == 0) loss_part[blockIdx.x] = t;
 }
 
-// projection weight gradient: thread (hidden unit j, half of the channels)
-// accumulates gP1[j][16 channels]; the first half also gp1[j] and gP2[.][j];
-// threads 0..8 also gp2. Per-block partials in parameter order from P1 on.
+// projection weight gradient of one sample: thread (hidden unit j, half of
+// the channels) accumulates gP1[j][16 channels]; the first half also gp1[j]
+// and G[.][j] = sum gq t_j; threads 0..8 also Gp = sum gq. Per-block rows of
+// kProjRow entries (P1, p1, G, Gp).
 __global__ void __launch_bounds__(kThreads) k_proj_bwd_b(const float* __restrict__ h4, const float* __restrict__ gq,
-                                                         const __nv_bfloat16* __restrict__ wq, long long nvox,
+                                                         const __nv_bfloat16* __restrict__ wq,
+                                                         const float* __restrict__ head, long long nvox,
                                                          float* __restrict__ partial) {
   __shared__ __align__(16) float sH[kTileProj * kC];
   __shared__ float sQ[kTileProj * kOut];
@@ -640,7 +684,7 @@ __global__ void __launch_bounds__(kThreads) k_proj_bwd_b(const float* __restrict
 #pragma unroll
   for (int c = 0; c < kC; ++c) P1j[c] = bf(wq, kOffP1 + j * kC + c);
 #pragma unroll
-  for (int i = 0; i < kOut; ++i) P2j[i] = bf(wq, kOffP2 + i * kHid + j);
+  for (int i = 0; i < kOut; ++i) P2j[i] = head[i * kHid + j];
   const float p1j = bf(wq, kOffp1 + j);
   float a1[16], a2[kOut];
   float ap1 = 0.0f, ap2 = 0.0f;
@@ -679,7 +723,7 @@ __global__ void __launch_bounds__(kThreads) k_proj_bwd_b(const float* __restrict
     }
     __syncthreads();
   }
-  float* p = partial + (long long)blockIdx.x * kProjLen;
+  float* p = partial + (long long)blockIdx.x * kProjRow;
 #pragma unroll
   for (int k = 0; k < 16; ++k) p[j * kC + c0 + k] = a1[k];
   if (half == 0) {
@@ -808,10 +852,10 @@ struct fh_fno {
   double* loss_part = nullptr;
   int n_loss_part = 0;
   double* fbar = nullptr;   // [max_batch][9]
-  float* su = nullptr;      // [max_batch][10]
+  float* su = nullptr;      // [max_batch][10]: s, u
+  float* head = nullptr;    // [max_batch][kHeadEff]: effective head of each sample
+  float* gh_head = nullptr; // [max_batch][kHeadEff]: per-sample head-gradient sums
   const uint8_t** phase_tab = nullptr;
-  float** q_tab = nullptr;
-  const float** t_tab = nullptr;
   float* qtmp = nullptr;    // [9][N] for the warm start
   std::vector<const uint8_t*> last_phase;
   int last_B = 0;
@@ -888,8 +932,8 @@ int spec_fwd(fh_fno* net, int B, int l, int ax, bool accum, const float* h, floa
   return FH_OK;
 }
 
-int reduce_into(fh_fno* net, int n_part, int len, float* out) {
-  k_reduce<<<grid_for(len, kThreads, 4 * net->sms), kThreads, 0, net->stream>>>(net->partial, n_part, len, out);
+int reduce_into(fh_fno* net, int n_part, int len, int stride, const float* partial, float* out) {
+  k_reduce<<<grid_for(len, kThreads, 4 * net->sms), kThreads, 0, net->stream>>>(partial, n_part, len, stride, out);
   FN_CUDA(cudaGetLastError());
   return FH_OK;
 }
@@ -950,7 +994,8 @@ int fh_fno_create(fh_fno** out, int nx, int ny, int nz, int max_batch, int train
     const long long n_chunks = (lines_max + kLinesPerChunk - 1) / kLinesPerChunk;
     long long np = n_chunks * kModes * 2 * kC * kC;
     np = np > (long long)4 * net->sms * kWarps * kPointLen ? np : (long long)4 * net->sms * kWarps * kPointLen;
-    np = np > (long long)2 * net->sms * kProjLen ? np : (long long)2 * net->sms * kProjLen;
+    const long long proj = (long long)max_batch * 2 * net->sms * kProjRow;
+    np = np > proj ? np : proj;
     const long long lift = (long long)max_batch * ((net->N + kLiftChunk - 1) / kLiftChunk) * 2 * kC;
     np = np > lift ? np : lift;
     net->n_partial = np;
@@ -959,13 +1004,13 @@ int fh_fno_create(fh_fno** out, int nx, int ny, int nz, int max_batch, int train
     A(&net->h[0], (size_t)act);
     A(&net->h[1], (size_t)act);
   }
-  net->n_loss_part = 4 * net->sms;
-  A(&net->loss_part, (size_t)net->n_loss_part);
+  net->n_loss_part = 4 * net->sms;  // per sample
+  A(&net->loss_part, (size_t)max_batch * net->n_loss_part);
   A(&net->fbar, (size_t)max_batch * 9);
   A(&net->su, (size_t)max_batch * 10);
+  A(&net->head, (size_t)max_batch * kHeadEff);
+  A(&net->gh_head, (size_t)max_batch * kHeadEff);
   A(&net->phase_tab, (size_t)max_batch);
-  A(&net->q_tab, (size_t)max_batch);
-  A(&net->t_tab, (size_t)max_batch);
   A(&net->qtmp, (size_t)9 * net->N);
   if (e != cudaSuccess) {
     free_all(net);
@@ -1039,14 +1084,13 @@ int fh_fno_forward(fh_fno* net, int B, const unsigned char* const* phase_ptrs, c
   }
   DevGuard dg(net->dev);
   cudaStream_t s = net->stream;
-  std::vector<float*> qp((size_t)B, nullptr);
-  if (q_ptrs)
-    for (int b = 0; b < B; ++b) qp[b] = q_ptrs[b];
   net->last_phase.assign(phase_ptrs, phase_ptrs + B);
   FN_CUDA(cudaMemcpyAsync(net->phase_tab, phase_ptrs, B * sizeof(void*), cudaMemcpyHostToDevice, s));
-  FN_CUDA(cudaMemcpyAsync(net->q_tab, qp.data(), B * sizeof(void*), cudaMemcpyHostToDevice, s));
   FN_CUDA(cudaMemcpyAsync(net->fbar, Fbar, (size_t)B * 9 * sizeof(double), cudaMemcpyHostToDevice, s));
   k_load_dir<<<(B + 63) / 64, 64, 0, s>>>(net->fbar, B, net->su);
+  FN_CUDA(cudaGetLastError());
+  k_head<<<grid_for((long long)B * kHeadEff, kThreads, 4 * net->sms), kThreads, 0, s>>>(net->wq, net->su, B,
+                                                                                       net->head);
   FN_CUDA(cudaGetLastError());
   const long long nvox = (long long)B * net->N;
   auto H = [&](int l) { return net->train ? net->h[l] : net->h[l & 1]; };
@@ -1063,9 +1107,14 @@ int fh_fno_forward(fh_fno* net, int B, const unsigned char* const* phase_ptrs, c
         H(l), net->acc, net->wq, l, z, H(l + 1), nvox, l < kLayers - 1 ? 1 : 0);
     FN_CUDA(cudaGetLastError());
   }
-  k_proj_fwd<<<grid_for(nvox, kThreads, 4 * net->sms), kThreads, 0, s>>>(H(kLayers), net->wq, net->q_tab, nullptr,
-                                                                        net->N, B, nullptr);
-  FN_CUDA(cudaGetLastError());
+  if (q_ptrs)
+    for (int b = 0; b < B; ++b) {
+      if (!q_ptrs[b]) continue;
+      k_proj_fwd<<<grid_for(net->N, kThreads, 4 * net->sms), kThreads, 0, s>>>(
+          H(kLayers) + (long long)b * net->N * kC, net->wq, net->head + (long long)b * kHeadEff, q_ptrs[b], nullptr,
+          net->N, nullptr);
+      FN_CUDA(cudaGetLastError());
+    }
   FN_CUDA(cudaStreamSynchronize(s));
   net->last_B = B;
   return FH_OK;
@@ -1081,30 +1130,47 @@ int fh_fno_loss_grad(fh_fno* net, const float* const* target_ptrs, double* loss_
     if (!target_ptrs[b]) return ffail(FH_ERR_ARG, "target pointer %d is NULL", b);
   DevGuard dg(net->dev);
   cudaStream_t s = net->stream;
-  FN_CUDA(cudaMemcpyAsync(net->t_tab, target_ptrs, B * sizeof(void*), cudaMemcpyHostToDevice, s));
   const long long nvox = (long long)B * net->N;
   const double count = (double)nvox * kOut;
   const unsigned gl = (unsigned)net->n_loss_part;
+  const long long N = net->N;
   if (!grad_dev) {
-    k_proj_fwd<<<gl, kThreads, 0, s>>>(net->h[kLayers], net->wq, nullptr, net->t_tab, net->N, B, net->loss_part);
-    FN_CUDA(cudaGetLastError());
+    for (int b = 0; b < B; ++b) {
+      k_proj_fwd<<<gl, kThreads, 0, s>>>(net->h[kLayers] + b * N * kC, net->wq, net->head + (long long)b * kHeadEff,
+                                         nullptr, target_ptrs[b], N, net->loss_part + (long long)b * gl);
+      FN_CUDA(cudaGetLastError());
+    }
   } else {
     int rc;
-    // projection
-    k_proj_bwd_a<<<gl, kThreads, 0, s>>>(net->h[kLayers], net->wq, net->t_tab, net->N, B, (float)(2.0 / count),
-                                         net->xs, net->gn, net->loss_part);
-    FN_CUDA(cudaGetLastError());
+    // projection, sample by sample (each has its own effective head)
     const unsigned gp = (unsigned)(2 * net->sms);
-    k_proj_bwd_b<<<gp, kThreads, 0, s>>>(net->h[kLayers], net->xs, net->wq, nvox, net->partial);
+    for (int b = 0; b < B; ++b) {
+      const float* hb = net->h[kLayers] + b * N * kC;
+      const float* headb = net->head + (long long)b * kHeadEff;
+      k_proj_bwd_a<<<gl, kThreads, 0, s>>>(hb, net->wq, headb, target_ptrs[b], N, (float)(2.0 / count),
+                                           net->xs + b * N * kOut, net->gn + b * N * kC,
+                                           net->loss_part + (long long)b * gl);
+      FN_CUDA(cudaGetLastError());
+      k_proj_bwd_b<<<gp, kThreads, 0, s>>>(hb, net->xs + b * N * kOut, net->wq, headb, N,
+                                           net->partial + (long long)b * gp * kProjRow);
+      FN_CUDA(cudaGetLastError());
+    }
+    if ((rc = reduce_into(net, (int)(B * gp), kProjShared, kProjRow, net->partial, grad_dev + kOffP1))) return rc;
+    for (int b = 0; b < B; ++b)
+      if ((rc = reduce_into(net, (int)gp, kHeadEff, kProjRow, net->partial + (long long)b * gp * kProjRow + kProjShared,
+                            net->gh_head + (long long)b * kHeadEff)))
+        return rc;
+    k_head_grad<<<grid_for(kHead * kHid + kHead, kThreads, 4 * net->sms), kThreads, 0, s>>>(net->gh_head, net->su, B,
+                                                                                           grad_dev);
     FN_CUDA(cudaGetLastError());
-    if ((rc = reduce_into(net, (int)gp, kProjLen, grad_dev + kOffP1))) return rc;
     // layers, last to first
     for (int l = kLayers - 1; l >= 0; --l) {
       const unsigned gpw = grid_for((nvox + 31) / 32, kWarps, 4 * net->sms);
       k_point_bwd<<<gpw, kThreads, kPointBwdSmem, s>>>(net->gn, l < kLayers - 1 ? net->z[l] : nullptr, net->h[l], net->wq, l,
                                            net->gz, net->gh, net->partial, nvox);
       FN_CUDA(cudaGetLastError());
-      if ((rc = reduce_into(net, (int)(gpw * kWarps), kPointLen, grad_dev + off_M(l)))) return rc;
+      if ((rc = reduce_into(net, (int)(gpw * kWarps), kPointLen, kPointLen, net->partial, grad_dev + off_M(l))))
+        return rc;
       for (int ax = 0; ax < 3; ++ax) {
         const int n = axis_len(net, ax);
         const long long lines = (long long)B * (net->N / n);
@@ -1115,7 +1181,8 @@ int fh_fno_loss_grad(fh_fno* net, const float* const* target_ptrs, double* loss_
         const unsigned chunks = (unsigned)((lines + kLinesPerChunk - 1) / kLinesPerChunk);
         k_wgrad<<<dim3(chunks, kModes), kThreads, 0, s>>>(net->xs, net->gys, lines, net->partial);
         FN_CUDA(cudaGetLastError());
-        if ((rc = reduce_into(net, (int)chunks, (int)kWAxis, grad_dev + off_W(l) + ax * kWAxis))) return rc;
+        if ((rc = reduce_into(net, (int)chunks, (int)kWAxis, (int)kWAxis, net->partial, grad_dev + off_W(l) + ax * kWAxis)))
+          return rc;
       }
       float* t = net->gn;
       net->gn = net->gh;
@@ -1130,8 +1197,8 @@ int fh_fno_loss_grad(fh_fno* net, const float* const* target_ptrs, double* loss_
     k_lift_finish<<<1, 32, 0, s>>>(net->partial, B, (int)nch, net->su, grad_dev);
     FN_CUDA(cudaGetLastError());
   }
-  std::vector<double> lp((size_t)gl);
-  FN_CUDA(cudaMemcpyAsync(lp.data(), net->loss_part, gl * sizeof(double), cudaMemcpyDeviceToHost, s));
+  std::vector<double> lp((size_t)B * gl);
+  FN_CUDA(cudaMemcpyAsync(lp.data(), net->loss_part, lp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   FN_CUDA(cudaStreamSynchronize(s));
   double L = 0.0;
   for (double v : lp) L += v;

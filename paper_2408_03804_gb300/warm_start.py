@@ -79,8 +79,8 @@ def init_params(seed: int) -> np.ndarray:
     for _ in range(L):
         parts += [rng.uniform(0, 1, 3 * K * 2 * C * C) / (C * C), rng.uniform(-1, 1, C * C) / math.sqrt(C),
                   np.zeros(C)]
-    parts += [rng.uniform(-1, 1, H * C) / math.sqrt(C), np.zeros(H), rng.uniform(-1, 1, 9 * H) / math.sqrt(H),
-              np.zeros(9)]
+    parts += [rng.uniform(-1, 1, H * C) / math.sqrt(C), np.zeros(H), rng.uniform(-1, 1, 81 * H) / math.sqrt(H),
+              np.zeros(81)]
     th = np.concatenate(parts).astype(np.float32)
     assert th.size == B.load().fh_fno_param_count()
     return th

@@ -1,6 +1,6 @@
 """Pins of the oracle's factorized FNO (learned warm start).
 
-* parameter layout: 352 lifting + 4 x 74784 layer + 5385 projection entries;
+* parameter layout: 352 lifting + 4 x 74784 layer + 14673 projection entries;
 * one spectral layer on a single Fourier mode along x (constant along y, z)
   returns the closed form Re(W^x_m[o,c] e^{i theta}) + Re(W^y_0 + W^z_0)[o,c] cos theta,
   and a mode above the retained ones contributes only through y and z;
@@ -44,7 +44,7 @@ def _inputs(seed, B=2, shape=(N, N, N)):
 
 
 def test_parameter_layout():
-    assert fno.n_params() == 352 + 4 * (3 * 12 * 2 * 32 * 32 + 32 * 32 + 32) + (128 * 32 + 128 + 9 * 128 + 9)
+    assert fno.n_params() == 352 + 4 * (3 * 12 * 2 * 32 * 32 + 32 * 32 + 32) + (128 * 32 + 128 + 81 * 128 + 81)
     p = fno.unpack(torch.arange(fno.n_params(), dtype=torch.float64))
     assert p["p2"][-1] == fno.n_params() - 1
 
@@ -95,7 +95,8 @@ def test_zero_spectral_weights_is_a_voxel_network():
         for l in range(fno.LAYERS):
             z = P[f"M{l}"] @ h + P[f"m{l}"]
             h = gelu(z) if l < fno.LAYERS - 1 else z
-        out = P["P2"] @ gelu(P["P1"] @ h + P["p1"]) + P["p2"]
+        R = (P["P2"] @ gelu(P["P1"] @ h + P["p1"]) + P["p2"]).reshape(9, 9)
+        out = np.array([sum(R[i, j] * u[j] for j in range(9)) for i in range(9)])
         np.testing.assert_allclose(q[0][(slice(None),) + v].numpy(), out, rtol=1e-12, atol=1e-12)
 
 
@@ -136,3 +137,15 @@ def test_adam_first_step_closed_form():
     # a constant gradient keeps the bias-corrected moments at g and g^2 at every step
     t2, m2, v2 = fno.adam_step(t1, g, m1, v1, 2, lr, eps=eps)
     np.testing.assert_allclose(t2, t1 - lr * g / (np.abs(g) + eps), rtol=1e-10, atol=1e-15)
+
+
+def test_prediction_is_odd_in_the_load_direction_when_the_body_ignores_it():
+    """With B = 0 the body sees only phi, and q = R(phi) u changes sign with u."""
+    th = _theta(9)
+    fno.unpack(th)["B"].zero_()
+    phi, Fbar = _inputs(10, B=1)
+    d = Fbar - torch.eye(3, dtype=torch.float64).reshape(1, 9)
+    qp, _ = fno.forward(th, phi, torch.eye(3, dtype=torch.float64).reshape(1, 9) + d)
+    qm, _ = fno.forward(th, phi, torch.eye(3, dtype=torch.float64).reshape(1, 9) - d)
+    np.testing.assert_allclose(qp.numpy(), -qm.numpy(), rtol=0, atol=1e-12)
+    assert float(qp.abs().max()) > 1e-3
