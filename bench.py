@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 N_GRID = 128
 N_INC = 5
 NEWTON_TOL = 1e-8
+WARM_WEIGHTS = os.path.join(ROOT, "paper_2408_03804_gb300", "weights", "fno_neo_hookean_64.npy")
 GAMMA = 0.05
 METRIC = "time-to-solve @1e-8 residual (128³ neo-Hookean); CG matvec GB/s vs HBM peak"
 WORKLOAD = ("neo-Hookean 128^3, RSA spheres r~U[4,10] vox, f=0.30, contrast 10 (mu=1, lambda=1.5), "
@@ -103,10 +104,14 @@ def cg_iteration_bytes(nx, ny, nz):
                                                            "cg_update"))
 
 
+# sources of the projection and CG kernels whose DRAM traffic profiles/ncu_traffic.json records
+TRAFFIC_SOURCES = ("kernels_fft.cu", "fft_core.cuh", "fh_common.cuh", "fh_kernels.h")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2408_03804_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in TRAFFIC_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh_:
             h.update(fh_.read())
     return h.hexdigest()[:16]
@@ -462,6 +467,106 @@ def run_batch(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_warm_start(args, world, rank, local):
+    """Learned warm start against the zero initial guess on held-out cells.
+
+    Each step is one held-out neo-Hookean cell (the training distribution of
+    the network: RSA spheres of radius U[4, 10]/128 of the box at a volume
+    fraction U[0.1, 0.3], matrix (lambda, mu) = (1.5, 1), inclusions 10x,
+    |Fbar - I| <= 0.05, one load increment, Newton tolerance 1e-8) solved from
+    Fbar and from the network's prediction; both times are CUDA-event times on
+    the solver's stream, the warm-started one including the network's forward
+    pass and the projection. Also times one training step (batch 8 at 64^3:
+    forward, loss gradient, Adam) of the network's own kernels.
+    """
+    import torch
+
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    import paper_2408_03804_gb300 as fh
+    from paper_2408_03804_gb300 import build as fhbuild
+    from paper_2408_03804_gb300 import warm_start as ws
+
+    fhbuild.build()
+    fh.load()
+    n = args.shape[0]
+    shape = (n, n, n)
+    theta = np.load(WARM_WEIGHTS).astype(np.float32)
+    n_cells = args.warmup + args.steps
+    seeds = [2_000_000 + 1000 * rank + i for i in range(n_cells)]
+    t_in = time.perf_counter()
+    cells = [(ph, fb) for _, ph, fb in ws.cells(n, seeds, max(1, min(16, (os.cpu_count() or 2) - 1)))]
+    t_in = time.perf_counter() - t_in
+    stream = torch.cuda.Stream()
+    rows = []
+    with torch.cuda.stream(stream), fh.Context(*shape, stream=stream.cuda_stream) as ctx, \
+            fh.Fno(*shape, max_batch=1, stream=stream.cuda_stream) as net:
+        net.set_params(torch.as_tensor(theta).cuda())
+        F = torch.empty((9,) + shape, dtype=torch.float64, device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with ClockSampler(local) as clk:
+            for i, (ph, fb) in enumerate(cells):
+                phd = torch.as_tensor(ph).cuda()
+                torch.cuda.synchronize()
+                ev[0].record(stream)
+                F.zero_()
+                st0, rc0 = ws.solve_cell(ctx, phd, fb, F)
+                ev[1].record(stream)
+                ref = F.clone()
+                ev[2].record(stream)
+                net.warm_start(ctx, phd, fb, F)
+                st1, rc1 = ws.solve_cell(ctx, phd, fb, F, init_given=True)
+                ev[3].record(stream)
+                torch.cuda.synchronize()
+                if i >= args.warmup:
+                    rows.append({"t0": ev[0].elapsed_time(ev[1]) / 1e3, "t1": ev[2].elapsed_time(ev[3]) / 1e3,
+                                 "n0": st0["n_newton"], "n1": st1["n_newton"], "c0": st0["n_cg"], "c1": st1["n_cg"],
+                                 "rc": (rc0, rc1), "diff": float((F - ref).abs().max())})
+        # one training step of the network's kernels (batch 8 at 64^3, synthetic cells and targets)
+        m = 64
+        with fh.Fno(m, m, m, max_batch=8, train=True, stream=stream.cuda_stream) as tnet:
+            th = torch.as_tensor(theta).cuda()
+            mom = torch.zeros_like(th)
+            var = torch.zeros_like(th)
+            g = torch.empty_like(th)
+            gen = torch.Generator(device="cuda").manual_seed(rank)
+            ph8 = [(torch.rand((m, m, m), generator=gen, device="cuda") < 0.25).to(torch.uint8) for _ in range(8)]
+            tg8 = [0.1 * torch.randn((9, m, m, m), generator=gen, device="cuda") for _ in range(8)]
+            fb8 = np.tile(np.eye(3).reshape(1, 9), (8, 1)) + 0.03 * np.random.default_rng(rank).normal(size=(8, 9))
+            times = []
+            for t in range(1, 6):
+                torch.cuda.synchronize()
+                ev[0].record(stream)
+                tnet.set_params(th)
+                tnet.forward(ph8, fb8)
+                tnet.loss_grad(tg8, g)
+                tnet.adam(th, g, mom, var, t, 1e-4)
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                times.append(ev[0].elapsed_time(ev[1]))
+            train_ms = statistics.median(times[2:])
+    t0 = max_over_ranks(world, float(np.mean([r["t0"] for r in rows])), torch.device("cuda", local))
+    t1 = max_over_ranks(world, float(np.mean([r["t1"] for r in rows])), torch.device("cuda", local))
+    if rank != 0:
+        return
+    line = {
+        "metric": f"time-to-solve @1e-8 of held-out {n}^3 neo-Hookean cells, learned warm start vs zero guess",
+        "value": t1, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": False, "scaling": "weak", "dtype": "f64 solve, bf16/f32 network", "data": "synthetic",
+        "config": {"workload": f"{n}^3 RSA spheres r U[4,10]/128 L, f U[0.1,0.3], inclusions 10x, "
+                               "|Fbar - I| <= 0.05, 1 increment, Newton tol 1e-8; network trained at 64^3",
+                   "weights": os.path.relpath(WARM_WEIGHTS, ROOT), "input_generation_s": t_in},
+        "zero_guess_s": t0, "time_saved_frac": 1.0 - t1 / t0,
+        "newton": [float(np.mean([r["n0"] for r in rows])), float(np.mean([r["n1"] for r in rows]))],
+        "cg": [float(np.mean([r["c0"] for r in rows])), float(np.mean([r["c1"] for r in rows]))],
+        "all_converged": all(r["rc"] == (0, 0) for r in rows),
+        "max_field_diff_vs_zero_guess": max(r["diff"] for r in rows),
+        "train_step_ms_batch8_64": train_ms,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -622,6 +727,8 @@ def main():
     ap.add_argument("--probe-newton", action="store_true",
                     help="run one Newton iteration with 16 CG products (for ncu launch lists) and exit")
     ap.add_argument("--no-cufft", action="store_true")
+    ap.add_argument("--warm-start", action="store_true",
+                    help="learned warm start vs zero guess on held-out cells of --shape (not the bench line)")
     ap.add_argument("--shape", type=int, nargs=3, default=[N_GRID] * 3,
                     help="grid of the solve (smaller cases are for profiling, not bench lines)")
     args = ap.parse_args()
@@ -631,6 +738,9 @@ def main():
         return
     if args.batch:
         run_batch(args, world, rank, local)
+        return
+    if args.warm_start:
+        run_warm_start(args, world, rank, local)
         return
     run_ours(args, world, rank, local)
 
