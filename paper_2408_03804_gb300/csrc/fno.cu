@@ -160,22 +160,22 @@ __global__ void k_lift(const uint8_t* const* __restrict__ phase, const float* __
 // ---------------------------------------------------------------------------
 // spectral convolution along one axis, forward: out (=/+=) S_ax(h)
 // ---------------------------------------------------------------------------
+// shared memory of the spectral kernels: twiddles (2 x n x 24) and one 24 x 32
+// coefficient block per warp; the complex weights (48 KiB per layer and axis)
+// are read through L1, which keeps more CTAs resident than staging them
 __host__ __device__ constexpr size_t spec_smem(int n) {
-  return (size_t)kModes * kC * kC * sizeof(__nv_bfloat162) + 2 * (size_t)n * kJ * sizeof(float) +
-         (size_t)kWarps * kJ * kC * sizeof(float);
+  return 2 * (size_t)n * kJ * sizeof(float) + (size_t)kWarps * kJ * kC * sizeof(float);
 }
 
 template <bool ACCUM>
-__global__ void __launch_bounds__(kThreads) k_spec_fwd(const float* __restrict__ h, float* __restrict__ out,
+__global__ void __launch_bounds__(kThreads, 4) k_spec_fwd(const float* __restrict__ h, float* __restrict__ out,
                                                        const __nv_bfloat162* __restrict__ W,
                                                        const float* __restrict__ tw, const float* __restrict__ itw,
                                                        Geom g, int ax, int n, long long n_lines) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __nv_bfloat162* sW = reinterpret_cast<__nv_bfloat162*>(smem);
-  float* stw = reinterpret_cast<float*>(smem + (size_t)kModes * kC * kC * sizeof(__nv_bfloat162));
+  float* stw = reinterpret_cast<float*>(smem);
   float* sitw = stw + n * kJ;
   float* sX = sitw + n * kJ;
-  for (int i = threadIdx.x; i < kModes * kC * kC; i += blockDim.x) sW[i] = W[i];
   for (int i = threadIdx.x; i < n * kJ; i += blockDim.x) {
     stw[i] = tw[i];
     sitw[i] = itw[i];
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kThreads) k_spec_fwd(const float* __restrict__
     for (int c = 0; c < kC; ++c) {
 #pragma unroll
       for (int k = 0; k < kModes; ++k) {
-        const float2 w = __bfloat1622float2(sW[(k * kC + c) * kC + lane]);
+        const float2 w = __bfloat1622float2(__ldg(&W[(k * kC + c) * kC + lane]));
         const float xr = X[(2 * k) * kC + c], xi = X[(2 * k + 1) * kC + c];
         y[2 * k] = fmaf(w.x, xr, fmaf(-w.y, xi, y[2 * k]));
         y[2 * k + 1] = fmaf(w.x, xi, fmaf(w.y, xr, y[2 * k + 1]));
@@ -249,17 +249,15 @@ __global__ void __launch_bounds__(kThreads) k_spec_fwd(const float* __restrict__
 // forward coefficients X of h and the coefficient gradient gY of every line
 // for the weight gradient
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_spec_bwd(const float* __restrict__ h, const float* __restrict__ gz,
+__global__ void __launch_bounds__(kThreads, 3) k_spec_bwd(const float* __restrict__ h, const float* __restrict__ gz,
                                                        float* __restrict__ gh, float* __restrict__ xs,
                                                        float* __restrict__ gys, const __nv_bfloat162* __restrict__ W,
                                                        const float* __restrict__ tw, const float* __restrict__ itw,
                                                        Geom g, int ax, int n, long long n_lines) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __nv_bfloat162* sW = reinterpret_cast<__nv_bfloat162*>(smem);
-  float* stw = reinterpret_cast<float*>(smem + (size_t)kModes * kC * kC * sizeof(__nv_bfloat162));
+  float* stw = reinterpret_cast<float*>(smem);
   float* sitw = stw + n * kJ;
   float* sG = sitw + n * kJ;
-  for (int i = threadIdx.x; i < kModes * kC * kC; i += blockDim.x) sW[i] = W[i];
   for (int i = threadIdx.x; i < n * kJ; i += blockDim.x) {
     stw[i] = tw[i];
     sitw[i] = itw[i];
@@ -310,7 +308,7 @@ __global__ void __launch_bounds__(kThreads) k_spec_bwd(const float* __restrict__
     for (int o = 0; o < kC; ++o) {
 #pragma unroll
       for (int k = 0; k < kModes; ++k) {
-        const float2 w = __bfloat1622float2(sW[(k * kC + o) * kC + lane]);
+        const float2 w = __bfloat1622float2(__ldg(&W[(k * kC + o) * kC + lane]));
         const float yr = G[(2 * k) * kC + o], yi = G[(2 * k + 1) * kC + o];
         gx[2 * k] = fmaf(yr, w.x, fmaf(yi, w.y, gx[2 * k]));
         gx[2 * k + 1] = fmaf(yi, w.x, fmaf(-yr, w.y, gx[2 * k + 1]));
@@ -365,13 +363,28 @@ __global__ void __launch_bounds__(kThreads) k_wgrad(const float* __restrict__ xs
   }
 }
 
-// out[i] = sum over p of partial[p * stride + i], in order of p (double accumulator)
-__global__ void k_reduce(const float* __restrict__ partial, int n_part, int len, int stride, float* __restrict__ out) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int p = 0; p < n_part; ++p) s += (double)partial[(long long)p * stride + i];
-    out[i] = (float)s;
-  }
+// Deterministic two-stage sum over partial rows: block (x, g) adds rows
+// g*group .. g*group+group-1 of partial[p * stride + i] in order into
+// tmp[g][i]; k_reduce_final adds the groups in order. Both use doubles.
+__global__ void k_reduce_groups(const float* __restrict__ partial, int n_part, int len, int stride, int group,
+                                double* __restrict__ tmp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  const int p0 = blockIdx.y * group;
+  const int p1 = p0 + group < n_part ? p0 + group : n_part;
+  double s = 0.0;
+#pragma unroll 8
+  for (int p = p0; p < p1; ++p) s += (double)partial[(long long)p * stride + i];
+  tmp[(long long)blockIdx.y * len + i] = s;
+}
+
+__global__ void k_reduce_final(const double* __restrict__ tmp, int n_groups, int len, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  double s = 0.0;
+#pragma unroll 8
+  for (int g = 0; g < n_groups; ++g) s += tmp[(long long)g * len + i];
+  out[i] = (float)s;
 }
 
 // effective head of every sample from P2, p2 and the sample's load direction u
@@ -849,6 +862,8 @@ struct fh_fno {
   float* gys = nullptr;
   float* partial = nullptr;
   long long n_partial = 0;
+  double* reduce_tmp = nullptr;
+  long long n_reduce_tmp = 0;
   double* loss_part = nullptr;
   int n_loss_part = 0;
   double* fbar = nullptr;   // [max_batch][9]
@@ -921,7 +936,7 @@ unsigned grid_for(long long work, int per_block, int cap) {
 int spec_fwd(fh_fno* net, int B, int l, int ax, bool accum, const float* h, float* out) {
   const int n = axis_len(net, ax);
   const long long lines = (long long)B * (net->N / n);
-  const unsigned grid = grid_for(lines, kWarps, 2 * net->sms);
+  const unsigned grid = grid_for(lines, kWarps, 4 * net->sms);  // 4 resident CTAs per SM
   const __nv_bfloat162* W = net->wf + (long long)(l * 3 + ax) * kModes * kC * kC;
   const size_t sm = spec_smem(n);
   if (accum)
@@ -932,8 +947,21 @@ int spec_fwd(fh_fno* net, int B, int l, int ax, bool accum, const float* h, floa
   return FH_OK;
 }
 
+int group_size(int n_part) {
+  int g = 1;
+  while ((long long)g * g < n_part) ++g;
+  return g;
+}
+
 int reduce_into(fh_fno* net, int n_part, int len, int stride, const float* partial, float* out) {
-  k_reduce<<<grid_for(len, kThreads, 4 * net->sms), kThreads, 0, net->stream>>>(partial, n_part, len, stride, out);
+  const int group = group_size(n_part);
+  const int n_groups = (n_part + group - 1) / group;
+  if ((long long)n_groups * len > net->n_reduce_tmp) return ffail(FH_ERR_ARG, "reduction scratch too small");
+  const unsigned bx = (unsigned)((len + kThreads - 1) / kThreads);
+  k_reduce_groups<<<dim3(bx, (unsigned)n_groups), kThreads, 0, net->stream>>>(partial, n_part, len, stride, group,
+                                                                             net->reduce_tmp);
+  FN_CUDA(cudaGetLastError());
+  k_reduce_final<<<bx, kThreads, 0, net->stream>>>(net->reduce_tmp, n_groups, len, out);
   FN_CUDA(cudaGetLastError());
   return FH_OK;
 }
@@ -1000,6 +1028,14 @@ int fh_fno_create(fh_fno** out, int nx, int ny, int nz, int max_batch, int train
     np = np > lift ? np : lift;
     net->n_partial = np;
     A(&net->partial, (size_t)np);
+    // groups of the two-stage reduction: at most ceil(sqrt(rows)) + 1 of the longest row
+    long long rows = n_chunks;
+    rows = rows > (long long)4 * net->sms * kWarps ? rows : (long long)4 * net->sms * kWarps;
+    rows = rows > (long long)max_batch * 2 * net->sms ? rows : (long long)max_batch * 2 * net->sms;
+    long long gmax = 1;
+    while (gmax * gmax < rows) ++gmax;
+    net->n_reduce_tmp = (gmax + 1) * kWAxis;
+    A(&net->reduce_tmp, (size_t)net->n_reduce_tmp);
   } else {
     A(&net->h[0], (size_t)act);
     A(&net->h[1], (size_t)act);
@@ -1175,7 +1211,7 @@ int fh_fno_loss_grad(fh_fno* net, const float* const* target_ptrs, double* loss_
         const int n = axis_len(net, ax);
         const long long lines = (long long)B * (net->N / n);
         const __nv_bfloat162* W = net->wb + (long long)(l * 3 + ax) * kModes * kC * kC;
-        k_spec_bwd<<<grid_for(lines, kWarps, 2 * net->sms), kThreads, spec_smem(n), s>>>(
+        k_spec_bwd<<<grid_for(lines, kWarps, 3 * net->sms), kThreads, spec_smem(n), s>>>(
             net->h[l], net->gz, net->gh, net->xs, net->gys, W, net->tw[ax], net->itw[ax], geom(net), ax, n, lines);
         FN_CUDA(cudaGetLastError());
         const unsigned chunks = (unsigned)((lines + kLinesPerChunk - 1) / kLinesPerChunk);
