@@ -567,6 +567,93 @@ def run_warm_start(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_examples(args, world, rank, local):
+    """The paper's 2D examples on this library, as z-invariant cells (nz = 2, exact plane strain).
+
+    svk_square   Section 4.1.1: St. Venant-Kirchhoff, stiff square L/3 at a corner, Fbar = I + 0.1 e_x e_y,
+                 one increment, Newton tolerance 1e-5, CG tolerance 1e-8; 256 x 256 (the paper: 299^2).
+    j2_biaxial   Section 4.1.2: J2 plasticity, hard disks, biaxial strain 0.01, 10 increments, Newton
+                 tolerance 1e-8; 192 x 192 (the paper: 199^2).
+    eshelby      Section 4.2.1: homogenized tangent of the 0.7 % disk, (lambda, mu) = (2, 1) / (10, 5);
+                 192 x 192 (the paper: 199^2).
+    Each is timed with CUDA events over K repetitions after W warm-up runs; the paper's times (one
+    4-core CPU, JAX) are quoted as context only.
+    """
+    import torch
+
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    import paper_2408_03804_gb300 as fh
+    from paper_2408_03804_gb300 import build as fhbuild
+    from rve_inputs import centered_disk, j2_config, svk_square_config
+
+    fhbuild.build()
+    fh.load()
+    stream = torch.cuda.Stream()
+    out = {}
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = None
+        for _ in range(args.steps):
+            res = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / args.steps, res
+
+    with torch.cuda.stream(stream), ClockSampler(local) as clk:
+        phase, params, Fbar = svk_square_config(256, nz=2)
+        with fh.Context(*phase.shape, stream=stream.cuda_stream) as ctx:
+            mat = fh.Material(fh.SVK, phase, params)
+            F = torch.empty((9,) + phase.shape, dtype=torch.float64, device="cuda")
+            opts = fh.default_options(newton_tol=1e-5, cg_tol=1e-8)
+
+            def svk():
+                F.zero_()
+                return ctx.fft_homog_solve(mat, Fbar, F, options=opts, allow=(fh.FH_ERR_NOT_CONVERGED,))
+
+            t, (pb, st, rc) = timed(svk)
+            out["svk_square"] = {"grid": [256, 256, 2], "s": t, "rc": rc, "newton": st["n_newton"], "cg": st["n_cg"],
+                                 "residuals": st["newton_residuals"], "paper_s": 19.5, "paper_grid": "299^2"}
+        phase, params, plastic, Ebar = j2_config(192, 0, nz=2)
+        with fh.Context(*phase.shape, stream=stream.cuda_stream) as ctx:
+            hist = torch.zeros((10,) + phase.shape, dtype=torch.float64, device="cuda")
+            mat = fh.Material(fh.J2, phase, params, plastic=plastic, history=hist)
+            F = torch.empty((9,) + phase.shape, dtype=torch.float64, device="cuda")
+            opts = fh.default_options(newton_tol=1e-8)
+
+            def j2():
+                F.zero_()
+                hist.zero_()
+                return ctx.fft_homog_solve(mat, Ebar, F, n_increments=10, options=opts,
+                                           allow=(fh.FH_ERR_NOT_CONVERGED,))
+
+            t, (pb, st, rc) = timed(j2)
+            out["j2_biaxial"] = {"grid": [192, 192, 2], "s": t, "rc": rc, "newton": st["n_newton"], "cg": st["n_cg"],
+                                 "sigma_xx_yy": [float(pb[0]), float(pb[4])], "paper_s": 0.25,
+                                 "paper_grid": "199^2"}
+        phase, f = centered_disk(192, 0.007, nz=2)
+        params = np.array([[2.0, 1.0], [10.0, 5.0]])
+        with fh.Context(*phase.shape, stream=stream.cuda_stream) as ctx:
+            mat = fh.Material(fh.LINEAR_ELASTIC, phase, params)
+            zero = torch.zeros((9,) + phase.shape, dtype=torch.float64, device="cuda")
+            t, C = timed(lambda: ctx.fft_homog_tangent(mat, zero))
+            out["eshelby"] = {"grid": [192, 192, 2], "s": t, "fraction": f,
+                              "Cxxxx_Cyyyy_Cxyxy": [float(C[0, 0]), float(C[4, 4]), float(C[1, 1])],
+                              "paper_s": 4.0, "paper_grid": "199^2", "paper_table1": [4.035, 4.035, 1.010]}
+    if rank != 0:
+        return
+    line = {"metric": "time of the paper's 2D examples (Sections 4.1.1, 4.1.2, 4.2.1) on one GPU",
+            "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 1),
+            "higher_is_better": False, "dtype": "f64", "data": "synthetic", "examples": out,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -727,6 +814,8 @@ def main():
     ap.add_argument("--probe-newton", action="store_true",
                     help="run one Newton iteration with 16 CG products (for ncu launch lists) and exit")
     ap.add_argument("--no-cufft", action="store_true")
+    ap.add_argument("--examples", action="store_true",
+                    help="time the paper's 2D examples (SVK square, J2 disks, Eshelby tangent); not the bench line")
     ap.add_argument("--warm-start", action="store_true",
                     help="learned warm start vs zero guess on held-out cells of --shape (not the bench line)")
     ap.add_argument("--shape", type=int, nargs=3, default=[N_GRID] * 3,
@@ -741,6 +830,9 @@ def main():
         return
     if args.warm_start:
         run_warm_start(args, world, rank, local)
+        return
+    if args.examples:
+        run_examples(args, world, rank, local)
         return
     run_ours(args, world, rank, local)
 

@@ -40,6 +40,9 @@ __all__ = [
     "batch_config",
     "random_disks",
     "j2_config",
+    "corner_square",
+    "svk_square_config",
+    "centered_disk",
 ]
 
 
@@ -324,3 +327,39 @@ def j2_config(n: int = 192, seed: int = 0, nz: int = 1, nu: float = 0.3):
     Ebar = np.zeros(9)
     Ebar[0] = Ebar[4] = 0.01
     return phase, params, plastic, Ebar
+
+
+def corner_square(n: int, frac: float = 1.0 / 3.0, nz: int = 1) -> np.ndarray:
+    """Square inclusion (phase 1) of side round(frac * n) voxels at the corner x, y < side.
+
+    Repeated nz times along z (a z-invariant 2D cell). Returns uint8 (n, n, nz).
+    """
+    side = int(round(frac * n))
+    phase = np.zeros((n, n, nz), dtype=np.uint8)
+    phase[:side, :side, :] = 1
+    return phase
+
+
+def svk_square_config(n: int = 256, nz: int = 2):
+    """St. Venant-Kirchhoff cell with a stiff square of side L/3 at a corner, under simple shear.
+
+    Matrix (lambda, mu) = (2, 1), inclusion 10x; Fbar = I + 0.1 e_x (x) e_y.
+    Returns (phase, params, Fbar).
+    """
+    phase = corner_square(n, 1.0 / 3.0, nz)
+    params = np.array([[2.0, 1.0], [20.0, 10.0]], dtype=np.float64)
+    Fbar = np.eye(3).reshape(9).copy()
+    Fbar[1] = 0.1
+    return phase, params, Fbar
+
+
+def centered_disk(n: int, fraction: float = 0.007, nz: int = 1):
+    """Disk (phase 1) of area fraction ``fraction`` centred in an n x n cell, repeated nz times.
+
+    A voxel belongs to the disk when its centre lies within r = sqrt(fraction / pi) n of the cell
+    centre. Returns (uint8 phase map (n, n, nz), the voxelised area fraction).
+    """
+    r = np.sqrt(fraction / np.pi) * n
+    x = np.arange(n) + 0.5 - n / 2
+    ph2 = ((x[:, None] ** 2 + x[None, :] ** 2) <= r * r).astype(np.uint8)
+    return np.repeat(ph2[:, :, None], nz, axis=2), float(ph2.mean())

@@ -293,3 +293,17 @@ def test_solve_is_deterministic(fh, torch):
             res.append((host(F), pbar, stats["cg_iterations"]))
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
     assert res[0][2] == res[1][2]
+
+
+def test_svk_square_inclusion_2d_matches_oracle(fh, torch):
+    """Section 4.1.1's St. Venant-Kirchhoff cell in the 2D mode (48 x 48 x 2): stiff square of side L/3
+    at a corner, simple shear 0.1, one increment, Newton tolerance 1e-5 and CG tolerance 1e-8 as in the
+    paper. The residual of every Newton iteration and the CG counts agree with the oracle."""
+    from rve_inputs import svk_square_config
+
+    phase, params, Fbar = svk_square_config(48, nz=2)
+    Fg, pbar, stats, _, ref = _solve_both(fh, torch, phase, params, 2, Fbar, 1, 1e-5, cg_tol=1e-8)
+    assert stats["n_newton"] == len(ref.newton_residuals) >= 2
+    np.testing.assert_allclose(stats["newton_residuals"], ref.newton_residuals, rtol=1e-6)
+    assert all(abs(a - b) <= 1 for a, b in zip(stats["cg_iterations"], ref.cg_iterations))
+    np.testing.assert_allclose(pbar, ref.Pbar, rtol=1e-8, atol=1e-8 * np.abs(ref.Pbar).max())

@@ -22,15 +22,13 @@ import os
 import numpy as np
 
 from oracle import homogenize
+from rve_inputs import centered_disk
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "eshelby_table1.json")
 
 
 def eshelby_cell(n, nz=1, fraction=0.007):
-    r = np.sqrt(fraction / np.pi) * n
-    x = np.arange(n) + 0.5 - n / 2
-    ph2 = ((x[:, None] ** 2 + x[None, :] ** 2) <= r * r).astype(np.uint8)
-    return np.repeat(ph2[:, :, None], nz, axis=2), float(ph2.mean())
+    return centered_disk(n, fraction, nz)
 
 
 def dilute_estimate(f, lam_m=2.0, mu_m=1.0, lam_i=10.0, mu_i=5.0):
