@@ -190,3 +190,19 @@ def test_adam_steps_lower_the_loss(fh):
             losses.append(net.loss_grad(targets, grad))
             net.adam(th, grad, m, v, t, 3e-3)
     assert losses[-1] < 0.5 * losses[0], losses
+
+
+def test_inference_buffers_give_the_training_forward(fh):
+    """A network created without training buffers (activations ping-pong between two fields) predicts
+    exactly what the training-mode network predicts, for a batch of two cells."""
+    th = _theta(15)
+    phases, Fbar = _cells(16, 2)
+    ph = [dev(p) for p in phases]
+    out = []
+    for train in (True, False):
+        with fh.Fno(*SHAPE, max_batch=2, train=train) as net:
+            net.set_params(th.cuda())
+            q = [torch.empty((9,) + SHAPE, dtype=torch.float32, device="cuda") for _ in range(2)]
+            net.forward(ph, Fbar, q)
+            out.append(np.stack([host(x) for x in q]))
+    assert np.array_equal(out[0], out[1])
