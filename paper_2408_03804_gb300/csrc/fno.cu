@@ -627,7 +627,7 @@ __global__ void __launch_bounds__(kThreads) k_proj_fwd(const float* __restrict__
 
 // projection backward, per voxel: gq = (2/count)(q - target) (kept [vox][9]),
 // gh4 = P1^T (gelu'(pre) . P2^T gq), and the loss partial sums
-__global__ void __launch_bounds__(kThreads) k_proj_bwd_a(const float* __restrict__ h4,
+__global__ void __launch_bounds__(kThreads, 2) k_proj_bwd_a(const float* __restrict__ h4,
                                                          const __nv_bfloat16* __restrict__ wq,
                                                          const float* __restrict__ head,
                                                          const float* __restrict__ target, long long N, float scale,
