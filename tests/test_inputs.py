@@ -29,3 +29,21 @@ def test_configs_shapes():
     phase, params, F = neo_hookean_config(48, seed=2)
     assert abs(phase.mean() - 0.30) < 0.03
     np.testing.assert_array_equal(params, [[1.5, 1.0], [15.0, 10.0]])
+
+
+def test_two_dimensional_cells():
+    from rve_inputs import centered_disk, corner_square, j2_config, random_disks, svk_square_config
+
+    ph, f = centered_disk(199, 0.007, nz=1)
+    assert ph.shape == (199, 199, 1) and abs(f - 0.007) < 5e-4
+    assert np.array_equal(ph[:, :, 0], ph[::-1, :, 0]) and np.array_equal(ph[:, :, 0], ph[:, :, 0].T)
+    sq = corner_square(48, nz=2)
+    assert sq.shape == (48, 48, 2) and sq[:16, :16].all() and sq.sum() == 16 * 16 * 2
+    ph, params, Fbar = svk_square_config(48, nz=2)
+    assert params[1, 0] == 10 * params[0, 0] and Fbar[1] == 0.1 and Fbar[0] == Fbar[4] == Fbar[8] == 1.0
+    d = random_disks(96, seed=3, nz=2)
+    assert np.array_equal(d, random_disks(96, seed=3, nz=2))
+    assert np.array_equal(d[:, :, 0], d[:, :, 1]) and 0.25 <= d.mean() < 0.35
+    ph, params, plastic, Ebar = j2_config(48, 0, nz=2)
+    assert ph.shape == (48, 48, 2) and np.allclose(plastic[1], 2 * plastic[0])
+    assert Ebar[0] == Ebar[4] == 0.01 and Ebar[8] == 0.0
