@@ -38,10 +38,11 @@ GAMMA = 0.05
 METRIC = "time-to-solve @1e-8 residual (128³ neo-Hookean); CG matvec GB/s vs HBM peak"
 WORKLOAD = ("neo-Hookean 128^3, RSA spheres r~U[4,10] vox, f=0.30, contrast 10 (mu=1, lambda=1.5), "
             "Fbar=I+0.05 e_x(x)e_y in 5 increments, Newton tol 1e-8, CG tol 1e-10, FP64")
+L2_NOTE = "working set ~1.6 GB per solve (inputs larger than L2), no explicit flush"
 HBM_PEAK_FALLBACK = 6694.5
-# FP64 peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA lanes per
-# clock x 2 flops x 2.07 GHz (MEASURED_PEAKS.json carries no FP64 figure)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 issue rate from unit counts and clock (152 SMs x 2 FP64 FMA lanes per
+# clock x 2.07 GHz), used only when the live DFMA probe cannot run
+FP64_LANE_PEAK_DERIVED = 152 * 2 * 2.07e9
 
 
 # ---------------------------------------------------------------------------
@@ -71,7 +72,6 @@ def algorithmic_work(cls: str, nx: int, ny: int, nz: int):
 # FP64 lane operations (DADD, DMUL, DFMA each one) per launch, counted from the
 # kernels' code: complex length-L transform per point = FP64_FFT_OPS[L]
 FP64_FFT_OPS = {1: 0.0, 2: 2.0, 4: 4.0, 8: 6.5, 16: 10.0, 32: 13.5, 64: 16.5, 128: 20.0, 256: 23.75}
-FP64_LANE_PEAK = 152 * 2 * 2.07e9   # lane operations per second at the maximum SM clock
 
 
 def fp64_ops(cls: str, nx: int, ny: int, nz: int):
@@ -94,9 +94,23 @@ def fp64_ops(cls: str, nx: int, ny: int, nz: int):
     return None
 
 
-def fp64_pipe_frac(cls, shape, avg_s):
+def fp64_pipe_frac(cls, shape, avg_s, lane_peak):
     ops = fp64_ops(cls, *shape)
-    return ops / avg_s / FP64_LANE_PEAK if ops else None
+    return ops / avg_s / lane_peak if ops else None
+
+
+def probe_fp64(fh, local):
+    """Measured FP64 FMA lane operations per second (the library's DFMA probe), with the SM clock during it."""
+    try:
+        with ClockSampler(local) as clk:
+            runs = [fh.fh_probe_fp64(ctas_per_sm=4, iters=1 << 18) for _ in range(3)]
+        best = max(ops / (ms / 1e3) for ms, ops in runs)
+        return {"lane_ops_per_s": best, "tflops": 2.0 * best / 1e12, "ms": [r[0] for r in runs],
+                "clocks": clk.summary(), "source": "measured in this run: fh_probe_fp64 (8 independent DFMA chains "
+                                                  "per thread, 4 x 256-thread CTAs per SM, best of 3 launches)"}
+    except Exception as exc:  # noqa: BLE001 -- report, fall back to the unit-count figure
+        return {"lane_ops_per_s": FP64_LANE_PEAK_DERIVED, "tflops": 2.0 * FP64_LANE_PEAK_DERIVED / 1e12,
+                "source": f"derived (probe failed: {exc}): 152 SM x 2 FP64 FMA/clk x 2.07 GHz"}
 
 
 def cg_iteration_bytes(nx, ny, nz):
@@ -276,6 +290,17 @@ def reference_counts():
     return d["n_newton"], d["n_cg"]
 
 
+def oracle_full_solve_record():
+    """The oracle's one recorded full solve of this workload (stored with its golden values)."""
+    path = os.path.join(ROOT, "tests", "golden", "neo_hookean_128_seed0.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    return {"wall_s": d.get("oracle_wall_s"), "cores": d.get("oracle_cores"), "n_newton": d.get("n_newton"),
+            "n_cg": d.get("n_cg"), "source": "tests/golden/neo_hookean_128_seed0.json (make_neo_hookean_128.py)"}
+
+
 def run_reference(args, world, rank):
     """The reference arm: the CPU oracle as it stands, on this host's cores."""
     if rank != 0:
@@ -300,10 +325,13 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [N_GRID] * 3},
-        "cpu_baseline": {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": f"per step: one Newton iteration at 128^3 with 3 CG products, extrapolated "
-                                   f"with the oracle's own counts ({n_newton} Newton, {n_cg} CG) of this workload"},
+        "config": {"workload": WORKLOAD, "grid": [N_GRID] * 3, "l2": L2_NOTE},
+        "extrapolated": True,
+        "cpu_baseline": {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle", "extrapolated": True,
+                         "sample": f"extrapolated from a sample: per step one Newton iteration at 128^3 with 3 CG "
+                                   f"products, times the oracle's own counts ({n_newton} Newton, {n_cg} CG) of this "
+                                   f"workload",
+                         "full_solve_recorded": oracle_full_solve_record()},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -312,37 +340,106 @@ def run_reference(args, world, rank):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
-def cufft_matvec_ms(torch, K, p, reps=5):
-    """A cuFFT-based matrix-vector product (torch.fft) of the same workload, for comparison."""
-    n = p.shape[1]
-    k = torch.fft.fftfreq(n, d=1.0 / n, device=p.device, dtype=torch.float64)
-    k[n // 2] = 0.0
-    kz = torch.fft.rfftfreq(n, d=1.0 / n, device=p.device, dtype=torch.float64)
-    kz[-1] = 0.0
-    xi = torch.meshgrid(k, k, kz, indexing="ij")
+def _events_ms(torch, fn, reps, stream):
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def cufft_projection_fns(torch, shape, device):
+    """The projection G(tau) and the bare FFT pair with cuFFT (torch.fft) and torch elementwise Ghat, for comparison.
+
+    Ghat is applied as v_i = (sum_j A_ij xi_j) / |xi|^2, out_ij = v_i xi_j, with the Nyquist wave number
+    of every even axis set to 0 as in the library. Nothing is gathered or expanded inside the timed calls.
+    """
+    nx, ny, nz = shape
+
+    def freq(n):
+        k = torch.fft.fftfreq(n, d=1.0 / n, device=device, dtype=torch.float64)
+        if n % 2 == 0:
+            k[n // 2] = 0.0
+        return k
+
+    kz = torch.fft.rfftfreq(nz, d=1.0 / nz, device=device, dtype=torch.float64)
+    if nz % 2 == 0:
+        kz[-1] = 0.0
+    xi = torch.meshgrid(freq(nx), freq(ny), kz, indexing="ij")
     xi2 = xi[0] ** 2 + xi[1] ** 2 + xi[2] ** 2
     inv = torch.where(xi2 > 0, 1.0 / torch.where(xi2 > 0, xi2, torch.ones_like(xi2)), torch.zeros_like(xi2))
-    idx = torch.tensor([[min(a, b) * 9 - min(a, b) * (min(a, b) - 1) // 2 + abs(a - b) for b in range(9)]
-                        for a in range(9)], device=p.device)
 
-    def mv():
-        Kf = K[idx.reshape(-1)].reshape(9, 9, *p.shape[1:])
-        tau = torch.einsum("ab...,b...->a...", Kf, p)
+    def project(tau):
         A = torch.fft.rfftn(tau, dim=(1, 2, 3)).reshape(3, 3, *xi2.shape)
         v = (A[:, 0] * xi[0] + A[:, 1] * xi[1] + A[:, 2] * xi[2]) * inv
         out = torch.stack([v * xi[j] for j in range(3)], dim=1).reshape(9, *xi2.shape)
-        return torch.fft.irfftn(out, s=p.shape[1:], dim=(1, 2, 3))
+        return torch.fft.irfftn(out, s=shape, dim=(1, 2, 3))
 
-    for _ in range(2):
-        mv()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        mv()
-    e1.record()
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / reps
+    def fft_pair(tau):
+        return torch.fft.irfftn(torch.fft.rfftn(tau, dim=(1, 2, 3)), s=shape, dim=(1, 2, 3))
+
+    return project, fft_pair
+
+
+def run_matvec_comparison(ctx, fh, torch, mat, F, shape, dev, stream, reps=5):
+    """Our five-pass projection and fused matrix-vector product against cuFFT (torch.fft) doing the same.
+
+    Both sides get the same resident inputs. The cuFFT matrix-vector product applies K : p from a dense
+    9x9 tangent per voxel expanded once outside the timed calls (torch.einsum), then the cuFFT projection.
+    """
+    K = torch.empty((45,) + shape, dtype=torch.float64, device=dev)
+    ctx.fh_constitutive(mat, F, None, K, want_pbar=False)
+    p = torch.randn((9,) + shape, dtype=torch.float64, device=dev)
+    y = torch.empty_like(p)
+    out = {}
+    out["matvec_ms_ours"] = _events_ms(torch, lambda: ctx.fh_matvec(p, y, K=K), reps, stream)
+    out["projection_ms_ours"] = _events_ms(torch, lambda: ctx.fh_project(p, y), reps, stream)
+    project, fft_pair = cufft_projection_fns(torch, shape, dev)
+    out["projection_ms_cufft_torch"] = _events_ms(torch, lambda: project(p), reps, stream)
+    out["fft_pair_ms_cufft"] = _events_ms(torch, lambda: fft_pair(p), reps, stream)
+    idx = torch.tensor([[min(a, b) * 9 - min(a, b) * (min(a, b) - 1) // 2 + abs(a - b) for b in range(9)]
+                        for a in range(9)], device=dev)
+    Kd = K[idx.reshape(-1)].reshape(9, 9, -1)
+    del K
+    pf = p.reshape(9, -1)
+    out["matvec_ms_cufft_torch"] = _events_ms(
+        torch, lambda: project(torch.einsum("abn,bn->an", Kd, pf).reshape((9,) + shape)), reps, stream)
+    out["note"] = ("same inputs on both sides; cuFFT side: cufft R2C/C2R via torch.fft, Ghat as torch elementwise "
+                   "ops, K:p as einsum over a dense 9x9 tangent expanded outside the timed calls")
+    del Kd, p, y, pf
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_small_strain_16(fh, torch, stream, reps=20):
+    """The 16^3 linear-elastic sphere cell (tol 1e-10): GPU time-to-solve beside the oracle's full solve."""
+    from oracle import solver as osolver
+    from rve_inputs import small_strain_config
+
+    phase, params, Ebar = small_strain_config(16)
+    with fh.Context(16, 16, 16, stream=stream.cuda_stream) as c16:
+        mat = fh.Material(fh.LINEAR_ELASTIC, phase, params)
+        F = torch.zeros((9, 16, 16, 16), dtype=torch.float64, device="cuda")
+        opts = fh.default_options(newton_tol=1e-10)
+        res = {}
+
+        def solve():
+            res["r"] = c16.fft_homog_solve(mat, Ebar, F, n_increments=1, options=opts)
+
+        gpu_ms = _events_ms(torch, solve, reps, stream)
+        pbar, st, _ = res["r"]
+    t0 = time.perf_counter()
+    ref = osolver.solve(phase, params, 0, Ebar, n_increments=1, newton_tol=1e-10)
+    cpu_s = time.perf_counter() - t0
+    return {"workload": "linear elastic 16^3, centred sphere r=0.25L, contrast 10, eps_xy=0.01, Newton tol 1e-10",
+            "gpu_ms": gpu_ms, "newton": st["n_newton"], "cg": st["n_cg"], "oracle_s": cpu_s,
+            "oracle_newton": len(ref.newton_residuals), "oracle_cg": int(sum(ref.cg_iterations)),
+            "sigma_xy_gpu_vs_oracle": [float(pbar[1]), float(ref.Pbar[1])]}
 
 
 def run_e2e(args, world, ctx, fh, torch, phase, params, Fbar, F, opts, dev, stream):
@@ -352,7 +449,6 @@ def run_e2e(args, world, ctx, fh, torch, phase, params, Fbar, F, opts, dev, stre
     phase_host = torch.from_numpy(phase.copy()).pin_memory()
     F_host = torch.empty((9,) + shape, dtype=torch.float64).pin_memory()
     phase_dev = torch.empty(shape, dtype=torch.uint8, device=dev)
-    ctx.fh_profile_enable(True)
     barrier(world, dev.index)
     torch.cuda.synchronize()
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -364,29 +460,7 @@ def run_e2e(args, world, ctx, fh, torch, phase, params, Fbar, F, opts, dev, stre
         F_host.copy_(F, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
-    ctx.fh_profile_enable(False)
     return max_over_ranks(world, e2.elapsed_time(e3) / 1e3, dev) / args.steps
-
-
-def run_matvec_comparison(ctx, fh, torch, mat, F, shape, dev, stream):
-    K = torch.empty((45,) + shape, dtype=torch.float64, device=dev)
-    ctx.fh_constitutive(mat, F, None, K, want_pbar=False)
-    p = torch.randn((9,) + shape, dtype=torch.float64, device=dev)
-    y = torch.empty_like(p)
-    for _ in range(2):
-        ctx.fh_matvec(p, y, K=K)
-    torch.cuda.synchronize()
-    e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e4.record(stream)
-    for _ in range(5):
-        ctx.fh_matvec(p, y, K=K)
-    e5.record(stream)
-    torch.cuda.synchronize()
-    ours = e4.elapsed_time(e5) / 5
-    theirs = cufft_matvec_ms(torch, K, p)
-    del K, p, y
-    torch.cuda.empty_cache()
-    return ours, theirs
 
 
 def run_batch(args, world, rank, local):
@@ -769,8 +843,8 @@ def run_ours(args, world, rank, local):
         step()
     torch.cuda.synchronize()
 
-    # ---- timed region: device-resident inputs ----
-    ctx.fh_profile_enable(True)
+    # ---- timed region: device-resident inputs; launches counted, not timed one by one ----
+    ctx.fh_profile_enable(False)
     barrier(world, local)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -785,8 +859,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     barrier(world, local)
-    prof = ctx.fh_profile_read()
-    ctx.fh_profile_enable(False)
+    counts_timed = ctx.fh_profile_read()
     elapsed_s = e0.elapsed_time(e1) / 1e3
     elapsed_s = max_over_ranks(world, elapsed_s, dev)
     per_step = elapsed_s / args.steps
@@ -796,10 +869,22 @@ def run_ours(args, world, rank, local):
     if not args.no_e2e:
         e2e_s = run_e2e(args, world, ctx, fh, torch, phase, params, Fbar, F, opts, dev, stream)
 
-    # ---- cuFFT comparison of one matrix-vector product ----
-    ours_mv_ms = cufft_ms = None
+    # ---- one more solve with CUDA events around every launch: the per-kernel split ----
+    ctx.fh_profile_enable(True)
+    step()
+    prof = ctx.fh_profile_read()
+    ctx.fh_profile_enable(False)
+
+    # ---- measured FP64 issue rate (the roofline of the FP64-bound passes) ----
+    fp64 = probe_fp64(fh, local)
+
+    # ---- cuFFT comparison and the 16^3 linear-elastic solve ----
+    cmp = None
     if not args.no_cufft:
-        ours_mv_ms, cufft_ms = run_matvec_comparison(ctx, fh, torch, mat, F, shape, dev, stream)
+        cmp = run_matvec_comparison(ctx, fh, torch, mat, F, shape, dev, stream)
+    small = None
+    if rank == 0 and not args.no_cpu_baseline:
+        small = run_small_strain_16(fh, torch, stream)
     if rank != 0:
         ctx.close()
         if world > 1:
@@ -808,34 +893,41 @@ def run_ours(args, world, rank, local):
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel ----
+    # ---- roofline of the dominant kernel (from the profiled solve; launches that did work only) ----
     hbm_peak, hbm_src = peaks()
-    classes = {c: v for c, v in prof.items() if v[0] > 0}
+    classes = {c: v for c, v in prof.items() if v[0] > 0 and c != "idle"}
     dom = max(classes, key=lambda c: classes[c][1])
     launches_dom, ms_dom = classes[dom]
     avg_s = ms_dom / 1e3 / launches_dom
     bytes_l, flops_l = algorithmic_work(dom, *shape)
     fp64_ach = flops_l / avg_s / 1e12 if flops_l else None
-    roofline = {"bound": "alu", "kernel": dom, "achieved": fp64_ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": fp64_ach / FP64_PEAK_TFLOPS if fp64_ach else None,
+    peak_tf = fp64["tflops"]
+    roofline = {"bound": "alu", "kernel": dom, "achieved": fp64_ach, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": fp64_ach / peak_tf if fp64_ach else None,
                 "traffic": committed_traffic(dom),
-                "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (no FP64 entry in "
-                               "MEASURED_PEAKS.json); achieved counts flops the conventional way (5 L log2 L "
-                               "per complex length-L FFT)",
+                "peak_source": fp64["source"] + " (x 2 flops per FMA), of measured",
+                "achieved_counts": "algorithmic flops of one launch (5 L log2 L per complex length-L FFT, 2 per "
+                                   "pointwise FMA) / its average CUDA-event duration in a profiled solve, launches "
+                                   "that did work only",
                 "avg_launch_ms": avg_s * 1e3, "launches": launches_dom,
                 "algorithmic_flops_per_launch": flops_l, "algorithmic_bytes_per_launch": bytes_l,
                 "hbm_gbs": bytes_l / avg_s / 1e9, "hbm_peak": hbm_peak, "hbm_peak_source": hbm_src,
-                "hbm_frac": bytes_l / avg_s / 1e9 / hbm_peak}
+                "hbm_frac": bytes_l / avg_s / 1e9 / hbm_peak,
+                "fp64_pipe_frac": fp64_pipe_frac(dom, shape, avg_s, fp64["lane_ops_per_s"]),
+                "fp64_probe": fp64}
     # CG iteration (matrix-vector product + vector update) effective bandwidth
-    cg_cls = ("fwd_z", "fwd_y", "x_ghat", "inv_y", "inv_z", "cg_update")
-    it_ms = sum(classes[c][1] / classes[c][0] for c in cg_cls if c in classes)
+    cg_cls = ("fwd_z", "fwd_y", "x_ghat", "inv_y", "inv_z", "cg_update", "cg_scalar")
+    it_ms = sum(classes[c][1] / classes[c][0] for c in cg_cls[:6] if c in classes)
     it_bytes = cg_iteration_bytes(*shape)
     cg_iter = {"ms": it_ms, "algorithmic_bytes": it_bytes, "gbs": it_bytes / (it_ms / 1e3) / 1e9,
                "hbm_frac": it_bytes / (it_ms / 1e3) / 1e9 / hbm_peak,
-               "matvec_ms_ours": ours_mv_ms, "matvec_ms_cufft_torch": cufft_ms}
-    roofline["fp64_pipe_frac"] = fp64_pipe_frac(dom, shape, avg_s)
-    kernels = {c: {"launches": v[0], "ms_total": v[1], "share": v[1] / sum(x[1] for x in classes.values())}
-               for c, v in classes.items()}
+               "fp64_ops": sum(fp64_ops(c, *shape) for c in cg_cls[:6]),
+               "fp64_pipe_frac": sum(fp64_ops(c, *shape) for c in cg_cls[:6]) / (it_ms / 1e3) / fp64["lane_ops_per_s"],
+               "note": "per-launch means of the six CG-iteration kernels in the profiled solve (launches that did "
+                       "work only); algorithmic bytes as in the scope table's per-voxel count",
+               "comparison": cmp}
+    tot = sum(x[1] for x in prof.values())
+    kernels = {c: {"launches": v[0], "ms_total": v[1], "share": v[1] / tot} for c, v in prof.items() if v[0]}
 
     # ---- CPU oracle on a bounded sample (rank 0 only, at N = 1) ----
     cpu = None
@@ -844,9 +936,11 @@ def run_ours(args, world, rank, local):
         st = stats[-1]
         est = st["n_newton"] * t_newton + st["n_cg"] * t_cg
         cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"one Newton iteration at 128^3 with {it} CG products on the host "
-                         f"({t_newton:.2f} s Newton overhead, {t_cg:.3f} s per CG iteration), extrapolated with "
-                         f"this run's counts ({st['n_newton']} Newton, {st['n_cg']} CG)"}
+               "extrapolated": True,
+               "sample": f"extrapolated from a sample: one Newton iteration at 128^3 with {it} CG products on the "
+                         f"host ({t_newton:.2f} s Newton overhead, {t_cg:.3f} s per CG iteration), times this run's "
+                         f"counts ({st['n_newton']} Newton, {st['n_cg']} CG)",
+               "full_solve_recorded": oracle_full_solve_record()}
 
     st = stats[-1]
     line = {
@@ -854,16 +948,18 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if shape == (N_GRID,) * 3 else WORKLOAD.replace("128^3", "x".join(map(str, shape))),
-                   "grid": list(shape), "replicas": world,
-                   "l2": "working set ~1.6 GB per solve (inputs larger than L2), no explicit flush",
-                   "newton_iterations": st["n_newton"], "cg_iterations": st["n_cg"],
-                   "pbar": pbar.tolist()},
+                   "grid": list(shape), "l2": L2_NOTE},
+        "replicas": world,
+        "timing": "CUDA events around the K solves, no per-launch events inside the timed region",
+        "result": {"newton_iterations": st["n_newton"], "cg_iterations": st["n_cg"], "pbar": pbar.tolist()},
         "e2e": ({"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(n), "d2h_bytes_per_step": int(9 * n * 8)}
                 if e2e_s is not None else None),
-        "gpu_launches": int(sum(v[0] for v in prof.values())),
+        "gpu_launches": int(sum(v[0] for v in counts_timed.values())),
+        "gpu_launches_idle": int(counts_timed["idle"][0]),
         "roofline": roofline,
         "cg_iteration": cg_iter,
         "kernels": kernels,
+        "small_strain_16": small,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
         "wall_s_timed": t_wall,

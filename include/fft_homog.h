@@ -271,8 +271,11 @@ FH_API int fft_homog_solve_batched(fh_batch* batch, int kind, int n_phase, const
  * 4 inverse z pass (complex-to-real + dot), 5 constitutive AD, 6 jvp tangent
  * apply, 7 CG scalar kernels, 8 CG vector update, 9 Newton update,
  * 10 fills and field sums, 11 partial-sum reductions, 12 tangent/sensitivity
- * contractions. */
-#define FH_PROF_NCLASS 13
+ * contractions, 13 idle: CG-loop launches queued after the loop had
+ * converged (the host reads the done flag only every check_every
+ * iterations), which found the flag set and returned without work. Classes
+ * 0-12 therefore count and time only launches that did work. */
+#define FH_PROF_NCLASS 14
 
 /* Reset the context's launch counters and, with enable != 0, bracket every
  * later launch with a pair of CUDA events on the context's stream (adds one
@@ -284,22 +287,35 @@ FH_API int fh_profile_enable(fh_ctx* ctx, int enable);
  * disabled). Waits for the context's stream. Either array may be NULL. */
 FH_API int fh_profile_read(fh_ctx* ctx, long long counts[FH_PROF_NCLASS], double ms[FH_PROF_NCLASS]);
 
+/* FP64 issue rate of the current device, measured (the roofline of the
+ * FP64-bound CG matrix-vector product; no counterpart in the paper). Runs
+ * ctas_per_sm (1..8) CTAs of 256 threads per SM, each thread `iters`
+ * (1..2^34) rounds of 8 independent FMA chains, on cuda_stream (NULL = legacy
+ * stream), after one untimed launch of iters/16 rounds. Outputs: *ms_out the
+ * CUDA-event time of the timed launch, *lane_ops_out its FP64 FMA lane
+ * operations (threads x 8 x iters; 2 flops each). Returns when done. */
+FH_API int fh_probe_fp64(int ctas_per_sm, long long iters, void* cuda_stream, double* ms_out,
+                         double* lane_ops_out);
+
 /* ---- projection without device allocation ----
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory, such as a plug-in inside an application that
  * owns the GPU's memory, or a loop that must not allocate once it runs. It
  * computes exactly what fh_project computes (out = scale * G(A)), with the
  * same kernels, but needs no fh_ctx: its scratch is a static device array of
- * 9 * 32768 complex doubles (4.5 MiB) plus 8 KiB of twiddle tables, which
- * every GPU that loads this library holds until the process exits.
+ * 9 * 32768 complex doubles (4.5 MiB) plus the twiddle tables (892 complex
+ * doubles, about 14 KiB), which every GPU that loads this library holds until
+ * the process exits.
  *   A_dev, out_dev  device [9][nx][ny][nz] fields (out may equal A)
  *   nx, ny, nz      extents as for fh_create, nx*ny*nz <= 32768;
  *                   larger grids return FH_ERR_ARG (use fh_project)
  *   lengths         box side lengths, or NULL for the unit box
  *   cuda_stream     stream to run on (NULL = legacy default stream)
- * The first call on a device (with that device current) resolves the static
- * arrays' device addresses and uploads the twiddle tables; make that first
- * call before any stream capture. Every call on a device shares the one
+ * Every call resolves the static arrays' device addresses on the current
+ * device and reads back one twiddle entry on cuda_stream; the first call on a
+ * device (and the first after its context was recreated, e.g. by
+ * cudaDeviceReset) also writes the twiddle tables, so make that first call
+ * before any stream capture. Every call on a device shares the one
  * array and leaves its contents behind; no value carries over from one call
  * to the next (each call overwrites all scratch it reads), but calls whose
  * work overlaps on the GPU (for example on two streams) race on the array and

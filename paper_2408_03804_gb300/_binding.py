@@ -41,13 +41,13 @@ _ERR_NAMES = {1: "FH_ERR_ARG", 2: "FH_ERR_CUDA", 3: "FH_ERR_NOT_CONVERGED", 4: "
 # every symbol include/fft_homog.h declares
 EXPORTS = ["fh_default_options", "fh_create", "fh_destroy", "fh_last_error_string", "fh_constitutive",
            "fh_project", "fh_matvec", "fft_homog_solve", "fh_profile_enable", "fh_profile_read", "fh_project_static", "fft_homog_tangent", "fft_homog_sensitivity",
-           "fh_batch_create", "fh_batch_destroy", "fft_homog_solve_batched", "fh_autotune",
+           "fh_batch_create", "fh_batch_destroy", "fft_homog_solve_batched", "fh_autotune", "fh_probe_fp64",
            "fh_fno_param_count", "fh_fno_create", "fh_fno_destroy", "fh_fno_set_params", "fh_fno_forward",
            "fh_fno_loss_grad", "fh_fno_adam", "fh_fno_make_target", "fh_fno_warm_start"]
 
-PROF_NCLASS = 13
+PROF_NCLASS = 14
 PROF_CLASSES = ["fwd_z", "fwd_y", "x_ghat", "inv_y", "inv_z", "constitutive", "jvp", "cg_scalar", "cg_update",
-                "newton_update", "fill", "reduce", "contract"]
+                "newton_update", "fill", "reduce", "contract", "idle"]
 
 
 class FhError(RuntimeError):
@@ -135,6 +135,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.fft_homog_solve_batched.restype = c_int
     lib.fh_autotune.argtypes = [c_void_p, c_int, POINTER(c_double), POINTER(c_int)]
     lib.fh_autotune.restype = c_int
+    lib.fh_probe_fp64.argtypes = [c_int, ctypes.c_longlong, c_void_p, POINTER(c_double), POINTER(c_double)]
+    lib.fh_probe_fp64.restype = c_int
     lib.fh_fno_param_count.argtypes = []
     lib.fh_fno_param_count.restype = ctypes.c_longlong
     lib.fh_fno_create.argtypes = [POINTER(c_void_p), c_int, c_int, c_int, c_int, c_int, c_void_p]
@@ -205,6 +207,17 @@ def fh_project_static(A, out, scale: float = 1.0, lengths=None, stream=None):
     nx, ny, nz = A.shape[1:]
     La = _dvec(lengths, 3) if lengths is not None else (None, None)
     return _check(load().fh_project_static(_ptr(A), _ptr(out), nx, ny, nz, float(scale), La[1], c_void_p(stream)))
+
+
+def fh_probe_fp64(ctas_per_sm: int = 4, iters: int = 1 << 18, stream=None):
+    """Measured FP64 FMA issue rate of the current device: (ms, lane operations) of one timed launch."""
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    ms, ops = c_double(), c_double()
+    _check(load().fh_probe_fp64(int(ctas_per_sm), int(iters), c_void_p(stream), ctypes.byref(ms), ctypes.byref(ops)))
+    return ms.value, ops.value
 
 
 class Material:

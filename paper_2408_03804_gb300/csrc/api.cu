@@ -3,7 +3,9 @@
 // kernels_fft.cu on the context's stream; the CG scalars stay on the device
 // and the host reads them every `check_every` iterations, so a CG iteration
 // costs no host round trip. Kernels queued after convergence see the device
-// flag and return at once.
+// flag and return at once; the launch accounting books them apart (class
+// "idle") so that per-kernel counts and times cover only launches that did
+// work.
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -59,7 +61,8 @@ struct DevScalars {
 
 struct ProfPair {
   int cls;
-  cudaEvent_t a, b;
+  int tag;           // CG loop iteration of the launch, or -1 outside a CG loop
+  cudaEvent_t a, b;  // null when events are off
 };
 
 struct fh_ctx {
@@ -68,8 +71,10 @@ struct fh_ctx {
   long long counts[FH_PROF_NCLASS] = {};
   double ms[FH_PROF_NCLASS] = {};
   bool prof = false;
+  int cg_tag = -1;                  // CG loop iteration being queued (-1 outside CG loops)
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<ProfPair> pending;
+  std::vector<ProfPair> pending;    // timed launches outside CG loops
+  std::vector<ProfPair> tagged;     // launches of the current CG loop, booked once its products are known
   cudaStream_t stream = nullptr;
   Grid g{};
   Tiling tiling{};
@@ -91,8 +96,9 @@ namespace {
 
 enum ProfClass : int {
   kPFwdZ = 0, kPFwdY, kPXGhat, kPInvY, kPInvZ, kPConst, kPJvp, kPCgScalar, kPCgUpdate, kPNewton, kPFill, kPReduce,
-  kPContract
+  kPContract, kPIdle
 };
+static_assert(kPIdle + 1 == FH_PROF_NCLASS, "profile classes");
 
 cudaEvent_t ev_get(fh_ctx* c) {
   if (!c->ev_pool.empty()) {
@@ -105,46 +111,49 @@ cudaEvent_t ev_get(fh_ctx* c) {
   return e;
 }
 
-// accumulate the timed pairs; call only when the stream is idle
-void prof_flush(fh_ctx* c) {
-  for (const ProfPair& q : c->pending) {
+// book one launch under class cls: its count, and its device time if timed
+void prof_book(fh_ctx* c, int cls, const ProfPair& q) {
+  c->counts[cls]++;
+  if (q.a) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) c->ms[q.cls] += ms;
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) c->ms[cls] += ms;
     c->ev_pool.push_back(q.a);
     c->ev_pool.push_back(q.b);
   }
+}
+
+// accumulate the timed pairs; call only when the stream is idle
+void prof_flush(fh_ctx* c) {
+  for (const ProfPair& q : c->pending) prof_book(c, q.cls, q);
   c->pending.clear();
+}
+
+// Book the launches of a CG loop queued so far, once the stream is idle.
+// `products` is the device's count of matrix-vector products that ran: the
+// launches of loop iterations below it did work, the later ones found the
+// done flag and returned at once, and go to the idle class.
+void prof_commit_cg(fh_ctx* c, int products) {
+  for (const ProfPair& q : c->tagged) prof_book(c, q.tag < products ? q.cls : (int)kPIdle, q);
+  c->tagged.clear();
 }
 
 template <class Fn>
 cudaError_t prof(fh_ctx* c, int cls, Fn&& fn) {
-  c->counts[cls]++;
-  if (!c->prof) return fn();
-  cudaEvent_t a = ev_get(c), b = ev_get(c);
-  cudaEventRecord(a, c->stream);
-  const cudaError_t e = fn();
-  cudaEventRecord(b, c->stream);
-  c->pending.push_back({cls, a, b});
-  return e;
-}
-
-void make_twiddles(std::vector<double2>& t) {
-  t.assign(kTwiddleTotal, make_double2(0.0, 0.0));
-  const long double two_pi = 6.283185307179586476925286766559005768L;
-  for (int L = 1; L <= kMaxN; ++L) {
-    if (!fft_length_ok(L)) continue;
-    for (int m = 0; m < L; ++m) {
-      const long double a = two_pi * (long double)m / (long double)L;
-      double c = (double)cosl(a), s = (double)-sinl(a);
-      // exact values at multiples of pi/2
-      if ((4 * m) % L == 0) {
-        const int q = (4 * m) / L;
-        c = (q == 0) ? 1.0 : (q == 2) ? -1.0 : 0.0;
-        s = (q == 1) ? -1.0 : (q == 3) ? 1.0 : 0.0;
-      }
-      t[twiddle_offset(L) + m] = make_double2(c, s);
-    }
+  ProfPair q{cls, c->cg_tag, nullptr, nullptr};
+  cudaError_t e;
+  if (c->prof) {
+    q.a = ev_get(c);
+    q.b = ev_get(c);
+    cudaEventRecord(q.a, c->stream);
+    e = fn();
+    cudaEventRecord(q.b, c->stream);
+  } else {
+    e = fn();
   }
+  if (q.tag >= 0) c->tagged.push_back(q);
+  else if (q.a) c->pending.push_back(q);
+  else c->counts[cls]++;
+  return e;
 }
 
 Grid grid_with_lengths(const fh_ctx* ctx, const double* lengths) {
@@ -221,8 +230,21 @@ int run_cg(fh_ctx* ctx, const Grid& g, const MatView& mv, const double* F_dev, b
   FH_CUDA(cudaMemsetAsync(ctx->x, 0, (size_t)9 * g.n * sizeof(double), s));
   int launched = 0;
   int rc;
+  // every exit below clears the tag; launches of the loop are booked by prof_commit_cg
+  struct TagReset {
+    fh_ctx* c;
+    ~TagReset() {
+      c->cg_tag = -1;
+      // launches still tagged here belong to an aborted loop: book them as idle
+      if (!c->tagged.empty()) {
+        cudaStreamSynchronize(c->stream);
+        prof_commit_cg(c, 0);
+      }
+    }
+  } tag_reset{ctx};
   while (true) {
     for (int k = 0; k < check_every; ++k, ++launched) {
+      ctx->cg_tag = launched;
       const int zmode = launched == 0 ? kZCgFirst : kZCg;
       if (stored) {
         if ((rc = run_projection(ctx, g, zmode, ctx->r, ctx->p, ctx->K, c_mv, kIZDot, ctx->y, ctx->p, cg, ctx->x)))
@@ -238,9 +260,11 @@ int run_cg(fh_ctx* ctx, const Grid& g, const MatView& mv, const double* F_dev, b
       FH_CUDA(prof(ctx, kPCgUpdate, [&] { return launch_cg_update(g, cg, ctx->r, ctx->y, ctx->partials, s); }));
       FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_beta(cg, ctx->partials, n_upd, s); }));
     }
+    ctx->cg_tag = -1;
     FH_CUDA(cudaMemcpyAsync(host_cg, cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
     FH_CUDA(cudaStreamSynchronize(s));
     prof_flush(ctx);
+    prof_commit_cg(ctx, host_cg->done ? host_cg->products : launched);
     if (host_cg->done) {
       FH_CUDA(prof(ctx, kPCgUpdate, [&] { return launch_cg_finalize(g, cg, ctx->x, ctx->p, s); }));
       return FH_OK;
@@ -335,8 +359,8 @@ int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
     fail(FH_ERR_CUDA, "fh_create: allocation failed: %s", cudaGetErrorString(e));
     return cleanup(FH_ERR_CUDA);
   }
-  std::vector<double2> tw;
-  make_twiddles(tw);
+  std::vector<double2> tw(kTwiddleTotal);
+  fill_twiddle_table(tw.data());
   if ((e = cudaMemcpy(c->tw, tw.data(), kTwiddleTotal * sizeof(double2), cudaMemcpyHostToDevice)) ||
       (e = cudaMemset(c->sc, 0, sizeof(DevScalars))) || (e = setup_fft_kernels(g, c->tiling))) {
     fail(FH_ERR_CUDA, "fh_create: setup failed: %s", cudaGetErrorString(e));

@@ -80,27 +80,6 @@ int dalloc(fh_batch* b, T** p, size_t bytes) {
   return FH_OK;
 }
 
-void make_twiddles(std::vector<double2>& t) {
-  t.assign(kTwiddleTotal, make_double2(0.0, 0.0));
-  const long double two_pi = 6.283185307179586476925286766559005768L;
-  for (int L = 1; L <= kMaxN; ++L) {
-    if (!fft_length_ok(L)) continue;
-    for (int m = 0; m < L; ++m) {
-      double c, s;
-      if ((4 * m) % L == 0) {
-        const int q = (4 * m) / L;
-        c = (q == 0) ? 1.0 : (q == 2) ? -1.0 : 0.0;
-        s = (q == 1) ? -1.0 : (q == 3) ? 1.0 : 0.0;
-      } else {
-        const long double a = two_pi * (long double)m / (long double)L;
-        c = (double)cosl(a);
-        s = (double)-sinl(a);
-      }
-      t[twiddle_offset(L) + m] = make_double2(c, s);
-    }
-  }
-}
-
 // one CG iteration (after the first) for every group
 int launch_cg_iteration(fh_batch* b, bool first) {
   cudaStream_t s = b->stream;
@@ -175,8 +154,8 @@ int fh_batch_create(fh_batch** out, const fh_cell* cells, int n_cells, void* cud
       (rc = dalloc(b, &b->newton_done, sizeof(int) * n_cells)) || (rc = dalloc(b, &b->flags, sizeof(int) * n_cells)) ||
       (rc = dalloc(b, &b->params, 512 * sizeof(double))) || (rc = dalloc(b, &b->tw, kTwiddleTotal * sizeof(double2))))
     return cleanup(rc);
-  std::vector<double2> tw;
-  make_twiddles(tw);
+  std::vector<double2> tw(kTwiddleTotal);
+  fill_twiddle_table(tw.data());
   if (cudaMemcpy(b->tw, tw.data(), kTwiddleTotal * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
     return cleanup(bfail(FH_ERR_CUDA, "twiddle upload failed"));
   // group the cells by grid shape

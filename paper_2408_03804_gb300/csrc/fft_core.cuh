@@ -268,4 +268,132 @@ __device__ __forceinline__ double2* fft_pencils(double2* a, double2* b, const Pe
   return out;
 }
 
+// ---- lengths without a compile-time plan ------------------------------------
+// An axis whose length has no template plan (any length up to kMaxNAny, e.g.
+// the odd grids 169, 199, 299 or 384, 512) runs a plan chosen at run time:
+// radix-16/8/4/2 and radix-3 stages with the butterflies above, and every other
+// prime factor p as one stage of a direct p-point DFT. Its twiddles
+// w_L^m = exp(-2 pi i m / L), m < L, sit at `tw_off` of the context's table;
+// the p-point roots of a direct stage are entries of the same table
+// (w_p^e = w_L^(e L / p)).
+
+template <int R, bool INV, bool JFAST>
+__device__ __forceinline__ void stockham_stage_rt(const double2* __restrict__ src, double2* __restrict__ dst,
+                                                  const PencilLayout& lay, const double2* __restrict__ tw, int L,
+                                                  int NS) {
+  const int NB = L / R;
+  const int nq = (lay.np / lay.group) * lay.valid;
+  const int total = nq * NB;
+  const int step = L / (NS * R);
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int q = pencil_of(JFAST ? t / NB : t % nq, lay);
+    const int j = JFAST ? t % NB : t / nq;
+    const double2* s = src + q * lay.q_stride;
+    double2* d = dst + q * lay.q_stride;
+    double2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = s[(j + r * NB) * lay.j_stride];
+    const int k = j % NS;
+    if (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const double2 w = tw[r * k * step];
+        v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+      }
+    }
+    dft_r<R, INV>(v);
+    const int base = (j / NS) * NS * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) d[(base + r * NS) * lay.j_stride] = v[r];
+  }
+}
+
+// One stage of odd radix R (any R >= 5) as a direct DFT: with the inputs
+// twiddled, S_m = v_m + v_{R-m} and D_m = v_m - v_{R-m} (m = 1 .. (R-1)/2),
+// X_r = v_0 + sum_m S_m cos(2 pi r m / R) -+ i D_m sin(2 pi r m / R) (minus
+// sign forward). Each butterfly owns its R source entries, so S and D are
+// written back over them; the source buffer is dead after the stage.
+template <bool INV, bool JFAST>
+__device__ __forceinline__ void stockham_stage_odd(double2* __restrict__ src, double2* __restrict__ dst,
+                                                   const PencilLayout& lay, const double2* __restrict__ tw, int L,
+                                                   int R, int NS) {
+  const int NB = L / R;
+  const int nq = (lay.np / lay.group) * lay.valid;
+  const int total = nq * NB;
+  const int step = L / (NS * R);
+  const int H = (R - 1) / 2;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int q = pencil_of(JFAST ? t / NB : t % nq, lay);
+    const int j = JFAST ? t % NB : t / nq;
+    double2* s = src + q * lay.q_stride;
+    double2* d = dst + q * lay.q_stride;
+    const int k = j % NS;
+    const double2 v0 = s[j * lay.j_stride];
+    double2 x0 = v0;
+    for (int m = 1; m <= H; ++m) {
+      double2 a = s[(j + m * NB) * lay.j_stride];
+      double2 b = s[(j + (R - m) * NB) * lay.j_stride];
+      if (NS > 1) {
+        const double2 wa = tw[m * k * step], wb = tw[(R - m) * k * step];
+        a = INV ? cmulc(a, wa) : cmul(a, wa);
+        b = INV ? cmulc(b, wb) : cmul(b, wb);
+      }
+      const double2 sm = cadd(a, b);
+      s[(j + m * NB) * lay.j_stride] = sm;
+      s[(j + (R - m) * NB) * lay.j_stride] = csub(a, b);
+      x0 = cadd(x0, sm);
+    }
+    const int base = (j / NS) * NS * R + k;
+    d[base * lay.j_stride] = x0;
+    for (int r = 1; r < R; ++r) {
+      double ar = v0.x, ai = v0.y;
+      int e = 0;
+      for (int m = 1; m <= H; ++m) {
+        e += r;
+        if (e >= R) e -= R;
+        const double2 w = tw[e * NB];  // (cos, -sin) of 2 pi e / R
+        const double c = w.x, sn = INV ? w.y : -w.y;
+        const double2 sm = s[(j + m * NB) * lay.j_stride];
+        const double2 dm = s[(j + (R - m) * NB) * lay.j_stride];
+        ar = fma(sm.x, c, fma(dm.y, sn, ar));
+        ai = fma(sm.y, c, fma(-dm.x, sn, ai));
+      }
+      d[(base + r * NS) * lay.j_stride] = make_double2(ar, ai);
+    }
+  }
+}
+
+// Transform all pencils of `a` with a run-time plan (see fft_pencils).
+template <bool INV, bool JFAST>
+__device__ __noinline__ double2* fft_pencils_rt(double2* a, double2* b, const PencilLayout lay, const double2* tw,
+                                                const FftPlan p) {
+  int NS = 1;
+  for (int st = 0; st < p.n; ++st) {
+    const int R = p.r[st];
+    __syncthreads();
+    switch (R) {
+      case 2: stockham_stage_rt<2, INV, JFAST>(a, b, lay, tw, p.L, NS); break;
+      case 3: stockham_stage_rt<3, INV, JFAST>(a, b, lay, tw, p.L, NS); break;
+      case 4: stockham_stage_rt<4, INV, JFAST>(a, b, lay, tw, p.L, NS); break;
+      case 8: stockham_stage_rt<8, INV, JFAST>(a, b, lay, tw, p.L, NS); break;
+      case 16: stockham_stage_rt<16, INV, JFAST>(a, b, lay, tw, p.L, NS); break;
+      default: stockham_stage_odd<INV, JFAST>(a, b, lay, tw, p.L, R, NS); break;
+    }
+    double2* t = a;
+    a = b;
+    b = t;
+    NS *= R;
+  }
+  __syncthreads();
+  return a;
+}
+
+// compile-time plan when L > 0, the run-time plan p otherwise
+template <int L, bool INV, bool JFAST>
+__device__ __forceinline__ double2* fft_pencils_any(double2* a, double2* b, const PencilLayout& lay,
+                                                    const double2* tw, const FftPlan& p) {
+  if constexpr (L > 0) return fft_pencils<L, INV, JFAST>(a, b, lay, tw);
+  else return fft_pencils_rt<INV, JFAST>(a, b, lay, tw, p);
+}
+
 }  // namespace fh

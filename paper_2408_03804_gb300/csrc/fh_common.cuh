@@ -10,7 +10,8 @@
 namespace fh {
 
 constexpr int kThreads = 256;          // threads per CTA of every kernel
-constexpr int kMaxN = 256;             // largest supported extent per axis
+constexpr int kMaxN = 256;             // largest extent with a compile-time plan
+constexpr int kMaxNAny = 512;          // largest x or y extent with a run-time plan
 
 // transform lengths with a radix plan: 2^a and 3 * 2^a, up to 256
 __host__ __device__ constexpr bool fft_length_ok(int L) {
@@ -64,6 +65,23 @@ __host__ __device__ constexpr bool grid_extents_ok(int nx, int ny, int nz) {
          fft_length_ok(nz / 2);
 }
 
+// the extents a solver context accepts: nx and ny any length 1 .. kMaxNAny
+// (run-time plans for those without a compile-time one), nz as above
+__host__ __device__ constexpr bool grid_extents_ok_any(int nx, int ny, int nz) {
+  return nx >= 1 && nx <= kMaxNAny && ny >= 1 && ny <= kMaxNAny && nz >= 2 && nz % 2 == 0 &&
+         fft_length_ok(nz) && fft_length_ok(nz / 2);
+}
+
+// Run-time FFT plan of an axis whose length has no compile-time plan (see
+// fft_core.cuh): stage radices in order and the offset of the length's
+// twiddle table.
+struct FftPlan {
+  int L;        // length (0 when the axis uses a compile-time plan)
+  int n;        // number of stages
+  int tw_off;   // offset of the length-L twiddles in the context's table
+  int r[12];    // radix of each stage, in order
+};
+
 // ---------------------------------------------------------------------------
 // Grid description passed by value to kernels
 // ---------------------------------------------------------------------------
@@ -72,6 +90,7 @@ struct Grid {
   long long n;              // voxels
   long long nspec;          // complex entries per spectral component nx*ny*nzh
   double sx, sy, sz;        // wave-vector scale 1/L_a (2 pi cancels in Ghat)
+  FftPlan px, py;           // run-time plans of x and y (L = 0: compile-time plan)
 };
 
 // Material tables passed by value (up to 256 phases live in a device buffer)

@@ -31,7 +31,7 @@ struct CgScalars {
   int it;           // matrix-vector products done
   int max_it;
   int done;         // 0 running, 1 converged, 2 iteration cap, 3 breakdown (p . y <= 0 or non-finite)
-  int pad;
+  int products;     // matrix-vector products whose result was used (it, plus one after a breakdown)
 };
 
 // per-cell pointers of a batched launch (device array, one entry per cell of a
@@ -73,6 +73,16 @@ struct Tiling {
   int bk_y;      // kz columns per CTA in the y passes
   int bk_x;      // kz columns per CTA in the x pass
 };
+
+// the twiddle tables of every supported length, w_L^m = exp(-2 pi i m / L) at
+// twiddle_offset(L) + m, into t[kTwiddleTotal] (host memory)
+void fill_twiddle_table(double2* t);
+
+// run-time plan of a length without a compile-time plan (L = 0 when it has
+// one); its twiddles go to offset tw_off of the context's table
+FftPlan make_fft_plan(int L, int tw_off);
+// w_L^m for m < L into t[L] (host memory)
+void fill_twiddles_of_length(double2* t, int L);
 
 Tiling choose_tiling(const Grid& g);
 size_t z_pass_smem(const Grid& g, const Tiling& t);

@@ -23,6 +23,7 @@
 // factor 1/2, so the constant c carries 1 / (2 N) together with the caller's
 // scale. Each CTA owns a disjoint region of S in every pass, so in-place
 // updates are race free.
+#include <cmath>
 #include <cstdio>
 
 #include "fft_core.cuh"
@@ -127,16 +128,29 @@ __device__ __forceinline__ void fwd_z_body(int cta, Grid g, int LB, const double
 // ---------------------------------------------------------------------------
 // forward y pass: row i, columns j = x, y, z along y; combine W_i
 // ---------------------------------------------------------------------------
+// twiddles of the y (AX = 1) or x (AX = 0) axis into shared memory: the
+// compile-time table of L, or the run-time plan's table
+template <int L, int AX>
+__device__ __forceinline__ void stage_axis_twiddles(double2* dst, const double2* __restrict__ tw, const Grid& g) {
+  if constexpr (L > 0) {
+    stage_twiddles<L>(dst, tw, L);
+  } else {
+    const FftPlan& p = AX ? g.py : g.px;
+    for (int i = threadIdx.x; i < p.L; i += blockDim.x) dst[i] = tw[p.tw_off + i];
+  }
+}
+
 template <int L>
 __device__ __forceinline__ void fwd_y_body(int cta, Grid g, int BK, double2* __restrict__ S,
                                                    const double2* __restrict__ tw, const CgScalars* __restrict__ cg) {
   extern __shared__ double2 smem[];
-  constexpr int QS = L + 1;
+  const int Ln = L > 0 ? L : g.ny;
+  const int QS = Ln + 1;
   const int np = 3 * BK;
   double2* bufA = smem;
   double2* bufB = smem + np * QS;
   double2* twL = bufB + np * QS;
-  stage_twiddles<L>(twL, tw, L);
+  stage_axis_twiddles<L, 1>(twL, tw, g);
   const int NC = (g.nzh + BK - 1) / BK;
   int b = cta;
   const int chunk = b % NC;
@@ -145,24 +159,24 @@ __device__ __forceinline__ void fwd_y_body(int cta, Grid g, int BK, double2* __r
   const int x = b / 3;
   const int kz0 = chunk * BK;
   const int valid = min(BK, g.nzh - kz0);
-  for (int t = threadIdx.x; t < 3 * L * BK; t += blockDim.x) {
+  for (int t = threadIdx.x; t < 3 * Ln * BK; t += blockDim.x) {
     const int kzl = t % BK, rest = t / BK;
-    const int y = rest % L, f = rest / L;
+    const int y = rest % Ln, f = rest / Ln;
     const int kz = kz0 + kzl;
     double2 v = make_double2(0.0, 0.0);
-    if (kz < g.nzh) v = S[(3 * i + f) * g.nspec + ((long long)x * L + y) * g.nzh + kz];
+    if (kz < g.nzh) v = S[(3 * i + f) * g.nspec + ((long long)x * Ln + y) * g.nzh + kz];
     bufA[(f * BK + kzl) * QS + y] = v;
   }
-  double2* R = fft_pencils<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL);
-  for (int t = threadIdx.x; t < L * BK; t += blockDim.x) {
+  double2* R = fft_pencils_any<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL, g.py);
+  for (int t = threadIdx.x; t < Ln * BK; t += blockDim.x) {
     const int kzl = t % BK, y = t / BK;
     const int kz = kz0 + kzl;
     if (kz >= g.nzh) continue;
-    const double xi_y = wave_int(y, L) * g.sy;
+    const double xi_y = wave_int(y, Ln) * g.sy;
     const double2 tx = R[(0 * BK + kzl) * QS + y];
     const double2 ty = R[(1 * BK + kzl) * QS + y];
     const double2 tz = R[(2 * BK + kzl) * QS + y];
-    const long long o = ((long long)x * L + y) * g.nzh + kz;
+    const long long o = ((long long)x * Ln + y) * g.nzh + kz;
     S[(3 * i + 0) * g.nspec + o] = tx;
     S[(3 * i + 1) * g.nspec + o] = make_double2(fma(xi_y, ty.x, tz.x), fma(xi_y, ty.y, tz.y));
   }
@@ -176,34 +190,35 @@ __device__ __forceinline__ void x_ghat_body(int cta, Grid g, int BK, double2* __
                                                     const double2* __restrict__ tw, double scale,
                                                     const CgScalars* __restrict__ cg) {
   extern __shared__ double2 smem[];
-  constexpr int QS = L + 1;
+  const int Ln = L > 0 ? L : g.nx;
+  const int QS = Ln + 1;
   const int np = 6 * BK;
   double2* bufA = smem;
   double2* bufB = smem + np * QS;
   double2* twL = bufB + np * QS;
-  stage_twiddles<L>(twL, tw, L);
+  stage_axis_twiddles<L, 0>(twL, tw, g);
   const int NC = (g.nzh + BK - 1) / BK;
   const int chunk = cta % NC;
   const int ky = cta / NC;
   const int kz0 = chunk * BK;
   const int valid = min(BK, g.nzh - kz0);
   const long long row = (long long)g.ny * g.nzh;  // stride of x in S
-  for (int t = threadIdx.x; t < 6 * L * BK; t += blockDim.x) {
+  for (int t = threadIdx.x; t < 6 * Ln * BK; t += blockDim.x) {
     const int kzl = t % BK, rest = t / BK;
-    const int x = rest % L, f = rest / L;
+    const int x = rest % Ln, f = rest / Ln;
     const int kz = kz0 + kzl;
     const int comp = 3 * (f >> 1) + (f & 1);
     double2 v = make_double2(0.0, 0.0);
     if (kz < g.nzh) v = S[comp * g.nspec + x * row + (long long)ky * g.nzh + kz];
     bufA[(f * BK + kzl) * QS + x] = v;
   }
-  double2* R = fft_pencils<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL);
+  double2* R = fft_pencils_any<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL, g.px);
   const double xi_y = wave_int(ky, g.ny) * g.sy;
-  for (int t = threadIdx.x; t < L * BK; t += blockDim.x) {
+  for (int t = threadIdx.x; t < Ln * BK; t += blockDim.x) {
     const int kzl = t % BK, kx = t / BK;
     const int kz = kz0 + kzl;
     if (kzl >= valid) continue;
-    const double xi_x = wave_int(kx, L) * g.sx;
+    const double xi_x = wave_int(kx, Ln) * g.sx;
     const double xi_z = wave_int(kz, g.nz) * g.sz;
     const double d = fma(xi_x, xi_x, fma(xi_y, xi_y, xi_z * xi_z));
     const double s = d > 0.0 ? scale / d : 0.0;
@@ -218,10 +233,10 @@ __device__ __forceinline__ void x_ghat_body(int cta, Grid g, int BK, double2* __
     }
   }
   double2* other = (R == bufA) ? bufB : bufA;
-  double2* R2 = fft_pencils<L, true, true>(R, other, PencilLayout{np, QS, 1, BK, valid}, twL);
-  for (int t = threadIdx.x; t < 6 * L * BK; t += blockDim.x) {
+  double2* R2 = fft_pencils_any<L, true, true>(R, other, PencilLayout{np, QS, 1, BK, valid}, twL, g.px);
+  for (int t = threadIdx.x; t < 6 * Ln * BK; t += blockDim.x) {
     const int kzl = t % BK, rest = t / BK;
-    const int x = rest % L, f = rest / L;
+    const int x = rest % Ln, f = rest / Ln;
     const int kz = kz0 + kzl;
     if (kz >= g.nzh) continue;
     const int comp = 3 * (f >> 1) + (f & 1);
@@ -236,12 +251,13 @@ template <int L>
 __device__ __forceinline__ void inv_y_body(int cta, Grid g, int BK, double2* __restrict__ S,
                                                    const double2* __restrict__ tw, const CgScalars* __restrict__ cg) {
   extern __shared__ double2 smem[];
-  constexpr int QS = L + 1;
+  const int Ln = L > 0 ? L : g.ny;
+  const int QS = Ln + 1;
   const int np = 3 * BK;
   double2* bufA = smem;
   double2* bufB = smem + np * QS;
   double2* twL = bufB + np * QS;
-  stage_twiddles<L>(twL, tw, L);
+  stage_axis_twiddles<L, 1>(twL, tw, g);
   const int NC = (g.nzh + BK - 1) / BK;
   int b = cta;
   const int chunk = b % NC;
@@ -250,25 +266,25 @@ __device__ __forceinline__ void inv_y_body(int cta, Grid g, int BK, double2* __r
   const int x = b / 3;
   const int kz0 = chunk * BK;
   const int valid = min(BK, g.nzh - kz0);
-  for (int t = threadIdx.x; t < 2 * L * BK; t += blockDim.x) {
+  for (int t = threadIdx.x; t < 2 * Ln * BK; t += blockDim.x) {
     const int kzl = t % BK, rest = t / BK;
-    const int y = rest % L, h = rest / L;
+    const int y = rest % Ln, h = rest / Ln;
     const int kz = kz0 + kzl;
     double2 v = make_double2(0.0, 0.0);
-    if (kz < g.nzh) v = S[(3 * i + h) * g.nspec + ((long long)x * L + y) * g.nzh + kz];
+    if (kz < g.nzh) v = S[(3 * i + h) * g.nspec + ((long long)x * Ln + y) * g.nzh + kz];
     if (h == 0) {
       bufA[(0 * BK + kzl) * QS + y] = v;
     } else {
-      bufA[(1 * BK + kzl) * QS + y] = cscale(v, wave_int(y, L) * g.sy);
+      bufA[(1 * BK + kzl) * QS + y] = cscale(v, wave_int(y, Ln) * g.sy);
       bufA[(2 * BK + kzl) * QS + y] = v;
     }
   }
-  double2* R = fft_pencils<L, true, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL);
-  for (int t = threadIdx.x; t < L * BK; t += blockDim.x) {
+  double2* R = fft_pencils_any<L, true, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL, g.py);
+  for (int t = threadIdx.x; t < Ln * BK; t += blockDim.x) {
     const int kzl = t % BK, y = t / BK;
     const int kz = kz0 + kzl;
     if (kz >= g.nzh) continue;
-    const long long o = ((long long)x * L + y) * g.nzh + kz;
+    const long long o = ((long long)x * Ln + y) * g.nzh + kz;
     S[(3 * i + 0) * g.nspec + o] = R[(0 * BK + kzl) * QS + y];
     S[(3 * i + 1) * g.nspec + o] = R[(1 * BK + kzl) * QS + y];
     S[(3 * i + 2) * g.nspec + o] = cscale(R[(2 * BK + kzl) * QS + y], wave_int(kz, g.nz) * g.sz);
@@ -412,8 +428,30 @@ __global__ void __launch_bounds__(kThreads) k_inv_z_b(Grid g, int LB, const Cell
 }
 
 // ---------------------------------------------------------------------------
-// host side: tiling, dispatch on the compile-time lengths
+// host side: twiddle tables, tiling, dispatch on the compile-time lengths
 // ---------------------------------------------------------------------------
+void fill_twiddle_table(double2* t) {
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  for (int i = 0; i < kTwiddleTotal; ++i) t[i] = make_double2(0.0, 0.0);
+  for (int L = 1; L <= kMaxN; ++L) {
+    if (!fft_length_ok(L)) continue;
+    for (int m = 0; m < L; ++m) {
+      double c, s;
+      if ((4 * m) % L == 0) {
+        // exact values at multiples of pi/2
+        const int q = (4 * m) / L;
+        c = (q == 0) ? 1.0 : (q == 2) ? -1.0 : 0.0;
+        s = (q == 1) ? -1.0 : (q == 3) ? 1.0 : 0.0;
+      } else {
+        const long double a = two_pi * (long double)m / (long double)L;
+        c = (double)cosl(a);
+        s = (double)-sinl(a);
+      }
+      t[twiddle_offset(L) + m] = make_double2(c, s);
+    }
+  }
+}
+
 Tiling choose_tiling(const Grid& g) {
   Tiling t;
   const long long lines = (long long)g.nx * g.ny;

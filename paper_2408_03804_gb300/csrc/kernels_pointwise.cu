@@ -335,6 +335,7 @@ __device__ __forceinline__ void cg_init_body(CgScalars* cg, const double* __rest
     cg->tol = tol;
     cg->py = 0.0;
     cg->it = 0;
+    cg->products = 0;
     cg->max_it = max_it;
     // the test of the loop head with r = b (converged at once only if b = 0 or tol >= 1)
     int done = 0;
@@ -382,6 +383,7 @@ __device__ __forceinline__ void cg_alpha_body(CgScalars* cg, const double* __res
   if (cg->done) return;
   const double py = sum_fixed(partials, n_parts, red);
   if (threadIdx.x == 0) {
+    cg->products += 1;
     cg->py = py;
     if (!(py > 0.0) || !isfinite(py)) {
       cg->done = 3;

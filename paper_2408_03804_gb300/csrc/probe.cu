@@ -1,0 +1,84 @@
+// fh_probe_fp64: the FP64 issue rate of this GPU, measured.
+//
+// The CG matrix-vector product is bound by FP64 instruction issue on this GPU
+// (its FFT butterflies and tangent contraction need about 650 FP64 operations
+// per voxel and iteration, against 72 bytes moved per field), so the roofline
+// it is held to is the FP64 one. That peak is measured here rather than taken
+// from unit counts: every thread runs eight independent chains of fused
+// multiply-adds a <- a * m + c (no dependency between chains, so the pipe, not
+// latency, sets the rate), on a grid of `ctas_per_sm` CTAs of 256 threads per
+// SM, and the launch is timed with CUDA events on the caller's stream.
+#include <cstdio>
+
+#include "fh_kernels.h"
+
+namespace fh {
+
+namespace {
+
+constexpr int kChains = 8;
+
+__device__ double g_probe_sink;
+
+__global__ void __launch_bounds__(kThreads) k_dfma_probe(long long iters, double m, double c, double sentinel) {
+  double a[kChains];
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) a[i] = 1e-3 * (threadIdx.x + 1) + 1e-6 * (blockIdx.x + i);
+  for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) a[i] = fma(a[i], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) s += a[i];
+  // never true for the arguments the host passes; keeps the chains alive
+  if (s == sentinel) g_probe_sink = s;
+}
+
+}  // namespace
+}  // namespace fh
+
+extern "C" void fh_internal_set_error(const char* msg);
+
+extern "C" int fh_probe_fp64(int ctas_per_sm, long long iters, void* cuda_stream, double* ms_out,
+                             double* lane_ops_out) {
+  using namespace fh;
+  char msg[256];
+  fh_internal_set_error("");
+  if (ctas_per_sm < 1 || ctas_per_sm > 8 || iters < 1 || iters > (1LL << 34)) {
+    fh_internal_set_error("fh_probe_fp64: ctas_per_sm must be 1..8 and iters 1..2^34");
+    return FH_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int dev = 0, sms = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.f;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const unsigned grid = (unsigned)(sms * ctas_per_sm);
+  if (e == cudaSuccess) {
+    // one short launch first so that the timed one finds the module loaded and clocks up
+    k_dfma_probe<<<grid, kThreads, 0, s>>>(iters / 16 + 1, 0.999999, 1e-9, -1.0);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess) {
+    k_dfma_probe<<<grid, kThreads, 0, s>>>(iters, 0.999999, 1e-9, -1.0);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    snprintf(msg, sizeof msg, "fh_probe_fp64: %s", cudaGetErrorString(e));
+    fh_internal_set_error(msg);
+    return FH_ERR_CUDA;
+  }
+  if (ms_out) *ms_out = ms;
+  if (lane_ops_out) *lane_ops_out = (double)grid * kThreads * kChains * (double)iters;
+  return FH_OK;
+}

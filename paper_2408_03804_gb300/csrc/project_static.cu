@@ -25,69 +25,45 @@ constexpr long long kStaticSpectrum = 9 * kStaticMaxVoxels;
 
 static __device__ __align__(256) double2 g_static_spectrum[kStaticSpectrum];
 static __device__ __align__(256) double2 g_static_twiddles[kTwiddleTotal];
+static_assert(kTwiddleTotal == 892, "the header states the size of the static twiddle tables");
 
 namespace {
 
-struct StaticSlot {
-  bool ready = false;
-  double2* spectrum = nullptr;  // device address of g_static_spectrum on this device
-  double2* twiddles = nullptr;  // device address of g_static_twiddles on this device
-};
-
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
-StaticSlot g_static_slots[kMaxDevices];
 
-void fill_twiddles(std::vector<double2>& t) {
-  t.assign(kTwiddleTotal, make_double2(0.0, 0.0));
-  const long double two_pi = 6.283185307179586476925286766559005768L;
-  for (int L = 1; L <= kMaxN; ++L) {
-    if (!fft_length_ok(L)) continue;
-    for (int m = 0; m < L; ++m) {
-      double c, s;
-      if ((4 * m) % L == 0) {
-        const int q = (4 * m) / L;
-        c = (q == 0) ? 1.0 : (q == 2) ? -1.0 : 0.0;
-        s = (q == 1) ? -1.0 : (q == 3) ? 1.0 : 0.0;
-      } else {
-        const long double a = two_pi * (long double)m / (long double)L;
-        c = (double)cosl(a);
-        s = (double)-sinl(a);
-      }
-      t[twiddle_offset(L) + m] = make_double2(c, s);
-    }
-  }
-}
-
-// One-time set-up of the calling thread's current device: resolve the device
-// addresses of the static arrays and write the twiddle tables into them.
-int static_setup(int dev, StaticSlot** out, char* msg, size_t len) {
+// Set-up of the calling thread's current device, on every call: resolve the
+// device addresses of the static arrays (they change when the device's context
+// is destroyed and created again, e.g. after cudaDeviceReset) and check the
+// first twiddle entry, the length-1 table, which holds (1, 0) once the tables
+// are written and 0 in a fresh module; write the tables if it does not.
+int static_setup(int dev, cudaStream_t s, double2** spectrum, double2** twiddles, char* msg, size_t len) {
   if (dev < 0 || dev >= kMaxDevices) {
     snprintf(msg, len, "fh_project_static: device %d outside 0..%d", dev, kMaxDevices - 1);
     return FH_ERR_ARG;
   }
   std::lock_guard<std::mutex> lock(g_static_mu);
-  StaticSlot& s = g_static_slots[dev];
-  if (!s.ready) {
-    cudaError_t e = cudaGetSymbolAddress((void**)&s.spectrum, g_static_spectrum);
-    if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&s.twiddles, g_static_twiddles);
-    if (e != cudaSuccess) {
-      snprintf(msg, len, "fh_project_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      return FH_ERR_CUDA;
-    }
-    std::vector<double2> tw;
-    fill_twiddles(tw);
-    e = cudaMemcpyToSymbol(g_static_twiddles, tw.data(), kTwiddleTotal * sizeof(double2));
-    if (e != cudaSuccess) {
-      snprintf(msg, len, "fh_project_static: twiddle upload failed: %s", cudaGetErrorString(e));
-      return FH_ERR_CUDA;
-    }
-    s.ready = true;
+  cudaError_t e = cudaGetSymbolAddress((void**)spectrum, g_static_spectrum);
+  if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)twiddles, g_static_twiddles);
+  if (e != cudaSuccess) {
+    snprintf(msg, len, "fh_project_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    return FH_ERR_CUDA;
   }
-  *out = &s;
+  double2 head = make_double2(0.0, 0.0);
+  e = cudaMemcpyAsync(&head, *twiddles, sizeof(double2), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && !(head.x == 1.0 && head.y == 0.0)) {
+    std::vector<double2> tw(kTwiddleTotal);
+    fill_twiddle_table(tw.data());
+    e = cudaMemcpyAsync(*twiddles, tw.data(), kTwiddleTotal * sizeof(double2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (e != cudaSuccess) {
+    snprintf(msg, len, "fh_project_static: twiddle set-up failed: %s", cudaGetErrorString(e));
+    return FH_ERR_CUDA;
+  }
   return FH_OK;
 }
-
 
 }  // namespace
 }  // namespace fh
@@ -130,8 +106,10 @@ extern "C" int fh_project_static(const double* A_dev, double* out_dev, int nx, i
     snprintf(msg, sizeof msg, "fh_project_static: cudaGetDevice: %s", cudaGetErrorString(e));
     return fail(FH_ERR_CUDA);
   }
-  StaticSlot* slot = nullptr;
-  int rc = static_setup(dev, &slot, msg, sizeof msg);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  double2* spectrum = nullptr;
+  double2* twiddles = nullptr;
+  int rc = static_setup(dev, s, &spectrum, &twiddles, msg, sizeof msg);
   if (rc) return fail(rc);
 
   Grid g{};
@@ -145,16 +123,15 @@ extern "C" int fh_project_static(const double* A_dev, double* out_dev, int nx, i
   g.sy = lengths ? 1.0 / lengths[1] : 1.0;
   g.sz = lengths ? 1.0 / lengths[2] : 1.0;
   const Tiling t = choose_tiling(g);
-  cudaStream_t s = (cudaStream_t)cuda_stream;
   const double c = scale / (2.0 * (double)n);
   if ((e = setup_fft_kernels(g, t)) != cudaSuccess ||
-      (e = launch_fwd_z(g, t, kZDirect, A_dev, nullptr, nullptr, nullptr, nullptr, slot->spectrum,
-                        slot->twiddles, s)) !=
+      (e = launch_fwd_z(g, t, kZDirect, A_dev, nullptr, nullptr, nullptr, nullptr, spectrum,
+                        twiddles, s)) !=
           cudaSuccess ||
-      (e = launch_fwd_y(g, t, slot->spectrum, slot->twiddles, nullptr, s)) != cudaSuccess ||
-      (e = launch_x_ghat(g, t, slot->spectrum, slot->twiddles, c, nullptr, s)) != cudaSuccess ||
-      (e = launch_inv_y(g, t, slot->spectrum, slot->twiddles, nullptr, s)) != cudaSuccess ||
-      (e = launch_inv_z(g, t, kIZOut, slot->spectrum, out_dev, nullptr, nullptr, slot->twiddles, nullptr, s)) !=
+      (e = launch_fwd_y(g, t, spectrum, twiddles, nullptr, s)) != cudaSuccess ||
+      (e = launch_x_ghat(g, t, spectrum, twiddles, c, nullptr, s)) != cudaSuccess ||
+      (e = launch_inv_y(g, t, spectrum, twiddles, nullptr, s)) != cudaSuccess ||
+      (e = launch_inv_z(g, t, kIZOut, spectrum, out_dev, nullptr, nullptr, twiddles, nullptr, s)) !=
           cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess) {
     snprintf(msg, sizeof msg, "fh_project_static: %s", cudaGetErrorString(e));

@@ -307,3 +307,36 @@ def test_svk_square_inclusion_2d_matches_oracle(fh, torch):
     np.testing.assert_allclose(stats["newton_residuals"], ref.newton_residuals, rtol=1e-6)
     assert all(abs(a - b) <= 1 for a, b in zip(stats["cg_iterations"], ref.cg_iterations))
     np.testing.assert_allclose(pbar, ref.Pbar, rtol=1e-8, atol=1e-8 * np.abs(ref.Pbar).max())
+
+
+# ---------------------------------------------------------------------------
+# launch accounting: per-kernel counts cover launches that did work only
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("check_every", [1, 16])
+def test_launch_accounting_books_idle_launches_apart(fh, torch, check_every):
+    """Each Newton iteration runs one right-hand-side projection and one product per CG iteration, so the
+    forward z pass must be counted n_newton + n_cg times whatever check_every is; the launches queued after
+    CG had converged are counted as idle (none with check_every = 1, when the host reads the flag after
+    every iteration)."""
+    shape = (16, 16, 16)
+    phase = centered_sphere(shape, 0.25)
+    params = two_phase_table(1.5, 1.0, 10.0)
+    Fbar = shear_macro(0.05, finite=True)
+    with fh.Context(*shape) as ctx:
+        F = torch.zeros((9,) + shape, dtype=torch.float64, device="cuda")
+        ctx.fh_profile_enable(True)
+        _, st, _ = ctx.fft_homog_solve(fh.Material(fh.NEO_HOOKEAN, phase, params), Fbar, F, n_increments=2,
+                                       options=fh.default_options(newton_tol=1e-10, check_every=check_every))
+        prof = ctx.fh_profile_read()
+    n_real = st["n_newton"] + st["n_cg"]
+    for cls in ("fwd_z", "fwd_y", "x_ghat", "inv_y", "inv_z"):
+        assert prof[cls][0] == n_real
+        assert prof[cls][1] > 0.0
+    assert prof["cg_update"][0] == st["n_cg"] + st["n_newton"]  # one update per product, one finalize per solve
+    if check_every == 1:
+        assert prof["idle"][0] == 0
+    else:
+        # each CG loop queues whole chunks of check_every iterations of 8 launches
+        idle = prof["idle"][0]
+        assert idle > 0 and idle % 8 == 0
+        assert (idle // 8 + st["n_cg"]) % check_every == 0
