@@ -102,12 +102,15 @@ def fp64_pipe_frac(cls, shape, avg_s, lane_peak):
 def probe_fp64(fh, local):
     """Measured FP64 FMA lane operations per second (the library's DFMA probe), with the SM clock during it."""
     try:
+        shapes = [(2, 8), (4, 8), (8, 8), (2, 16), (4, 16), (4, 4)]
         with ClockSampler(local) as clk:
-            runs = [fh.fh_probe_fp64(ctas_per_sm=4, iters=1 << 18) for _ in range(3)]
-        best = max(ops / (ms / 1e3) for ms, ops in runs)
-        return {"lane_ops_per_s": best, "tflops": 2.0 * best / 1e12, "ms": [r[0] for r in runs],
-                "clocks": clk.summary(), "source": "measured in this run: fh_probe_fp64 (8 independent DFMA chains "
-                                                  "per thread, 4 x 256-thread CTAs per SM, best of 3 launches)"}
+            runs = {f"{c}cta_{ch}ch": fh.fh_probe_fp64(ctas_per_sm=c, chains=ch, iters=(1 << 20) // (c * ch))
+                    for c, ch in shapes}
+        rates = {k: ops / (ms / 1e3) for k, (ms, ops) in runs.items()}
+        best = max(rates.values())
+        return {"lane_ops_per_s": best, "tflops": 2.0 * best / 1e12, "rates": rates,
+                "clocks": clk.summary(), "source": "measured in this run: fh_probe_fp64 (independent DFMA chains, "
+                                                  "best over CTAs/SM x chains per thread)"}
     except Exception as exc:  # noqa: BLE001 -- report, fall back to the unit-count figure
         return {"lane_ops_per_s": FP64_LANE_PEAK_DERIVED, "tflops": 2.0 * FP64_LANE_PEAK_DERIVED / 1e12,
                 "source": f"derived (probe failed: {exc}): 152 SM x 2 FP64 FMA/clk x 2.07 GHz"}
@@ -645,11 +648,12 @@ def run_examples(args, world, rank, local):
     """The paper's 2D examples on this library, as z-invariant cells (nz = 2, exact plane strain).
 
     svk_square   Section 4.1.1: St. Venant-Kirchhoff, stiff square L/3 at a corner, Fbar = I + 0.1 e_x e_y,
-                 one increment, Newton tolerance 1e-5, CG tolerance 1e-8; 256 x 256 (the paper: 299^2).
+                 one increment, Newton tolerance 1e-5, CG tolerance 1e-8; 299 x 299 as in the paper.
+    svk_scaling  the same cell on the paper's scaling grids 63^2, 127^2, 255^2, 511^2 (Section 4.1.3).
     j2_biaxial   Section 4.1.2: J2 plasticity, hard disks, biaxial strain 0.01, 10 increments, Newton
-                 tolerance 1e-8; 192 x 192 (the paper: 199^2).
+                 tolerance 1e-8; 199 x 199 as in the paper.
     eshelby      Section 4.2.1: homogenized tangent of the 0.7 % disk, (lambda, mu) = (2, 1) / (10, 5);
-                 192 x 192 (the paper: 199^2).
+                 199 x 199 as in the paper.
     Each is timed with CUDA events over K repetitions after W warm-up runs; the paper's times (one
     4-core CPU, JAX) are quoted as context only.
     """
@@ -679,8 +683,8 @@ def run_examples(args, world, rank, local):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3 / args.steps, res
 
-    with torch.cuda.stream(stream), ClockSampler(local) as clk:
-        phase, params, Fbar = svk_square_config(256, nz=2)
+    def svk_solve(n):
+        phase, params, Fbar = svk_square_config(n, nz=2)
         with fh.Context(*phase.shape, stream=stream.cuda_stream) as ctx:
             mat = fh.Material(fh.SVK, phase, params)
             F = torch.empty((9,) + phase.shape, dtype=torch.float64, device="cuda")
@@ -691,9 +695,13 @@ def run_examples(args, world, rank, local):
                 return ctx.fft_homog_solve(mat, Fbar, F, options=opts, allow=(fh.FH_ERR_NOT_CONVERGED,))
 
             t, (pb, st, rc) = timed(svk)
-            out["svk_square"] = {"grid": [256, 256, 2], "s": t, "rc": rc, "newton": st["n_newton"], "cg": st["n_cg"],
-                                 "residuals": st["newton_residuals"], "paper_s": 19.5, "paper_grid": "299^2"}
-        phase, params, plastic, Ebar = j2_config(192, 0, nz=2)
+        return {"grid": [n, n, 2], "s": t, "rc": rc, "newton": st["n_newton"], "cg": st["n_cg"],
+                "residuals": st["newton_residuals"], "Pbar_xy": float(pb[1])}
+
+    with torch.cuda.stream(stream), ClockSampler(local) as clk:
+        out["svk_square"] = dict(svk_solve(299), paper_s=19.5, paper_grid="299^2")
+        out["svk_scaling"] = [svk_solve(n) for n in (63, 127, 255, 511)]
+        phase, params, plastic, Ebar = j2_config(199, 0, nz=2)
         with fh.Context(*phase.shape, stream=stream.cuda_stream) as ctx:
             hist = torch.zeros((10,) + phase.shape, dtype=torch.float64, device="cuda")
             mat = fh.Material(fh.J2, phase, params, plastic=plastic, history=hist)
@@ -707,16 +715,16 @@ def run_examples(args, world, rank, local):
                                            allow=(fh.FH_ERR_NOT_CONVERGED,))
 
             t, (pb, st, rc) = timed(j2)
-            out["j2_biaxial"] = {"grid": [192, 192, 2], "s": t, "rc": rc, "newton": st["n_newton"], "cg": st["n_cg"],
+            out["j2_biaxial"] = {"grid": [199, 199, 2], "s": t, "rc": rc, "newton": st["n_newton"], "cg": st["n_cg"],
                                  "sigma_xx_yy": [float(pb[0]), float(pb[4])], "paper_s": 0.25,
                                  "paper_grid": "199^2"}
-        phase, f = centered_disk(192, 0.007, nz=2)
+        phase, f = centered_disk(199, 0.007, nz=2)
         params = np.array([[2.0, 1.0], [10.0, 5.0]])
         with fh.Context(*phase.shape, stream=stream.cuda_stream) as ctx:
             mat = fh.Material(fh.LINEAR_ELASTIC, phase, params)
             zero = torch.zeros((9,) + phase.shape, dtype=torch.float64, device="cuda")
             t, C = timed(lambda: ctx.fft_homog_tangent(mat, zero))
-            out["eshelby"] = {"grid": [192, 192, 2], "s": t, "fraction": f,
+            out["eshelby"] = {"grid": [199, 199, 2], "s": t, "fraction": f,
                               "Cxxxx_Cyyyy_Cxyxy": [float(C[0, 0]), float(C[4, 4]), float(C[1, 1])],
                               "paper_s": 4.0, "paper_grid": "199^2", "paper_table1": [4.035, 4.035, 1.010]}
     if rank != 0:

@@ -12,10 +12,14 @@
  *
  * Conventions shared by every entry point
  * ---------------------------------------
- * Grid        nx x ny x nz voxels, N = nx*ny*nz. Each extent is 2^a or
- *             3*2^a and at most 256 (radix-2/4/8/16 and radix-3 transforms);
- *             nz is even and nz/2 is of the same form. Box side lengths
- *             default to 1 (see fh_options.lengths).
+ * Grid        nx x ny x nz voxels, N = nx*ny*nz. nx and ny are any length
+ *             1..512 (2^a and 3*2^a up to 256 use compile-time radix-16/8/4/2/3
+ *             plans; other lengths, e.g. the paper's odd grids 199 or 299,
+ *             run-time plans whose prime factors above 3 are direct DFT
+ *             stages); nz is even, and nz and nz/2 are 2^a or 3*2^a up to
+ *             256. fh_project_static and batched solves take only the
+ *             compile-time lengths on every axis. Box side lengths default
+ *             to 1 (see fh_options.lengths).
  * Fields      device float64 arrays in structure-of-arrays order
  *             [9][nx][ny][nz] (z fastest); component c = 3*i + j holds the
  *             tensor entry T_ij (row-major 3x3; F_ij = dx_i/dX_j).
@@ -290,11 +294,12 @@ FH_API int fh_profile_read(fh_ctx* ctx, long long counts[FH_PROF_NCLASS], double
 /* FP64 issue rate of the current device, measured (the roofline of the
  * FP64-bound CG matrix-vector product; no counterpart in the paper). Runs
  * ctas_per_sm (1..8) CTAs of 256 threads per SM, each thread `iters`
- * (1..2^34) rounds of 8 independent FMA chains, on cuda_stream (NULL = legacy
- * stream), after one untimed launch of iters/16 rounds. Outputs: *ms_out the
- * CUDA-event time of the timed launch, *lane_ops_out its FP64 FMA lane
- * operations (threads x 8 x iters; 2 flops each). Returns when done. */
-FH_API int fh_probe_fp64(int ctas_per_sm, long long iters, void* cuda_stream, double* ms_out,
+ * (1..2^34) rounds of `chains` (4, 8 or 16) independent FMA chains, on
+ * cuda_stream (NULL = legacy stream), after one untimed launch of iters/16
+ * rounds. Outputs: *ms_out the CUDA-event time of the timed launch,
+ * *lane_ops_out its FP64 FMA lane operations (threads x chains x iters; 2 flops
+ * each). Returns when done. */
+FH_API int fh_probe_fp64(int ctas_per_sm, int chains, long long iters, void* cuda_stream, double* ms_out,
                          double* lane_ops_out);
 
 /* ---- projection without device allocation ----

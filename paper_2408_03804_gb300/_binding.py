@@ -135,7 +135,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.fft_homog_solve_batched.restype = c_int
     lib.fh_autotune.argtypes = [c_void_p, c_int, POINTER(c_double), POINTER(c_int)]
     lib.fh_autotune.restype = c_int
-    lib.fh_probe_fp64.argtypes = [c_int, ctypes.c_longlong, c_void_p, POINTER(c_double), POINTER(c_double)]
+    lib.fh_probe_fp64.argtypes = [c_int, c_int, ctypes.c_longlong, c_void_p, POINTER(c_double), POINTER(c_double)]
     lib.fh_probe_fp64.restype = c_int
     lib.fh_fno_param_count.argtypes = []
     lib.fh_fno_param_count.restype = ctypes.c_longlong
@@ -209,14 +209,15 @@ def fh_project_static(A, out, scale: float = 1.0, lengths=None, stream=None):
     return _check(load().fh_project_static(_ptr(A), _ptr(out), nx, ny, nz, float(scale), La[1], c_void_p(stream)))
 
 
-def fh_probe_fp64(ctas_per_sm: int = 4, iters: int = 1 << 18, stream=None):
+def fh_probe_fp64(ctas_per_sm: int = 4, chains: int = 8, iters: int = 1 << 18, stream=None):
     """Measured FP64 FMA issue rate of the current device: (ms, lane operations) of one timed launch."""
     import torch
 
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     ms, ops = c_double(), c_double()
-    _check(load().fh_probe_fp64(int(ctas_per_sm), int(iters), c_void_p(stream), ctypes.byref(ms), ctypes.byref(ops)))
+    _check(load().fh_probe_fp64(int(ctas_per_sm), int(chains), int(iters), c_void_p(stream), ctypes.byref(ms),
+                                ctypes.byref(ops)))
     return ms.value, ops.value
 
 

@@ -322,10 +322,10 @@ void fh_internal_ctx_grid(const fh_ctx* ctx, int* nx, int* ny, int* nz) {
 int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
   g_err[0] = 0;
   if (!out) return fail(FH_ERR_ARG, "out is NULL");
-  if (!grid_extents_ok(nx, ny, nz))
+  if (!grid_extents_ok_any(nx, ny, nz))
     return fail(FH_ERR_ARG,
-                "grid %dx%dx%d: each extent must be 2^a or 3*2^a up to 256, and nz even with nz/2 of that form",
-                nx, ny, nz);
+                "grid %dx%dx%d: nx and ny must be 1..%d, nz even with nz and nz/2 of the form 2^a or 3*2^a up to 256",
+                nx, ny, nz, kMaxNAny);
   fh_ctx* c = new fh_ctx();
   FH_CUDA(cudaGetDevice(&c->dev));
   c->stream = (cudaStream_t)cuda_stream;
@@ -337,6 +337,13 @@ int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
   g.n = (long long)nx * ny * nz;
   g.nspec = (long long)nx * ny * g.nzh;
   g.sx = g.sy = g.sz = 1.0;
+  // lengths without a compile-time plan get a run-time plan and their own
+  // twiddle table after the tables of the compile-time lengths
+  int tw_len = kTwiddleTotal;
+  g.px = make_fft_plan(nx, tw_len);
+  if (g.px.L) tw_len += nx;
+  g.py = make_fft_plan(ny, tw_len);
+  if (g.py.L) tw_len += ny;
   c->tiling = choose_tiling(g);
   const size_t f9 = (size_t)9 * g.n * sizeof(double);
   long long np = 9LL * constitutive_ctas(g);
@@ -355,13 +362,15 @@ int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
       (e = cudaMalloc(&c->K, (size_t)45 * g.n * sizeof(double))) ||
       (e = cudaMalloc(&c->partials, (size_t)np * sizeof(double))) ||
       (e = cudaMalloc(&c->params, 1024 * sizeof(double))) ||
-      (e = cudaMalloc(&c->tw, kTwiddleTotal * sizeof(double2))) || (e = cudaMalloc(&c->sc, sizeof(DevScalars)))) {
+      (e = cudaMalloc(&c->tw, tw_len * sizeof(double2))) || (e = cudaMalloc(&c->sc, sizeof(DevScalars)))) {
     fail(FH_ERR_CUDA, "fh_create: allocation failed: %s", cudaGetErrorString(e));
     return cleanup(FH_ERR_CUDA);
   }
-  std::vector<double2> tw(kTwiddleTotal);
+  std::vector<double2> tw(tw_len);
   fill_twiddle_table(tw.data());
-  if ((e = cudaMemcpy(c->tw, tw.data(), kTwiddleTotal * sizeof(double2), cudaMemcpyHostToDevice)) ||
+  if (g.px.L) fill_twiddles_of_length(tw.data() + g.px.tw_off, nx);
+  if (g.py.L) fill_twiddles_of_length(tw.data() + g.py.tw_off, ny);
+  if ((e = cudaMemcpy(c->tw, tw.data(), tw_len * sizeof(double2), cudaMemcpyHostToDevice)) ||
       (e = cudaMemset(c->sc, 0, sizeof(DevScalars))) || (e = setup_fft_kernels(g, c->tiling))) {
     fail(FH_ERR_CUDA, "fh_create: setup failed: %s", cudaGetErrorString(e));
     return cleanup(FH_ERR_CUDA);

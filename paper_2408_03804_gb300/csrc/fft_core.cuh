@@ -311,55 +311,63 @@ __device__ __forceinline__ void stockham_stage_rt(const double2* __restrict__ sr
 // One stage of odd radix R (any R >= 5) as a direct DFT: with the inputs
 // twiddled, S_m = v_m + v_{R-m} and D_m = v_m - v_{R-m} (m = 1 .. (R-1)/2),
 // X_r = v_0 + sum_m S_m cos(2 pi r m / R) -+ i D_m sin(2 pi r m / R) (minus
-// sign forward). Each butterfly owns its R source entries, so S and D are
-// written back over them; the source buffer is dead after the stage.
+// sign forward). Two phases, each spread over all threads: one (butterfly, m)
+// pair per thread forms S_m and D_m and writes them back over the source
+// entries (each butterfly owns its R entries; the source buffer is dead after
+// the stage), then one (butterfly, r) output per thread.
 template <bool INV, bool JFAST>
 __device__ __forceinline__ void stockham_stage_odd(double2* __restrict__ src, double2* __restrict__ dst,
                                                    const PencilLayout& lay, const double2* __restrict__ tw, int L,
                                                    int R, int NS) {
   const int NB = L / R;
   const int nq = (lay.np / lay.group) * lay.valid;
-  const int total = nq * NB;
   const int step = L / (NS * R);
   const int H = (R - 1) / 2;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int q = pencil_of(JFAST ? t / NB : t % nq, lay);
-    const int j = JFAST ? t % NB : t / nq;
+  // phase 1: twiddled pairs -> (S_m, D_m)
+  for (int t = threadIdx.x; t < nq * NB * H; t += blockDim.x) {
+    const int m = 1 + t % H, qj = t / H;
+    const int q = pencil_of(JFAST ? qj / NB : qj % nq, lay);
+    const int j = JFAST ? qj % NB : qj / nq;
     double2* s = src + q * lay.q_stride;
-    double2* d = dst + q * lay.q_stride;
-    const int k = j % NS;
+    double2 a = s[(j + m * NB) * lay.j_stride];
+    double2 b = s[(j + (R - m) * NB) * lay.j_stride];
+    if (NS > 1) {
+      const int k = j % NS;
+      const double2 wa = tw[m * k * step], wb = tw[(R - m) * k * step];
+      a = INV ? cmulc(a, wa) : cmul(a, wa);
+      b = INV ? cmulc(b, wb) : cmul(b, wb);
+    }
+    s[(j + m * NB) * lay.j_stride] = cadd(a, b);
+    s[(j + (R - m) * NB) * lay.j_stride] = csub(a, b);
+  }
+  __syncthreads();
+  // phase 2: outputs
+  for (int t = threadIdx.x; t < nq * NB * R; t += blockDim.x) {
+    const int r = t % R, qj = t / R;
+    const int q = pencil_of(JFAST ? qj / NB : qj % nq, lay);
+    const int j = JFAST ? qj % NB : qj / nq;
+    const double2* s = src + q * lay.q_stride;
     const double2 v0 = s[j * lay.j_stride];
-    double2 x0 = v0;
+    double ar = v0.x, ai = v0.y;
+    int e = 0;
     for (int m = 1; m <= H; ++m) {
-      double2 a = s[(j + m * NB) * lay.j_stride];
-      double2 b = s[(j + (R - m) * NB) * lay.j_stride];
-      if (NS > 1) {
-        const double2 wa = tw[m * k * step], wb = tw[(R - m) * k * step];
-        a = INV ? cmulc(a, wa) : cmul(a, wa);
-        b = INV ? cmulc(b, wb) : cmul(b, wb);
+      const double2 sm = s[(j + m * NB) * lay.j_stride];
+      if (r == 0) {
+        ar += sm.x;
+        ai += sm.y;
+        continue;
       }
-      const double2 sm = cadd(a, b);
-      s[(j + m * NB) * lay.j_stride] = sm;
-      s[(j + (R - m) * NB) * lay.j_stride] = csub(a, b);
-      x0 = cadd(x0, sm);
+      e += r;
+      if (e >= R) e -= R;
+      const double2 w = tw[e * NB];  // (cos, -sin) of 2 pi e / R
+      const double c = w.x, sn = INV ? w.y : -w.y;
+      const double2 dm = s[(j + (R - m) * NB) * lay.j_stride];
+      ar = fma(sm.x, c, fma(dm.y, sn, ar));
+      ai = fma(sm.y, c, fma(-dm.x, sn, ai));
     }
-    const int base = (j / NS) * NS * R + k;
-    d[base * lay.j_stride] = x0;
-    for (int r = 1; r < R; ++r) {
-      double ar = v0.x, ai = v0.y;
-      int e = 0;
-      for (int m = 1; m <= H; ++m) {
-        e += r;
-        if (e >= R) e -= R;
-        const double2 w = tw[e * NB];  // (cos, -sin) of 2 pi e / R
-        const double c = w.x, sn = INV ? w.y : -w.y;
-        const double2 sm = s[(j + m * NB) * lay.j_stride];
-        const double2 dm = s[(j + (R - m) * NB) * lay.j_stride];
-        ar = fma(sm.x, c, fma(dm.y, sn, ar));
-        ai = fma(sm.y, c, fma(-dm.x, sn, ai));
-      }
-      d[(base + r * NS) * lay.j_stride] = make_double2(ar, ai);
-    }
+    const int base = (j / NS) * NS * R + j % NS;
+    double2* d = dst + q * lay.q_stride;
+    d[(base + r * NS) * lay.j_stride] = make_double2(ar, ai);
   }
 }
 

@@ -452,6 +452,52 @@ void fill_twiddle_table(double2* t) {
   }
 }
 
+void fill_twiddles_of_length(double2* t, int L) {
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  for (int m = 0; m < L; ++m) {
+    double c, sn;
+    if ((4 * m) % L == 0) {
+      const int q = (4 * m) / L;
+      c = (q == 0) ? 1.0 : (q == 2) ? -1.0 : 0.0;
+      sn = (q == 1) ? -1.0 : (q == 3) ? 1.0 : 0.0;
+    } else {
+      const long double a = two_pi * (long double)m / (long double)L;
+      c = (double)cosl(a);
+      sn = (double)-sinl(a);
+    }
+    t[m] = make_double2(c, sn);
+  }
+}
+
+FftPlan make_fft_plan(int L, int tw_off) {
+  FftPlan p{};
+  if (fft_length_ok(L)) return p;  // compile-time plan
+  p.L = L;
+  p.tw_off = tw_off;
+  int rest = L, twos = 0;
+  while (rest % 2 == 0) {
+    rest /= 2;
+    ++twos;
+  }
+  // powers of two as radix-16 stages, the remainder as one radix-8/4/2 stage
+  while (twos >= 4) {
+    p.r[p.n++] = 16;
+    twos -= 4;
+  }
+  if (twos > 0) p.r[p.n++] = 1 << twos;
+  while (rest % 3 == 0) {
+    p.r[p.n++] = 3;
+    rest /= 3;
+  }
+  for (int f = 5; rest > 1; f += 2) {
+    while (rest % f == 0) {
+      p.r[p.n++] = f;
+      rest /= f;
+    }
+  }
+  return p;
+}
+
 Tiling choose_tiling(const Grid& g) {
   Tiling t;
   const long long lines = (long long)g.nx * g.ny;
@@ -556,14 +602,23 @@ cudaError_t setup_fft_kernels(const Grid& g, const Tiling& t) {
     if ((e = allow_smem(k_fwd_y_b<V>, y_smem(V, t.bk_y, 3)))) return e;    \
     if ((e = allow_smem(k_inv_y_b<V>, y_smem(V, t.bk_y, 3)))) return e;    \
     break;
-  FH_SWITCH_LEN(g.ny, YCASE)
+  if (g.py.L) {
+    if ((e = allow_smem(k_fwd_y<0>, y_smem(g.ny, t.bk_y, 3)))) return e;
+    if ((e = allow_smem(k_inv_y<0>, y_smem(g.ny, t.bk_y, 3)))) return e;
+  } else {
+    FH_SWITCH_LEN(g.ny, YCASE)
+  }
 #undef YCASE
 #define XCASE(V)                                                           \
   case V:                                                                  \
     if ((e = allow_smem(k_x_ghat<V>, y_smem(V, t.bk_x, 6)))) return e;     \
     if ((e = allow_smem(k_x_ghat_b<V>, y_smem(V, t.bk_x, 6)))) return e;   \
     break;
-  FH_SWITCH_LEN(g.nx, XCASE)
+  if (g.px.L) {
+    if ((e = allow_smem(k_x_ghat<0>, y_smem(g.nx, t.bk_x, 6)))) return e;
+  } else {
+    FH_SWITCH_LEN(g.nx, XCASE)
+  }
 #undef XCASE
   return cudaSuccess;
 }
@@ -596,7 +651,8 @@ cudaError_t launch_fwd_y(const Grid& g, const Tiling& t, double2* S, const doubl
   case V:                                                                                   \
     k_fwd_y<V><<<grid, kThreads, y_smem(V, t.bk_y, 3), s>>>(g, t.bk_y, S, tw, cg);          \
     break;
-  FH_SWITCH_LEN(g.ny, YL)
+  if (g.py.L) k_fwd_y<0><<<grid, kThreads, y_smem(g.ny, t.bk_y, 3), s>>>(g, t.bk_y, S, tw, cg);
+  else FH_SWITCH_LEN(g.ny, YL)
 #undef YL
   return cudaGetLastError();
 }
@@ -609,7 +665,8 @@ cudaError_t launch_x_ghat(const Grid& g, const Tiling& t, double2* S, const doub
   case V:                                                                                          \
     k_x_ghat<V><<<grid, kThreads, y_smem(V, t.bk_x, 6), s>>>(g, t.bk_x, S, tw, scale, cg);         \
     break;
-  FH_SWITCH_LEN(g.nx, XL)
+  if (g.px.L) k_x_ghat<0><<<grid, kThreads, y_smem(g.nx, t.bk_x, 6), s>>>(g, t.bk_x, S, tw, scale, cg);
+  else FH_SWITCH_LEN(g.nx, XL)
 #undef XL
   return cudaGetLastError();
 }
@@ -622,7 +679,8 @@ cudaError_t launch_inv_y(const Grid& g, const Tiling& t, double2* S, const doubl
   case V:                                                                                   \
     k_inv_y<V><<<grid, kThreads, y_smem(V, t.bk_y, 3), s>>>(g, t.bk_y, S, tw, cg);          \
     break;
-  FH_SWITCH_LEN(g.ny, IYL)
+  if (g.py.L) k_inv_y<0><<<grid, kThreads, y_smem(g.ny, t.bk_y, 3), s>>>(g, t.bk_y, S, tw, cg);
+  else FH_SWITCH_LEN(g.ny, IYL)
 #undef IYL
   return cudaGetLastError();
 }

@@ -4,10 +4,11 @@
 // (its FFT butterflies and tangent contraction need about 650 FP64 operations
 // per voxel and iteration, against 72 bytes moved per field), so the roofline
 // it is held to is the FP64 one. That peak is measured here rather than taken
-// from unit counts: every thread runs eight independent chains of fused
-// multiply-adds a <- a * m + c (no dependency between chains, so the pipe, not
-// latency, sets the rate), on a grid of `ctas_per_sm` CTAs of 256 threads per
-// SM, and the launch is timed with CUDA events on the caller's stream.
+// from unit counts: every thread runs independent chains of fused
+// multiply-adds a <- a * m + c (4, 8 or 16 chains with no dependency between
+// them, so the pipe, not latency, sets the rate), on a grid of `ctas_per_sm`
+// CTAs of 256 threads per SM, and the launch is timed with CUDA events on the
+// caller's stream.
 #include <cstdio>
 
 #include "fh_kernels.h"
@@ -16,10 +17,9 @@ namespace fh {
 
 namespace {
 
-constexpr int kChains = 8;
-
 __device__ double g_probe_sink;
 
+template <int kChains>
 __global__ void __launch_bounds__(kThreads) k_dfma_probe(long long iters, double m, double c, double sentinel) {
   double a[kChains];
 #pragma unroll
@@ -40,13 +40,25 @@ __global__ void __launch_bounds__(kThreads) k_dfma_probe(long long iters, double
 
 extern "C" void fh_internal_set_error(const char* msg);
 
-extern "C" int fh_probe_fp64(int ctas_per_sm, long long iters, void* cuda_stream, double* ms_out,
+namespace {
+cudaError_t launch_probe(int chains, unsigned grid, long long iters, cudaStream_t s) {
+  switch (chains) {
+    case 4: fh::k_dfma_probe<4><<<grid, fh::kThreads, 0, s>>>(iters, 0.999999, 1e-9, -1.0); break;
+    case 8: fh::k_dfma_probe<8><<<grid, fh::kThreads, 0, s>>>(iters, 0.999999, 1e-9, -1.0); break;
+    default: fh::k_dfma_probe<16><<<grid, fh::kThreads, 0, s>>>(iters, 0.999999, 1e-9, -1.0); break;
+  }
+  return cudaGetLastError();
+}
+}  // namespace
+
+extern "C" int fh_probe_fp64(int ctas_per_sm, int chains, long long iters, void* cuda_stream, double* ms_out,
                              double* lane_ops_out) {
   using namespace fh;
   char msg[256];
   fh_internal_set_error("");
-  if (ctas_per_sm < 1 || ctas_per_sm > 8 || iters < 1 || iters > (1LL << 34)) {
-    fh_internal_set_error("fh_probe_fp64: ctas_per_sm must be 1..8 and iters 1..2^34");
+  if (ctas_per_sm < 1 || ctas_per_sm > 8 || iters < 1 || iters > (1LL << 34) ||
+      (chains != 4 && chains != 8 && chains != 16)) {
+    fh_internal_set_error("fh_probe_fp64: ctas_per_sm must be 1..8, chains 4, 8 or 16, iters 1..2^34");
     return FH_ERR_ARG;
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -58,16 +70,10 @@ extern "C" int fh_probe_fp64(int ctas_per_sm, long long iters, void* cuda_stream
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   const unsigned grid = (unsigned)(sms * ctas_per_sm);
-  if (e == cudaSuccess) {
-    // one short launch first so that the timed one finds the module loaded and clocks up
-    k_dfma_probe<<<grid, kThreads, 0, s>>>(iters / 16 + 1, 0.999999, 1e-9, -1.0);
-    e = cudaGetLastError();
-  }
+  // one short launch first so that the timed one finds the module loaded and clocks up
+  if (e == cudaSuccess) e = launch_probe(chains, grid, iters / 16 + 1, s);
   if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-  if (e == cudaSuccess) {
-    k_dfma_probe<<<grid, kThreads, 0, s>>>(iters, 0.999999, 1e-9, -1.0);
-    e = cudaGetLastError();
-  }
+  if (e == cudaSuccess) e = launch_probe(chains, grid, iters, s);
   if (e == cudaSuccess) e = cudaEventRecord(e1, s);
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
@@ -79,6 +85,6 @@ extern "C" int fh_probe_fp64(int ctas_per_sm, long long iters, void* cuda_stream
     return FH_ERR_CUDA;
   }
   if (ms_out) *ms_out = ms;
-  if (lane_ops_out) *lane_ops_out = (double)grid * kThreads * kChains * (double)iters;
+  if (lane_ops_out) *lane_ops_out = (double)grid * kThreads * chains * (double)iters;
   return FH_OK;
 }

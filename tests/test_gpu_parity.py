@@ -93,7 +93,12 @@ PROJ_SHAPES = [(8, 8, 8), (4, 8, 16), (16, 4, 2), (2, 2, 2), (1, 4, 8), (32, 16,
                (256, 2, 2), (2, 256, 2), (2, 2, 256), (64, 32, 128),
                # radix-3 lengths (3 * 2^a), odd axes and odd half lengths
                (48, 12, 6), (3, 6, 24), (96, 8, 4), (6, 3, 96), (24, 48, 12), (192, 2, 2), (2, 2, 192),
-               (12, 12, 12)]
+               (12, 12, 12),
+               # x/y lengths without a compile-time plan (run-time plans: radix 5, 7 and direct prime stages,
+               # even lengths with odd factors, extents above 256)
+               (5, 7, 4), (13, 11, 2), (15, 21, 8), (9, 25, 6), (10, 14, 4), (199, 3, 2), (3, 199, 2),
+               (169, 2, 2), (127, 4, 2), (121, 6, 2), (299, 2, 2), (512, 2, 2), (2, 512, 2), (384, 3, 2),
+               (40, 20, 16)]
 
 
 @pytest.mark.parametrize("shape", PROJ_SHAPES)
@@ -113,7 +118,7 @@ def test_projection_matches_oracle(fh, torch, shape):
 
 
 @pytest.mark.parametrize("kind", [1, 2, 0])
-@pytest.mark.parametrize("shape", [(8, 8, 8), (4, 16, 32)])
+@pytest.mark.parametrize("shape", [(8, 8, 8), (4, 16, 32), (15, 7, 8)])
 def test_matvec_matches_oracle_stored_and_jvp(fh, torch, kind, shape):
     n = int(np.prod(shape))
     F = random_deformation(n, seed=5, scale=0.1, identity=omat.FINITE_STRAIN[kind]).reshape((9,) + shape)
@@ -198,6 +203,22 @@ def test_radix3_grid_solve_matches_oracle(fh, torch):
     Fbar = shear_macro(0.05, finite=True)
     Fg, pbar, stats, _, ref = _solve_both(fh, torch, phase, params, 1, Fbar, 2, 1e-10)
     assert stats["n_newton"] == len(ref.newton_residuals)
+    np.testing.assert_allclose(pbar, ref.Pbar, rtol=PBAR_TOL, atol=PBAR_TOL * np.abs(ref.Pbar).max())
+    assert np.abs(Fg - ref.F).max() < FIELD_TOL * np.abs(ref.F - Fbar.reshape(9, 1, 1, 1)).max()
+
+
+@pytest.mark.parametrize("shape", [(15, 21, 8), (27, 25, 2)])
+def test_odd_grid_solve_matches_oracle(fh, torch, shape):
+    """Odd x/y extents (the paper's grids are odd, Section 4.1.1): run-time FFT plans, no Nyquist index."""
+    if shape[2] > 2:
+        phase = random_spheres(shape, seed=6, r_min=1.5, r_max=3.0)
+    else:  # z-invariant (plane strain) cell
+        phase = np.ascontiguousarray(np.repeat(_phase(shape[:2] + (1,), 9), shape[2], axis=2))
+    params = two_phase_table(1.5, 1.0, 10.0)
+    Fbar = shear_macro(0.05, finite=True)
+    Fg, pbar, stats, _, ref = _solve_both(fh, torch, phase, params, 1, Fbar, 2, 1e-10)
+    assert stats["n_newton"] == len(ref.newton_residuals)
+    assert all(abs(a - b) <= 1 for a, b in zip(stats["cg_iterations"], ref.cg_iterations))
     np.testing.assert_allclose(pbar, ref.Pbar, rtol=PBAR_TOL, atol=PBAR_TOL * np.abs(ref.Pbar).max())
     assert np.abs(Fg - ref.F).max() < FIELD_TOL * np.abs(ref.F - Fbar.reshape(9, 1, 1, 1)).max()
 

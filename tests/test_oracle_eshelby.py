@@ -25,6 +25,9 @@ from oracle import homogenize
 from rve_inputs import centered_disk
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "eshelby_table1.json")
+# Table 1 prints three digits of a numerical result whose disk is only approximately specified; the cell
+# here (area fraction 0.007 at 99^2 and 199^2) gives 4.0295 / 1.0081, within 1.9e-3 of the printed values
+TABLE1_RTOL = 2e-3
 
 
 def eshelby_cell(n, nz=1, fraction=0.007):
@@ -50,6 +53,6 @@ def test_eshelby_table1_and_dilute_estimate():
     cxxxx, cyyyy, cxyxy = C[0, 0], C[4, 4], C[1, 1]
     np.testing.assert_allclose(cxxxx, cyyyy, rtol=1e-12)
     num = table["numerical"]
-    np.testing.assert_allclose([cxxxx, cyyyy, cxyxy], [num["Cxxxx"], num["Cyyyy"], num["Cxyxy"]], rtol=3e-3)
+    np.testing.assert_allclose([cxxxx, cyyyy, cxyxy], [num["Cxxxx"], num["Cyyyy"], num["Cxyxy"]], rtol=TABLE1_RTOL)
     d_xxxx, d_xyxy = dilute_estimate(f)
     np.testing.assert_allclose([cxxxx, cxyxy], [d_xxxx, d_xyxy], rtol=2e-4)
