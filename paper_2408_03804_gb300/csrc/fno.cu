@@ -7,10 +7,17 @@
 // the spectral kernels is a coalesced 128-byte row whatever the axis. The
 // truncated real DFT along a line keeps 12 modes, so it is computed as a
 // direct sum against precomputed twiddles (24 cosines/sines per position)
-// rather than by an FFT. All arithmetic is float32 on the CUDA cores with
-// bfloat16 weights; every reduction over voxels (weight gradients, loss)
-// runs in a fixed order through per-block partials, so a training step is
-// deterministic.
+// rather than by an FFT (float32 on the CUDA cores). The channel
+// contractions run on the tensor cores as bfloat16 MMAs (mma.sync m16n8k16)
+// with float32 accumulation: the per-mode complex 32x32 mixing as a real
+// 64x64 block per mode applied to the coefficients of the CTA's 8 lines at
+// once, the pointwise 32x32 mixing and the 32 -> 128 -> 9 projection head on
+// tiles of 16 voxels. The bfloat16 weights enter exactly; a float32 operand
+// (activation, coefficient, effective head) enters as a pair of bfloat16
+// terms hi + lo (about 16 significant bits), so each product takes two or
+// three MMAs and the result stays close to float32 arithmetic. Every
+// reduction over voxels (weight gradients, loss) runs in a fixed order
+// through per-block partials, so a training step is deterministic.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -57,7 +64,6 @@ constexpr int kHeadEff = kOut * kHid + kOut;                        // 1161
 constexpr int kProjRow = kHid * kC + kHid + kHeadEff;               // 5385
 constexpr int kProjShared = kHid * kC + kHid;                       // 4224
 constexpr int kPointLen = kC * kC + kC;                             // 1056
-constexpr long long kSpecW = (long long)kLayers * 3 * kModes * kC * kC;  // complex spectral weights
 static_assert(kNParam == 314161, "parameter layout");
 
 constexpr int kThreads = 256;
@@ -101,27 +107,77 @@ __device__ __forceinline__ float gelu_d(float z) {
 __device__ __forceinline__ float bf(const __nv_bfloat16* p, long long i) { return __bfloat162float(p[i]); }
 
 // ---------------------------------------------------------------------------
+// tensor-core helpers. mma.sync m16n8k16, bf16 inputs, f32 accumulators; with
+// g = lane / 4, t = lane % 4 a thread holds A[g][2t, 2t+1], A[g+8][2t, 2t+1],
+// A[g][2t+8, 2t+9], A[g+8][2t+8, 2t+9] (four bf16 pairs), B[2t, 2t+1][g] and
+// B[2t+8, 2t+9][g] (two pairs), and D[g][2t, 2t+1], D[g+8][2t, 2t+1].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint4& a, uint32_t b0, uint32_t b1) {
+  mma_bf16(d, a.x, a.y, a.z, a.w, b0, b1);
+}
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
+// (x, y) -> hi = bf16(x, y) and lo = bf16(x - hi.x, y - hi.y)
+__device__ __forceinline__ void split_bf2(float x, float y, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+  const float2 hf = __bfloat1622float2(h);
+  hi = bf2_bits(h);
+  lo = bf2_bits(__floats2bfloat162_rn(x - hf.x, y - hf.y));
+}
+
+// Real 64x64 form of the complex mixing of mode k of layer l, axis ax:
+// row r = (ri_o, o), column kap = (ri_c, c), each as 32 * ri + index, with
+// [[Wr, -Wi], [Wi, Wr]] so that (Yr, Yi) = Wt (Xr, Xi) is Y = W X.
+__device__ __forceinline__ float wtilde(const float* __restrict__ theta, int l, int ax, int k, int r, int kap) {
+  const int ro = r >> 5, o = r & 31, rc = kap >> 5, c = kap & 31;
+  const long long src = off_W(l) + ((long long)(ax * kModes + k) * 2) * kC * kC + (long long)o * kC + c;
+  const float wr = theta[src], wi = theta[src + kC * kC];
+  return ro == rc ? wr : (ro == 0 ? -wi : wi);
+}
+
+// A fragments of the mixing matrices in mma order, for the forward (Wt) and
+// backward (Wt^T) passes: entry ((((l*3 + ax)*kModes + k)*4 + mt)*4 + ks)*32
+// + lane is the uint4 that lane holds for row tile mt, k-step ks
+constexpr long long kFragPerMode = 4 * 4 * 32;
+constexpr long long kFrag = (long long)kLayers * 3 * kModes * kFragPerMode;
+
+// ---------------------------------------------------------------------------
 // parameters: bfloat16 copies, spectral weights also as (re, im) pairs in the
 // two transposed orders the forward ([k][c][o]) and backward ([k][o][c])
 // passes read with lane-contiguous addresses
 // ---------------------------------------------------------------------------
-__global__ void k_prepare(const float* __restrict__ theta, __nv_bfloat16* __restrict__ wq,
-                          __nv_bfloat162* __restrict__ wf, __nv_bfloat162* __restrict__ wb) {
+__global__ void k_prepare(const float* __restrict__ theta, __nv_bfloat16* __restrict__ wq, uint4* __restrict__ wfa,
+                          uint4* __restrict__ wba) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < kNParam; i += stride)
     wq[i] = __float2bfloat16_rn(theta[i]);
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < kSpecW; e += stride) {
-    const int c = (int)(e % kC);
-    const int o = (int)((e / kC) % kC);
-    const long long lak = e / (kC * kC);  // (l * 3 + ax) * kModes + k
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < kFrag; e += stride) {
+    const int lane = (int)(e & 31), g = lane >> 2, t = lane & 3;
+    const int ks = (int)((e >> 5) & 3), mt = (int)((e >> 7) & 3);
+    const long long lak = e >> 9;  // (l * 3 + ax) * kModes + k
     const int k = (int)(lak % kModes);
-    const long long la = lak / kModes;
-    const int ax = (int)(la % 3);
-    const int l = (int)(la / 3);
-    const long long src = off_W(l) + ((long long)(ax * kModes + k) * 2) * kC * kC + (long long)o * kC + c;
-    const __nv_bfloat162 w = __floats2bfloat162_rn(theta[src], theta[src + kC * kC]);
-    wf[lak * kC * kC + (long long)c * kC + o] = w;
-    wb[lak * kC * kC + (long long)o * kC + c] = w;
+    const int ax = (int)((lak / kModes) % 3);
+    const int l = (int)(lak / (3 * kModes));
+    const int r0 = mt * 16 + g, r1 = r0 + 8, c0 = ks * 16 + 2 * t, c1 = c0 + 8;
+    // forward: A[r][kap] = Wt[r][kap]; backward: A[kap][r] = Wt[r][kap]
+    uint4 f, b;
+    f.x = bf2_bits(__floats2bfloat162_rn(wtilde(theta, l, ax, k, r0, c0), wtilde(theta, l, ax, k, r0, c0 + 1)));
+    f.y = bf2_bits(__floats2bfloat162_rn(wtilde(theta, l, ax, k, r1, c0), wtilde(theta, l, ax, k, r1, c0 + 1)));
+    f.z = bf2_bits(__floats2bfloat162_rn(wtilde(theta, l, ax, k, r0, c1), wtilde(theta, l, ax, k, r0, c1 + 1)));
+    f.w = bf2_bits(__floats2bfloat162_rn(wtilde(theta, l, ax, k, r1, c1), wtilde(theta, l, ax, k, r1, c1 + 1)));
+    b.x = bf2_bits(__floats2bfloat162_rn(wtilde(theta, l, ax, k, c0, r0), wtilde(theta, l, ax, k, c0 + 1, r0)));
+    b.y = bf2_bits(__floats2bfloat162_rn(wtilde(theta, l, ax, k, c0, r1), wtilde(theta, l, ax, k, c0 + 1, r1)));
+    b.z = bf2_bits(__floats2bfloat162_rn(wtilde(theta, l, ax, k, c1, r0), wtilde(theta, l, ax, k, c1 + 1, r0)));
+    b.w = bf2_bits(__floats2bfloat162_rn(wtilde(theta, l, ax, k, c1, r1), wtilde(theta, l, ax, k, c1 + 1, r1)));
+    wfa[e] = f;
+    wba[e] = b;
   }
 }
 
@@ -160,69 +216,103 @@ __global__ void k_lift(const uint8_t* const* __restrict__ phase, const float* __
 // ---------------------------------------------------------------------------
 // spectral convolution along one axis, forward: out (=/+=) S_ax(h)
 // ---------------------------------------------------------------------------
-// shared memory of the spectral kernels: twiddles (2 x n x 24) and one 24 x 32
-// coefficient block per warp; the complex weights (48 KiB per layer and axis)
-// are read through L1, which keeps more CTAs resident than staging them
+// shared memory of the spectral kernels: twiddles (2 x n x 24) and two
+// coefficient blocks (24 x 32, rows padded) per warp, one for the DFT of its
+// line and one for the mixed coefficients. The mixing matrices are read as
+// mma fragments through L1.
+constexpr int kXStride = kJ * kC + 8;  // floats per line block (padding spreads the banks of the 8 lines)
 __host__ __device__ constexpr size_t spec_smem(int n) {
-  return 2 * (size_t)n * kJ * sizeof(float) + (size_t)kWarps * kJ * kC * sizeof(float);
+  return 2 * (size_t)n * kJ * sizeof(float) + 2 * (size_t)kWarps * kXStride * sizeof(float);
+}
+
+// Complex mixing of the CTA's 8 lines on the tensor cores: for every mode k,
+// Y_k = Wt_k X_k with Wt_k the real 64x64 block (rows (ri, o), columns
+// (ri, c)) and X_k the 64 x 8 matrix of the 8 lines' coefficients of mode k
+// (split hi + lo). Warp w takes row tile w % 4 of the modes k = w/4, w/4 + 2,
+// ...; X and Y are [line][j][channel] blocks in shared memory (j = 2k + ri).
+__device__ __forceinline__ void mix_modes_tc(const float* __restrict__ sX, float* __restrict__ sY,
+                                             const uint4* __restrict__ WA, int warp, int lane) {
+  const int mt = warp & 3, gi = lane >> 2, t = lane & 3;
+  const float* Xl = sX + gi * kXStride;
+  for (int k = warp >> 2; k < kModes; k += 2) {
+    float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const uint4* wa = WA + (long long)((k * 4 + mt) * 4) * 32 + lane;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const uint4 af = __ldg(wa + ks * 32);
+      const int kap0 = ks * 16 + 2 * t, kap1 = kap0 + 8;  // B rows kap, kap + 1 (same half of 32)
+      const float2 x0 = *reinterpret_cast<const float2*>(Xl + (2 * k + (kap0 >> 5)) * kC + (kap0 & 31));
+      const float2 x1 = *reinterpret_cast<const float2*>(Xl + (2 * k + (kap1 >> 5)) * kC + (kap1 & 31));
+      uint32_t h0, l0, h1, l1;
+      split_bf2(x0.x, x0.y, h0, l0);
+      split_bf2(x1.x, x1.y, h1, l1);
+      mma_bf16(d, af, h0, h1);
+      mma_bf16(d, af, l0, l1);
+    }
+    // D rows r (output (ri, o)), columns = lines 2t, 2t + 1
+    const int r0 = mt * 16 + gi, r1 = r0 + 8;
+    float* y0 = sY + (2 * t) * kXStride;
+    float* y1 = y0 + kXStride;
+    y0[(2 * k + (r0 >> 5)) * kC + (r0 & 31)] = d[0];
+    y1[(2 * k + (r0 >> 5)) * kC + (r0 & 31)] = d[1];
+    y0[(2 * k + (r1 >> 5)) * kC + (r1 & 31)] = d[2];
+    y1[(2 * k + (r1 >> 5)) * kC + (r1 & 31)] = d[3];
+  }
 }
 
 template <bool ACCUM>
-__global__ void __launch_bounds__(kThreads, 4) k_spec_fwd(const float* __restrict__ h, float* __restrict__ out,
-                                                       const __nv_bfloat162* __restrict__ W,
+__global__ void __launch_bounds__(kThreads, 3) k_spec_fwd(const float* __restrict__ h, float* __restrict__ out,
+                                                       const uint4* __restrict__ WA,
                                                        const float* __restrict__ tw, const float* __restrict__ itw,
                                                        Geom g, int ax, int n, long long n_lines) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* stw = reinterpret_cast<float*>(smem);
   float* sitw = stw + n * kJ;
   float* sX = sitw + n * kJ;
+  float* sY = sX + kWarps * kXStride;
   for (int i = threadIdx.x; i < n * kJ; i += blockDim.x) {
     stw[i] = tw[i];
     sitw[i] = itw[i];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* X = sX + warp * kJ * kC;
-  for (long long li = (long long)blockIdx.x * kWarps + warp; li < n_lines; li += (long long)gridDim.x * kWarps) {
-    long long base, stride;
-    line_of(g, ax, li, base, stride);
-    const float* src = h + base * kC + lane;
+  float* X = sX + warp * kXStride;
+  for (long long l0 = (long long)blockIdx.x * kWarps; l0 < n_lines; l0 += (long long)gridDim.x * kWarps) {
+    const long long li = l0 + warp;
+    const bool valid = li < n_lines;
+    long long base = 0, stride = 0;
+    if (valid) line_of(g, ax, li, base, stride);
     const long long step = stride * kC;
     // truncated DFT of this lane's channel: X[2k] = sum h cos, X[2k+1] = -sum h sin
     float a[kJ];
 #pragma unroll
     for (int j = 0; j < kJ; ++j) a[j] = 0.0f;
+    if (valid) {
+      const float* src = h + base * kC + lane;
 #pragma unroll 4
-    for (int x = 0; x < n; ++x) {
-      const float v = src[x * step];
-      const float4* t4 = reinterpret_cast<const float4*>(stw + x * kJ);
+      for (int x = 0; x < n; ++x) {
+        const float v = src[x * step];
+        const float4* t4 = reinterpret_cast<const float4*>(stw + x * kJ);
 #pragma unroll
-      for (int q = 0; q < kJ / 4; ++q) {
-        const float4 t = t4[q];
-        a[4 * q] = fmaf(v, t.x, a[4 * q]);
-        a[4 * q + 1] = fmaf(v, t.y, a[4 * q + 1]);
-        a[4 * q + 2] = fmaf(v, t.z, a[4 * q + 2]);
-        a[4 * q + 3] = fmaf(v, t.w, a[4 * q + 3]);
+        for (int q = 0; q < kJ / 4; ++q) {
+          const float4 t = t4[q];
+          a[4 * q] = fmaf(v, t.x, a[4 * q]);
+          a[4 * q + 1] = fmaf(v, t.y, a[4 * q + 1]);
+          a[4 * q + 2] = fmaf(v, t.z, a[4 * q + 2]);
+          a[4 * q + 3] = fmaf(v, t.w, a[4 * q + 3]);
+        }
       }
     }
 #pragma unroll
     for (int j = 0; j < kJ; ++j) X[j * kC + lane] = a[j];
-    __syncwarp();
-    // channel mixing per mode (lane = output channel): Y_k = W_k X_k
+    __syncthreads();
+    mix_modes_tc(sX, sY, WA, warp, lane);
+    __syncthreads();
+    if (!valid) continue;
+    // truncated real inverse DFT: S[x] = sum_j y[j] itw[x][j]
     float y[kJ];
 #pragma unroll
-    for (int j = 0; j < kJ; ++j) y[j] = 0.0f;
-    for (int c = 0; c < kC; ++c) {
-#pragma unroll
-      for (int k = 0; k < kModes; ++k) {
-        const float2 w = __bfloat1622float2(__ldg(&W[(k * kC + c) * kC + lane]));
-        const float xr = X[(2 * k) * kC + c], xi = X[(2 * k + 1) * kC + c];
-        y[2 * k] = fmaf(w.x, xr, fmaf(-w.y, xi, y[2 * k]));
-        y[2 * k + 1] = fmaf(w.x, xi, fmaf(w.y, xr, y[2 * k + 1]));
-      }
-    }
-    __syncwarp();
-    // truncated real inverse DFT: S[x] = sum_j y[j] itw[x][j]
+    for (int j = 0; j < kJ; ++j) y[j] = sY[warp * kXStride + j * kC + lane];
     float* dst = out + base * kC + lane;
 #pragma unroll 2
     for (int x = 0; x < n; ++x) {
@@ -251,70 +341,69 @@ __global__ void __launch_bounds__(kThreads, 4) k_spec_fwd(const float* __restric
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads, 3) k_spec_bwd(const float* __restrict__ h, const float* __restrict__ gz,
                                                        float* __restrict__ gh, float* __restrict__ xs,
-                                                       float* __restrict__ gys, const __nv_bfloat162* __restrict__ W,
+                                                       float* __restrict__ gys, const uint4* __restrict__ WB,
                                                        const float* __restrict__ tw, const float* __restrict__ itw,
                                                        Geom g, int ax, int n, long long n_lines) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* stw = reinterpret_cast<float*>(smem);
   float* sitw = stw + n * kJ;
-  float* sG = sitw + n * kJ;
+  float* sG = sitw + n * kJ;           // coefficient gradients gY of the CTA's lines
+  float* sGX = sG + kWarps * kXStride;  // gX = Wt^T gY
   for (int i = threadIdx.x; i < n * kJ; i += blockDim.x) {
     stw[i] = tw[i];
     sitw[i] = itw[i];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* G = sG + warp * kJ * kC;
-  for (long long li = (long long)blockIdx.x * kWarps + warp; li < n_lines; li += (long long)gridDim.x * kWarps) {
-    long long base, stride;
-    line_of(g, ax, li, base, stride);
+  float* G = sG + warp * kXStride;
+  for (long long l0 = (long long)blockIdx.x * kWarps; l0 < n_lines; l0 += (long long)gridDim.x * kWarps) {
+    const long long li = l0 + warp;
+    const bool valid = li < n_lines;
+    long long base = 0, stride = 0;
+    if (valid) line_of(g, ax, li, base, stride);
     const long long step = stride * kC;
-    const float* hs = h + base * kC + lane;
-    const float* gs = gz + base * kC + lane;
     float a[kJ], b[kJ];
 #pragma unroll
     for (int j = 0; j < kJ; ++j) a[j] = b[j] = 0.0f;
+    if (valid) {
+      const float* hs = h + base * kC + lane;
+      const float* gs = gz + base * kC + lane;
 #pragma unroll 2
-    for (int x = 0; x < n; ++x) {
-      const float v = hs[x * step], w = gs[x * step];
-      const float4* t4 = reinterpret_cast<const float4*>(stw + x * kJ);
-      const float4* u4 = reinterpret_cast<const float4*>(sitw + x * kJ);
+      for (int x = 0; x < n; ++x) {
+        const float v = hs[x * step], w = gs[x * step];
+        const float4* t4 = reinterpret_cast<const float4*>(stw + x * kJ);
+        const float4* u4 = reinterpret_cast<const float4*>(sitw + x * kJ);
 #pragma unroll
-      for (int q = 0; q < kJ / 4; ++q) {
-        const float4 t = t4[q], u = u4[q];
-        a[4 * q] = fmaf(v, t.x, a[4 * q]);
-        a[4 * q + 1] = fmaf(v, t.y, a[4 * q + 1]);
-        a[4 * q + 2] = fmaf(v, t.z, a[4 * q + 2]);
-        a[4 * q + 3] = fmaf(v, t.w, a[4 * q + 3]);
-        b[4 * q] = fmaf(w, u.x, b[4 * q]);
-        b[4 * q + 1] = fmaf(w, u.y, b[4 * q + 1]);
-        b[4 * q + 2] = fmaf(w, u.z, b[4 * q + 2]);
-        b[4 * q + 3] = fmaf(w, u.w, b[4 * q + 3]);
+        for (int q = 0; q < kJ / 4; ++q) {
+          const float4 t = t4[q], u = u4[q];
+          a[4 * q] = fmaf(v, t.x, a[4 * q]);
+          a[4 * q + 1] = fmaf(v, t.y, a[4 * q + 1]);
+          a[4 * q + 2] = fmaf(v, t.z, a[4 * q + 2]);
+          a[4 * q + 3] = fmaf(v, t.w, a[4 * q + 3]);
+          b[4 * q] = fmaf(w, u.x, b[4 * q]);
+          b[4 * q + 1] = fmaf(w, u.y, b[4 * q + 1]);
+          b[4 * q + 2] = fmaf(w, u.z, b[4 * q + 2]);
+          b[4 * q + 3] = fmaf(w, u.w, b[4 * q + 3]);
+        }
+      }
+      float* xo = xs + li * (kJ * kC) + lane;
+      float* go = gys + li * (kJ * kC) + lane;
+#pragma unroll
+      for (int j = 0; j < kJ; ++j) {
+        xo[j * kC] = a[j];
+        go[j * kC] = b[j];
       }
     }
-    float* xo = xs + li * (kJ * kC) + lane;
-    float* go = gys + li * (kJ * kC) + lane;
 #pragma unroll
-    for (int j = 0; j < kJ; ++j) {
-      xo[j * kC] = a[j];
-      go[j * kC] = b[j];
-      G[j * kC + lane] = b[j];
-    }
-    __syncwarp();
-    // gX = W^T gY (lane = input channel c)
+    for (int j = 0; j < kJ; ++j) G[j * kC + lane] = b[j];
+    __syncthreads();
+    // gX = Wt^T gY on the tensor cores (same pattern as the forward mixing)
+    mix_modes_tc(sG, sGX, WB, warp, lane);
+    __syncthreads();
+    if (!valid) continue;
     float gx[kJ];
 #pragma unroll
-    for (int j = 0; j < kJ; ++j) gx[j] = 0.0f;
-    for (int o = 0; o < kC; ++o) {
-#pragma unroll
-      for (int k = 0; k < kModes; ++k) {
-        const float2 w = __bfloat1622float2(__ldg(&W[(k * kC + o) * kC + lane]));
-        const float yr = G[(2 * k) * kC + o], yi = G[(2 * k + 1) * kC + o];
-        gx[2 * k] = fmaf(yr, w.x, fmaf(yi, w.y, gx[2 * k]));
-        gx[2 * k + 1] = fmaf(yi, w.x, fmaf(-yr, w.y, gx[2 * k + 1]));
-      }
-    }
-    __syncwarp();
+    for (int j = 0; j < kJ; ++j) gx[j] = sGX[warp * kXStride + j * kC + lane];
     float* dst = gh + base * kC + lane;
 #pragma unroll 2
     for (int x = 0; x < n; ++x) {
@@ -436,33 +525,61 @@ __global__ void __launch_bounds__(kThreads) k_point_fwd(const float* __restrict_
                                                         const __nv_bfloat16* __restrict__ wq, int layer,
                                                         float* __restrict__ z, float* __restrict__ hn,
                                                         long long nvox, int act) {
-  __shared__ __align__(16) float sh[kWarps][32 * kC];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float Mr[kC];
+  // tiles of 16 voxels per warp: D[vox][o] = sum_c h[vox][c] M[o][c] on the tensor cores
+  // (A = h split hi + lo, B[c][o] = M[o][c] exact in bfloat16)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gi = lane >> 2, t = lane & 3;
+  uint32_t bm[4][2][2];
+  float mb[4][2];
 #pragma unroll
-  for (int c = 0; c < kC; ++c) Mr[c] = bf(wq, off_M(layer) + lane * kC + c);
-  const float mb = bf(wq, off_m(layer) + lane);
-  const long long tiles = (nvox + 31) / 32;
-  for (long long t = (long long)blockIdx.x * kWarps + warp; t < tiles; t += (long long)gridDim.x * kWarps) {
-    const long long v0 = t * 32;
-    for (int i = 0; i < 32; ++i) sh[warp][i * kC + lane] = v0 + i < nvox ? h[(v0 + i) * kC + lane] : 0.0f;
-    __syncwarp();
-    for (int i = 0; i < 32 && v0 + i < nvox; ++i) {
-      const long long e = (v0 + i) * kC + lane;
-      float s = mb + acc[e];
-      const float4* r = reinterpret_cast<const float4*>(&sh[warp][i * kC]);
+  for (int nt = 0; nt < 4; ++nt) {
+    const int o = nt * 8 + gi;
 #pragma unroll
-      for (int q = 0; q < kC / 4; ++q) {
-        const float4 hv = r[q];
-        s = fmaf(Mr[4 * q], hv.x, s);
-        s = fmaf(Mr[4 * q + 1], hv.y, s);
-        s = fmaf(Mr[4 * q + 2], hv.z, s);
-        s = fmaf(Mr[4 * q + 3], hv.w, s);
-      }
-      if (z) z[e] = s;
-      hn[e] = act ? gelu(s) : s;
+    for (int ks = 0; ks < 2; ++ks) {
+      const __nv_bfloat162* row = reinterpret_cast<const __nv_bfloat162*>(wq + off_M(layer) + o * kC + ks * 16 + 2 * t);
+      bm[nt][ks][0] = bf2_bits(row[0]);
+      bm[nt][ks][1] = bf2_bits(row[4]);
     }
-    __syncwarp();
+    mb[nt][0] = bf(wq, off_m(layer) + nt * 8 + 2 * t);
+    mb[nt][1] = bf(wq, off_m(layer) + nt * 8 + 2 * t + 1);
+  }
+  const long long tiles = (nvox + 15) / 16;
+  for (long long tile = (long long)blockIdx.x * kWarps + warp; tile < tiles; tile += (long long)gridDim.x * kWarps) {
+    const long long va = tile * 16 + gi, vb = va + 8;
+    const bool oka = va < nvox, okb = vb < nvox;
+    uint32_t ah[2][4], al[2][4];
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      const int c = ks * 16 + 2 * t;
+      const float2 z2 = make_float2(0.0f, 0.0f);
+      const float2 p0 = oka ? *reinterpret_cast<const float2*>(h + va * kC + c) : z2;
+      const float2 p1 = okb ? *reinterpret_cast<const float2*>(h + vb * kC + c) : z2;
+      const float2 p2 = oka ? *reinterpret_cast<const float2*>(h + va * kC + c + 8) : z2;
+      const float2 p3 = okb ? *reinterpret_cast<const float2*>(h + vb * kC + c + 8) : z2;
+      split_bf2(p0.x, p0.y, ah[ks][0], al[ks][0]);
+      split_bf2(p1.x, p1.y, ah[ks][1], al[ks][1]);
+      split_bf2(p2.x, p2.y, ah[ks][2], al[ks][2]);
+      split_bf2(p3.x, p3.y, ah[ks][3], al[ks][3]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        mma_bf16(d, ah[ks][0], ah[ks][1], ah[ks][2], ah[ks][3], bm[nt][ks][0], bm[nt][ks][1]);
+        mma_bf16(d, al[ks][0], al[ks][1], al[ks][2], al[ks][3], bm[nt][ks][0], bm[nt][ks][1]);
+      }
+      const int o = nt * 8 + 2 * t;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const long long v = r ? vb : va;
+        if (r ? !okb : !oka) continue;
+        const long long e = v * kC + o;
+        const float2 ac = *reinterpret_cast<const float2*>(acc + e);
+        const float s0 = d[2 * r] + mb[nt][0] + ac.x, s1 = d[2 * r + 1] + mb[nt][1] + ac.y;
+        if (z) *reinterpret_cast<float2*>(z + e) = make_float2(s0, s1);
+        *reinterpret_cast<float2*>(hn + e) = act ? make_float2(gelu(s0), gelu(s1)) : make_float2(s0, s1);
+      }
+    }
   }
 }
 
@@ -590,96 +707,272 @@ __device__ __forceinline__ double block_sum_d(double v) {
   return s;
 }
 
+// Shared memory of the tensor-core projection: B fragments of P1 (hidden =
+// h P1^T, exact bfloat16) and of the per-sample effective head P2u (q = t
+// P2u^T, float32 as bfloat16 hi + lo), with the two bias vectors.
+struct ProjFrag {
+  uint2 P1[16 * 2 * 32];   // [n-tile of hidden units][k-step of channels][lane]
+  uint2 P2h[2 * 8 * 32];   // [n-tile of outputs][k-step of hidden units][lane], hi terms
+  uint2 P2l[2 * 8 * 32];   // lo terms
+  float p1[kHid];
+  float p2[16];
+};
+
+__device__ __forceinline__ void load_proj_frag(ProjFrag& s, const __nv_bfloat16* __restrict__ wq,
+                                               const float* __restrict__ head) {
+  for (int e = threadIdx.x; e < 16 * 2 * 32; e += blockDim.x) {
+    const int lane = e & 31, ks = (e >> 5) & 1, nt = e >> 6, gi = lane >> 2, t = lane & 3;
+    const __nv_bfloat162* row =
+        reinterpret_cast<const __nv_bfloat162*>(wq + kOffP1 + (nt * 8 + gi) * kC + ks * 16 + 2 * t);
+    s.P1[e] = make_uint2(bf2_bits(row[0]), bf2_bits(row[4]));
+  }
+  for (int e = threadIdx.x; e < 2 * 8 * 32; e += blockDim.x) {
+    const int lane = e & 31, ks = (e >> 5) & 7, nt = e >> 8, gi = lane >> 2, t = lane & 3;
+    const int i = nt * 8 + gi, j = ks * 16 + 2 * t;
+    float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (i < kOut) {
+      v[0] = head[i * kHid + j];
+      v[1] = head[i * kHid + j + 1];
+      v[2] = head[i * kHid + j + 8];
+      v[3] = head[i * kHid + j + 9];
+    }
+    uint32_t h0, l0, h1, l1;
+    split_bf2(v[0], v[1], h0, l0);
+    split_bf2(v[2], v[3], h1, l1);
+    s.P2h[e] = make_uint2(h0, h1);
+    s.P2l[e] = make_uint2(l0, l1);
+  }
+  for (int i = threadIdx.x; i < kHid; i += blockDim.x) s.p1[i] = bf(wq, kOffp1 + i);
+  for (int i = threadIdx.x; i < 16; i += blockDim.x) s.p2[i] = i < kOut ? head[kOut * kHid + i] : 0.0f;
+  __syncthreads();
+}
+
+// A fragments (hi, lo) of the 16 voxels va = tile*16 + g and vb = va + 8 of h4, both k-steps
+__device__ __forceinline__ void load_h_frag(const float* __restrict__ h4, long long va, long long vb, bool oka,
+                                            bool okb, int t, uint32_t (&ah)[2][4], uint32_t (&al)[2][4]) {
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks) {
+    const int c = ks * 16 + 2 * t;
+    const float2 z2 = make_float2(0.0f, 0.0f);
+    const float2 p0 = oka ? *reinterpret_cast<const float2*>(h4 + va * kC + c) : z2;
+    const float2 p1 = okb ? *reinterpret_cast<const float2*>(h4 + vb * kC + c) : z2;
+    const float2 p2 = oka ? *reinterpret_cast<const float2*>(h4 + va * kC + c + 8) : z2;
+    const float2 p3 = okb ? *reinterpret_cast<const float2*>(h4 + vb * kC + c + 8) : z2;
+    split_bf2(p0.x, p0.y, ah[ks][0], al[ks][0]);
+    split_bf2(p1.x, p1.y, ah[ks][1], al[ks][1]);
+    split_bf2(p2.x, p2.y, ah[ks][2], al[ks][2]);
+    split_bf2(p3.x, p3.y, ah[ks][3], al[ks][3]);
+  }
+}
+
+// pre-activations of hidden units 16 kc .. 16 kc + 15 of the tile (two n-tiles of D = h P1^T + p1)
+__device__ __forceinline__ void hidden_chunk(const ProjFrag& s, int kc, int lane, const uint32_t (&ah)[2][4],
+                                             const uint32_t (&al)[2][4], float (&pre)[2][4]) {
+  const int t = lane & 3;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int nt = 2 * kc + q;
+    float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      const uint2 b = s.P1[(nt * 2 + ks) * 32 + lane];
+      mma_bf16(d, ah[ks][0], ah[ks][1], ah[ks][2], ah[ks][3], b.x, b.y);
+      mma_bf16(d, al[ks][0], al[ks][1], al[ks][2], al[ks][3], b.x, b.y);
+    }
+    const float b0 = s.p1[nt * 8 + 2 * t], b1 = s.p1[nt * 8 + 2 * t + 1];
+    pre[q][0] = d[0] + b0;
+    pre[q][1] = d[1] + b1;
+    pre[q][2] = d[2] + b0;
+    pre[q][3] = d[3] + b1;
+  }
+}
+
+// q[2][4] (D fragments of outputs 0..7 and 8..15 of the tile) = P2u gelu(P1 h + p1) + p2u
+__device__ __forceinline__ void proj_q_tc(const ProjFrag& s, int lane, const uint32_t (&ah)[2][4],
+                                          const uint32_t (&al)[2][4], float (&q)[2][4]) {
+  const int t = lane & 3;
+#pragma unroll
+  for (int n2 = 0; n2 < 2; ++n2) {
+    q[n2][0] = q[n2][2] = s.p2[n2 * 8 + 2 * t];
+    q[n2][1] = q[n2][3] = s.p2[n2 * 8 + 2 * t + 1];
+  }
+  for (int kc = 0; kc < kHid / 16; ++kc) {
+    float pre[2][4];
+    hidden_chunk(s, kc, lane, ah, al, pre);
+    // A fragment of t = gelu(pre) for k-step kc of the second product
+    uint32_t th[4], tl[4];
+    split_bf2(gelu(pre[0][0]), gelu(pre[0][1]), th[0], tl[0]);
+    split_bf2(gelu(pre[0][2]), gelu(pre[0][3]), th[1], tl[1]);
+    split_bf2(gelu(pre[1][0]), gelu(pre[1][1]), th[2], tl[2]);
+    split_bf2(gelu(pre[1][2]), gelu(pre[1][3]), th[3], tl[3]);
+#pragma unroll
+    for (int n2 = 0; n2 < 2; ++n2) {
+      const uint2 bh = s.P2h[(n2 * 8 + kc) * 32 + lane], bl = s.P2l[(n2 * 8 + kc) * 32 + lane];
+      mma_bf16(q[n2], th[0], th[1], th[2], th[3], bh.x, bh.y);
+      mma_bf16(q[n2], tl[0], tl[1], tl[2], tl[3], bh.x, bh.y);
+      mma_bf16(q[n2], th[0], th[1], th[2], th[3], bl.x, bl.y);
+    }
+  }
+}
+
+// projection on the tensor cores, tiles of 16 voxels per warp; q written
+// [9][N] when qo is given, and the per-block partial sums of (q - target)^2
 __global__ void __launch_bounds__(kThreads) k_proj_fwd(const float* __restrict__ h4,
                                                        const __nv_bfloat16* __restrict__ wq,
                                                        const float* __restrict__ head, float* __restrict__ qo,
                                                        const float* __restrict__ target, long long N,
                                                        double* __restrict__ loss_part) {
-  __shared__ __align__(16) ProjSmem s;
-  load_proj(s, wq, head);
+  __shared__ __align__(16) ProjFrag s;
+  load_proj_frag(s, wq, head);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gi = lane >> 2, t = lane & 3;
   double loss = 0.0;
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (long long)gridDim.x * blockDim.x) {
-    float hv[kC];
-    load_h(h4, v, hv);
-    float q[kOut];
+  const long long tiles = (N + 15) / 16;
+  for (long long tile = (long long)blockIdx.x * kWarps + warp; tile < tiles; tile += (long long)gridDim.x * kWarps) {
+    const long long va = tile * 16 + gi, vb = va + 8;
+    const bool oka = va < N, okb = vb < N;
+    uint32_t ah[2][4], al[2][4];
+    load_h_frag(h4, va, vb, oka, okb, t, ah, al);
+    float q[2][4];
+    proj_q_tc(s, lane, ah, al, q);
 #pragma unroll
-    for (int i = 0; i < kOut; ++i) q[i] = s.p2[i];
-    for (int j = 0; j < kHid; ++j) {
-      const float t = gelu(hidden_pre(s, j, hv));
+    for (int n2 = 0; n2 < 2; ++n2)
 #pragma unroll
-      for (int i = 0; i < kOut; ++i) q[i] = fmaf(s.P2[i * kHid + j], t, q[i]);
-    }
-    if (qo)
-#pragma unroll
-      for (int i = 0; i < kOut; ++i) qo[i * N + v] = q[i];
-    if (target)
-#pragma unroll
-      for (int i = 0; i < kOut; ++i) {
-        const double d = (double)q[i] - (double)target[i * N + v];
-        loss += d * d;
+      for (int e = 0; e < 4; ++e) {
+        const int i = n2 * 8 + 2 * t + (e & 1);
+        const long long v = (e < 2) ? va : vb;
+        if (i >= kOut || !(e < 2 ? oka : okb)) continue;
+        if (qo) qo[i * N + v] = q[n2][e];
+        if (target) {
+          const double dd = (double)q[n2][e] - (double)target[i * N + v];
+          loss += dd * dd;
+        }
       }
   }
   if (loss_part) {
-    const double t = block_sum_d(loss);
-    if (threadIdx.x == 0) loss_part[blockIdx.x] = t;
+    const double tot = block_sum_d(loss);
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = tot;
   }
 }
 
 // projection backward, per voxel: gq = (2/count)(q - target) (kept [vox][9]),
 // gh4 = P1^T (gelu'(pre) . P2^T gq), and the loss partial sums
+// B fragments of the backward products: gt = gq P2u (B[i][j] = P2u[i][j],
+// float32 as hi + lo) and gh4 = gp P1 (B[j][c] = P1[j][c], exact)
+struct ProjFragBwd {
+  uint2 P2Th[8 * 2 * 32];  // [k-chunk of hidden units][n-tile][lane]
+  uint2 P2Tl[8 * 2 * 32];
+  uint2 P1T[8 * 4 * 32];   // [k-chunk of hidden units][n-tile of channels][lane]
+};
+
+__device__ __forceinline__ void load_proj_frag_bwd(ProjFragBwd& s, const __nv_bfloat16* __restrict__ wq,
+                                                   const float* __restrict__ head) {
+  for (int e = threadIdx.x; e < 8 * 2 * 32; e += blockDim.x) {
+    const int lane = e & 31, nt = (e >> 5) & 1, kc = e >> 6, gi = lane >> 2, t = lane & 3;
+    const int j = kc * 16 + nt * 8 + gi, i0 = 2 * t;
+    const float v0 = i0 < kOut ? head[i0 * kHid + j] : 0.0f;
+    const float v1 = i0 + 1 < kOut ? head[(i0 + 1) * kHid + j] : 0.0f;
+    const float v2 = i0 + 8 < kOut ? head[(i0 + 8) * kHid + j] : 0.0f;
+    const float v3 = i0 + 9 < kOut ? head[(i0 + 9) * kHid + j] : 0.0f;
+    uint32_t h0, l0, h1, l1;
+    split_bf2(v0, v1, h0, l0);
+    split_bf2(v2, v3, h1, l1);
+    s.P2Th[e] = make_uint2(h0, h1);
+    s.P2Tl[e] = make_uint2(l0, l1);
+  }
+  for (int e = threadIdx.x; e < 8 * 4 * 32; e += blockDim.x) {
+    const int lane = e & 31, nt = (e >> 5) & 3, kc = e >> 7, gi = lane >> 2, t = lane & 3;
+    const int c = nt * 8 + gi, j = kc * 16 + 2 * t;
+    const __nv_bfloat16* P1 = wq + kOffP1;
+    const __nv_bfloat162 b0 = __halves2bfloat162(P1[j * kC + c], P1[(j + 1) * kC + c]);
+    const __nv_bfloat162 b1 = __halves2bfloat162(P1[(j + 8) * kC + c], P1[(j + 9) * kC + c]);
+    s.P1T[e] = make_uint2(bf2_bits(b0), bf2_bits(b1));
+  }
+  __syncthreads();
+}
+
+// projection backward on the tensor cores, tiles of 16 voxels per warp:
+// gq = scale (q - target) (kept [vox][9]), gh4 = P1^T (gelu'(pre) . P2u^T gq),
+// and the per-block partial sums of (q - target)^2
 __global__ void __launch_bounds__(kThreads, 2) k_proj_bwd_a(const float* __restrict__ h4,
                                                          const __nv_bfloat16* __restrict__ wq,
                                                          const float* __restrict__ head,
                                                          const float* __restrict__ target, long long N, float scale,
                                                          float* __restrict__ gq_out, float* __restrict__ gh4,
                                                          double* __restrict__ loss_part) {
-  __shared__ __align__(16) ProjSmem s;
-  load_proj(s, wq, head);
+  __shared__ __align__(16) ProjFrag s;
+  __shared__ __align__(16) ProjFragBwd sb;
+  load_proj_frag(s, wq, head);
+  load_proj_frag_bwd(sb, wq, head);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gi = lane >> 2, t = lane & 3;
   double loss = 0.0;
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (long long)gridDim.x * blockDim.x) {
-    const long long vox = v;
-    float hv[kC];
-    load_h(h4, vox, hv);
-    float q[kOut];
+  const long long tiles = (N + 15) / 16;
+  for (long long tile = (long long)blockIdx.x * kWarps + warp; tile < tiles; tile += (long long)gridDim.x * kWarps) {
+    const long long va = tile * 16 + gi, vb = va + 8;
+    const bool oka = va < N, okb = vb < N;
+    uint32_t ah[2][4], al[2][4];
+    load_h_frag(h4, va, vb, oka, okb, t, ah, al);
+    float q[2][4];
+    proj_q_tc(s, lane, ah, al, q);
+    // q -> gq (zero outside the 9 outputs and the grid)
 #pragma unroll
-    for (int i = 0; i < kOut; ++i) q[i] = s.p2[i];
-    for (int j = 0; j < kHid; ++j) {
-      const float t = gelu(hidden_pre(s, j, hv));
+    for (int n2 = 0; n2 < 2; ++n2)
 #pragma unroll
-      for (int i = 0; i < kOut; ++i) q[i] = fmaf(s.P2[i * kHid + j], t, q[i]);
-    }
+      for (int e = 0; e < 4; ++e) {
+        const int i = n2 * 8 + 2 * t + (e & 1);
+        const long long v = (e < 2) ? va : vb;
+        float gv = 0.0f;
+        if (i < kOut && (e < 2 ? oka : okb)) {
+          const float d = q[n2][e] - target[i * N + v];
+          loss += (double)d * (double)d;
+          gv = scale * d;
+          gq_out[v * kOut + i] = gv;
+        }
+        q[n2][e] = gv;
+      }
+    uint32_t gh_[4], gl_[4];
+    split_bf2(q[0][0], q[0][1], gh_[0], gl_[0]);
+    split_bf2(q[0][2], q[0][3], gh_[1], gl_[1]);
+    split_bf2(q[1][0], q[1][1], gh_[2], gl_[2]);
+    split_bf2(q[1][2], q[1][3], gh_[3], gl_[3]);
+    float g4[4][4];
 #pragma unroll
-    for (int i = 0; i < kOut; ++i) {
-      const float d = q[i] - target[i * N + v];
-      loss += (double)d * (double)d;
-      q[i] = scale * d;  // now gq
-      gq_out[vox * kOut + i] = q[i];
-    }
-  float g[kC];
+    for (int nt = 0; nt < 4; ++nt) g4[nt][0] = g4[nt][1] = g4[nt][2] = g4[nt][3] = 0.0f;
+    for (int kc = 0; kc < kHid / 16; ++kc) {
+      float pre[2][4];
+      hidden_chunk(s, kc, lane, ah, al, pre);
+      // gt = gq P2u over this chunk's 16 hidden units, then gp = gt gelu'(pre)
+      float gp[2][4];
 #pragma unroll
-    for (int c = 0; c < kC; ++c) g[c] = 0.0f;
-    for (int j = 0; j < kHid; ++j) {
-      const float pre = hidden_pre(s, j, hv);
-      float gt = 0.0f;
+      for (int nt = 0; nt < 2; ++nt) {
+        float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        const uint2 bh = sb.P2Th[(kc * 2 + nt) * 32 + lane], bl = sb.P2Tl[(kc * 2 + nt) * 32 + lane];
+        mma_bf16(d, gh_[0], gh_[1], gh_[2], gh_[3], bh.x, bh.y);
+        mma_bf16(d, gl_[0], gl_[1], gl_[2], gl_[3], bh.x, bh.y);
+        mma_bf16(d, gh_[0], gh_[1], gh_[2], gh_[3], bl.x, bl.y);
 #pragma unroll
-      for (int i = 0; i < kOut; ++i) gt = fmaf(s.P2[i * kHid + j], q[i], gt);
-      const float gp = gt * gelu_d(pre);
-      const float4* r = reinterpret_cast<const float4*>(&s.P1[j * kC]);
+        for (int e = 0; e < 4; ++e) gp[nt][e] = d[e] * gelu_d(pre[nt][e]);
+      }
+      uint32_t ph[4], pl[4];
+      split_bf2(gp[0][0], gp[0][1], ph[0], pl[0]);
+      split_bf2(gp[0][2], gp[0][3], ph[1], pl[1]);
+      split_bf2(gp[1][0], gp[1][1], ph[2], pl[2]);
+      split_bf2(gp[1][2], gp[1][3], ph[3], pl[3]);
 #pragma unroll
-      for (int qq = 0; qq < kC / 4; ++qq) {
-        const float4 w = r[qq];
-        g[4 * qq] = fmaf(w.x, gp, g[4 * qq]);
-        g[4 * qq + 1] = fmaf(w.y, gp, g[4 * qq + 1]);
-        g[4 * qq + 2] = fmaf(w.z, gp, g[4 * qq + 2]);
-        g[4 * qq + 3] = fmaf(w.w, gp, g[4 * qq + 3]);
+      for (int nt = 0; nt < 4; ++nt) {
+        const uint2 b = sb.P1T[(kc * 4 + nt) * 32 + lane];
+        mma_bf16(g4[nt], ph[0], ph[1], ph[2], ph[3], b.x, b.y);
+        mma_bf16(g4[nt], pl[0], pl[1], pl[2], pl[3], b.x, b.y);
       }
     }
-    float4* o = reinterpret_cast<float4*>(gh4 + vox * kC);
 #pragma unroll
-    for (int qq = 0; qq < kC / 4; ++qq) o[qq] = make_float4(g[4 * qq], g[4 * qq + 1], g[4 * qq + 2], g[4 * qq + 3]);
+    for (int nt = 0; nt < 4; ++nt) {
+      const int c = nt * 8 + 2 * t;
+      if (oka) *reinterpret_cast<float2*>(gh4 + va * kC + c) = make_float2(g4[nt][0], g4[nt][1]);
+      if (okb) *reinterpret_cast<float2*>(gh4 + vb * kC + c) = make_float2(g4[nt][2], g4[nt][3]);
+    }
   }
-  const double t = block_sum_d(loss);
-  if (threadIdx.x == 0) loss_part[blockIdx.x] = t;
+  const double tot = block_sum_d(loss);
+  if (threadIdx.x == 0) loss_part[blockIdx.x] = tot;
 }
 
 // projection weight gradient of one sample: thread (hidden unit j, half of
@@ -848,8 +1141,8 @@ struct fh_fno {
   long long N = 0;
   cudaStream_t stream = nullptr;
   __nv_bfloat16* wq = nullptr;
-  __nv_bfloat162* wf = nullptr;
-  __nv_bfloat162* wb = nullptr;
+  uint4* wfa = nullptr;  // mma fragments of the forward mixing matrices
+  uint4* wba = nullptr;  // and of their transposes (backward)
   float* tw[3] = {nullptr, nullptr, nullptr};
   float* itw[3] = {nullptr, nullptr, nullptr};
   float* h[5] = {};
@@ -936,8 +1229,8 @@ unsigned grid_for(long long work, int per_block, int cap) {
 int spec_fwd(fh_fno* net, int B, int l, int ax, bool accum, const float* h, float* out) {
   const int n = axis_len(net, ax);
   const long long lines = (long long)B * (net->N / n);
-  const unsigned grid = grid_for(lines, kWarps, 4 * net->sms);  // 4 resident CTAs per SM
-  const __nv_bfloat162* W = net->wf + (long long)(l * 3 + ax) * kModes * kC * kC;
+  const unsigned grid = grid_for(lines, kWarps, 3 * net->sms);  // 3 resident CTAs per SM
+  const uint4* W = net->wfa + (long long)(l * 3 + ax) * kModes * kFragPerMode;
   const size_t sm = spec_smem(n);
   if (accum)
     k_spec_fwd<true><<<grid, kThreads, sm, net->stream>>>(h, out, W, net->tw[ax], net->itw[ax], geom(net), ax, n, lines);
@@ -997,8 +1290,8 @@ int fh_fno_create(fh_fno** out, int nx, int ny, int nz, int max_batch, int train
     if (e == cudaSuccess) e = nalloc(net, p, count);
   };
   A(&net->wq, (size_t)kNParam);
-  A(&net->wf, (size_t)kSpecW);
-  A(&net->wb, (size_t)kSpecW);
+  A(&net->wfa, (size_t)kFrag);
+  A(&net->wba, (size_t)kFrag);
   for (int ax = 0; ax < 3; ++ax) {
     A(&net->tw[ax], (size_t)axis_len(net, ax) * kJ);
     A(&net->itw[ax], (size_t)axis_len(net, ax) * kJ);
@@ -1099,8 +1392,8 @@ int fh_fno_set_params(fh_fno* net, const float* theta_dev) {
   fh_internal_set_error("");
   if (!net || !theta_dev) return ffail(FH_ERR_ARG, "NULL argument");
   DevGuard dg(net->dev);
-  k_prepare<<<grid_for(kNParam, kThreads, 4 * net->sms), kThreads, 0, net->stream>>>(theta_dev, net->wq, net->wf,
-                                                                                     net->wb);
+  k_prepare<<<grid_for(kNParam, kThreads, 4 * net->sms), kThreads, 0, net->stream>>>(theta_dev, net->wq, net->wfa,
+                                                                                     net->wba);
   FN_CUDA(cudaGetLastError());
   FN_CUDA(cudaStreamSynchronize(net->stream));
   net->params_set = true;
@@ -1139,7 +1432,7 @@ int fh_fno_forward(fh_fno* net, int B, const unsigned char* const* phase_ptrs, c
     if ((rc = spec_fwd(net, B, l, 1, true, H(l), net->acc))) return rc;
     if ((rc = spec_fwd(net, B, l, 0, true, H(l), net->acc))) return rc;
     float* z = (net->train && l < kLayers - 1) ? net->z[l] : nullptr;
-    k_point_fwd<<<grid_for((nvox + 31) / 32, kWarps, 4 * net->sms), kThreads, 0, s>>>(
+    k_point_fwd<<<grid_for((nvox + 15) / 16, kWarps, 4 * net->sms), kThreads, 0, s>>>(
         H(l), net->acc, net->wq, l, z, H(l + 1), nvox, l < kLayers - 1 ? 1 : 0);
     FN_CUDA(cudaGetLastError());
   }
@@ -1210,7 +1503,7 @@ int fh_fno_loss_grad(fh_fno* net, const float* const* target_ptrs, double* loss_
       for (int ax = 0; ax < 3; ++ax) {
         const int n = axis_len(net, ax);
         const long long lines = (long long)B * (net->N / n);
-        const __nv_bfloat162* W = net->wb + (long long)(l * 3 + ax) * kModes * kC * kC;
+        const uint4* W = net->wba + (long long)(l * 3 + ax) * kModes * kFragPerMode;
         k_spec_bwd<<<grid_for(lines, kWarps, 3 * net->sms), kThreads, spec_smem(n), s>>>(
             net->h[l], net->gz, net->gh, net->xs, net->gys, W, net->tw[ax], net->itw[ax], geom(net), ax, n, lines);
         FN_CUDA(cudaGetLastError());
