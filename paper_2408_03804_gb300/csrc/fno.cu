@@ -216,13 +216,150 @@ __global__ void k_lift(const uint8_t* const* __restrict__ phase, const float* __
 // ---------------------------------------------------------------------------
 // spectral convolution along one axis, forward: out (=/+=) S_ax(h)
 // ---------------------------------------------------------------------------
-// shared memory of the spectral kernels: twiddles (2 x n x 24) and two
-// coefficient blocks (24 x 32, rows padded) per warp, one for the DFT of its
-// line and one for the mixed coefficients. The mixing matrices are read as
-// mma fragments through L1.
+// ---------------------------------------------------------------------------
+// spectral convolution along one axis on the tensor cores. For a line h[x][c]
+// (x < n positions, 32 channels) the truncated DFT X[j][c] = sum_x T[j][x]
+// h[x][c] (j < 24: cosine and minus sine rows of the 12 modes) is an MMA with
+// M = j (two 16-row tiles), N = c (four 8-column tiles), K = x; the inverse
+// S[x][o] = sum_j I[x][j] Y[j][o] an MMA with M = x, N = o, K = j. The twiddle
+// matrices T and I (and the transposes the backward pass needs) are split
+// into bf16 hi + lo fragments once per CTA; the line values are split as
+// they are loaded, and each product takes three MMAs (hi hi, hi lo, lo hi).
+// ---------------------------------------------------------------------------
 constexpr int kXStride = kJ * kC + 8;  // floats per line block (padding spreads the banks of the 8 lines)
-__host__ __device__ constexpr size_t spec_smem(int n) {
-  return 2 * (size_t)n * kJ * sizeof(float) + 2 * (size_t)kWarps * kXStride * sizeof(float);
+
+__host__ __device__ constexpr int ksteps(int n) { return (n + 15) / 16; }
+// fragments (hi and lo uint4 per lane) of a rows x cols matrix split into 16 x 16 tiles
+__host__ __device__ constexpr int frag_count(int rows, int cols) { return ((rows + 15) / 16) * ksteps(cols) * 32; }
+__host__ __device__ constexpr size_t spec_smem(int n, bool bwd) {
+  // forward: T (24 x n) and I (n x 24); backward: T, I^T (24 x n) and T^T (n x 24); two line blocks per warp
+  return (size_t)(bwd ? 2 * frag_count(kJ, n) + frag_count(n, kJ) : frag_count(kJ, n) + frag_count(n, kJ)) * 2 *
+             sizeof(uint4) +
+         2 * (size_t)kWarps * kXStride * sizeof(float);
+}
+
+// Build the hi/lo A fragments of the rows x cols matrix M(r, k) (zero outside)
+// into Ah/Al: entry (mt * ksteps(cols) + ks) * 32 + lane.
+template <class Fn>
+__device__ __forceinline__ void build_frags(uint4* __restrict__ Ah, uint4* __restrict__ Al, int rows, int cols,
+                                            Fn M) {
+  const int nks = ksteps(cols);
+  const int total = frag_count(rows, cols);
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int lane = e & 31, ks = (e >> 5) % nks, mt = (e >> 5) / nks, g = lane >> 2, t = lane & 3;
+    const int r0 = mt * 16 + g, r1 = r0 + 8, k0 = ks * 16 + 2 * t, k1 = k0 + 8;
+    auto at = [&](int r, int k) { return (r < rows && k < cols) ? M(r, k) : 0.0f; };
+    uint4 h, l;
+    split_bf2(at(r0, k0), at(r0, k0 + 1), h.x, l.x);
+    split_bf2(at(r1, k0), at(r1, k0 + 1), h.y, l.y);
+    split_bf2(at(r0, k1), at(r0, k1 + 1), h.z, l.z);
+    split_bf2(at(r1, k1), at(r1, k1 + 1), h.w, l.w);
+    Ah[e] = h;
+    Al[e] = l;
+  }
+}
+
+// d[mt][nt] += T[rows of tile mt][x] h[x][channels of tile nt] for one line of
+// global memory (element x, channel c at src + x * step + c); two row tiles (24
+// coefficient rows), four channel tiles, K = n positions
+__device__ __forceinline__ void line_dft_tc(const float* __restrict__ src, long long step, int n,
+                                            const uint4* __restrict__ Ah, const uint4* __restrict__ Al, int lane,
+                                            float (&d)[2][4][4]) {
+  const int g = lane >> 2, t = lane & 3, nks = ksteps(n);
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) d[mt][nt][0] = d[mt][nt][1] = d[mt][nt][2] = d[mt][nt][3] = 0.0f;
+  for (int ks = 0; ks < nks; ++ks) {
+    const int x0 = ks * 16 + 2 * t;
+    const uint4 a0h = Ah[(0 * nks + ks) * 32 + lane], a0l = Al[(0 * nks + ks) * 32 + lane];
+    const uint4 a1h = Ah[(1 * nks + ks) * 32 + lane], a1l = Al[(1 * nks + ks) * 32 + lane];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const float* col = src + nt * 8 + g;
+      const float v0 = x0 < n ? col[x0 * step] : 0.0f, v1 = x0 + 1 < n ? col[(x0 + 1) * step] : 0.0f;
+      const float v2 = x0 + 8 < n ? col[(x0 + 8) * step] : 0.0f, v3 = x0 + 9 < n ? col[(x0 + 9) * step] : 0.0f;
+      uint32_t b0h, b0l, b1h, b1l;
+      split_bf2(v0, v1, b0h, b0l);
+      split_bf2(v2, v3, b1h, b1l);
+      mma_bf16(d[0][nt], a0h, b0h, b1h);
+      mma_bf16(d[0][nt], a0h, b0l, b1l);
+      mma_bf16(d[0][nt], a0l, b0h, b1h);
+      mma_bf16(d[1][nt], a1h, b0h, b1h);
+      mma_bf16(d[1][nt], a1h, b0l, b1l);
+      mma_bf16(d[1][nt], a1l, b0h, b1h);
+    }
+  }
+}
+
+// the D fragments of line_dft_tc as a [j][c] block (rows j < 24) in shared or global memory
+__device__ __forceinline__ void store_coef(float* __restrict__ dst, int lane, const float (&d)[2][4][4]) {
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int j0 = mt * 16 + g, c = nt * 8 + 2 * t;
+      if (j0 < kJ) *reinterpret_cast<float2*>(dst + j0 * kC + c) = make_float2(d[mt][nt][0], d[mt][nt][1]);
+      if (j0 + 8 < kJ) *reinterpret_cast<float2*>(dst + (j0 + 8) * kC + c) = make_float2(d[mt][nt][2], d[mt][nt][3]);
+    }
+}
+
+// dst[x][o] (+)= sum_j I[x][j] Y[j][o] for one line (x < n): Y a [j][o] block in
+// shared memory, I as A fragments (row tiles of 16 positions, two k-steps of j)
+template <bool ACCUM>
+__device__ __forceinline__ void line_idft_tc(const float* __restrict__ Y, float* __restrict__ dst, long long step,
+                                             int n, const uint4* __restrict__ Ah, const uint4* __restrict__ Al,
+                                             int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  uint32_t bh[2][4][2], bl[2][4][2];
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int j0 = ks * 16 + 2 * t, o = nt * 8 + g;
+      const float v0 = j0 < kJ ? Y[j0 * kC + o] : 0.0f, v1 = j0 + 1 < kJ ? Y[(j0 + 1) * kC + o] : 0.0f;
+      const float v2 = j0 + 8 < kJ ? Y[(j0 + 8) * kC + o] : 0.0f, v3 = j0 + 9 < kJ ? Y[(j0 + 9) * kC + o] : 0.0f;
+      split_bf2(v0, v1, bh[ks][nt][0], bl[ks][nt][0]);
+      split_bf2(v2, v3, bh[ks][nt][1], bl[ks][nt][1]);
+    }
+  const int nmt = ksteps(n);
+  for (int mt = 0; mt < nmt; ++mt) {
+    const uint4 a0h = Ah[(mt * 2 + 0) * 32 + lane], a0l = Al[(mt * 2 + 0) * 32 + lane];
+    const uint4 a1h = Ah[(mt * 2 + 1) * 32 + lane], a1l = Al[(mt * 2 + 1) * 32 + lane];
+    const int x0 = mt * 16 + g, x1 = x0 + 8;
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      mma_bf16(d, a0h, bh[0][nt][0], bh[0][nt][1]);
+      mma_bf16(d, a0h, bl[0][nt][0], bl[0][nt][1]);
+      mma_bf16(d, a0l, bh[0][nt][0], bh[0][nt][1]);
+      mma_bf16(d, a1h, bh[1][nt][0], bh[1][nt][1]);
+      mma_bf16(d, a1h, bl[1][nt][0], bl[1][nt][1]);
+      mma_bf16(d, a1l, bh[1][nt][0], bh[1][nt][1]);
+      const int o = nt * 8 + 2 * t;
+      if (x0 < n) {
+        float2* p = reinterpret_cast<float2*>(dst + x0 * step + o);
+        float2 v = make_float2(d[0], d[1]);
+        if (ACCUM) {
+          const float2 u = *p;
+          v.x += u.x;
+          v.y += u.y;
+        }
+        *p = v;
+      }
+      if (x1 < n) {
+        float2* p = reinterpret_cast<float2*>(dst + x1 * step + o);
+        float2 v = make_float2(d[2], d[3]);
+        if (ACCUM) {
+          const float2 u = *p;
+          v.x += u.x;
+          v.y += u.y;
+        }
+        *p = v;
+      }
+    }
+  }
 }
 
 // Complex mixing of the CTA's 8 lines on the tensor cores: for every mode k,
@@ -260,77 +397,44 @@ __device__ __forceinline__ void mix_modes_tc(const float* __restrict__ sX, float
   }
 }
 
+// forward: out (=/+=) S_ax(h); each CTA takes 8 lines at a time, one per warp
 template <bool ACCUM>
-__global__ void __launch_bounds__(kThreads, 3) k_spec_fwd(const float* __restrict__ h, float* __restrict__ out,
+__global__ void __launch_bounds__(kThreads, 2) k_spec_fwd(const float* __restrict__ h, float* __restrict__ out,
                                                        const uint4* __restrict__ WA,
                                                        const float* __restrict__ tw, const float* __restrict__ itw,
                                                        Geom g, int ax, int n, long long n_lines) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float* stw = reinterpret_cast<float*>(smem);
-  float* sitw = stw + n * kJ;
-  float* sX = sitw + n * kJ;
+  const int fT = frag_count(kJ, n), fI = frag_count(n, kJ);
+  uint4* Th = reinterpret_cast<uint4*>(smem);
+  uint4* Tl = Th + fT;
+  uint4* Ih = Tl + fT;
+  uint4* Il = Ih + fI;
+  float* sX = reinterpret_cast<float*>(Il + fI);
   float* sY = sX + kWarps * kXStride;
-  for (int i = threadIdx.x; i < n * kJ; i += blockDim.x) {
-    stw[i] = tw[i];
-    sitw[i] = itw[i];
-  }
+  build_frags(Th, Tl, kJ, n, [&](int j, int x) { return tw[x * kJ + j]; });
+  build_frags(Ih, Il, n, kJ, [&](int x, int j) { return itw[x * kJ + j]; });
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* X = sX + warp * kXStride;
   for (long long l0 = (long long)blockIdx.x * kWarps; l0 < n_lines; l0 += (long long)gridDim.x * kWarps) {
     const long long li = l0 + warp;
     const bool valid = li < n_lines;
     long long base = 0, stride = 0;
     if (valid) line_of(g, ax, li, base, stride);
     const long long step = stride * kC;
-    // truncated DFT of this lane's channel: X[2k] = sum h cos, X[2k+1] = -sum h sin
-    float a[kJ];
-#pragma unroll
-    for (int j = 0; j < kJ; ++j) a[j] = 0.0f;
+    float d[2][4][4];
     if (valid) {
-      const float* src = h + base * kC + lane;
-#pragma unroll 4
-      for (int x = 0; x < n; ++x) {
-        const float v = src[x * step];
-        const float4* t4 = reinterpret_cast<const float4*>(stw + x * kJ);
+      line_dft_tc(h + base * kC, step, n, Th, Tl, lane, d);
+    } else {
 #pragma unroll
-        for (int q = 0; q < kJ / 4; ++q) {
-          const float4 t = t4[q];
-          a[4 * q] = fmaf(v, t.x, a[4 * q]);
-          a[4 * q + 1] = fmaf(v, t.y, a[4 * q + 1]);
-          a[4 * q + 2] = fmaf(v, t.z, a[4 * q + 2]);
-          a[4 * q + 3] = fmaf(v, t.w, a[4 * q + 3]);
-        }
-      }
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) d[mt][nt][0] = d[mt][nt][1] = d[mt][nt][2] = d[mt][nt][3] = 0.0f;
     }
-#pragma unroll
-    for (int j = 0; j < kJ; ++j) X[j * kC + lane] = a[j];
+    store_coef(sX + warp * kXStride, lane, d);
     __syncthreads();
     mix_modes_tc(sX, sY, WA, warp, lane);
     __syncthreads();
-    if (!valid) continue;
-    // truncated real inverse DFT: S[x] = sum_j y[j] itw[x][j]
-    float y[kJ];
-#pragma unroll
-    for (int j = 0; j < kJ; ++j) y[j] = sY[warp * kXStride + j * kC + lane];
-    float* dst = out + base * kC + lane;
-#pragma unroll 2
-    for (int x = 0; x < n; ++x) {
-      const float4* t4 = reinterpret_cast<const float4*>(sitw + x * kJ);
-      float s = 0.0f;
-#pragma unroll
-      for (int q = 0; q < kJ / 4; ++q) {
-        const float4 t = t4[q];
-        s = fmaf(y[4 * q], t.x, s);
-        s = fmaf(y[4 * q + 1], t.y, s);
-        s = fmaf(y[4 * q + 2], t.z, s);
-        s = fmaf(y[4 * q + 3], t.w, s);
-      }
-      if (ACCUM)
-        dst[x * step] += s;
-      else
-        dst[x * step] = s;
-    }
+    if (valid) line_idft_tc<ACCUM>(sY + warp * kXStride, out + base * kC, step, n, Ih, Il, lane);
   }
 }
 
@@ -339,86 +443,50 @@ __global__ void __launch_bounds__(kThreads, 3) k_spec_fwd(const float* __restric
 // forward coefficients X of h and the coefficient gradient gY of every line
 // for the weight gradient
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads, 3) k_spec_bwd(const float* __restrict__ h, const float* __restrict__ gz,
+__global__ void __launch_bounds__(kThreads, 2) k_spec_bwd(const float* __restrict__ h, const float* __restrict__ gz,
                                                        float* __restrict__ gh, float* __restrict__ xs,
                                                        float* __restrict__ gys, const uint4* __restrict__ WB,
                                                        const float* __restrict__ tw, const float* __restrict__ itw,
                                                        Geom g, int ax, int n, long long n_lines) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float* stw = reinterpret_cast<float*>(smem);
-  float* sitw = stw + n * kJ;
-  float* sG = sitw + n * kJ;           // coefficient gradients gY of the CTA's lines
-  float* sGX = sG + kWarps * kXStride;  // gX = Wt^T gY
-  for (int i = threadIdx.x; i < n * kJ; i += blockDim.x) {
-    stw[i] = tw[i];
-    sitw[i] = itw[i];
-  }
+  const int fT = frag_count(kJ, n), fI = frag_count(n, kJ);
+  uint4* Th = reinterpret_cast<uint4*>(smem);    // X = T h
+  uint4* Tl = Th + fT;
+  uint4* Uh = Tl + fT;                           // gY = I^T gz
+  uint4* Ul = Uh + fT;
+  uint4* Vh = Ul + fT;                           // gh += T^T gX
+  uint4* Vl = Vh + fI;
+  float* sG = reinterpret_cast<float*>(Vl + fI);  // coefficient gradients gY of the CTA's lines
+  float* sGX = sG + kWarps * kXStride;           // gX = Wt^T gY
+  build_frags(Th, Tl, kJ, n, [&](int j, int x) { return tw[x * kJ + j]; });
+  build_frags(Uh, Ul, kJ, n, [&](int j, int x) { return itw[x * kJ + j]; });
+  build_frags(Vh, Vl, n, kJ, [&](int x, int j) { return tw[x * kJ + j]; });
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* G = sG + warp * kXStride;
   for (long long l0 = (long long)blockIdx.x * kWarps; l0 < n_lines; l0 += (long long)gridDim.x * kWarps) {
     const long long li = l0 + warp;
     const bool valid = li < n_lines;
     long long base = 0, stride = 0;
     if (valid) line_of(g, ax, li, base, stride);
     const long long step = stride * kC;
-    float a[kJ], b[kJ];
-#pragma unroll
-    for (int j = 0; j < kJ; ++j) a[j] = b[j] = 0.0f;
+    float d[2][4][4];
     if (valid) {
-      const float* hs = h + base * kC + lane;
-      const float* gs = gz + base * kC + lane;
-#pragma unroll 2
-      for (int x = 0; x < n; ++x) {
-        const float v = hs[x * step], w = gs[x * step];
-        const float4* t4 = reinterpret_cast<const float4*>(stw + x * kJ);
-        const float4* u4 = reinterpret_cast<const float4*>(sitw + x * kJ);
+      line_dft_tc(h + base * kC, step, n, Th, Tl, lane, d);
+      store_coef(xs + li * (kJ * kC), lane, d);
+      line_dft_tc(gz + base * kC, step, n, Uh, Ul, lane, d);
+      store_coef(gys + li * (kJ * kC), lane, d);
+    } else {
 #pragma unroll
-        for (int q = 0; q < kJ / 4; ++q) {
-          const float4 t = t4[q], u = u4[q];
-          a[4 * q] = fmaf(v, t.x, a[4 * q]);
-          a[4 * q + 1] = fmaf(v, t.y, a[4 * q + 1]);
-          a[4 * q + 2] = fmaf(v, t.z, a[4 * q + 2]);
-          a[4 * q + 3] = fmaf(v, t.w, a[4 * q + 3]);
-          b[4 * q] = fmaf(w, u.x, b[4 * q]);
-          b[4 * q + 1] = fmaf(w, u.y, b[4 * q + 1]);
-          b[4 * q + 2] = fmaf(w, u.z, b[4 * q + 2]);
-          b[4 * q + 3] = fmaf(w, u.w, b[4 * q + 3]);
-        }
-      }
-      float* xo = xs + li * (kJ * kC) + lane;
-      float* go = gys + li * (kJ * kC) + lane;
+      for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-      for (int j = 0; j < kJ; ++j) {
-        xo[j * kC] = a[j];
-        go[j * kC] = b[j];
-      }
+        for (int nt = 0; nt < 4; ++nt) d[mt][nt][0] = d[mt][nt][1] = d[mt][nt][2] = d[mt][nt][3] = 0.0f;
     }
-#pragma unroll
-    for (int j = 0; j < kJ; ++j) G[j * kC + lane] = b[j];
+    store_coef(sG + warp * kXStride, lane, d);
     __syncthreads();
     // gX = Wt^T gY on the tensor cores (same pattern as the forward mixing)
     mix_modes_tc(sG, sGX, WB, warp, lane);
     __syncthreads();
-    if (!valid) continue;
-    float gx[kJ];
-#pragma unroll
-    for (int j = 0; j < kJ; ++j) gx[j] = sGX[warp * kXStride + j * kC + lane];
-    float* dst = gh + base * kC + lane;
-#pragma unroll 2
-    for (int x = 0; x < n; ++x) {
-      const float4* t4 = reinterpret_cast<const float4*>(stw + x * kJ);
-      float s = 0.0f;
-#pragma unroll
-      for (int q = 0; q < kJ / 4; ++q) {
-        const float4 t = t4[q];
-        s = fmaf(gx[4 * q], t.x, s);
-        s = fmaf(gx[4 * q + 1], t.y, s);
-        s = fmaf(gx[4 * q + 2], t.z, s);
-        s = fmaf(gx[4 * q + 3], t.w, s);
-      }
-      dst[x * step] += s;
-    }
+    if (valid) line_idft_tc<true>(sGX + warp * kXStride, gh + base * kC, step, n, Vh, Vl, lane);
   }
 }
 
@@ -1229,9 +1297,9 @@ unsigned grid_for(long long work, int per_block, int cap) {
 int spec_fwd(fh_fno* net, int B, int l, int ax, bool accum, const float* h, float* out) {
   const int n = axis_len(net, ax);
   const long long lines = (long long)B * (net->N / n);
-  const unsigned grid = grid_for(lines, kWarps, 3 * net->sms);  // 3 resident CTAs per SM
+  const unsigned grid = grid_for(lines, kWarps, 2 * net->sms);  // 2 resident CTAs per SM
   const uint4* W = net->wfa + (long long)(l * 3 + ax) * kModes * kFragPerMode;
-  const size_t sm = spec_smem(n);
+  const size_t sm = spec_smem(n, false);
   if (accum)
     k_spec_fwd<true><<<grid, kThreads, sm, net->stream>>>(h, out, W, net->tw[ax], net->itw[ax], geom(net), ax, n, lines);
   else
@@ -1365,10 +1433,10 @@ int fh_fno_create(fh_fno** out, int nx, int ny, int nz, int max_batch, int train
     if (e != cudaSuccess) break;
   }
   const int nmax = nx > ny ? (nx > nz ? nx : nz) : (ny > nz ? ny : nz);
-  const size_t sm = spec_smem(nmax);
+  const size_t sm = spec_smem(nmax, false), smb = spec_smem(nmax, true);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_point_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPointBwdSmem);
   if (e != cudaSuccess) {
@@ -1504,7 +1572,7 @@ int fh_fno_loss_grad(fh_fno* net, const float* const* target_ptrs, double* loss_
         const int n = axis_len(net, ax);
         const long long lines = (long long)B * (net->N / n);
         const uint4* W = net->wba + (long long)(l * 3 + ax) * kModes * kFragPerMode;
-        k_spec_bwd<<<grid_for(lines, kWarps, 3 * net->sms), kThreads, spec_smem(n), s>>>(
+        k_spec_bwd<<<grid_for(lines, kWarps, 2 * net->sms), kThreads, spec_smem(n, true), s>>>(
             net->h[l], net->gz, net->gh, net->xs, net->gys, W, net->tw[ax], net->itw[ax], geom(net), ax, n, lines);
         FN_CUDA(cudaGetLastError());
         const unsigned chunks = (unsigned)((lines + kLinesPerChunk - 1) / kLinesPerChunk);
