@@ -548,8 +548,8 @@ def run_warm_start(args, world, rank, local):
     """Learned warm start against the zero initial guess on held-out cells.
 
     Each step is one held-out neo-Hookean cell (the training distribution of
-    the network: RSA spheres of radius U[4, 10]/128 of the box at a volume
-    fraction U[0.1, 0.3], matrix (lambda, mu) = (1.5, 1), inclusions 10x,
+    the network: random spheres of radius U[4, 10]/128 of the box at a volume
+    fraction U[0.1, 0.4], matrix (lambda, mu) = (1.5, 1), inclusions 10x,
     |Fbar - I| <= 0.05, one load increment, Newton tolerance 1e-8) solved from
     Fbar and from the network's prediction; both times are CUDA-event times on
     the solver's stream, the warm-started one including the network's forward
@@ -630,7 +630,7 @@ def run_warm_start(args, world, rank, local):
         "metric": f"time-to-solve @1e-8 of held-out {n}^3 neo-Hookean cells, learned warm start vs zero guess",
         "value": t1, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": False, "scaling": "weak", "dtype": "f64 solve, bf16/f32 network", "data": "synthetic",
-        "config": {"workload": f"{n}^3 RSA spheres r U[4,10]/128 L, f U[0.1,0.3], inclusions 10x, "
+        "config": {"workload": f"{n}^3 random spheres r U[4,10]/128 L, f U[0.1,0.4], inclusions 10x, "
                                "|Fbar - I| <= 0.05, 1 increment, Newton tol 1e-8; network trained at 64^3",
                    "weights": os.path.relpath(WARM_WEIGHTS, ROOT), "input_generation_s": t_in},
         "zero_guess_s": t0, "time_saved_frac": 1.0 - t1 / t0,

@@ -237,9 +237,11 @@ FH_API int fh_autotune(fh_ctx* ctx, int reps, double* best_ms, int chosen[3]);
 
 /* ---- batched solves of many cells (Section 4.4.1's many-sample setting) ----
  * A batch binds cells of possibly different grids; each keeps its own Newton
- * and CG state (its own convergence), while every pass of the solve is one
- * launch per group of equal grids and the CG iterations of the whole batch
- * run as a captured CUDA graph. */
+ * and CG state (its own convergence, decided on the device), while every pass
+ * of the solve is one launch per group of equal grids. One captured CUDA
+ * graph (the Newton step bookkeeping of every cell, then check_every CG
+ * iterations of every group) is replayed until every cell has finished, so a
+ * cell never waits for another cell's CG at a Newton step. */
 typedef struct fh_batch fh_batch;
 
 typedef struct fh_cell {

@@ -29,8 +29,11 @@
  *   for l = 0..3: W_l[3 axes x,y,z][12 modes][2 re,im][32 o][32 c], M_l[32 o][32 c], m_l[32];
  *   P1[128][32], p1[128], P2[81][128] (row 9i + j), p2[81].
  * The forward and backward passes use a bfloat16 copy of every parameter
- * (made by fh_fno_set_params); activations, accumulations and gradients are
- * float32.
+ * (made by fh_fno_set_params); activations and gradients are stored as
+ * float32. The channel contractions (truncated DFTs, spectral mixing,
+ * pointwise mixing, projection head, weight gradients) run on the tensor
+ * cores as bfloat16 MMAs with float32 accumulation, float32 operands split
+ * into a bfloat16 pair hi + lo (about 16 significant bits).
  *
  * Layouts: phase maps are device uint8 [nx][ny][nz] (z fastest); q, targets
  * and gradients are float32, q and targets [9][nx][ny][nz] per sample.

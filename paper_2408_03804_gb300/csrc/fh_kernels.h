@@ -64,7 +64,7 @@ struct CellState {
   CgScalars* cg;
   const uint8_t* phase;
   const double* scale;
-  const int* newton_done;   // set once the cell's Newton loop has finished
+  const int* newton_done;   // skip mask of the launch: batched kernels leave the cell alone when set
   int* flags;
 };
 

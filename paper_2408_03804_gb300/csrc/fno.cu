@@ -68,8 +68,6 @@ static_assert(kNParam == 314161, "parameter layout");
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kTileProj = 64;
-constexpr size_t kPointBwdSmem = 2 * (size_t)kWarps * 32 * kC * sizeof(float);  // 64 KiB      // voxels per tile of the projection weight gradient
 constexpr int kLinesPerChunk = 128;  // lines per block of the spectral weight gradient
 constexpr long long kLiftChunk = 4096;  // voxels per block of the lifting gradient
 constexpr double kPi = 3.14159265358979323846;
@@ -490,33 +488,73 @@ __global__ void __launch_bounds__(kThreads, 2) k_spec_bwd(const float* __restric
   }
 }
 
-// spectral weight gradient of one axis: per block (chunk of lines, mode k),
-// gWr[o][c] = sum gYr[o] Xr[c] + gYi[o] Xi[c], gWi[o][c] = sum gYi[o] Xr[c] - gYr[o] Xi[c]
+// spectral weight gradient of one axis: per block (chunk of 128 lines, mode k),
+// gWr[o][c] = sum gYr[o] Xr[c] + gYi[o] Xi[c], gWi[o][c] = sum gYi[o] Xr[c] - gYr[o] Xi[c].
+// On the tensor cores as the real product D[(ri, o)][(ri', c)] = sum_lines
+// gY[(ri, o)] X[(ri', c)] (64 x 64, K = the chunk's lines, both operands split
+// hi + lo), staged in shared memory, then combined per quadrant.
+constexpr int kWgradSmem = 2 * kLinesPerChunk * 64 * (int)sizeof(float);
 __global__ void __launch_bounds__(kThreads) k_wgrad(const float* __restrict__ xs, const float* __restrict__ gys,
                                                     long long n_lines, float* __restrict__ partial) {
+  extern __shared__ __align__(16) float wsm[];
+  float* sA = wsm;                          // [line][64] = gY of mode k, (ri, o)
+  float* sB = wsm + kLinesPerChunk * 64;    // [line][64] = X of mode k, (ri, c)
   const int k = blockIdx.y;
-  const int o = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
-  float ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
   const long long l0 = (long long)blockIdx.x * kLinesPerChunk;
-  const long long l1 = l0 + kLinesPerChunk < n_lines ? l0 + kLinesPerChunk : n_lines;
-  for (long long li = l0; li < l1; ++li) {
-    const float* X = xs + li * (kJ * kC);
-    const float* Gy = gys + li * (kJ * kC);
-    const float yr = Gy[(2 * k) * kC + o], yi = Gy[(2 * k + 1) * kC + o];
-    const float4 xr = *reinterpret_cast<const float4*>(X + (2 * k) * kC + c0);
-    const float4 xi = *reinterpret_cast<const float4*>(X + (2 * k + 1) * kC + c0);
-    const float r4[4] = {xr.x, xr.y, xr.z, xr.w}, i4[4] = {xi.x, xi.y, xi.z, xi.w};
+  const int nl = (int)(n_lines - l0 < kLinesPerChunk ? n_lines - l0 : kLinesPerChunk);
+  for (int e = threadIdx.x; e < kLinesPerChunk * 64; e += blockDim.x) {
+    const int l = e >> 6, q = e & 63;
+    float a = 0.0f, b = 0.0f;
+    if (l < nl) {
+      const long long off = (l0 + l) * (kJ * kC) + (2 * k) * kC + q;  // rows 2k (re) and 2k + 1 (im) are contiguous
+      a = gys[off];
+      b = xs[off];
+    }
+    sA[e] = a;
+    sB[e] = b;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gi = lane >> 2, t = lane & 3;
+  const int mt = warp >> 1, nt0 = (warp & 1) * 4;
+  float d[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) d[q][0] = d[q][1] = d[q][2] = d[q][3] = 0.0f;
+  for (int ks = 0; ks < kLinesPerChunk / 16; ++ks) {
+    const int v = ks * 16 + 2 * t, r0 = mt * 16 + gi, r1 = r0 + 8;
+    uint32_t ah[4], al[4];
+    split_bf2(sA[v * 64 + r0], sA[(v + 1) * 64 + r0], ah[0], al[0]);
+    split_bf2(sA[v * 64 + r1], sA[(v + 1) * 64 + r1], ah[1], al[1]);
+    split_bf2(sA[(v + 8) * 64 + r0], sA[(v + 9) * 64 + r0], ah[2], al[2]);
+    split_bf2(sA[(v + 8) * 64 + r1], sA[(v + 9) * 64 + r1], ah[3], al[3]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      ar[q] = fmaf(yr, r4[q], fmaf(yi, i4[q], ar[q]));
-      ai[q] = fmaf(yi, r4[q], fmaf(-yr, i4[q], ai[q]));
+      const int c = (nt0 + q) * 8 + gi;
+      uint32_t b0h, b0l, b1h, b1l;
+      split_bf2(sB[v * 64 + c], sB[(v + 1) * 64 + c], b0h, b0l);
+      split_bf2(sB[(v + 8) * 64 + c], sB[(v + 9) * 64 + c], b1h, b1l);
+      mma_bf16(d[q], ah[0], ah[1], ah[2], ah[3], b0h, b1h);
+      mma_bf16(d[q], ah[0], ah[1], ah[2], ah[3], b0l, b1l);
+      mma_bf16(d[q], al[0], al[1], al[2], al[3], b0h, b1h);
     }
   }
-  float* p = partial + ((long long)blockIdx.x * kModes + k) * 2 * kC * kC;
+  __syncthreads();
+  // the 64 x 64 product into shared memory (over sA), then the complex combination
+  float* D = sA;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    p[o * kC + c0 + q] = ar[q];
-    p[kC * kC + o * kC + c0 + q] = ai[q];
+    const int r = mt * 16 + gi, c = (nt0 + q) * 8 + 2 * t;
+    D[r * 64 + c] = d[q][0];
+    D[r * 64 + c + 1] = d[q][1];
+    D[(r + 8) * 64 + c] = d[q][2];
+    D[(r + 8) * 64 + c + 1] = d[q][3];
+  }
+  __syncthreads();
+  float* p = partial + ((long long)blockIdx.x * kModes + k) * 2 * kC * kC;
+  for (int e = threadIdx.x; e < kC * kC; e += blockDim.x) {
+    const int o = e >> 5, c = e & 31;
+    // quadrants: (re, re) = D[o][c], (im, im) = D[32 + o][32 + c], (im, re) = D[32 + o][c], (re, im) = D[o][32 + c]
+    p[e] = D[o * 64 + c] + D[(32 + o) * 64 + 32 + c];
+    p[kC * kC + e] = D[(32 + o) * 64 + c] - D[o * 64 + 32 + c];
   }
 }
 
@@ -651,28 +689,44 @@ __global__ void __launch_bounds__(kThreads) k_point_fwd(const float* __restrict_
   }
 }
 
-// pointwise part, backward: gz = gn * gelu'(z) (or gn), gh = M^T gz, and the
-// per-warp partial sums gM[o][c] = sum gz[o] h[c], gm[o] = sum gz[o]
+// pointwise part, backward, tiles of 16 voxels per warp on the tensor cores:
+// gz = gn * gelu'(z) (or gn), gh = M^T gz (A = gz split, B[o][c] = M[o][c]
+// exact), and the per-warp partial sums gM[o][c] = sum_vox gz[o] h[c] (A =
+// gz^T, B = h, both split; K = the tile's voxels) and gm[o] = sum_vox gz[o]
 __global__ void __launch_bounds__(kThreads) k_point_bwd(const float* __restrict__ gn, const float* __restrict__ z,
                                                         const float* __restrict__ h,
                                                         const __nv_bfloat16* __restrict__ wq, int layer,
                                                         float* __restrict__ gz, float* __restrict__ gh,
                                                         float* __restrict__ partial, long long nvox) {
-  extern __shared__ __align__(16) unsigned char psmem[];
-  float(*sg)[32 * kC] = reinterpret_cast<float(*)[32 * kC]>(psmem);
-  float(*sh)[32 * kC] = reinterpret_cast<float(*)[32 * kC]>(psmem + (size_t)kWarps * 32 * kC * sizeof(float));
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float Mc[kC], gM[kC];
-  float gm = 0.0f;
+  __shared__ __align__(16) float sg[kWarps][16 * kC];
+  __shared__ __align__(16) float sh[kWarps][16 * kC];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gi = lane >> 2, t = lane & 3;
+  float* G = sg[warp];
+  float* Hs = sh[warp];
+  // B fragments of M for gh = gz M: B[k = o][n = c] = M[o][c]
+  uint32_t bm[4][2][2];
+  {
+    const __nv_bfloat16* M = wq + off_M(layer);
 #pragma unroll
-  for (int o = 0; o < kC; ++o) {
-    Mc[o] = bf(wq, off_M(layer) + o * kC + lane);
-    gM[o] = 0.0f;
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        const int c = nt * 8 + gi, o = ks * 16 + 2 * t;
+        bm[nt][ks][0] = bf2_bits(__halves2bfloat162(M[o * kC + c], M[(o + 1) * kC + c]));
+        bm[nt][ks][1] = bf2_bits(__halves2bfloat162(M[(o + 8) * kC + c], M[(o + 9) * kC + c]));
+      }
   }
-  const long long tiles = (nvox + 31) / 32;
-  for (long long t = (long long)blockIdx.x * kWarps + warp; t < tiles; t += (long long)gridDim.x * kWarps) {
-    const long long v0 = t * 32;
-    for (int i = 0; i < 32; ++i) {
+  float gM[2][4][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) gM[mt][nt][0] = gM[mt][nt][1] = gM[mt][nt][2] = gM[mt][nt][3] = 0.0f;
+  float gm = 0.0f;
+  const long long tiles = (nvox + 15) / 16;
+  for (long long tile = (long long)blockIdx.x * kWarps + warp; tile < tiles; tile += (long long)gridDim.x * kWarps) {
+    const long long v0 = tile * 16;
+    // gz and h of the tile into shared memory (zero past the end), gz to global
+    for (int i = 0; i < 16; ++i) {
       float gv = 0.0f, hv = 0.0f;
       if (v0 + i < nvox) {
         const long long e = (v0 + i) * kC + lane;
@@ -681,41 +735,69 @@ __global__ void __launch_bounds__(kThreads) k_point_bwd(const float* __restrict_
         gz[e] = gv;
         hv = h[e];
       }
-      sg[warp][i * kC + lane] = gv;
-      sh[warp][i * kC + lane] = hv;
+      G[i * kC + lane] = gv;
+      Hs[i * kC + lane] = hv;
+      gm += gv;
     }
     __syncwarp();
-    for (int i = 0; i < 32; ++i) {
-      const float4* gr = reinterpret_cast<const float4*>(&sg[warp][i * kC]);
-      const float4* hr = reinterpret_cast<const float4*>(&sh[warp][i * kC]);
-      // lane = input channel c: gh[c] = sum_o M[o][c] gz[o]
-      float s = 0.0f;
+    // gh[vox][c] = sum_o gz[vox][o] M[o][c]
+    uint32_t ah[2][4], al[2][4];
 #pragma unroll
-      for (int q = 0; q < kC / 4; ++q) {
-        const float4 gv = gr[q];
-        s = fmaf(Mc[4 * q], gv.x, s);
-        s = fmaf(Mc[4 * q + 1], gv.y, s);
-        s = fmaf(Mc[4 * q + 2], gv.z, s);
-        s = fmaf(Mc[4 * q + 3], gv.w, s);
+    for (int ks = 0; ks < 2; ++ks) {
+      const int o = ks * 16 + 2 * t;
+      split_bf2(G[gi * kC + o], G[gi * kC + o + 1], ah[ks][0], al[ks][0]);
+      split_bf2(G[(gi + 8) * kC + o], G[(gi + 8) * kC + o + 1], ah[ks][1], al[ks][1]);
+      split_bf2(G[gi * kC + o + 8], G[gi * kC + o + 9], ah[ks][2], al[ks][2]);
+      split_bf2(G[(gi + 8) * kC + o + 8], G[(gi + 8) * kC + o + 9], ah[ks][3], al[ks][3]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        mma_bf16(d, ah[ks][0], ah[ks][1], ah[ks][2], ah[ks][3], bm[nt][ks][0], bm[nt][ks][1]);
+        mma_bf16(d, al[ks][0], al[ks][1], al[ks][2], al[ks][3], bm[nt][ks][0], bm[nt][ks][1]);
       }
-      if (v0 + i < nvox) gh[(v0 + i) * kC + lane] = s;
-      // lane = output channel o: gM[o][c] += gz[o] h[c]
-      const float go = sg[warp][i * kC + lane];
-      gm += go;
+      const int c = nt * 8 + 2 * t;
+      if (v0 + gi < nvox) *reinterpret_cast<float2*>(gh + (v0 + gi) * kC + c) = make_float2(d[0], d[1]);
+      if (v0 + gi + 8 < nvox) *reinterpret_cast<float2*>(gh + (v0 + gi + 8) * kC + c) = make_float2(d[2], d[3]);
+    }
+    // gM[o][c] += sum over the tile's voxels of gz[vox][o] h[vox][c] (K = 16 voxels)
+    uint32_t gth[2][4], gtl[2][4];
 #pragma unroll
-      for (int q = 0; q < kC / 4; ++q) {
-        const float4 hv = hr[q];
-        gM[4 * q] = fmaf(go, hv.x, gM[4 * q]);
-        gM[4 * q + 1] = fmaf(go, hv.y, gM[4 * q + 1]);
-        gM[4 * q + 2] = fmaf(go, hv.z, gM[4 * q + 2]);
-        gM[4 * q + 3] = fmaf(go, hv.w, gM[4 * q + 3]);
+    for (int mt = 0; mt < 2; ++mt) {
+      const int o0 = mt * 16 + gi, o1 = o0 + 8, v = 2 * t;
+      split_bf2(G[v * kC + o0], G[(v + 1) * kC + o0], gth[mt][0], gtl[mt][0]);
+      split_bf2(G[v * kC + o1], G[(v + 1) * kC + o1], gth[mt][1], gtl[mt][1]);
+      split_bf2(G[(v + 8) * kC + o0], G[(v + 9) * kC + o0], gth[mt][2], gtl[mt][2]);
+      split_bf2(G[(v + 8) * kC + o1], G[(v + 9) * kC + o1], gth[mt][3], gtl[mt][3]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int c = nt * 8 + gi, v = 2 * t;
+      uint32_t b0h, b0l, b1h, b1l;
+      split_bf2(Hs[v * kC + c], Hs[(v + 1) * kC + c], b0h, b0l);
+      split_bf2(Hs[(v + 8) * kC + c], Hs[(v + 9) * kC + c], b1h, b1l);
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        mma_bf16(gM[mt][nt], gth[mt][0], gth[mt][1], gth[mt][2], gth[mt][3], b0h, b1h);
+        mma_bf16(gM[mt][nt], gth[mt][0], gth[mt][1], gth[mt][2], gth[mt][3], b0l, b1l);
+        mma_bf16(gM[mt][nt], gtl[mt][0], gtl[mt][1], gtl[mt][2], gtl[mt][3], b0h, b1h);
       }
     }
     __syncwarp();
   }
   float* p = partial + ((long long)blockIdx.x * kWarps + warp) * kPointLen;
 #pragma unroll
-  for (int c = 0; c < kC; ++c) p[lane * kC + c] = gM[c];
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int o = mt * 16 + gi, c = nt * 8 + 2 * t;
+      p[o * kC + c] = gM[mt][nt][0];
+      p[o * kC + c + 1] = gM[mt][nt][1];
+      p[(o + 8) * kC + c] = gM[mt][nt][2];
+      p[(o + 8) * kC + c + 1] = gM[mt][nt][3];
+    }
   p[kC * kC + lane] = gm;
 }
 
@@ -883,47 +965,255 @@ __device__ __forceinline__ void proj_q_tc(const ProjFrag& s, int lane, const uin
   }
 }
 
-// projection on the tensor cores, tiles of 16 voxels per warp; q written
-// [9][N] when qo is given, and the per-block partial sums of (q - target)^2
-__global__ void __launch_bounds__(kThreads) k_proj_fwd(const float* __restrict__ h4,
-                                                       const __nv_bfloat16* __restrict__ wq,
-                                                       const float* __restrict__ head, float* __restrict__ qo,
-                                                       const float* __restrict__ target, long long N,
-                                                       double* __restrict__ loss_part) {
-  __shared__ __align__(16) ProjFrag s;
-  load_proj_frag(s, wq, head);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gi = lane >> 2, t = lane & 3;
+// ---------------------------------------------------------------------------
+// 5th-generation tensor-core (tcgen05) helpers: shared-memory operands in the
+// canonical K-major layout without swizzle (core matrices of 8 rows x 16
+// bytes; LBO = byte step between core matrices along K, SBO = between groups
+// of 8 rows), fp32 accumulators in tensor memory (TMEM), one thread issuing
+// the MMAs and an mbarrier signalled by tcgen05.commit. Every wait is bounded.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t umma_smem_desc(const void* base, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((smem_u32(base) >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version; base offset 0, relative LBO, no swizzle
+  return d;
+}
+// kind::f16 instruction descriptor: bf16 A and B, both K-major, f32 accumulator, M x N
+constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+}
+// wait for the completion of phase `parity` of the mbarrier, for at most ~2^31 clock ticks; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1LL << 31)) return false;
+  }
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 16 consecutive fp32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+// byte offset of element (row r, k) in a K-major no-swizzle operand with rows of K elements (bf16)
+__device__ __forceinline__ uint32_t kmajor_off(int r, int k, int K) {
+  return (uint32_t)((r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Shared memory of the tcgen05 projection: operand tiles (bf16, K-major) and the biases
+constexpr int kT5 = 128;  // threads = voxels per tile = accumulator rows
+struct ProjT5 {
+  __nv_bfloat16 Ah[kT5 * kC], Al[kT5 * kC];     // h tile, hi and lo terms      (128 x 32)
+  __nv_bfloat16 B1[kHid * kC];                  // P1 [hidden][channel]          (128 x 32)
+  __nv_bfloat16 Th[kT5 * kHid], Tl[kT5 * kHid]; // gelu(hidden), hi and lo       (128 x 128)
+  __nv_bfloat16 B2h[16 * kHid], B2l[16 * kHid]; // effective head [output][hidden] (16 x 128)
+  float p1[kHid];
+  float p2[16];
+  uint64_t mbar;
+  uint32_t tmem;
+  double red[kT5 / 32];
+};
+
+// projection on the 5th-generation tensor cores: tiles of 128 voxels, one
+// thread per voxel. hidden = h P1^T (M 128, N 128, K 32; h as hi + lo, P1 exact)
+// accumulates in TMEM columns 0..127; t = gelu(hidden + p1) goes back to shared
+// memory (hi + lo) as the A operand of q = t P2u^T (M 128, N 16, K 128; P2u as
+// hi + lo, three products) in TMEM columns 128..143. q written [9][N] when qo
+// is given, and the per-block partial sums of (q - target)^2. A wait that runs
+// out sets *err and ends the kernel after releasing its TMEM.
+__global__ void __launch_bounds__(kT5) k_proj_fwd(const float* __restrict__ h4, const __nv_bfloat16* __restrict__ wq,
+                                                  const float* __restrict__ head, float* __restrict__ qo,
+                                                  const float* __restrict__ target, long long N,
+                                                  double* __restrict__ loss_part, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char t5raw[];
+  ProjT5& s = *reinterpret_cast<ProjT5*>(t5raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // constant operands: P1 (exact), P2u split, biases
+  for (int e = tid; e < kHid * kC; e += kT5) {
+    const int r = e / kC, k = e % kC;
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(s.B1) + kmajor_off(r, k, kC)) =
+        wq[kOffP1 + e];
+  }
+  for (int e = tid; e < 16 * kHid; e += kT5) {
+    const int i = e / kHid, k = e % kHid;
+    const float v = i < kOut ? head[i * kHid + k] : 0.0f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(s.B2h) + kmajor_off(i, k, kHid)) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(s.B2l) + kmajor_off(i, k, kHid)) = lo;
+  }
+  for (int i = tid; i < kHid; i += kT5) s.p1[i] = bf(wq, kOffp1 + i);
+  if (tid < 16) s.p2[tid] = tid < kOut ? head[kOut * kHid + tid] : 0.0f;
+  if (tid == 0) mbar_init(&s.mbar, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s.tmem)),
+                 "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s.tmem;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lanes
+  constexpr uint32_t id1 = umma_idesc_bf16(128, 128), id2 = umma_idesc_bf16(128, 16);
+  uint32_t phase = 0;
+  bool ok = true;
   double loss = 0.0;
-  const long long tiles = (N + 15) / 16;
-  for (long long tile = (long long)blockIdx.x * kWarps + warp; tile < tiles; tile += (long long)gridDim.x * kWarps) {
-    const long long va = tile * 16 + gi, vb = va + 8;
-    const bool oka = va < N, okb = vb < N;
-    uint32_t ah[2][4], al[2][4];
-    load_h_frag(h4, va, vb, oka, okb, t, ah, al);
-    float q[2][4];
-    proj_q_tc(s, lane, ah, al, q);
+  const long long tiles = (N + kT5 - 1) / kT5;
+  for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+    const long long v = tile * kT5 + tid;
+    const bool valid = v < N;
+    // A operand of the first product: this thread's voxel row, split
 #pragma unroll
-    for (int n2 = 0; n2 < 2; ++n2)
+    for (int q = 0; q < kC / 8; ++q) {
+      float x[8];
+      if (valid) {
+        const float4 a = *reinterpret_cast<const float4*>(h4 + v * kC + 8 * q);
+        const float4 b = *reinterpret_cast<const float4*>(h4 + v * kC + 8 * q + 4);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+      } else {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int i = n2 * 8 + 2 * t + (e & 1);
-        const long long v = (e < 2) ? va : vb;
-        if (i >= kOut || !(e < 2 ? oka : okb)) continue;
-        if (qo) qo[i * N + v] = q[n2][e];
+        for (int e = 0; e < 8; ++e) x[e] = 0.0f;
+      }
+      uint4 hi, lo;
+      split_bf2(x[0], x[1], hi.x, lo.x);
+      split_bf2(x[2], x[3], hi.y, lo.y);
+      split_bf2(x[4], x[5], hi.z, lo.z);
+      split_bf2(x[6], x[7], hi.w, lo.w);
+      *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(s.Ah) + kmajor_off(tid, 8 * q, kC)) = hi;
+      *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(s.Al) + kmajor_off(tid, 8 * q, kC)) = lo;
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < kC / 16; ++ks) {
+        const uint64_t b = umma_smem_desc(reinterpret_cast<unsigned char*>(s.B1) + ks * 256, 128, (kC / 8) * 128);
+        umma_bf16(tmem, umma_smem_desc(reinterpret_cast<unsigned char*>(s.Ah) + ks * 256, 128, (kC / 8) * 128), b, id1,
+                  ks > 0);
+        umma_bf16(tmem, umma_smem_desc(reinterpret_cast<unsigned char*>(s.Al) + ks * 256, 128, (kC / 8) * 128), b, id1,
+                  1);
+      }
+      umma_commit(&s.mbar);
+    }
+    ok = mbar_wait(&s.mbar, phase);
+    phase ^= 1u;
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    // t = gelu(hidden + p1) into the A operand of the second product
+#pragma unroll
+    for (int c16 = 0; c16 < kHid / 16; ++c16) {
+      float d[16];
+      tmem_ld16(tmem + lane_base + (uint32_t)(c16 * 16), d);
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        uint4 hi, lo;
+        const int k0 = c16 * 16 + half * 8;
+        float t8[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) t8[e] = gelu(d[half * 8 + e] + s.p1[k0 + e]);
+        split_bf2(t8[0], t8[1], hi.x, lo.x);
+        split_bf2(t8[2], t8[3], hi.y, lo.y);
+        split_bf2(t8[4], t8[5], hi.z, lo.z);
+        split_bf2(t8[6], t8[7], hi.w, lo.w);
+        *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(s.Th) + kmajor_off(tid, k0, kHid)) = hi;
+        *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(s.Tl) + kmajor_off(tid, k0, kHid)) = lo;
+      }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      constexpr uint32_t sbo = (kHid / 8) * 128;
+      for (int ks = 0; ks < kHid / 16; ++ks) {
+        const uint64_t th = umma_smem_desc(reinterpret_cast<unsigned char*>(s.Th) + ks * 256, 128, sbo);
+        const uint64_t tl = umma_smem_desc(reinterpret_cast<unsigned char*>(s.Tl) + ks * 256, 128, sbo);
+        const uint64_t bh = umma_smem_desc(reinterpret_cast<unsigned char*>(s.B2h) + ks * 256, 128, sbo);
+        const uint64_t bl = umma_smem_desc(reinterpret_cast<unsigned char*>(s.B2l) + ks * 256, 128, sbo);
+        umma_bf16(tmem + 128, th, bh, id2, ks > 0);
+        umma_bf16(tmem + 128, tl, bh, id2, 1);
+        umma_bf16(tmem + 128, th, bl, id2, 1);
+      }
+      umma_commit(&s.mbar);
+    }
+    ok = mbar_wait(&s.mbar, phase);
+    phase ^= 1u;
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    float q[16];
+    tmem_ld16(tmem + lane_base + 128u, q);
+    if (valid) {
+#pragma unroll
+      for (int i = 0; i < kOut; ++i) {
+        const float qi = q[i] + s.p2[i];
+        if (qo) qo[i * N + v] = qi;
         if (target) {
-          const double dd = (double)q[n2][e] - (double)target[i * N + v];
+          const double dd = (double)qi - (double)target[i * N + v];
           loss += dd * dd;
         }
       }
+    }
+    tc_fence_before();
+    __syncthreads();  // every thread has read TMEM and the operands may be rewritten
+    tc_fence_after();
   }
+  if (!ok && tid == 0) atomicExch(err, 1);
   if (loss_part) {
-    const double tot = block_sum_d(loss);
-    if (threadIdx.x == 0) loss_part[blockIdx.x] = tot;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    if (lane == 0) s.red[warp] = loss;
+    __syncthreads();
+    if (tid == 0) loss_part[blockIdx.x] = s.red[0] + s.red[1] + s.red[2] + s.red[3];
   }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
 }
 
-// projection backward, per voxel: gq = (2/count)(q - target) (kept [vox][9]),
-// gh4 = P1^T (gelu'(pre) . P2^T gq), and the loss partial sums
 // B fragments of the backward products: gt = gq P2u (B[i][j] = P2u[i][j],
 // float32 as hi + lo) and gh4 = gp P1 (B[j][c] = P1[j][c], exact)
 struct ProjFragBwd {
@@ -1043,69 +1333,161 @@ __global__ void __launch_bounds__(kThreads, 2) k_proj_bwd_a(const float* __restr
   if (threadIdx.x == 0) loss_part[blockIdx.x] = tot;
 }
 
-// projection weight gradient of one sample: thread (hidden unit j, half of
-// the channels) accumulates gP1[j][16 channels]; the first half also gp1[j]
-// and G[.][j] = sum gq t_j; threads 0..8 also Gp = sum gq. Per-block rows of
+// projection weight gradient of one sample on the tensor cores. Warp w owns
+// the hidden units 16w .. 16w + 15; for every tile of 16 voxels of the CTA it
+// recomputes pre = P1 h + p1 and gp = (P2u^T gq) gelu'(pre) for its units
+// (as k_proj_bwd_a does) and accumulates gP1[j][c] += sum_vox gp[j] h[c] (A =
+// gp^T, B = h), gp1[j] += sum gp, G[i][j] += sum_vox gq[i] gelu(pre)[j] (A =
+// gq^T, B = t) and Gp[i] += sum gq[i], in a fixed order. Per-block rows of
 // kProjRow entries (P1, p1, G, Gp).
+struct ProjFragB2 {
+  uint2 P2Th[8 * 2 * 32];
+  uint2 P2Tl[8 * 2 * 32];
+};
 __global__ void __launch_bounds__(kThreads) k_proj_bwd_b(const float* __restrict__ h4, const float* __restrict__ gq,
                                                          const __nv_bfloat16* __restrict__ wq,
                                                          const float* __restrict__ head, long long nvox,
                                                          float* __restrict__ partial) {
-  __shared__ __align__(16) float sH[kTileProj * kC];
-  __shared__ float sQ[kTileProj * kOut];
-  const int j = threadIdx.x & (kHid - 1), half = threadIdx.x >> 7, c0 = half * 16;
-  float P1j[kC], P2j[kOut];
+  __shared__ __align__(16) ProjFrag s;
+  __shared__ __align__(16) ProjFragB2 sb;
+  __shared__ __align__(16) float sH[16 * kC];       // the tile's h
+  __shared__ __align__(16) float sQ[16 * 16];       // the tile's gq (outputs 9..15 zero)
+  __shared__ __align__(16) float sGP[kWarps][16 * 16];  // per warp: gp[vox][unit]
+  __shared__ __align__(16) float sT[kWarps][16 * 16];   // per warp: gelu(pre)[vox][unit]
+  load_proj_frag(s, wq, head);
+  for (int e = threadIdx.x; e < 8 * 2 * 32; e += blockDim.x) {
+    const int lane = e & 31, nt = (e >> 5) & 1, kc = e >> 6, gi = lane >> 2, t = lane & 3;
+    const int j = kc * 16 + nt * 8 + gi, i0 = 2 * t;
+    const float v0 = i0 < kOut ? head[i0 * kHid + j] : 0.0f;
+    const float v1 = i0 + 1 < kOut ? head[(i0 + 1) * kHid + j] : 0.0f;
+    const float v2 = i0 + 8 < kOut ? head[(i0 + 8) * kHid + j] : 0.0f;
+    const float v3 = i0 + 9 < kOut ? head[(i0 + 9) * kHid + j] : 0.0f;
+    uint32_t h0, l0, h1, l1;
+    split_bf2(v0, v1, h0, l0);
+    split_bf2(v2, v3, h1, l1);
+    sb.P2Th[e] = make_uint2(h0, h1);
+    sb.P2Tl[e] = make_uint2(l0, l1);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gi = lane >> 2, t = lane & 3;
+  const int kc = warp;
+  float* GP = sGP[warp];
+  float* T = sT[warp];
+  float a1[4][4], a2[2][4];
 #pragma unroll
-  for (int c = 0; c < kC; ++c) P1j[c] = bf(wq, kOffP1 + j * kC + c);
+  for (int q = 0; q < 4; ++q) a1[q][0] = a1[q][1] = a1[q][2] = a1[q][3] = 0.0f;
 #pragma unroll
-  for (int i = 0; i < kOut; ++i) P2j[i] = head[i * kHid + j];
-  const float p1j = bf(wq, kOffp1 + j);
-  float a1[16], a2[kOut];
+  for (int q = 0; q < 2; ++q) a2[q][0] = a2[q][1] = a2[q][2] = a2[q][3] = 0.0f;
   float ap1 = 0.0f, ap2 = 0.0f;
-#pragma unroll
-  for (int k = 0; k < 16; ++k) a1[k] = 0.0f;
-#pragma unroll
-  for (int i = 0; i < kOut; ++i) a2[i] = 0.0f;
-  const long long tiles = (nvox + kTileProj - 1) / kTileProj;
-  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const long long v0 = t * kTileProj;
-    for (int e = threadIdx.x; e < kTileProj * kC; e += blockDim.x)
-      sH[e] = v0 + e / kC < nvox ? h4[v0 * kC + e] : 0.0f;
-    for (int e = threadIdx.x; e < kTileProj * kOut; e += blockDim.x)
-      sQ[e] = v0 + e / kOut < nvox ? gq[v0 * kOut + e] : 0.0f;
-    __syncthreads();
-    const int nv = (int)(nvox - v0 < kTileProj ? nvox - v0 : kTileProj);
-    for (int v = 0; v < nv; ++v) {
-      const float* hr = &sH[v * kC];
-      float pre = p1j;
-#pragma unroll
-      for (int c = 0; c < kC; ++c) pre = fmaf(P1j[c], hr[c], pre);
-      const float* qr = &sQ[v * kOut];
-      float gt = 0.0f;
-#pragma unroll
-      for (int i = 0; i < kOut; ++i) gt = fmaf(P2j[i], qr[i], gt);
-      const float gp = gt * gelu_d(pre);
-#pragma unroll
-      for (int k = 0; k < 16; ++k) a1[k] = fmaf(gp, hr[c0 + k], a1[k]);
-      if (half == 0) {
-        const float tt = gelu(pre);
-        ap1 += gp;
-#pragma unroll
-        for (int i = 0; i < kOut; ++i) a2[i] = fmaf(qr[i], tt, a2[i]);
-      }
-      if (threadIdx.x < kOut) ap2 += qr[threadIdx.x];
+  const long long tiles = (nvox + 15) / 16;
+  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const long long v0 = tile * 16;
+    for (int e = threadIdx.x; e < 16 * kC; e += blockDim.x) sH[e] = v0 + e / kC < nvox ? h4[v0 * kC + e] : 0.0f;
+    for (int e = threadIdx.x; e < 16 * 16; e += blockDim.x) {
+      const int v = e >> 4, i = e & 15;
+      sQ[e] = (i < kOut && v0 + v < nvox) ? gq[(v0 + v) * kOut + i] : 0.0f;
     }
+    __syncthreads();
+    // h fragments (rows = voxels g, g + 8), pre and t of this warp's 16 units
+    uint32_t ah[2][4], al[2][4];
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      const int c = ks * 16 + 2 * t;
+      split_bf2(sH[gi * kC + c], sH[gi * kC + c + 1], ah[ks][0], al[ks][0]);
+      split_bf2(sH[(gi + 8) * kC + c], sH[(gi + 8) * kC + c + 1], ah[ks][1], al[ks][1]);
+      split_bf2(sH[gi * kC + c + 8], sH[gi * kC + c + 9], ah[ks][2], al[ks][2]);
+      split_bf2(sH[(gi + 8) * kC + c + 8], sH[(gi + 8) * kC + c + 9], ah[ks][3], al[ks][3]);
+    }
+    float pre[2][4];
+    hidden_chunk(s, kc, lane, ah, al, pre);
+    // gt = gq P2u over the units (A = gq [vox][i], K = 16 outputs)
+    uint32_t qh[4], ql[4];
+    split_bf2(sQ[gi * 16 + 2 * t], sQ[gi * 16 + 2 * t + 1], qh[0], ql[0]);
+    split_bf2(sQ[(gi + 8) * 16 + 2 * t], sQ[(gi + 8) * 16 + 2 * t + 1], qh[1], ql[1]);
+    split_bf2(sQ[gi * 16 + 2 * t + 8], sQ[gi * 16 + 2 * t + 9], qh[2], ql[2]);
+    split_bf2(sQ[(gi + 8) * 16 + 2 * t + 8], sQ[(gi + 8) * 16 + 2 * t + 9], qh[3], ql[3]);
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      const uint2 bh = sb.P2Th[(kc * 2 + nt) * 32 + lane], bl = sb.P2Tl[(kc * 2 + nt) * 32 + lane];
+      mma_bf16(d, qh[0], qh[1], qh[2], qh[3], bh.x, bh.y);
+      mma_bf16(d, ql[0], ql[1], ql[2], ql[3], bh.x, bh.y);
+      mma_bf16(d, qh[0], qh[1], qh[2], qh[3], bl.x, bl.y);
+      // D rows vox g / g + 8, columns units nt*8 + 2t, + 1 (local to the warp's 16)
+      const int u = nt * 8 + 2 * t;
+      GP[gi * 16 + u] = d[0] * gelu_d(pre[nt][0]);
+      GP[gi * 16 + u + 1] = d[1] * gelu_d(pre[nt][1]);
+      GP[(gi + 8) * 16 + u] = d[2] * gelu_d(pre[nt][2]);
+      GP[(gi + 8) * 16 + u + 1] = d[3] * gelu_d(pre[nt][3]);
+      T[gi * 16 + u] = gelu(pre[nt][0]);
+      T[gi * 16 + u + 1] = gelu(pre[nt][1]);
+      T[(gi + 8) * 16 + u] = gelu(pre[nt][2]);
+      T[(gi + 8) * 16 + u + 1] = gelu(pre[nt][3]);
+    }
+    __syncwarp();
+    // gP1[unit][c] += sum_vox gp[vox][unit] h[vox][c]: A = gp^T (rows = units), B = h (K = voxels)
+    uint32_t ph[4], pl[4];
+    split_bf2(GP[(2 * t) * 16 + gi], GP[(2 * t + 1) * 16 + gi], ph[0], pl[0]);
+    split_bf2(GP[(2 * t) * 16 + gi + 8], GP[(2 * t + 1) * 16 + gi + 8], ph[1], pl[1]);
+    split_bf2(GP[(2 * t + 8) * 16 + gi], GP[(2 * t + 9) * 16 + gi], ph[2], pl[2]);
+    split_bf2(GP[(2 * t + 8) * 16 + gi + 8], GP[(2 * t + 9) * 16 + gi + 8], ph[3], pl[3]);
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int c = nt * 8 + gi;
+      uint32_t b0h, b0l, b1h, b1l;
+      split_bf2(sH[(2 * t) * kC + c], sH[(2 * t + 1) * kC + c], b0h, b0l);
+      split_bf2(sH[(2 * t + 8) * kC + c], sH[(2 * t + 9) * kC + c], b1h, b1l);
+      mma_bf16(a1[nt], ph[0], ph[1], ph[2], ph[3], b0h, b1h);
+      mma_bf16(a1[nt], ph[0], ph[1], ph[2], ph[3], b0l, b1l);
+      mma_bf16(a1[nt], pl[0], pl[1], pl[2], pl[3], b0h, b1h);
+    }
+    // G[i][unit] += sum_vox gq[vox][i] t[vox][unit]: A = gq^T (rows = outputs), B = t
+    uint32_t gth[4], gtl[4];
+    split_bf2(sQ[(2 * t) * 16 + gi], sQ[(2 * t + 1) * 16 + gi], gth[0], gtl[0]);
+    split_bf2(sQ[(2 * t) * 16 + gi + 8], sQ[(2 * t + 1) * 16 + gi + 8], gth[1], gtl[1]);
+    split_bf2(sQ[(2 * t + 8) * 16 + gi], sQ[(2 * t + 9) * 16 + gi], gth[2], gtl[2]);
+    split_bf2(sQ[(2 * t + 8) * 16 + gi + 8], sQ[(2 * t + 9) * 16 + gi + 8], gth[3], gtl[3]);
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const int u = nt * 8 + gi;
+      uint32_t b0h, b0l, b1h, b1l;
+      split_bf2(T[(2 * t) * 16 + u], T[(2 * t + 1) * 16 + u], b0h, b0l);
+      split_bf2(T[(2 * t + 8) * 16 + u], T[(2 * t + 9) * 16 + u], b1h, b1l);
+      mma_bf16(a2[nt], gth[0], gth[1], gth[2], gth[3], b0h, b1h);
+      mma_bf16(a2[nt], gth[0], gth[1], gth[2], gth[3], b0l, b1l);
+      mma_bf16(a2[nt], gtl[0], gtl[1], gtl[2], gtl[3], b0h, b1h);
+    }
+    // bias sums in voxel order: lane u < 16 takes unit u; lanes 0..8 of warp 0 take gq[i]
+    if (lane < 16)
+      for (int v = 0; v < 16; ++v) ap1 += GP[v * 16 + lane];
+    if (warp == 0 && lane < kOut)
+      for (int v = 0; v < 16; ++v) ap2 += sQ[v * 16 + lane];
     __syncthreads();
   }
   float* p = partial + (long long)blockIdx.x * kProjRow;
 #pragma unroll
-  for (int k = 0; k < 16; ++k) p[j * kC + c0 + k] = a1[k];
-  if (half == 0) {
-    p[kHid * kC + j] = ap1;
-#pragma unroll
-    for (int i = 0; i < kOut; ++i) p[kHid * kC + kHid + i * kHid + j] = a2[i];
+  for (int nt = 0; nt < 4; ++nt) {
+    const int j = kc * 16 + gi, c = nt * 8 + 2 * t;
+    p[j * kC + c] = a1[nt][0];
+    p[j * kC + c + 1] = a1[nt][1];
+    p[(j + 8) * kC + c] = a1[nt][2];
+    p[(j + 8) * kC + c + 1] = a1[nt][3];
   }
-  if (threadIdx.x < kOut) p[kHid * kC + kHid + kOut * kHid + threadIdx.x] = ap2;
+  if (lane < 16) p[kHid * kC + kc * 16 + lane] = ap1;
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt) {
+    const int i0 = gi, i1 = gi + 8, j = kc * 16 + nt * 8 + 2 * t;
+    float* G = p + kHid * kC + kHid;
+    if (i0 < kOut) {
+      G[i0 * kHid + j] = a2[nt][0];
+      G[i0 * kHid + j + 1] = a2[nt][1];
+    }
+    if (i1 < kOut) {
+      G[i1 * kHid + j] = a2[nt][2];
+      G[i1 * kHid + j + 1] = a2[nt][3];
+    }
+  }
+  if (warp == 0 && lane < kOut) p[kHid * kC + kHid + kOut * kHid + lane] = ap2;
 }
 
 // lifting backward: per (sample, chunk) sums of gh0 and of gh0 phi per channel
@@ -1233,6 +1615,7 @@ struct fh_fno {
   float* gh_head = nullptr; // [max_batch][kHeadEff]: per-sample head-gradient sums
   const uint8_t** phase_tab = nullptr;
   float* qtmp = nullptr;    // [9][N] for the warm start
+  int* err = nullptr;       // set by a kernel whose bounded wait ran out
   std::vector<const uint8_t*> last_phase;
   int last_B = 0;
   bool params_set = false;
@@ -1327,6 +1710,17 @@ int reduce_into(fh_fno* net, int n_part, int len, int stride, const float* parti
   return FH_OK;
 }
 
+// FH_ERR_TIMEOUT (and the flag cleared) when a kernel's bounded wait ran out; call with the stream idle
+int check_err(fh_fno* net) {
+  int h = 0;
+  FN_CUDA(cudaMemcpy(&h, net->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    FN_CUDA(cudaMemset(net->err, 0, sizeof(int)));
+    return ffail(FH_ERR_TIMEOUT, "a tensor-core wait of the projection kernel ran out");
+  }
+  return FH_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1409,6 +1803,8 @@ int fh_fno_create(fh_fno** out, int nx, int ny, int nz, int max_batch, int train
   A(&net->gh_head, (size_t)max_batch * kHeadEff);
   A(&net->phase_tab, (size_t)max_batch);
   A(&net->qtmp, (size_t)9 * net->N);
+  A(&net->err, (size_t)1);
+  if (e == cudaSuccess) e = cudaMemset(net->err, 0, sizeof(int));
   if (e != cudaSuccess) {
     free_all(net);
     delete net;
@@ -1437,8 +1833,9 @@ int fh_fno_create(fh_fno** out, int nx, int ny, int nz, int max_batch, int train
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spec_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgradSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_point_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPointBwdSmem);
+    e = cudaFuncSetAttribute(k_proj_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ProjT5));
   if (e != cudaSuccess) {
     free_all(net);
     delete net;
@@ -1507,12 +1904,14 @@ int fh_fno_forward(fh_fno* net, int B, const unsigned char* const* phase_ptrs, c
   if (q_ptrs)
     for (int b = 0; b < B; ++b) {
       if (!q_ptrs[b]) continue;
-      k_proj_fwd<<<grid_for(net->N, kThreads, 4 * net->sms), kThreads, 0, s>>>(
+      k_proj_fwd<<<grid_for(net->N, kT5, 2 * net->sms), kT5, sizeof(ProjT5), s>>>(
           H(kLayers) + (long long)b * net->N * kC, net->wq, net->head + (long long)b * kHeadEff, q_ptrs[b], nullptr,
-          net->N, nullptr);
+          net->N, nullptr, net->err);
       FN_CUDA(cudaGetLastError());
     }
   FN_CUDA(cudaStreamSynchronize(s));
+  int rc_err;
+  if ((rc_err = check_err(net))) return rc_err;
   net->last_B = B;
   return FH_OK;
 }
@@ -1533,8 +1932,9 @@ int fh_fno_loss_grad(fh_fno* net, const float* const* target_ptrs, double* loss_
   const long long N = net->N;
   if (!grad_dev) {
     for (int b = 0; b < B; ++b) {
-      k_proj_fwd<<<gl, kThreads, 0, s>>>(net->h[kLayers] + b * N * kC, net->wq, net->head + (long long)b * kHeadEff,
-                                         nullptr, target_ptrs[b], N, net->loss_part + (long long)b * gl);
+      k_proj_fwd<<<gl, kT5, sizeof(ProjT5), s>>>(net->h[kLayers] + b * N * kC, net->wq,
+                                                 net->head + (long long)b * kHeadEff, nullptr, target_ptrs[b], N,
+                                                 net->loss_part + (long long)b * gl, net->err);
       FN_CUDA(cudaGetLastError());
     }
   } else {
@@ -1562,8 +1962,8 @@ int fh_fno_loss_grad(fh_fno* net, const float* const* target_ptrs, double* loss_
     FN_CUDA(cudaGetLastError());
     // layers, last to first
     for (int l = kLayers - 1; l >= 0; --l) {
-      const unsigned gpw = grid_for((nvox + 31) / 32, kWarps, 4 * net->sms);
-      k_point_bwd<<<gpw, kThreads, kPointBwdSmem, s>>>(net->gn, l < kLayers - 1 ? net->z[l] : nullptr, net->h[l], net->wq, l,
+      const unsigned gpw = grid_for((nvox + 15) / 16, kWarps, 4 * net->sms);
+      k_point_bwd<<<gpw, kThreads, 0, s>>>(net->gn, l < kLayers - 1 ? net->z[l] : nullptr, net->h[l], net->wq, l,
                                            net->gz, net->gh, net->partial, nvox);
       FN_CUDA(cudaGetLastError());
       if ((rc = reduce_into(net, (int)(gpw * kWarps), kPointLen, kPointLen, net->partial, grad_dev + off_M(l))))
@@ -1576,7 +1976,7 @@ int fh_fno_loss_grad(fh_fno* net, const float* const* target_ptrs, double* loss_
             net->h[l], net->gz, net->gh, net->xs, net->gys, W, net->tw[ax], net->itw[ax], geom(net), ax, n, lines);
         FN_CUDA(cudaGetLastError());
         const unsigned chunks = (unsigned)((lines + kLinesPerChunk - 1) / kLinesPerChunk);
-        k_wgrad<<<dim3(chunks, kModes), kThreads, 0, s>>>(net->xs, net->gys, lines, net->partial);
+        k_wgrad<<<dim3(chunks, kModes), kThreads, kWgradSmem, s>>>(net->xs, net->gys, lines, net->partial);
         FN_CUDA(cudaGetLastError());
         if ((rc = reduce_into(net, (int)chunks, (int)kWAxis, (int)kWAxis, net->partial, grad_dev + off_W(l) + ax * kWAxis)))
           return rc;
@@ -1597,6 +1997,10 @@ int fh_fno_loss_grad(fh_fno* net, const float* const* target_ptrs, double* loss_
   std::vector<double> lp((size_t)B * gl);
   FN_CUDA(cudaMemcpyAsync(lp.data(), net->loss_part, lp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   FN_CUDA(cudaStreamSynchronize(s));
+  if (!grad_dev) {
+    const int rc_err = check_err(net);
+    if (rc_err) return rc_err;
+  }
   double L = 0.0;
   for (double v : lp) L += v;
   if (loss_out) *loss_out = L / count;

@@ -241,11 +241,12 @@ cudaError_t launch_sum_partials(const double* partials, int n_parts, int width, 
   return cudaGetLastError();
 }
 
-// one CTA per cell: the cell's partials to its sums
+// one CTA per cell: the cell's partials to its sums (cells whose mask is set are skipped)
 __global__ void __launch_bounds__(kThreads) k_sum_partials_b(const CellState* __restrict__ cells, int n_parts,
                                                             int width) {
   __shared__ double red[32];
   const CellState& c = cells[blockIdx.x];
+  if (*c.newton_done) return;
   for (int w = 0; w < width; ++w) {
     const double s = sum_fixed(c.partials + (long long)w * n_parts, n_parts, red);
     if (threadIdx.x == 0) c.sums[w] = s;
@@ -293,11 +294,13 @@ __global__ void __launch_bounds__(kThreads) k_fill(Grid g, double* __restrict__ 
   }
 }
 
-// per cell: F (field 0) or the CG solution x (field 1) set to / incremented by val
+// per cell: F (field 0), the CG solution x (field 1) or the CG direction p
+// (field 2) set to / incremented by val (cells whose mask is set are skipped)
 __global__ void __launch_bounds__(kThreads) k_fill_b(Grid g, const CellState* __restrict__ cells, int field, Nine val,
                                                     int add) {
   const CellState& c = cells[blockIdx.y];
-  double* F = field == 0 ? c.F : c.x;
+  if (*c.newton_done) return;
+  double* F = field == 0 ? c.F : (field == 1 ? c.x : c.p);
   const long long n = g.n;
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
@@ -351,17 +354,11 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(CgScalars* cg, const doubl
   cg_init_body(cg, partials, n_parts, tol, max_it);
 }
 
-// one CTA per cell; a cell whose Newton loop has finished gets done = 1
+// one CTA per cell; cells whose mask is set keep their CG state
 __global__ void __launch_bounds__(kThreads) k_cg_init_b(const CellState* __restrict__ cells, int n_parts, double tol,
                                                        int max_it) {
   const CellState& c = cells[blockIdx.x];
-  if (*c.newton_done) {
-    if (threadIdx.x == 0) {
-      c.cg->done = 1;
-      c.cg->it = 0;
-    }
-    return;
-  }
+  if (*c.newton_done) return;
   cg_init_body(c.cg, c.partials, n_parts, tol, max_it);
 }
 
@@ -470,6 +467,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_finalize(Grid g, const CgScalar
 }
 __global__ void __launch_bounds__(kThreads) k_cg_finalize_b(Grid g, const CellState* __restrict__ cells) {
   const CellState& c = cells[blockIdx.y];
+  if (*c.newton_done) return;
   cg_finalize_body(g, c.cg, c.x, c.p);
 }
 

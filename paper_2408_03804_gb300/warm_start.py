@@ -7,8 +7,9 @@ arranges cells into batches and records counts and times.
 
 Workload (neo-Hookean cells like the 128^3 benchmark): matrix (lambda, mu) =
 (1.5, 1), inclusions 10x, random non-overlapping spheres of radius
-U[4, 10]/128 of the box filling a volume fraction U[0.1, 0.3] (random
-sequential addition jams near 0.38 and needs minutes per cell above 0.35), and a
+U[4, 10]/128 of the box filling a volume fraction U[0.1, 0.4] (random
+sequential addition whose radius range shrinks when additions stall, since
+plain RSA jams near 0.38; rve_inputs.random_spheres_dense), and a
 macroscopic tensor Fbar = I + m d with d uniform on the unit sphere of the
 nine entries and m ~ U[0.005, 0.05] (so |Fbar - I| <= 0.05). Each training
 target is the solver's converged fluctuation (F - Fbar)/|Fbar - I| at Newton
@@ -42,13 +43,18 @@ def params_table() -> np.ndarray:
     return np.array([[lam, mu], [CONTRAST * lam, CONTRAST * mu]], dtype=np.float64)
 
 
+def cell_fraction(seed: int) -> float:
+    """Target inclusion fraction of the seeded cell ``seed`` (the first draw of its recipe)."""
+    return float(np.random.default_rng([seed, 20240807]).uniform(0.1, 0.4))
+
+
 def make_cell(n: int, seed: int):
     """Phase map (uint8 n^3) and Fbar (9) of the seeded cell ``seed``."""
-    from rve_inputs import random_spheres
+    from rve_inputs import random_spheres_dense
 
     rng = np.random.default_rng([seed, 20240807])
-    frac = rng.uniform(0.1, 0.3)
-    phase = random_spheres(n, seed, r_min=4.0 * n / 128, r_max=10.0 * n / 128, target_fraction=frac)
+    frac = rng.uniform(0.1, 0.4)
+    phase = random_spheres_dense(n, seed, r_min=4.0 * n / 128, r_max=10.0 * n / 128, target_fraction=frac)
     d = rng.normal(size=9)
     d /= np.linalg.norm(d)
     Fbar = np.eye(3).reshape(9) + rng.uniform(0.005, 0.05) * d
@@ -209,7 +215,8 @@ def evaluate(n: int, theta, seeds, workers: int, n_increments: int = 1, log=None
             torch.cuda.synchronize()
             t_warm = time.perf_counter() - t
             diff = float((F - P0).abs().max())
-            rows.append({"seed": int(s), "rc": [rc0, rc1], "newton": [st0["n_newton"], st1["n_newton"]],
+            rows.append({"seed": int(s), "fraction": float(ph.mean()), "rc": [rc0, rc1],
+                         "newton": [st0["n_newton"], st1["n_newton"]],
                          "cg": [st0["n_cg"], st1["n_cg"]], "s": [t_zero, t_warm], "inference_s": t_inf,
                          "max_field_diff": diff})
             if log:
@@ -217,7 +224,17 @@ def evaluate(n: int, theta, seeds, workers: int, n_increments: int = 1, log=None
     return rows
 
 
-def summarize(rows):
+def summarize(rows, split: float | None = 0.3):
+    """Means over the cells that converged from both starts; with ``split``, also for the cells at or below
+    and above that inclusion fraction."""
+    out = _summary(rows)
+    if split is not None:
+        out["fraction_le_%g" % split] = _summary([r for r in rows if r.get("fraction", 0.0) <= split])
+        out["fraction_gt_%g" % split] = _summary([r for r in rows if r.get("fraction", 0.0) > split])
+    return out
+
+
+def _summary(rows):
     ok = [r for r in rows if r["rc"] == [0, 0]]
     f = lambda key, i: float(np.mean([r[key][i] for r in ok])) if ok else float("nan")  # noqa: E731
     return {"cases": len(rows), "converged_both": len(ok),
@@ -227,6 +244,7 @@ def summarize(rows):
             "inference_s": float(np.mean([r["inference_s"] for r in ok])) if ok else float("nan"),
             "time_saved_frac": 1.0 - f("s", 1) / f("s", 0) if ok else float("nan"),
             "max_field_diff": float(max(r["max_field_diff"] for r in ok)) if ok else float("nan")}
+
 
 
 def _log(rec):

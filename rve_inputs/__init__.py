@@ -74,6 +74,29 @@ def centered_sphere(n: tuple[int, int, int], radius_frac: float = 0.25,
     return (d2 <= r * r).astype(np.uint8)
 
 
+def _stamp_sphere(phase: np.ndarray, c: np.ndarray, r: float) -> int:
+    """Mark the voxels whose centres lie within r of c (periodic); returns how many were newly filled."""
+    shape = phase.shape
+    lo = np.floor(c - r - 1).astype(int)
+    hi = np.ceil(c + r + 1).astype(int)
+    ix = np.arange(lo[0], hi[0] + 1)
+    iy = np.arange(lo[1], hi[1] + 1)
+    iz = np.arange(lo[2], hi[2] + 1)
+    dx = ix + 0.5 - c[0]
+    dy = iy + 0.5 - c[1]
+    dz = iz + 0.5 - c[2]
+    inside = (dx[:, None, None] ** 2 + dy[None, :, None] ** 2 + dz[None, None, :] ** 2) <= r * r
+    sel = np.ix_(ix % shape[0], iy % shape[1], iz % shape[2])
+    sub = phase[sel]
+    # a sphere wider than a short axis may wrap onto itself: count each voxel once
+    keys = (ix % shape[0])[:, None, None] * (shape[1] * shape[2]) + \
+           (iy % shape[1])[None, :, None] * shape[2] + (iz % shape[2])[None, None, :]
+    new_vox = np.unique(keys[inside & (sub == 0)])
+    sub[inside] = 1
+    phase[sel] = np.maximum(phase[sel], sub)
+    return int(new_vox.size)
+
+
 def random_spheres(n, seed: int, r_min: float = 4.0, r_max: float = 10.0,
                    target_fraction: float = 0.30, max_attempts: int = 200000) -> np.ndarray:
     """Random sequential addition of non-overlapping spheres on a periodic grid.
@@ -105,27 +128,58 @@ def random_spheres(n, seed: int, r_min: float = 4.0, r_max: float = 10.0,
                 continue
         centres.append(c)
         radii.append(r)
-        lo = np.floor(c - r - 1).astype(int)
-        hi = np.ceil(c + r + 1).astype(int)
-        ix = np.arange(lo[0], hi[0] + 1)
-        iy = np.arange(lo[1], hi[1] + 1)
-        iz = np.arange(lo[2], hi[2] + 1)
-        dx = ix + 0.5 - c[0]
-        dy = iy + 0.5 - c[1]
-        dz = iz + 0.5 - c[2]
-        inside = (dx[:, None, None] ** 2 + dy[None, :, None] ** 2 + dz[None, None, :] ** 2) <= r * r
-        sel = np.ix_(ix % shape[0], iy % shape[1], iz % shape[2])
-        sub = phase[sel]
-        # a sphere wider than a short axis may wrap onto itself: count each voxel once
-        keys = (ix % shape[0])[:, None, None] * (shape[1] * shape[2]) + \
-               (iy % shape[1])[None, :, None] * shape[2] + (iz % shape[2])[None, None, :]
-        new_vox = np.unique(keys[inside & (sub == 0)])
-        filled += int(new_vox.size)
-        sub[inside] = 1
-        phase[sel] = np.maximum(phase[sel], sub)
+        filled += _stamp_sphere(phase, c, r)
     else:
         raise RuntimeError("random_spheres: target fraction not reached")
     return phase
+
+
+def random_spheres_dense(n, seed: int, r_min: float, r_max: float, target_fraction: float,
+                         r_floor: float | None = None, patience: int = 500, shrink: float = 0.85,
+                         max_attempts: int = 3_000_000, return_spheres: bool = False):
+    """Random sequential addition that keeps going past the jamming limit of plain RSA (about 0.38).
+
+    As ``random_spheres`` (radius uniform in [lo, hi], centre uniform, rejected on periodic overlap),
+    starting from [lo, hi] = [r_min, r_max]; after ``patience`` consecutive rejections the range
+    shrinks: hi by the factor ``shrink`` (not below lo), and once hi = lo both shrink, down to
+    ``r_floor`` (default r_min / 2). Until the first stall the draws are those of plain RSA. Spheres
+    never overlap. Returns a uint8 phase map (1 = inclusion) at the first fraction >= target, and with
+    ``return_spheres`` also the centres (k, 3) and radii (k,) in voxel units.
+    """
+    shape = (n, n, n) if np.isscalar(n) else tuple(int(v) for v in n)
+    box = np.asarray(shape, dtype=np.float64)
+    floor_r = r_min / 2.0 if r_floor is None else r_floor
+    rng = np.random.default_rng(seed)
+    phase = np.zeros(shape, dtype=np.uint8)
+    centres = np.zeros((0, 3))
+    radii = np.zeros(0)
+    filled, fails = 0, 0
+    lo, hi = r_min, r_max
+    target = target_fraction * phase.size
+    for _ in range(max_attempts):
+        if filled >= target:
+            break
+        r = rng.uniform(lo, hi)
+        c = rng.uniform(0.0, 1.0, size=3) * box
+        if radii.size:
+            d = centres - c
+            d -= box * np.round(d / box)
+            if np.any(np.sqrt((d * d).sum(axis=1)) < radii + r):
+                fails += 1
+                if fails >= patience:
+                    fails = 0
+                    if hi > lo:
+                        hi = max(lo, hi * shrink)
+                    else:
+                        lo = hi = max(floor_r, lo * shrink)
+                continue
+        fails = 0
+        centres = np.vstack([centres, c])
+        radii = np.append(radii, r)
+        filled += _stamp_sphere(phase, c, r)
+    else:
+        raise RuntimeError("random_spheres_dense: target fraction not reached")
+    return (phase, centres, radii) if return_spheres else phase
 
 
 def laminate(n: tuple[int, int, int], thickness: int, axis: int = 0) -> np.ndarray:

@@ -2,7 +2,8 @@
 
 import numpy as np
 
-from rve_inputs import centered_sphere, neo_hookean_config, random_spheres, small_strain_config
+from rve_inputs import (centered_sphere, neo_hookean_config, random_spheres, random_spheres_dense,
+                        small_strain_config)
 
 
 def test_random_spheres_fraction_and_determinism():
@@ -47,3 +48,31 @@ def test_two_dimensional_cells():
     ph, params, plastic, Ebar = j2_config(48, 0, nz=2)
     assert ph.shape == (48, 48, 2) and np.allclose(plastic[1], 2 * plastic[0])
     assert Ebar[0] == Ebar[4] == 0.01 and Ebar[8] == 0.0
+
+
+def test_dense_packing_passes_the_rsa_jamming_limit_without_overlap():
+    ph, c, r = random_spheres_dense(48, seed=3, r_min=1.5, r_max=3.75, target_fraction=0.4, return_spheres=True)
+    assert 0.40 <= ph.mean() < 0.42
+    assert r.min() >= 0.75 - 1e-12 and r.max() <= 3.75
+    box = np.array(ph.shape, dtype=float)
+    d = c[:, None, :] - c[None, :, :]
+    d -= box * np.round(d / box)
+    dist = np.sqrt((d * d).sum(-1))
+    gap = dist - (r[:, None] + r[None, :])
+    np.fill_diagonal(gap, 1.0)
+    assert gap.min() >= 0.0
+    # every stamped voxel lies in some sphere and every voxel centre inside a sphere is stamped
+    idx = np.stack(np.meshgrid(*[np.arange(n) + 0.5 for n in ph.shape], indexing="ij"), -1).reshape(-1, 3)
+    inside = np.zeros(idx.shape[0], bool)
+    for ci, ri in zip(c, r):
+        e = idx - ci
+        e -= box * np.round(e / box)
+        inside |= (e * e).sum(1) <= ri * ri
+    assert np.array_equal(inside.reshape(ph.shape), ph.astype(bool))
+    assert np.array_equal(ph, random_spheres_dense(48, seed=3, r_min=1.5, r_max=3.75, target_fraction=0.4))
+
+
+def test_dense_packing_equals_plain_rsa_below_the_first_stall():
+    a = random_spheres(40, seed=5, r_min=2.0, r_max=4.0, target_fraction=0.15)
+    b = random_spheres_dense(40, seed=5, r_min=2.0, r_max=4.0, target_fraction=0.15)
+    assert np.array_equal(a, b)
