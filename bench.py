@@ -71,7 +71,13 @@ def algorithmic_work(cls: str, nx: int, ny: int, nz: int):
 
 # FP64 lane operations (DADD, DMUL, DFMA each one) per launch, counted from the
 # kernels' code: complex length-L transform per point = FP64_FFT_OPS[L]
-FP64_FFT_OPS = {1: 0.0, 2: 2.0, 4: 4.0, 8: 6.5, 16: 10.0, 32: 13.5, 64: 16.5, 128: 20.0, 256: 23.75}
+# compile-time plans of the library (radix of each stage) and FP64 operations per point of an R-point
+# butterfly; a stage after the first adds 4 (R-1)/R per point for its twiddle multiplications
+FFT_PLANS = {1: (), 2: (2,), 3: (3,), 4: (4,), 6: (2, 3), 8: (8,), 12: (4, 3), 16: (16,), 24: (8, 3),
+             32: (8, 4), 48: (16, 3), 64: (8, 8), 96: (8, 4, 3), 128: (16, 8), 192: (16, 4, 3), 256: (16, 16)}
+BUTTERFLY_OPS = {2: 2.0, 3: 4.0, 4: 4.0, 8: 6.5, 16: 10.0}
+FP64_FFT_OPS = {L: sum(BUTTERFLY_OPS[r] + (4.0 * (r - 1) / r if k else 0.0) for k, r in enumerate(plan))
+                for L, plan in FFT_PLANS.items()}
 
 
 def fp64_ops(cls: str, nx: int, ny: int, nz: int):
@@ -528,6 +534,16 @@ def run_batch(args, world, rank, local):
     c1111 = pbar[:, 0] / Ebar[0]
     diff = float(np.abs(pbar - np.asarray(seq_pbar)).max() / np.abs(pbar).max())
     it_bytes = sum(cg_iteration_bytes(*c[0].shape) * int(k) for c, k in zip(cells, cg))
+    # FP64 floor of the batch: counted FP64 lane operations of every cell's CG iterations and
+    # right-hand-side projections at the measured DFMA issue rate
+    fp64 = probe_fp64(fh, local)
+    cg_cls = ("fwd_z", "fwd_y", "x_ghat", "inv_y", "inv_z", "cg_update")
+    rhs_cls = ("fwd_z", "fwd_y", "x_ghat", "inv_y", "inv_z")
+    ops = 0.0
+    for (ph, _), k, nw in zip(cells, cg, newton):
+        shp = ph.shape
+        ops += int(k) * sum(fp64_ops(c, *shp) for c in cg_cls) + int(nw) * sum(fp64_ops(c, *shp) for c in rhs_cls)
+    floor_s = ops / fp64["lane_ops_per_s"]
     line = {
         "metric": f"batched time-to-solve of {args.batch} uneven RVEs @1e-8 (linear elastic, log-normal E)",
         "value": t_batch, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 1),
@@ -540,6 +556,9 @@ def run_batch(args, world, rank, local):
         "cbar1111_mean": float(c1111.mean()), "cbar1111_var": float(c1111.var(ddof=1)),
         "max_rel_diff_batched_vs_single": diff,
         "cg_bytes_gbs": it_bytes / t_batch / 1e9,
+        "fp64_floor_s": floor_s, "fp64_floor_frac_batched": floor_s / t_batch,
+        "fp64_floor_frac_sequential": floor_s / t_seq, "max_speedup_at_fp64_floor": t_seq / floor_s,
+        "fp64_lane_ops": ops, "fp64_probe_lane_ops_per_s": fp64["lane_ops_per_s"],
     }
     print(json.dumps(line), flush=True)
 

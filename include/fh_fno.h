@@ -107,6 +107,16 @@ FH_API int fh_fno_make_target(fh_fno* net, const double* F_dev, const double Fba
 FH_API int fh_fno_warm_start(fh_fno* net, fh_ctx* ctx, const unsigned char* phase_dev, const double Fbar[9],
                              double* F_dev);
 
+/* Failure-detection test hook (no counterpart in the paper). The projection
+ * head runs on the tcgen05 tensor cores and waits on an mbarrier for its MMAs,
+ * a wait bounded at about 2^31 clock ticks (about a second), after which the
+ * kernel records the failure, releases its tensor memory and returns, and the
+ * calling entry point reports FH_ERR_TIMEOUT. With skip != 0 the kernel issues
+ * no MMA and never signals the mbarrier, so that wait runs out: a test can
+ * check the reported status, with no MMA in flight and the GPU context still
+ * usable. skip = 0 restores normal operation. */
+FH_API int fh_fno_test_skip_mma(fh_fno* net, int skip);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,7 +43,7 @@ EXPORTS = ["fh_default_options", "fh_create", "fh_destroy", "fh_last_error_strin
            "fh_project", "fh_matvec", "fft_homog_solve", "fh_profile_enable", "fh_profile_read", "fh_project_static", "fft_homog_tangent", "fft_homog_sensitivity",
            "fh_batch_create", "fh_batch_destroy", "fft_homog_solve_batched", "fh_autotune", "fh_probe_fp64",
            "fh_fno_param_count", "fh_fno_create", "fh_fno_destroy", "fh_fno_set_params", "fh_fno_forward",
-           "fh_fno_loss_grad", "fh_fno_adam", "fh_fno_make_target", "fh_fno_warm_start"]
+           "fh_fno_loss_grad", "fh_fno_adam", "fh_fno_make_target", "fh_fno_warm_start", "fh_fno_test_skip_mma"]
 
 PROF_NCLASS = 14
 PROF_CLASSES = ["fwd_z", "fwd_y", "x_ghat", "inv_y", "inv_z", "constitutive", "jvp", "cg_scalar", "cg_update",
@@ -156,6 +156,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.fh_fno_make_target.restype = c_int
     lib.fh_fno_warm_start.argtypes = [c_void_p, c_void_p, c_void_p, POINTER(c_double), c_void_p]
     lib.fh_fno_warm_start.restype = c_int
+    lib.fh_fno_test_skip_mma.argtypes = [c_void_p, c_int]
+    lib.fh_fno_test_skip_mma.restype = c_int
     _lib = lib
     return lib
 
@@ -451,6 +453,10 @@ class Fno:
         h = c_void_p()
         _check(lib.fh_fno_create(ctypes.byref(h), nx, ny, nz, int(max_batch), 1 if train else 0, c_void_p(stream)))
         self._h = h
+
+    def test_skip_mma(self, skip: bool = True):
+        """Failure-detection test hook: the tcgen05 projection issues no MMA, so its bounded wait runs out."""
+        _check(load().fh_fno_test_skip_mma(self._h, 1 if skip else 0))
 
     def set_params(self, theta):
         _check(load().fh_fno_set_params(self._h, _ptr(theta)))

@@ -341,9 +341,9 @@ int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
   // twiddle table after the tables of the compile-time lengths
   int tw_len = kTwiddleTotal;
   g.px = make_fft_plan(nx, tw_len);
-  if (g.px.L) tw_len += nx;
+  tw_len += g.px.tw_len;
   g.py = make_fft_plan(ny, tw_len);
-  if (g.py.L) tw_len += ny;
+  tw_len += g.py.tw_len;
   c->tiling = choose_tiling(g);
   const size_t f9 = (size_t)9 * g.n * sizeof(double);
   long long np = 9LL * constitutive_ctas(g);
@@ -368,8 +368,8 @@ int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
   }
   std::vector<double2> tw(tw_len);
   fill_twiddle_table(tw.data());
-  if (g.px.L) fill_twiddles_of_length(tw.data() + g.px.tw_off, nx);
-  if (g.py.L) fill_twiddles_of_length(tw.data() + g.py.tw_off, ny);
+  if (g.px.L) fill_plan_tables(tw.data() + g.px.tw_off, g.px);
+  if (g.py.L) fill_plan_tables(tw.data() + g.py.tw_off, g.py);
   if ((e = cudaMemcpy(c->tw, tw.data(), tw_len * sizeof(double2), cudaMemcpyHostToDevice)) ||
       (e = cudaMemset(c->sc, 0, sizeof(DevScalars))) || (e = setup_fft_kernels(g, c->tiling))) {
     fail(FH_ERR_CUDA, "fh_create: setup failed: %s", cudaGetErrorString(e));
@@ -709,8 +709,9 @@ bool tiling_fits(const Grid& g, const Tiling& t) {
   if (t.bk_y < 1 || t.bk_y > g.nzh || t.bk_x < 1 || t.bk_x > g.nzh) return false;
   const size_t limit = 227 * 1024;
   const size_t zs = ((size_t)9 * t.lines_z * g.nz + g.nz) * sizeof(double2);
-  const size_t ys = ((size_t)2 * 3 * t.bk_y * (g.ny + 1) + g.ny) * sizeof(double2);
-  const size_t xs = ((size_t)2 * 6 * t.bk_x * (g.nx + 1) + g.nx) * sizeof(double2);
+  const int twy = g.py.L ? g.py.tw_len : g.ny, twx = g.px.L ? g.px.tw_len : g.nx;
+  const size_t ys = ((size_t)2 * 3 * t.bk_y * (g.ny + 1) + twy) * sizeof(double2);
+  const size_t xs = ((size_t)2 * 6 * t.bk_x * (g.nx + 1) + twx) * sizeof(double2);
   return zs <= limit && ys <= limit && xs <= limit;
 }
 

@@ -371,21 +371,22 @@ __device__ __forceinline__ void stockham_stage_odd(double2* __restrict__ src, do
   }
 }
 
-// Transform all pencils of `a` with a run-time plan (see fft_pencils).
+// The stages `r[0..n)` of a run-time plan of length L over the pencils of a
+// (partner b); returns the buffer holding the result.
 template <bool INV, bool JFAST>
-__device__ __noinline__ double2* fft_pencils_rt(double2* a, double2* b, const PencilLayout lay, const double2* tw,
-                                                const FftPlan p) {
+__device__ __forceinline__ double2* run_stages_rt(double2* a, double2* b, const PencilLayout& lay,
+                                                  const double2* tw, int L, int n, const int* r) {
   int NS = 1;
-  for (int st = 0; st < p.n; ++st) {
-    const int R = p.r[st];
+  for (int st = 0; st < n; ++st) {
+    const int R = r[st];
     __syncthreads();
     switch (R) {
-      case 2: stockham_stage_rt<2, INV, JFAST>(a, b, lay, tw, p.L, NS); break;
-      case 3: stockham_stage_rt<3, INV, JFAST>(a, b, lay, tw, p.L, NS); break;
-      case 4: stockham_stage_rt<4, INV, JFAST>(a, b, lay, tw, p.L, NS); break;
-      case 8: stockham_stage_rt<8, INV, JFAST>(a, b, lay, tw, p.L, NS); break;
-      case 16: stockham_stage_rt<16, INV, JFAST>(a, b, lay, tw, p.L, NS); break;
-      default: stockham_stage_odd<INV, JFAST>(a, b, lay, tw, p.L, R, NS); break;
+      case 2: stockham_stage_rt<2, INV, JFAST>(a, b, lay, tw, L, NS); break;
+      case 3: stockham_stage_rt<3, INV, JFAST>(a, b, lay, tw, L, NS); break;
+      case 4: stockham_stage_rt<4, INV, JFAST>(a, b, lay, tw, L, NS); break;
+      case 8: stockham_stage_rt<8, INV, JFAST>(a, b, lay, tw, L, NS); break;
+      case 16: stockham_stage_rt<16, INV, JFAST>(a, b, lay, tw, L, NS); break;
+      default: stockham_stage_odd<INV, JFAST>(a, b, lay, tw, L, R, NS); break;
     }
     double2* t = a;
     a = b;
@@ -394,6 +395,66 @@ __device__ __noinline__ double2* fft_pencils_rt(double2* a, double2* b, const Pe
   }
   __syncthreads();
   return a;
+}
+
+// Prime length L by Rader's algorithm. With g a primitive root of L and
+// M = L - 1: X_0 = sum_m v_m and, for q < M, X_{g^-q} = v_0 + sum_r v_{g^r}
+// w^{g^(r-q)}, a cyclic convolution of a_r = v_{g^r} with b_s = w^{g^-s}
+// (w = exp(-+ 2 pi i / L)). It is computed as IFFT_M(FFT_M(a) Bhat) with
+// Bhat = FFT_M(b) / M precomputed for both directions. Tables at `tab`:
+// length-M twiddles, Bhat forward, Bhat inverse, then (g^r, g^-r) as
+// doubles. Each pencil keeps v_0 in slot 0 of both buffers and runs the
+// inner transforms on slots 1..M; slot L (the pencil's padding) holds X_0.
+template <bool INV, bool JFAST>
+__device__ __forceinline__ double2* rader_pencils(double2* a, double2* b, const PencilLayout& lay,
+                                                  const double2* tab, const FftPlan& p) {
+  const int L = p.L, M = L - 1;
+  const double2* itw = tab;
+  const double2* bhat = tab + (INV ? 2 : 1) * M;
+  const double2* perm = tab + 3 * M;
+  const int nq = (lay.np / lay.group) * lay.valid;
+  const int js = lay.j_stride;
+  __syncthreads();
+  // gather a_r = v_{g^r} into slots 1..M of b; copy v_0
+  for (int t = threadIdx.x; t < nq * L; t += blockDim.x) {
+    const int q = pencil_of(JFAST ? t / L : t % nq, lay);
+    const int e = JFAST ? t % L : t / nq;
+    const double2* s = a + q * lay.q_stride;
+    double2* d = b + q * lay.q_stride;
+    d[e * js] = e == 0 ? s[0] : s[(int)perm[e - 1].x * js];
+  }
+  double2* C = run_stages_rt<false, JFAST>(b + js, a + js, lay, itw, M, p.in_n, p.in_r) - js;
+  // Ahat * Bhat; X_0 = v_0 + Ahat_0 into slot L
+  for (int t = threadIdx.x; t < nq * M; t += blockDim.x) {
+    const int q = pencil_of(JFAST ? t / M : t % nq, lay);
+    const int k = JFAST ? t % M : t / nq;
+    double2* c = C + q * lay.q_stride;
+    const double2 ah = c[(1 + k) * js];
+    if (k == 0) c[L * js] = cadd(c[0], ah);
+    c[(1 + k) * js] = make_double2(ah.x * bhat[k].x - ah.y * bhat[k].y, ah.x * bhat[k].y + ah.y * bhat[k].x);
+  }
+  double2* D = (C == a) ? b : a;
+  double2* E = run_stages_rt<true, JFAST>(C + js, D + js, lay, itw, M, p.in_n, p.in_r) - js;
+  double2* O = (E == a) ? b : a;
+  // X_{g^-k} = v_0 + c_k, X_0 from slot L of C
+  for (int t = threadIdx.x; t < nq * L; t += blockDim.x) {
+    const int q = pencil_of(JFAST ? t / L : t % nq, lay);
+    const int e = JFAST ? t % L : t / nq;
+    const double2* ee = E + q * lay.q_stride;
+    double2* o = O + q * lay.q_stride;
+    if (e == 0) o[0] = C[q * lay.q_stride + L * js];
+    else o[(int)perm[e - 1].y * js] = cadd(ee[0], ee[e * js]);
+  }
+  __syncthreads();
+  return O;
+}
+
+// Transform all pencils of `a` with a run-time plan (see fft_pencils).
+template <bool INV, bool JFAST>
+__device__ __noinline__ double2* fft_pencils_rt(double2* a, double2* b, const PencilLayout lay, const double2* tw,
+                                                const FftPlan p) {
+  if (p.rader) return rader_pencils<INV, JFAST>(a, b, lay, tw, p);
+  return run_stages_rt<INV, JFAST>(a, b, lay, tw, p.L, p.n, p.r);
 }
 
 // compile-time plan when L > 0, the run-time plan p otherwise

@@ -77,9 +77,13 @@ __host__ __device__ constexpr bool grid_extents_ok_any(int nx, int ny, int nz) {
 // twiddle table.
 struct FftPlan {
   int L;        // length (0 when the axis uses a compile-time plan)
-  int n;        // number of stages
-  int tw_off;   // offset of the length-L twiddles in the context's table
+  int n;        // number of stages (0 for a Rader plan)
+  int tw_off;   // offset of the plan's tables in the context's twiddle table
+  int tw_len;   // entries of those tables (L, or 4 (L - 1) for a Rader plan)
   int r[12];    // radix of each stage, in order
+  int rader;    // 1: prime L by Rader's algorithm, a cyclic convolution of length L - 1
+  int in_n;     // stages of the inner length-(L - 1) transforms
+  int in_r[10]; // their radices
 };
 
 // ---------------------------------------------------------------------------

@@ -79,10 +79,12 @@ struct Tiling {
 void fill_twiddle_table(double2* t);
 
 // run-time plan of a length without a compile-time plan (L = 0 when it has
-// one); its twiddles go to offset tw_off of the context's table
+// one); its tables (tw_len entries) go to offset tw_off of the context's table
 FftPlan make_fft_plan(int L, int tw_off);
 // w_L^m for m < L into t[L] (host memory)
 void fill_twiddles_of_length(double2* t, int L);
+// the tables of a run-time plan into t[p.tw_len] (host memory)
+void fill_plan_tables(double2* t, const FftPlan& p);
 
 Tiling choose_tiling(const Grid& g);
 size_t z_pass_smem(const Grid& g, const Tiling& t);

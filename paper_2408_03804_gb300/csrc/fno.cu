@@ -1058,7 +1058,8 @@ struct ProjT5 {
 __global__ void __launch_bounds__(kT5) k_proj_fwd(const float* __restrict__ h4, const __nv_bfloat16* __restrict__ wq,
                                                   const float* __restrict__ head, float* __restrict__ qo,
                                                   const float* __restrict__ target, long long N,
-                                                  double* __restrict__ loss_part, int* __restrict__ err) {
+                                                  double* __restrict__ loss_part, int* __restrict__ err,
+                                                  int skip_mma) {
   extern __shared__ __align__(128) unsigned char t5raw[];
   ProjT5& s = *reinterpret_cast<ProjT5*>(t5raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1122,7 +1123,7 @@ __global__ void __launch_bounds__(kT5) k_proj_fwd(const float* __restrict__ h4, 
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (tid == 0) {
+    if (tid == 0 && !skip_mma) {
 #pragma unroll
       for (int ks = 0; ks < kC / 16; ++ks) {
         const uint64_t b = umma_smem_desc(reinterpret_cast<unsigned char*>(s.B1) + ks * 256, 128, (kC / 8) * 128);
@@ -1164,7 +1165,7 @@ __global__ void __launch_bounds__(kT5) k_proj_fwd(const float* __restrict__ h4, 
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (tid == 0) {
+    if (tid == 0 && !skip_mma) {
       constexpr uint32_t sbo = (kHid / 8) * 128;
       for (int ks = 0; ks < kHid / 16; ++ks) {
         const uint64_t th = umma_smem_desc(reinterpret_cast<unsigned char*>(s.Th) + ks * 256, 128, sbo);
@@ -1616,6 +1617,7 @@ struct fh_fno {
   const uint8_t** phase_tab = nullptr;
   float* qtmp = nullptr;    // [9][N] for the warm start
   int* err = nullptr;       // set by a kernel whose bounded wait ran out
+  int test_skip_mma = 0;    // fh_fno_test_skip_mma
   std::vector<const uint8_t*> last_phase;
   int last_B = 0;
   bool params_set = false;
@@ -1726,6 +1728,13 @@ int check_err(fh_fno* net) {
 extern "C" {
 
 long long fh_fno_param_count(void) { return kNParam; }
+
+int fh_fno_test_skip_mma(fh_fno* net, int skip) {
+  fh_internal_set_error("");
+  if (!net) return ffail(FH_ERR_ARG, "NULL argument");
+  net->test_skip_mma = skip ? 1 : 0;
+  return FH_OK;
+}
 
 int fh_fno_create(fh_fno** out, int nx, int ny, int nz, int max_batch, int train, void* cuda_stream) {
   fh_internal_set_error("");
@@ -1906,7 +1915,7 @@ int fh_fno_forward(fh_fno* net, int B, const unsigned char* const* phase_ptrs, c
       if (!q_ptrs[b]) continue;
       k_proj_fwd<<<grid_for(net->N, kT5, 2 * net->sms), kT5, sizeof(ProjT5), s>>>(
           H(kLayers) + (long long)b * net->N * kC, net->wq, net->head + (long long)b * kHeadEff, q_ptrs[b], nullptr,
-          net->N, nullptr, net->err);
+          net->N, nullptr, net->err, net->test_skip_mma);
       FN_CUDA(cudaGetLastError());
     }
   FN_CUDA(cudaStreamSynchronize(s));
@@ -1934,7 +1943,8 @@ int fh_fno_loss_grad(fh_fno* net, const float* const* target_ptrs, double* loss_
     for (int b = 0; b < B; ++b) {
       k_proj_fwd<<<gl, kT5, sizeof(ProjT5), s>>>(net->h[kLayers] + b * N * kC, net->wq,
                                                  net->head + (long long)b * kHeadEff, nullptr, target_ptrs[b], N,
-                                                 net->loss_part + (long long)b * gl, net->err);
+                                                 net->loss_part + (long long)b * gl, net->err,
+                                                 net->test_skip_mma);
       FN_CUDA(cudaGetLastError());
     }
   } else {

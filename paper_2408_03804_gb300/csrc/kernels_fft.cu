@@ -25,6 +25,7 @@
 // updates are race free.
 #include <cmath>
 #include <cstdio>
+#include <vector>
 
 #include "fft_core.cuh"
 #include "fh_kernels.h"
@@ -136,7 +137,7 @@ __device__ __forceinline__ void stage_axis_twiddles(double2* dst, const double2*
     stage_twiddles<L>(dst, tw, L);
   } else {
     const FftPlan& p = AX ? g.py : g.px;
-    for (int i = threadIdx.x; i < p.L; i += blockDim.x) dst[i] = tw[p.tw_off + i];
+    for (int i = threadIdx.x; i < p.tw_len; i += blockDim.x) dst[i] = tw[p.tw_off + i];
   }
 }
 
@@ -469,33 +470,123 @@ void fill_twiddles_of_length(double2* t, int L) {
   }
 }
 
+// stage radices of a length: powers of two as radix-16 stages and one radix-8/4/2
+// stage, then radix-3 stages, then the other prime factors in increasing order
+static int plan_radices(int L, int* r) {
+  int n = 0, rest = L, twos = 0;
+  while (rest % 2 == 0) {
+    rest /= 2;
+    ++twos;
+  }
+  while (twos >= 4) {
+    r[n++] = 16;
+    twos -= 4;
+  }
+  if (twos > 0) r[n++] = 1 << twos;
+  while (rest % 3 == 0) {
+    r[n++] = 3;
+    rest /= 3;
+  }
+  for (int f = 5; rest > 1; f += 2) {
+    while (rest % f == 0) {
+      r[n++] = f;
+      rest /= f;
+    }
+  }
+  return n;
+}
+
+static bool is_prime(int L) {
+  if (L < 2) return false;
+  for (int f = 2; f * f <= L; ++f)
+    if (L % f == 0) return false;
+  return true;
+}
+
+// primes from this length on use Rader's algorithm; shorter ones a direct stage
+constexpr int kRaderMin = 37;
+
 FftPlan make_fft_plan(int L, int tw_off) {
   FftPlan p{};
   if (fft_length_ok(L)) return p;  // compile-time plan
   p.L = L;
   p.tw_off = tw_off;
-  int rest = L, twos = 0;
-  while (rest % 2 == 0) {
-    rest /= 2;
-    ++twos;
-  }
-  // powers of two as radix-16 stages, the remainder as one radix-8/4/2 stage
-  while (twos >= 4) {
-    p.r[p.n++] = 16;
-    twos -= 4;
-  }
-  if (twos > 0) p.r[p.n++] = 1 << twos;
-  while (rest % 3 == 0) {
-    p.r[p.n++] = 3;
-    rest /= 3;
-  }
-  for (int f = 5; rest > 1; f += 2) {
-    while (rest % f == 0) {
-      p.r[p.n++] = f;
-      rest /= f;
-    }
+  if (L >= kRaderMin && is_prime(L)) {
+    p.rader = 1;
+    p.tw_len = 4 * (L - 1);
+    p.in_n = plan_radices(L - 1, p.in_r);
+  } else {
+    p.tw_len = L;
+    p.n = plan_radices(L, p.r);
   }
   return p;
+}
+
+static long long pow_mod(long long b, long long e, long long m) {
+  long long r = 1 % m;
+  b %= m;
+  while (e > 0) {
+    if (e & 1) r = r * b % m;
+    b = b * b % m;
+    e >>= 1;
+  }
+  return r;
+}
+
+// smallest primitive root of the prime L
+static int primitive_root(int L) {
+  int f[16], nf = 0, m = L - 1;
+  for (int q = 2; q * q <= m; ++q)
+    if (m % q == 0) {
+      f[nf++] = q;
+      while (m % q == 0) m /= q;
+    }
+  if (m > 1) f[nf++] = m;
+  for (int g = 2; g < L; ++g) {
+    bool ok = true;
+    for (int i = 0; i < nf && ok; ++i) ok = pow_mod(g, (L - 1) / f[i], L) != 1;
+    if (ok) return g;
+  }
+  return 1;
+}
+
+void fill_plan_tables(double2* t, const FftPlan& p) {
+  if (!p.rader) {
+    fill_twiddles_of_length(t, p.L);
+    return;
+  }
+  const int L = p.L, M = L - 1;
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  fill_twiddles_of_length(t, M);
+  const long long g = primitive_root(L), ginv = pow_mod(g, L - 2, L);
+  // b_s = exp(-2 pi i g^-s / L); Bhat_k = (1/M) sum_s b_s exp(-2 pi i s k / M) (and with conj b)
+  std::vector<long double> br(M), bi(M);
+  long long e = 1;
+  for (int s = 0; s < M; ++s) {
+    const long double a = two_pi * (long double)e / (long double)L;
+    br[s] = cosl(a);
+    bi[s] = -sinl(a);
+    e = e * ginv % L;
+  }
+  for (int k = 0; k < M; ++k) {
+    long double fr = 0, fi = 0, ir = 0, ii = 0;
+    for (int s = 0; s < M; ++s) {
+      const long double a = two_pi * (long double)(((long long)s * k) % M) / (long double)M;
+      const long double c = cosl(a), sn = -sinl(a);
+      fr += br[s] * c - bi[s] * sn;
+      fi += br[s] * sn + bi[s] * c;
+      ir += br[s] * c + bi[s] * sn;  // conj(b) times the same root
+      ii += br[s] * sn - bi[s] * c;
+    }
+    t[M + k] = make_double2((double)(fr / M), (double)(fi / M));
+    t[2 * M + k] = make_double2((double)(ir / M), (double)(ii / M));
+  }
+  long long gr = 1, gi = 1;
+  for (int r = 0; r < M; ++r) {
+    t[3 * M + r] = make_double2((double)gr, (double)gi);
+    gr = gr * g % L;
+    gi = gi * ginv % L;
+  }
 }
 
 Tiling choose_tiling(const Grid& g) {
@@ -525,6 +616,10 @@ size_t z_pass_smem(const Grid& g, const Tiling& t) {
 long long z_pass_ctas(const Grid& g, const Tiling& t) { return (long long)g.nx * g.ny / t.lines_z; }
 static size_t y_smem(int L, int bk, int fields) {
   return ((size_t)2 * fields * bk * (L + 1) + L) * sizeof(double2);
+}
+// shared memory of a pass along an axis with a run-time plan (its tables may exceed L entries)
+static size_t y_smem_rt(const FftPlan& p, int bk, int fields) {
+  return ((size_t)2 * fields * bk * (p.L + 1) + p.tw_len) * sizeof(double2);
 }
 
 #define FH_SWITCH_LEN(v, MACRO) \
@@ -603,8 +698,8 @@ cudaError_t setup_fft_kernels(const Grid& g, const Tiling& t) {
     if ((e = allow_smem(k_inv_y_b<V>, y_smem(V, t.bk_y, 3)))) return e;    \
     break;
   if (g.py.L) {
-    if ((e = allow_smem(k_fwd_y<0>, y_smem(g.ny, t.bk_y, 3)))) return e;
-    if ((e = allow_smem(k_inv_y<0>, y_smem(g.ny, t.bk_y, 3)))) return e;
+    if ((e = allow_smem(k_fwd_y<0>, y_smem_rt(g.py, t.bk_y, 3)))) return e;
+    if ((e = allow_smem(k_inv_y<0>, y_smem_rt(g.py, t.bk_y, 3)))) return e;
   } else {
     FH_SWITCH_LEN(g.ny, YCASE)
   }
@@ -615,7 +710,7 @@ cudaError_t setup_fft_kernels(const Grid& g, const Tiling& t) {
     if ((e = allow_smem(k_x_ghat_b<V>, y_smem(V, t.bk_x, 6)))) return e;   \
     break;
   if (g.px.L) {
-    if ((e = allow_smem(k_x_ghat<0>, y_smem(g.nx, t.bk_x, 6)))) return e;
+    if ((e = allow_smem(k_x_ghat<0>, y_smem_rt(g.px, t.bk_x, 6)))) return e;
   } else {
     FH_SWITCH_LEN(g.nx, XCASE)
   }
@@ -651,7 +746,7 @@ cudaError_t launch_fwd_y(const Grid& g, const Tiling& t, double2* S, const doubl
   case V:                                                                                   \
     k_fwd_y<V><<<grid, kThreads, y_smem(V, t.bk_y, 3), s>>>(g, t.bk_y, S, tw, cg);          \
     break;
-  if (g.py.L) k_fwd_y<0><<<grid, kThreads, y_smem(g.ny, t.bk_y, 3), s>>>(g, t.bk_y, S, tw, cg);
+  if (g.py.L) k_fwd_y<0><<<grid, kThreads, y_smem_rt(g.py, t.bk_y, 3), s>>>(g, t.bk_y, S, tw, cg);
   else FH_SWITCH_LEN(g.ny, YL)
 #undef YL
   return cudaGetLastError();
@@ -665,7 +760,7 @@ cudaError_t launch_x_ghat(const Grid& g, const Tiling& t, double2* S, const doub
   case V:                                                                                          \
     k_x_ghat<V><<<grid, kThreads, y_smem(V, t.bk_x, 6), s>>>(g, t.bk_x, S, tw, scale, cg);         \
     break;
-  if (g.px.L) k_x_ghat<0><<<grid, kThreads, y_smem(g.nx, t.bk_x, 6), s>>>(g, t.bk_x, S, tw, scale, cg);
+  if (g.px.L) k_x_ghat<0><<<grid, kThreads, y_smem_rt(g.px, t.bk_x, 6), s>>>(g, t.bk_x, S, tw, scale, cg);
   else FH_SWITCH_LEN(g.nx, XL)
 #undef XL
   return cudaGetLastError();
@@ -679,7 +774,7 @@ cudaError_t launch_inv_y(const Grid& g, const Tiling& t, double2* S, const doubl
   case V:                                                                                   \
     k_inv_y<V><<<grid, kThreads, y_smem(V, t.bk_y, 3), s>>>(g, t.bk_y, S, tw, cg);          \
     break;
-  if (g.py.L) k_inv_y<0><<<grid, kThreads, y_smem(g.ny, t.bk_y, 3), s>>>(g, t.bk_y, S, tw, cg);
+  if (g.py.L) k_inv_y<0><<<grid, kThreads, y_smem_rt(g.py, t.bk_y, 3), s>>>(g, t.bk_y, S, tw, cg);
   else FH_SWITCH_LEN(g.ny, IYL)
 #undef IYL
   return cudaGetLastError();

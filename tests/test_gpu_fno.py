@@ -206,3 +206,24 @@ def test_inference_buffers_give_the_training_forward(fh):
             net.forward(ph, Fbar, q)
             out.append(np.stack([host(x) for x in q]))
     assert np.array_equal(out[0], out[1])
+
+
+def test_projection_wait_that_runs_out_reports_timeout(fh):
+    """The tcgen05 projection's bounded mbarrier wait: with the test hook set, no MMA is issued and nothing
+    signals the barrier, so the wait runs out (about a second); the forward pass must report FH_ERR_TIMEOUT,
+    and with the hook cleared the same network must run again and give the normal prediction."""
+    th = _theta(4)
+    phases, Fbar = _cells(5, 1)
+    with fh.Fno(*SHAPE, max_batch=1) as net:
+        net.set_params(th.cuda())
+        ph = [dev(phases[0])]
+        q0 = [torch.empty((9,) + SHAPE, dtype=torch.float32, device="cuda")]
+        net.forward(ph, Fbar, q0)
+        net.test_skip_mma(True)
+        with pytest.raises(fh.FhError) as exc:
+            net.forward(ph, Fbar, [torch.empty_like(q0[0])])
+        assert exc.value.code == fh.FH_ERR_TIMEOUT
+        net.test_skip_mma(False)
+        q1 = [torch.empty_like(q0[0])]
+        net.forward(ph, Fbar, q1)
+        assert torch.equal(q0[0], q1[0])

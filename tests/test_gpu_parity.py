@@ -98,7 +98,9 @@ PROJ_SHAPES = [(8, 8, 8), (4, 8, 16), (16, 4, 2), (2, 2, 2), (1, 4, 8), (32, 16,
                # even lengths with odd factors, extents above 256)
                (5, 7, 4), (13, 11, 2), (15, 21, 8), (9, 25, 6), (10, 14, 4), (199, 3, 2), (3, 199, 2),
                (169, 2, 2), (127, 4, 2), (121, 6, 2), (299, 2, 2), (512, 2, 2), (2, 512, 2), (384, 3, 2),
-               (40, 20, 16)]
+               (40, 20, 16),
+               # primes from 37 on by Rader's algorithm (inner lengths 36, 508 = 4 x 127 with a direct stage)
+               (37, 5, 2), (2, 37, 4), (509, 2, 2)]
 
 
 @pytest.mark.parametrize("shape", PROJ_SHAPES)
