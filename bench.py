@@ -717,9 +717,7 @@ def run_examples(args, world, rank, local):
         return {"grid": [n, n, 2], "s": t, "rc": rc, "newton": st["n_newton"], "cg": st["n_cg"],
                 "residuals": st["newton_residuals"], "Pbar_xy": float(pb[1])}
 
-    with torch.cuda.stream(stream), ClockSampler(local) as clk:
-        out["svk_square"] = dict(svk_solve(299), paper_s=19.5, paper_grid="299^2")
-        out["svk_scaling"] = [svk_solve(n) for n in (63, 127, 255, 511)]
+    def j2_solve():
         phase, params, plastic, Ebar = j2_config(199, 0, nz=2)
         with fh.Context(*phase.shape, stream=stream.cuda_stream) as ctx:
             hist = torch.zeros((10,) + phase.shape, dtype=torch.float64, device="cuda")
@@ -734,18 +732,32 @@ def run_examples(args, world, rank, local):
                                            allow=(fh.FH_ERR_NOT_CONVERGED,))
 
             t, (pb, st, rc) = timed(j2)
-            out["j2_biaxial"] = {"grid": [199, 199, 2], "s": t, "rc": rc, "newton": st["n_newton"], "cg": st["n_cg"],
-                                 "sigma_xx_yy": [float(pb[0]), float(pb[4])], "paper_s": 0.25,
-                                 "paper_grid": "199^2"}
+        return {"grid": [199, 199, 2], "s": t, "rc": rc, "newton": st["n_newton"], "cg": st["n_cg"],
+                "sigma_xx_yy": [float(pb[0]), float(pb[4])], "paper_s": 0.25, "paper_grid": "199^2"}
+
+    def eshelby_tangent():
         phase, f = centered_disk(199, 0.007, nz=2)
         params = np.array([[2.0, 1.0], [10.0, 5.0]])
         with fh.Context(*phase.shape, stream=stream.cuda_stream) as ctx:
             mat = fh.Material(fh.LINEAR_ELASTIC, phase, params)
             zero = torch.zeros((9,) + phase.shape, dtype=torch.float64, device="cuda")
             t, C = timed(lambda: ctx.fft_homog_tangent(mat, zero))
-            out["eshelby"] = {"grid": [199, 199, 2], "s": t, "fraction": f,
-                              "Cxxxx_Cyyyy_Cxyxy": [float(C[0, 0]), float(C[4, 4]), float(C[1, 1])],
-                              "paper_s": 4.0, "paper_grid": "199^2", "paper_table1": [4.035, 4.035, 1.010]}
+        return {"grid": [199, 199, 2], "s": t, "fraction": f,
+                "Cxxxx_Cyyyy_Cxyxy": [float(C[0, 0]), float(C[4, 4]), float(C[1, 1])],
+                "paper_s": 4.0, "paper_grid": "199^2", "paper_table1": [4.035, 4.035, 1.010]}
+
+    def wanted(name):
+        return args.only is None or name in args.only
+
+    with torch.cuda.stream(stream), ClockSampler(local) as clk:
+        if wanted("svk_square"):
+            out["svk_square"] = dict(svk_solve(299), paper_s=19.5, paper_grid="299^2")
+        if wanted("svk_scaling"):
+            out["svk_scaling"] = [svk_solve(n) for n in (63, 127, 255, 511)]
+        if wanted("j2_biaxial"):
+            out["j2_biaxial"] = j2_solve()
+        if wanted("eshelby"):
+            out["eshelby"] = eshelby_tangent()
     if rank != 0:
         return
     line = {"metric": "time of the paper's 2D examples (Sections 4.1.1, 4.1.2, 4.2.1) on one GPU",
@@ -1012,6 +1024,9 @@ def main():
                     help="config 4: SIMP 64^3 tangent and sensitivities (not the bench line)")
     ap.add_argument("--examples", action="store_true",
                     help="time the paper's 2D examples (SVK square, J2 disks, Eshelby tangent); not the bench line")
+    ap.add_argument("--only", nargs="+", default=None,
+                    choices=("svk_square", "svk_scaling", "j2_biaxial", "eshelby"),
+                    help="with --examples: run only these examples (for launch lists)")
     ap.add_argument("--warm-start", action="store_true",
                     help="learned warm start vs zero guess on held-out cells of --shape (not the bench line)")
     ap.add_argument("--shape", type=int, nargs=3, default=[N_GRID] * 3,

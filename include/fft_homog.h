@@ -227,6 +227,24 @@ FH_API int fft_homog_tangent(fh_ctx* ctx, const fh_material* mat, const double* 
 FH_API int fft_homog_sensitivity(fh_ctx* ctx, const fh_material* mat, const fh_options* opt, int i, int j,
                                  int k, int l, const double* dscale_dev, double* out_dev);
 
+/* Sensitivity of one homogenized stress entry to a voxel density field at a
+ * converged state, for laws whose voxel moduli are s(rho_v) times those of the
+ * voxel's phase (mat->scale holds s): P = s(rho) P0(F) (Section 4.4's
+ * gradients for finite strain; the linear law too). Differentiating the
+ * equilibrium of Eq. 1 and using the major symmetry of K, the adjoint solve is
+ * the unit response d_ab of fft_homog_tangent (one CG solve):
+ *   dPbar_ab / d rho_v = (1/N) (E_ab + d_ab)_v : P0(F_v) * ds/drho_v,
+ * with ab = 3*i + j and P0 by AD with the unscaled moduli.
+ *   F_dev       in   [9][N] converged field (H for small strain)
+ *   opt         CG tolerance (cg_tol, or 1e-2 newton_tol), max_cg, lengths; NULL = defaults
+ *   dscale_dev  in   device double[N], ds/drho per voxel
+ *   out_dev     out  device double[N], the sensitivity per voxel
+ * Returns FH_ERR_UNSUPPORTED for FH_J2, FH_ERR_NOT_CONVERGED if the CG solve
+ * hits max_cg. */
+FH_API int fft_homog_stress_sensitivity(fh_ctx* ctx, const fh_material* mat, const double* F_dev,
+                                        const fh_options* opt, int i, int j, const double* dscale_dev,
+                                        double* out_dev);
+
 /* Pick the tile shapes of the five projection passes for this context's grid
  * by timing them: z lines per CTA in the z passes, kz columns per CTA in the
  * y and x passes (a handful of candidates around the default, all within the

@@ -22,6 +22,17 @@ follows without an extra adjoint solve, because the cell problem is
 self-adjoint and d_ab, d_cd are stationary:
 
     dC_ab,cd / d rho_v = (1/N) (E_ab + d_ab)_v : C0_v : (E_cd + d_cd)_v * ds_v/d rho_v.
+
+For a hyperelastic law (finite strain) whose moduli a voxel scale multiplies,
+P = s(rho) P0(F), the first-order quantity of Section 4.4 is the sensitivity
+of the homogenized stress at the converged state. Differentiating the
+equilibrium G(P) = 0 gives the fluctuation response dF/d rho_v, and with the
+unit response d_ab of the linearised problem (K symmetric, d_ab compatible,
+K : (E_ab + d_ab) equilibrated) the adjoint argument leaves
+
+    dPbar_ab / d rho_v = (1/N) (E_ab + d_ab)_v : P0(F_v) * ds_v/d rho_v,
+
+one linear CG solve per component ab.
 """
 
 from __future__ import annotations
@@ -71,3 +82,17 @@ def sensitivity(phase, params, scale, dscale, ab: int, cd: int, cg_tol: float = 
     lam0, mu0 = voxel_lame(phase, params, None)
     K0 = mat.tangent(mat.LINEAR_ELASTIC, np.zeros((9,) + shape), lam0, mu0)
     return np.einsum("a...,a...->...", Ha, mat.apply_tangent(K0, Hc)) * dscale / phase.size
+
+
+def stress_sensitivity(phase, params, kind: int, F, scale, dscale, ab: int, cg_tol: float = 1e-12,
+                       max_cg: int = 5000, lengths=(1.0, 1.0, 1.0)) -> np.ndarray:
+    """dPbar_ab / d rho at every voxel at the converged state F (any hyperelastic law, or linear elasticity).
+
+    scale: per-voxel modulus multiplier s(rho); dscale: ds/d rho per voxel.
+    """
+    lam, mu = voxel_lame(phase, params, scale)
+    K = mat.tangent(kind, F, lam, mu)
+    H, _ = unit_response(K, ab, cg_tol, max_cg, lengths)
+    lam0, mu0 = voxel_lame(phase, params, None)
+    P0 = mat.stress(kind, F, lam0, mu0)
+    return np.einsum("a...,a...->...", H, P0) * dscale / phase.size

@@ -40,7 +40,7 @@ _ERR_NAMES = {1: "FH_ERR_ARG", 2: "FH_ERR_CUDA", 3: "FH_ERR_NOT_CONVERGED", 4: "
 
 # every symbol include/fft_homog.h declares
 EXPORTS = ["fh_default_options", "fh_create", "fh_destroy", "fh_last_error_string", "fh_constitutive",
-           "fh_project", "fh_matvec", "fft_homog_solve", "fh_profile_enable", "fh_profile_read", "fh_project_static", "fft_homog_tangent", "fft_homog_sensitivity",
+           "fh_project", "fh_matvec", "fft_homog_solve", "fh_profile_enable", "fh_profile_read", "fh_project_static", "fft_homog_tangent", "fft_homog_sensitivity", "fft_homog_stress_sensitivity",
            "fh_batch_create", "fh_batch_destroy", "fft_homog_solve_batched", "fh_autotune", "fh_probe_fp64",
            "fh_fno_param_count", "fh_fno_create", "fh_fno_destroy", "fh_fno_set_params", "fh_fno_forward",
            "fh_fno_loss_grad", "fh_fno_adam", "fh_fno_make_target", "fh_fno_warm_start", "fh_fno_test_skip_mma"]
@@ -125,6 +125,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.fft_homog_sensitivity.argtypes = [c_void_p, POINTER(FhMaterial), POINTER(FhOptions), c_int, c_int, c_int,
                                           c_int, c_void_p, c_void_p]
     lib.fft_homog_sensitivity.restype = c_int
+    lib.fft_homog_stress_sensitivity.argtypes = [c_void_p, POINTER(FhMaterial), c_void_p, POINTER(FhOptions), c_int,
+                                                 c_int, c_void_p, c_void_p]
+    lib.fft_homog_stress_sensitivity.restype = c_int
     lib.fh_batch_create.argtypes = [POINTER(c_void_p), POINTER(FhCell), c_int, c_void_p]
     lib.fh_batch_create.restype = c_int
     lib.fh_batch_destroy.argtypes = [c_void_p]
@@ -338,6 +341,13 @@ class Context:
         i, j, k, l = (int(v) for v in ijkl)
         _check(load().fft_homog_sensitivity(self._h, mat.c, ctypes.byref(options) if options is not None else None,
                                             i, j, k, l, _ptr(dscale), _ptr(out)))
+
+    def fft_homog_stress_sensitivity(self, mat: Material, F, ij, dscale, out, options: FhOptions | None = None):
+        """dPbar_ij / d rho per voxel at the converged state F into out (CUDA float64 tensor of the grid shape)."""
+        i, j = (int(v) for v in ij)
+        _check(load().fft_homog_stress_sensitivity(self._h, mat.c, _ptr(F),
+                                                   ctypes.byref(options) if options is not None else None, i, j,
+                                                   _ptr(dscale), _ptr(out)))
 
     def fft_homog_solve(self, mat: Material, Fbar, F, n_increments: int = 1, options: FhOptions | None = None,
                         capacity: int = 512, allow=()):

@@ -700,6 +700,42 @@ int fft_homog_sensitivity(fh_ctx* ctx, const fh_material* mat, const fh_options*
   return FH_OK;
 }
 
+int fft_homog_stress_sensitivity(fh_ctx* ctx, const fh_material* mat, const double* F_dev, const fh_options* opt_in,
+                                 int i, int j, const double* dscale_dev, double* out_dev) {
+  g_err[0] = 0;
+  if (!ctx || !F_dev || !dscale_dev || !out_dev) return fail(FH_ERR_ARG, "NULL argument");
+  int rc = check_material(mat);
+  if (rc) return rc;
+  if (mat->kind == FH_J2)
+    return fail(FH_ERR_UNSUPPORTED, "stress sensitivities are implemented for hyperelastic and linear elastic laws");
+  if (i < 0 || i > 2 || j < 0 || j > 2) return fail(FH_ERR_ARG, "tensor indices must be 0, 1 or 2");
+  fh_options opt;
+  if ((rc = options_or_default(opt_in, &opt))) return rc;
+  const double cg_tol = opt.cg_tol > 0.0 ? opt.cg_tol : 1e-2 * opt.newton_tol;
+  DeviceGuard dg(ctx->dev);
+  cudaStream_t s = ctx->stream;
+  const Grid g = grid_with_lengths(ctx, opt.lengths);
+  MatView mv;
+  if ((rc = upload_material(ctx, mat, &mv))) return rc;
+  FH_CUDA(cudaMemsetAsync(&ctx->sc->flags, 0, sizeof(int), s));
+  // tangent of the converged state with the scaled moduli, then the unit response d_ab
+  FH_CUDA(prof(ctx, kPConst, [&] {
+    return launch_constitutive(g, mv, F_dev, nullptr, ctx->K, ctx->partials, &ctx->sc->flags, s);
+  }));
+  int flags = 0;
+  if ((rc = read_flags(ctx, &flags))) return rc;
+  if (flags & kFlagNonPhysical) return fail(FH_ERR_NONPHYSICAL, "det F <= 0 or non-finite value in some voxel");
+  const int ab = 3 * i + j;
+  CgScalars host_cg{};
+  if ((rc = unit_response(ctx, g, mv, ab, cg_tol, opt, &host_cg))) return rc;
+  FH_CUDA(prof(ctx, kPContract, [&] {
+    return launch_stress_sensitivity(g, mv, F_dev, ctx->x, ab, dscale_dev, out_dev, s);
+  }));
+  FH_CUDA(cudaStreamSynchronize(s));
+  prof_flush(ctx);
+  return FH_OK;
+}
+
 namespace {
 
 // z lines per CTA must divide nx*ny; shared memory of a z pass must fit a CTA

@@ -148,6 +148,8 @@ long long kapply_sums_ctas(const Grid& g);
 cudaError_t launch_j2_update(const Grid& g, const MatView& m, const double* H, double* history, cudaStream_t s);
 cudaError_t launch_kapply_sums(const Grid& g, const double* K, const double* x, int cd, double* partials,
                                cudaStream_t s);
+cudaError_t launch_stress_sensitivity(const Grid& g, const MatView& m, const double* F, const double* x, int ab,
+                                      const double* dscale, double* out, cudaStream_t s);
 cudaError_t launch_sensitivity(const Grid& g, const MatView& m, const double* xa, int ab, const double* xc, int cd,
                                const double* dscale, double* out, cudaStream_t s);
 

@@ -629,6 +629,45 @@ cudaError_t launch_sensitivity(const Grid& g, const MatView& m, const double* xa
   return cudaGetLastError();
 }
 
+// Stress sensitivity dPbar_ab/drho_v = (1/N) (E_ab + d_ab)_v : P0(F_v) ds/drho_v:
+// P0 by AD of the law with the unscaled moduli of the voxel's phase (m.scale
+// is ignored), d_ab the unit response in x
+template <class Law>
+__global__ void __launch_bounds__(kThreads) k_stress_sensitivity(Grid g, MatView m, const double* __restrict__ F,
+                                                                const double* __restrict__ x, int ab,
+                                                                const double* __restrict__ dscale,
+                                                                double* __restrict__ out) {
+  const long long n = g.n;
+  const double inv_n = 1.0 / (double)n;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    double f[9], pv[9], kv[45];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) f[c] = F[c * n + v];
+    const int ph = m.phase[v];
+    ad::energy_derivatives<Law>(f, m.params[2 * ph], m.params[2 * ph + 1], pv, kv);
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc = fma(x[c * n + v] + (c == ab ? 1.0 : 0.0), pv[c], acc);
+    out[v] = acc * dscale[v] * inv_n;
+  }
+}
+
+cudaError_t launch_stress_sensitivity(const Grid& g, const MatView& m, const double* F, const double* x, int ab,
+                                      const double* dscale, double* out, cudaStream_t s) {
+  const unsigned grid = pointwise_grid(g);
+  switch (m.kind) {
+    case FH_LINEAR_ELASTIC:
+      k_stress_sensitivity<LinearElasticLaw><<<grid, kThreads, 0, s>>>(g, m, F, x, ab, dscale, out);
+      break;
+    case FH_NEO_HOOKEAN:
+      k_stress_sensitivity<NeoHookeanLaw><<<grid, kThreads, 0, s>>>(g, m, F, x, ab, dscale, out);
+      break;
+    case FH_SVK: k_stress_sensitivity<SVKLaw><<<grid, kThreads, 0, s>>>(g, m, F, x, ab, dscale, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // J2 history after a converged increment: plastic strain and cumulative
 // plastic strain of the return map at the converged total strain

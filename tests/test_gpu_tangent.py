@@ -148,3 +148,49 @@ def test_eshelby_2d_mode_matches_oracle_and_table1(fh, n):
     np.testing.assert_allclose([C[0, 0], C[4, 4], C[1, 1]], [num["Cxxxx"], num["Cyyyy"], num["Cxyxy"]],
                                rtol=TABLE1_RTOL)
     np.testing.assert_allclose([C[0, 0], C[1, 1]], dilute_estimate(f), rtol=2e-4)
+
+
+@pytest.mark.parametrize("kind,ij", [(1, (0, 1)), (2, (1, 1)), (0, (0, 1))])
+def test_stress_sensitivity_matches_oracle_euler_and_finite_differences(fh, kind, ij):
+    """dPbar_ij/drho per voxel at a converged finite-strain (or small-strain) state of a SIMP cell
+    (modulus scale rho^3): against the oracle's adjoint formula (1e-9), Euler's identity
+    sum_v rho_v dPbar/drho_v = 3 Pbar_ij, and central differences of two GPU solves (step 1e-4, whose
+    truncation error is of order (h/rho)^2 ~ 1e-7) on eight voxels (1e-5)."""
+    import torch
+
+    n = 12
+    rho = 0.35 + 0.65 * simp_config(n, seed=11)[2]  # densities in [0.35, 1]: modulus contrast 23
+    scale, dscale = rho ** 3, 3.0 * rho ** 2
+    phase = np.zeros((n, n, n), np.uint8)
+    params = np.array([[1.5, 1.0]])
+    if kind == 0:
+        Fbar = np.zeros(9)
+        Fbar[1] = Fbar[3] = 0.01
+        Fbar[0] = 0.005
+    else:
+        Fbar = shear_macro(0.05, finite=True)
+        Fbar[8] += 0.01
+    ab = 3 * ij[0] + ij[1]
+    opts = fh.default_options(newton_tol=1e-12, cg_tol=1e-13)
+    with fh.Context(n, n, n) as ctx:
+        def solve(sc):
+            F = torch.zeros((9, n, n, n), dtype=torch.float64, device="cuda")
+            pbar, _, _ = ctx.fft_homog_solve(fh.Material(kind, phase, params, scale=dev(sc)), Fbar, F, options=opts)
+            return pbar, F
+
+        pbar, F = solve(scale)
+        out = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+        ctx.fft_homog_stress_sensitivity(fh.Material(kind, phase, params, scale=dev(scale)), F, ij, dev(dscale), out,
+                                         options=opts)
+        s = host(out)
+        ref = homogenize.stress_sensitivity(phase, params, kind, host(F), scale, dscale, ab, cg_tol=1e-13)
+        assert np.abs(s - ref).max() < TOL * np.abs(ref).max()
+        np.testing.assert_allclose((s * rho).sum(), 3.0 * pbar[ab], rtol=1e-9)
+        h = 1e-4
+        rng = np.random.default_rng(5)
+        for v in rng.integers(0, n, size=(8, 3)):
+            v = tuple(int(t) for t in v)
+            rp = rho.copy(); rp[v] += h
+            rm = rho.copy(); rm[v] -= h
+            fd = (solve(rp ** 3)[0][ab] - solve(rm ** 3)[0][ab]) / (2 * h)
+            assert abs(fd - s[v]) <= 1e-5 * abs(s[v]) + 1e-7 * np.abs(s).max(), (v, fd, s[v])

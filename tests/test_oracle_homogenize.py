@@ -7,7 +7,12 @@
   and Voigt bounds for a random two-phase linear cell;
 * the voxel sensitivities equal central finite differences of the tangent in
   the voxel density, and satisfy Euler's identity for a modulus scale rho^3
-  (the tangent is homogeneous of degree one in the moduli).
+  (the tangent is homogeneous of degree one in the moduli);
+* the finite-strain stress sensitivities (neo-Hookean and SVK) equal central
+  finite differences of the homogenized stress of two full solves in the
+  voxel density, and satisfy Euler's identity sum_v rho_v dPbar/drho_v =
+  3 Pbar for a modulus scale rho^3 (the equilibrium field does not change when
+  every modulus is scaled alike, so Pbar is homogeneous of degree three in rho).
 """
 
 import numpy as np
@@ -99,3 +104,25 @@ def test_sensitivity_matches_finite_differences_and_euler_identity(ab, cd):
         Cp = homogenize.tangent(phase, params, 0, zero, scale=rp ** 3)[ab, cd]
         Cm = homogenize.tangent(phase, params, 0, zero, scale=rm ** 3)[ab, cd]
         np.testing.assert_allclose(s[v], (Cp - Cm) / (2 * h), rtol=1e-6, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind,ab", [(mat.NEO_HOOKEAN, 1), (mat.NEO_HOOKEAN, 0), (mat.SVK, 3)])
+def test_stress_sensitivity_matches_finite_differences_and_euler_identity(kind, ab):
+    shape = (4, 4, 4)
+    phase, params, rho, scale, dscale = simp_config(4, seed=7)
+    params = two_phase_table(1.5, 1.0, 5.0)[:1]
+    phase = np.zeros(shape, np.uint8)
+    Fbar = np.eye(3).reshape(9) + np.array([0.02, 0.05, 0.0, -0.01, 0.01, 0.02, 0.0, 0.01, -0.02])
+
+    def pbar(r):
+        return solver.solve(phase, params, kind, Fbar, newton_tol=1e-13, cg_tol=1e-14, scale=r ** 3).Pbar
+
+    ref = solver.solve(phase, params, kind, Fbar, newton_tol=1e-13, cg_tol=1e-14, scale=scale)
+    s = homogenize.stress_sensitivity(phase, params, kind, ref.F, scale, dscale, ab, cg_tol=1e-14)
+    np.testing.assert_allclose((s * rho).sum(), 3.0 * ref.Pbar[ab], rtol=1e-9)
+    h = 1e-5
+    for v in [(0, 0, 0), (1, 2, 3), (3, 1, 0)]:
+        rp = rho.copy(); rp[v] += h
+        rm = rho.copy(); rm[v] -= h
+        fd = (pbar(rp)[ab] - pbar(rm)[ab]) / (2 * h)
+        np.testing.assert_allclose(s[v], fd, rtol=1e-6, atol=1e-11)
