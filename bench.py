@@ -664,7 +664,7 @@ def run_warm_start(args, world, rank, local):
 
 
 def run_examples(args, world, rank, local):
-    """The paper's 2D examples on this library, as z-invariant cells (nz = 2, exact plane strain).
+    """The paper's 2D examples on this library, as cells one voxel thick (nz = 1: exact plane strain).
 
     svk_square   Section 4.1.1: St. Venant-Kirchhoff, stiff square L/3 at a corner, Fbar = I + 0.1 e_x e_y,
                  one increment, Newton tolerance 1e-5, CG tolerance 1e-8; 299 x 299 as in the paper.
@@ -703,7 +703,7 @@ def run_examples(args, world, rank, local):
         return e0.elapsed_time(e1) / 1e3 / args.steps, res
 
     def svk_solve(n):
-        phase, params, Fbar = svk_square_config(n, nz=2)
+        phase, params, Fbar = svk_square_config(n, nz=1)
         with fh.Context(*phase.shape, stream=stream.cuda_stream) as ctx:
             mat = fh.Material(fh.SVK, phase, params)
             F = torch.empty((9,) + phase.shape, dtype=torch.float64, device="cuda")
@@ -714,11 +714,11 @@ def run_examples(args, world, rank, local):
                 return ctx.fft_homog_solve(mat, Fbar, F, options=opts, allow=(fh.FH_ERR_NOT_CONVERGED,))
 
             t, (pb, st, rc) = timed(svk)
-        return {"grid": [n, n, 2], "s": t, "rc": rc, "newton": st["n_newton"], "cg": st["n_cg"],
+        return {"grid": [n, n, 1], "s": t, "rc": rc, "newton": st["n_newton"], "cg": st["n_cg"],
                 "residuals": st["newton_residuals"], "Pbar_xy": float(pb[1])}
 
     def j2_solve():
-        phase, params, plastic, Ebar = j2_config(199, 0, nz=2)
+        phase, params, plastic, Ebar = j2_config(199, 0, nz=1)
         with fh.Context(*phase.shape, stream=stream.cuda_stream) as ctx:
             hist = torch.zeros((10,) + phase.shape, dtype=torch.float64, device="cuda")
             mat = fh.Material(fh.J2, phase, params, plastic=plastic, history=hist)
@@ -732,17 +732,17 @@ def run_examples(args, world, rank, local):
                                            allow=(fh.FH_ERR_NOT_CONVERGED,))
 
             t, (pb, st, rc) = timed(j2)
-        return {"grid": [199, 199, 2], "s": t, "rc": rc, "newton": st["n_newton"], "cg": st["n_cg"],
+        return {"grid": [199, 199, 1], "s": t, "rc": rc, "newton": st["n_newton"], "cg": st["n_cg"],
                 "sigma_xx_yy": [float(pb[0]), float(pb[4])], "paper_s": 0.25, "paper_grid": "199^2"}
 
     def eshelby_tangent():
-        phase, f = centered_disk(199, 0.007, nz=2)
+        phase, f = centered_disk(199, 0.007, nz=1)
         params = np.array([[2.0, 1.0], [10.0, 5.0]])
         with fh.Context(*phase.shape, stream=stream.cuda_stream) as ctx:
             mat = fh.Material(fh.LINEAR_ELASTIC, phase, params)
             zero = torch.zeros((9,) + phase.shape, dtype=torch.float64, device="cuda")
             t, C = timed(lambda: ctx.fft_homog_tangent(mat, zero))
-        return {"grid": [199, 199, 2], "s": t, "fraction": f,
+        return {"grid": [199, 199, 1], "s": t, "fraction": f,
                 "Cxxxx_Cyyyy_Cxyxy": [float(C[0, 0]), float(C[4, 4]), float(C[1, 1])],
                 "paper_s": 4.0, "paper_grid": "199^2", "paper_table1": [4.035, 4.035, 1.010]}
 

@@ -15,11 +15,13 @@
  * Grid        nx x ny x nz voxels, N = nx*ny*nz. nx and ny are any length
  *             1..512 (2^a and 3*2^a up to 256 use compile-time radix-16/8/4/2/3
  *             plans; other lengths, e.g. the paper's odd grids 199 or 299,
- *             run-time plans whose prime factors above 3 are direct DFT
- *             stages); nz is even, and nz and nz/2 are 2^a or 3*2^a up to
- *             256. fh_project_static and batched solves take only the
- *             compile-time lengths on every axis. Box side lengths default
- *             to 1 (see fh_options.lengths).
+ *             run-time plans: prime lengths from 37 up by Rader's algorithm,
+ *             other prime factors above 3 as direct DFT stages); nz is 1 (a
+ *             plane problem: every field is z-invariant and xi_z = 0), or
+ *             even with nz and nz/2 of the form 2^a or 3*2^a up to 256.
+ *             fh_project_static and batched solves take only the
+ *             compile-time lengths on every axis and an even nz. Box side
+ *             lengths default to 1 (see fh_options.lengths).
  * Fields      device float64 arrays in structure-of-arrays order
  *             [9][nx][ny][nz] (z fastest); component c = 3*i + j holds the
  *             tensor entry T_ij (row-major 3x3; F_ij = dx_i/dX_j).

@@ -324,7 +324,7 @@ int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
   if (!out) return fail(FH_ERR_ARG, "out is NULL");
   if (!grid_extents_ok_any(nx, ny, nz))
     return fail(FH_ERR_ARG,
-                "grid %dx%dx%d: nx and ny must be 1..%d, nz even with nz and nz/2 of the form 2^a or 3*2^a up to 256",
+                "grid %dx%dx%d: nx and ny must be 1..%d, nz 1 or even with nz and nz/2 of the form 2^a or 3*2^a up to 256",
                 nx, ny, nz, kMaxNAny);
   fh_ctx* c = new fh_ctx();
   FH_CUDA(cudaGetDevice(&c->dev));

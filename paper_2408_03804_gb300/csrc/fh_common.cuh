@@ -66,10 +66,11 @@ __host__ __device__ constexpr bool grid_extents_ok(int nx, int ny, int nz) {
 }
 
 // the extents a solver context accepts: nx and ny any length 1 .. kMaxNAny
-// (run-time plans for those without a compile-time one), nz as above
+// (run-time plans for those without a compile-time one), nz as above or 1 (a
+// cell one voxel thick: plane problems without a redundant second layer)
 __host__ __device__ constexpr bool grid_extents_ok_any(int nx, int ny, int nz) {
-  return nx >= 1 && nx <= kMaxNAny && ny >= 1 && ny <= kMaxNAny && nz >= 2 && nz % 2 == 0 &&
-         fft_length_ok(nz) && fft_length_ok(nz / 2);
+  return nx >= 1 && nx <= kMaxNAny && ny >= 1 && ny <= kMaxNAny &&
+         (nz == 1 || (nz >= 2 && nz % 2 == 0 && fft_length_ok(nz) && fft_length_ok(nz / 2)));
 }
 
 // Run-time FFT plan of an axis whose length has no compile-time plan (see

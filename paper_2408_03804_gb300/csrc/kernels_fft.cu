@@ -37,92 +37,116 @@ __device__ __forceinline__ bool cg_done(const CgScalars* cg) { return cg != null
 // ---------------------------------------------------------------------------
 // forward z pass: real-to-complex along z of LB consecutive z lines
 // ---------------------------------------------------------------------------
+// tau = K : p (or the source field) at voxel gi; the CG modes first advance
+// x and p of the previous iteration at this voxel
+template <int MODE>
+__device__ __forceinline__ void z_pass_tau(long long gi, long long n, const double* __restrict__ src,
+                                           double* __restrict__ p, double* __restrict__ x,
+                                           const double* __restrict__ K, double alpha, double beta, double tau[9]) {
+  if constexpr (MODE == kZDirect) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) tau[c] = src[c * n + gi];
+  } else {
+    double pv[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      if constexpr (MODE == kZKApply) {
+        pv[c] = src[c * n + gi];
+      } else if constexpr (MODE == kZCgFirst) {
+        pv[c] = src[c * n + gi];
+        p[c * n + gi] = pv[c];
+      } else {
+        // the previous iteration's x += alpha p, then p = r + beta p
+        const double po = p[c * n + gi];
+        x[c * n + gi] = fma(alpha, po, x[c * n + gi]);
+        pv[c] = fma(beta, po, src[c * n + gi]);
+        p[c * n + gi] = pv[c];
+      }
+    }
+    double k[45];
+#pragma unroll
+    for (int s = 0; s < 45; ++s) k[s] = K[s * n + gi];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      double acc = k[sym_slot(a, 0)] * pv[0];
+#pragma unroll
+      for (int b = 1; b < 9; ++b) acc = fma(k[sym_slot(a, b)], pv[b], acc);
+      tau[a] = acc;
+    }
+  }
+}
+
+// M = nz / 2; M = 0 is a cell one voxel thick along z (nz = 1), whose
+// transform along z is the identity
 template <int M, int MODE>
 __device__ __forceinline__ void fwd_z_body(int cta, Grid g, int LB, const double* __restrict__ src,
                                                    double* __restrict__ p, double* __restrict__ x,
                                                    const double* __restrict__ K, const CgScalars* __restrict__ cg,
                                                    double2* __restrict__ S, const double2* __restrict__ tw) {
-  extern __shared__ double2 smem[];
-  constexpr int NZ = 2 * M;
-  double2* bufA = smem;
-  double2* bufB = smem + 9 * LB * M;
-  double2* twM = bufB + 9 * LB * M;   // length-M table (half-length FFT)
-  double2* twN = twM + M;              // first M/2 + 1 entries of the length-NZ table (unpack)
-  stage_twiddles<M>(twM, tw, M);
-  stage_twiddles<NZ>(twN, tw, M / 2 + 1);
-  double* ra = reinterpret_cast<double*>(bufA);
-  const long long line0 = (long long)cta * LB;
-  const long long v0 = line0 * NZ;
   const long long n = g.n;
   double beta = 0.0, alpha = 0.0;
   if constexpr (MODE == kZCg) {
     beta = cg->beta;
     alpha = cg->alpha;
   }
-
-  for (int t = threadIdx.x; t < LB * NZ; t += blockDim.x) {
-    const long long gi = v0 + t;
-    const int line = t / NZ, z = t % NZ;
-    double tau[9];
-    if constexpr (MODE == kZDirect) {
+  if constexpr (M == 0) {
+    // X_0 = 2 tau (the factor 2 every real-to-complex step of this pass
+    // carries); the j = z column is multiplied by xi_z = 0
+    const long long v0 = (long long)cta * LB;
+    for (int t = threadIdx.x; t < LB; t += blockDim.x) {
+      const long long gi = v0 + t;
+      double tau[9];
+      z_pass_tau<MODE>(gi, n, src, p, x, K, alpha, beta, tau);
 #pragma unroll
-      for (int c = 0; c < 9; ++c) tau[c] = src[c * n + gi];
-    } else {
-      double pv[9];
-#pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        if constexpr (MODE == kZKApply) {
-          pv[c] = src[c * n + gi];
-        } else if constexpr (MODE == kZCgFirst) {
-          pv[c] = src[c * n + gi];
-          p[c * n + gi] = pv[c];
-        } else {
-          // the previous iteration's x += alpha p, then p = r + beta p
-          const double po = p[c * n + gi];
-          x[c * n + gi] = fma(alpha, po, x[c * n + gi]);
-          pv[c] = fma(beta, po, src[c * n + gi]);
-          p[c * n + gi] = pv[c];
-        }
-      }
-      double k[45];
-#pragma unroll
-      for (int s = 0; s < 45; ++s) k[s] = K[s * n + gi];
-#pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        double acc = k[sym_slot(a, 0)] * pv[0];
-#pragma unroll
-        for (int b = 1; b < 9; ++b) acc = fma(k[sym_slot(a, b)], pv[b], acc);
-        tau[a] = acc;
-      }
+      for (int c = 0; c < 9; ++c) S[c * g.nspec + gi] = make_double2(c % 3 == 2 ? 0.0 : 2.0 * tau[c], 0.0);
     }
+  } else {
+    extern __shared__ double2 smem[];
+    constexpr int NZ = 2 * M;
+    double2* bufA = smem;
+    double2* bufB = smem + 9 * LB * M;
+    double2* twM = bufB + 9 * LB * M;   // length-M table (half-length FFT)
+    double2* twN = twM + M;              // first M/2 + 1 entries of the length-NZ table (unpack)
+    stage_twiddles<M>(twM, tw, M);
+    stage_twiddles<NZ>(twN, tw, M / 2 + 1);
+    double* ra = reinterpret_cast<double*>(bufA);
+    const long long line0 = (long long)cta * LB;
+    const long long v0 = line0 * NZ;
+
+    for (int t = threadIdx.x; t < LB * NZ; t += blockDim.x) {
+      const long long gi = v0 + t;
+      const int line = t / NZ, z = t % NZ;
+      double tau[9];
+      z_pass_tau<MODE>(gi, n, src, p, x, K, alpha, beta, tau);
 #pragma unroll
-    for (int c = 0; c < 9; ++c) ra[(c * LB + line) * NZ + z] = tau[c];
-  }
-
-  double2* R = fft_pencils<M, false, true>(bufA, bufB, PencilLayout{9 * LB, M, 1, 1, 1}, twM);
-
-  // unpack the half-length transform Z of z_m = x_2m + i x_2m+1 into
-  // 2 X_k = (Z_k + conj Z_{M-k}) - i w^k (Z_k - conj Z_{M-k}), k = 0..M
-  constexpr int KH = M / 2 + 1;
-  for (int t = threadIdx.x; t < 9 * LB * KH; t += blockDim.x) {
-    const int q = t / KH, k = t % KH;
-    const int c = q / LB, line = q % LB;
-    const double2* Zq = R + q * M;
-    const double2 zk = Zq[k];
-    const double2 zm = Zq[k == 0 ? 0 : M - k];
-    const double2 e = make_double2(zk.x + zm.x, zk.y - zm.y);  // Z_k + conj Z_{M-k}
-    const double2 o = make_double2(zk.x - zm.x, zk.y + zm.y);  // Z_k - conj Z_{M-k}
-    const double2 wo = cmul(o, twN[k]);
-    const double2 tt = make_double2(wo.y, -wo.x);               // -i w^k o
-    double2 xk = cadd(e, tt);
-    double2 xm = make_double2(e.x - tt.x, tt.y - e.y);         // conj(e - tt)
-    double2* out = S + (long long)c * g.nspec + (line0 + line) * g.nzh;
-    if (c % 3 == 2) {
-      xk = cscale(xk, wave_int(k, NZ) * g.sz);
-      xm = cscale(xm, wave_int(M - k, NZ) * g.sz);
+      for (int c = 0; c < 9; ++c) ra[(c * LB + line) * NZ + z] = tau[c];
     }
-    out[k] = xk;
-    if (M - k != k) out[M - k] = xm;
+
+    double2* R = fft_pencils<M, false, true>(bufA, bufB, PencilLayout{9 * LB, M, 1, 1, 1}, twM);
+
+    // unpack the half-length transform Z of z_m = x_2m + i x_2m+1 into
+    // 2 X_k = (Z_k + conj Z_{M-k}) - i w^k (Z_k - conj Z_{M-k}), k = 0..M
+    constexpr int KH = M / 2 + 1;
+    for (int t = threadIdx.x; t < 9 * LB * KH; t += blockDim.x) {
+      const int q = t / KH, k = t % KH;
+      const int c = q / LB, line = q % LB;
+      const double2* Zq = R + q * M;
+      const double2 zk = Zq[k];
+      const double2 zm = Zq[k == 0 ? 0 : M - k];
+      const double2 e = make_double2(zk.x + zm.x, zk.y - zm.y);  // Z_k + conj Z_{M-k}
+      const double2 o = make_double2(zk.x - zm.x, zk.y + zm.y);  // Z_k - conj Z_{M-k}
+      const double2 wo = cmul(o, twN[k]);
+      const double2 tt = make_double2(wo.y, -wo.x);               // -i w^k o
+      double2 xk = cadd(e, tt);
+      double2 xm = make_double2(e.x - tt.x, tt.y - e.y);         // conj(e - tt)
+      double2* out = S + (long long)c * g.nspec + (line0 + line) * g.nzh;
+      if (c % 3 == 2) {
+        xk = cscale(xk, wave_int(k, NZ) * g.sz);
+        xm = cscale(xm, wave_int(M - k, NZ) * g.sz);
+      }
+      out[k] = xk;
+      if (M - k != k) out[M - k] = xm;
+    }
   }
 }
 
@@ -300,49 +324,63 @@ __device__ __forceinline__ void inv_z_body(int cta, Grid g, int LB, const double
                                                    double* __restrict__ out, const double* __restrict__ p,
                                                    double* __restrict__ partials, const double2* __restrict__ tw,
                                                    const CgScalars* __restrict__ cg) {
-  extern __shared__ double2 smem[];
   __shared__ double red[32];
-  constexpr int NZ = 2 * M;
-  double2* bufA = smem;
-  double2* bufB = smem + 9 * LB * M;
-  double2* twM = bufB + 9 * LB * M;
-  double2* twN = twM + M;
-  stage_twiddles<M>(twM, tw, M);
-  stage_twiddles<NZ>(twN, tw, M / 2 + 1);
-  __syncthreads();
   const long long line0 = (long long)cta * LB;
   const long long n = g.n;
-  // pack Z_k = (X_k + conj X_{M-k}) + i w^-k (X_k - conj X_{M-k}); the
-  // imaginary parts of X_0 and X_M are dropped (complex-to-real semantics)
-  constexpr int KH = M / 2 + 1;
-  for (int t = threadIdx.x; t < 9 * LB * KH; t += blockDim.x) {
-    const int q = t / KH, k = t % KH;
-    const int c = q / LB, line = q % LB;
-    const double2* in = S + (long long)c * g.nspec + (line0 + line) * g.nzh;
-    double2 xk = in[k], xm = in[M - k];
-    if (k == 0) {
-      xk.y = 0.0;
-      xm.y = 0.0;
-    }
-    const double2 a = make_double2(xk.x + xm.x, xk.y - xm.y);
-    const double2 bb = make_double2(xk.x - xm.x, xk.y + xm.y);
-    const double2 bw = cmulc(bb, twN[k]);
-    const double2 u = make_double2(-bw.y, bw.x);  // i w^-k b
-    bufA[q * M + k] = cadd(a, u);
-    if (k != 0 && M - k != k) bufA[q * M + (M - k)] = make_double2(a.x - u.x, u.y - a.y);
-  }
-  double2* R = fft_pencils<M, true, true>(bufA, bufB, PencilLayout{9 * LB, M, 1, 1, 1}, twM);
-  const double* rr = reinterpret_cast<const double*>(R);
   double acc = 0.0;
-  for (int t = threadIdx.x; t < LB * NZ; t += blockDim.x) {
-    const int line = t / NZ, z = t % NZ;
-    const long long gi = (line0 + line) * NZ + z;
+  if constexpr (M == 0) {
+    // nz = 1: the real part of X_0 (complex-to-real semantics)
+    for (int t = threadIdx.x; t < LB; t += blockDim.x) {
+      const long long gi = line0 + t;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      const double yv = rr[(c * LB + line) * NZ + z];
-      out[c * n + gi] = yv;
-      if constexpr (MODE == kIZDot) acc = fma(p[c * n + gi], yv, acc);
-      if constexpr (MODE == kIZRhs) acc = fma(yv, yv, acc);
+      for (int c = 0; c < 9; ++c) {
+        const double yv = S[c * g.nspec + gi].x;
+        out[c * n + gi] = yv;
+        if constexpr (MODE == kIZDot) acc = fma(p[c * n + gi], yv, acc);
+        if constexpr (MODE == kIZRhs) acc = fma(yv, yv, acc);
+      }
+    }
+  } else {
+    extern __shared__ double2 smem[];
+    constexpr int NZ = 2 * M;
+    double2* bufA = smem;
+    double2* bufB = smem + 9 * LB * M;
+    double2* twM = bufB + 9 * LB * M;
+    double2* twN = twM + M;
+    stage_twiddles<M>(twM, tw, M);
+    stage_twiddles<NZ>(twN, tw, M / 2 + 1);
+    __syncthreads();
+    // pack Z_k = (X_k + conj X_{M-k}) + i w^-k (X_k - conj X_{M-k}); the
+    // imaginary parts of X_0 and X_M are dropped (complex-to-real semantics)
+    constexpr int KH = M / 2 + 1;
+    for (int t = threadIdx.x; t < 9 * LB * KH; t += blockDim.x) {
+      const int q = t / KH, k = t % KH;
+      const int c = q / LB, line = q % LB;
+      const double2* in = S + (long long)c * g.nspec + (line0 + line) * g.nzh;
+      double2 xk = in[k], xm = in[M - k];
+      if (k == 0) {
+        xk.y = 0.0;
+        xm.y = 0.0;
+      }
+      const double2 a = make_double2(xk.x + xm.x, xk.y - xm.y);
+      const double2 bb = make_double2(xk.x - xm.x, xk.y + xm.y);
+      const double2 bw = cmulc(bb, twN[k]);
+      const double2 u = make_double2(-bw.y, bw.x);  // i w^-k b
+      bufA[q * M + k] = cadd(a, u);
+      if (k != 0 && M - k != k) bufA[q * M + (M - k)] = make_double2(a.x - u.x, u.y - a.y);
+    }
+    double2* R = fft_pencils<M, true, true>(bufA, bufB, PencilLayout{9 * LB, M, 1, 1, 1}, twM);
+    const double* rr = reinterpret_cast<const double*>(R);
+    for (int t = threadIdx.x; t < LB * NZ; t += blockDim.x) {
+      const int line = t / NZ, z = t % NZ;
+      const long long gi = (line0 + line) * NZ + z;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const double yv = rr[(c * LB + line) * NZ + z];
+        out[c * n + gi] = yv;
+        if constexpr (MODE == kIZDot) acc = fma(p[c * n + gi], yv, acc);
+        if constexpr (MODE == kIZRhs) acc = fma(yv, yv, acc);
+      }
     }
   }
   if constexpr (MODE != kIZOut) {
@@ -643,9 +681,10 @@ static size_t y_smem_rt(const FftPlan& p, int bk, int fields) {
     default:                     \
       return cudaErrorInvalidValue; \
   }
-// half lengths of the real-to-complex axis (nz/2 <= 128)
+// half lengths of the real-to-complex axis (nz/2 <= 128; 0 for nz = 1)
 #define FH_SWITCH_HALF(v, MACRO) \
   switch (v) {                   \
+    MACRO(0)                     \
     MACRO(1)                     \
     MACRO(2)                     \
     MACRO(3)                     \

@@ -394,7 +394,7 @@ def corner_square(n: int, frac: float = 1.0 / 3.0, nz: int = 1) -> np.ndarray:
     return phase
 
 
-def svk_square_config(n: int = 256, nz: int = 2):
+def svk_square_config(n: int = 256, nz: int = 1):
     """St. Venant-Kirchhoff cell with a stiff square of side L/3 at a corner, under simple shear.
 
     Matrix (lambda, mu) = (2, 1), inclusion 10x; Fbar = I + 0.1 e_x (x) e_y.

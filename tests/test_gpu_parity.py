@@ -100,7 +100,9 @@ PROJ_SHAPES = [(8, 8, 8), (4, 8, 16), (16, 4, 2), (2, 2, 2), (1, 4, 8), (32, 16,
                (169, 2, 2), (127, 4, 2), (121, 6, 2), (299, 2, 2), (512, 2, 2), (2, 512, 2), (384, 3, 2),
                (40, 20, 16),
                # primes from 37 on by Rader's algorithm (inner lengths 36, 508 = 4 x 127 with a direct stage)
-               (37, 5, 2), (2, 37, 4), (509, 2, 2)]
+               (37, 5, 2), (2, 37, 4), (509, 2, 2),
+               # cells one voxel thick (nz = 1: plane problems, the z transform is the identity)
+               (8, 8, 1), (199, 5, 1), (12, 37, 1), (1, 6, 1), (1, 1, 1)]
 
 
 @pytest.mark.parametrize("shape", PROJ_SHAPES)
@@ -120,7 +122,7 @@ def test_projection_matches_oracle(fh, torch, shape):
 
 
 @pytest.mark.parametrize("kind", [1, 2, 0])
-@pytest.mark.parametrize("shape", [(8, 8, 8), (4, 16, 32), (15, 7, 8)])
+@pytest.mark.parametrize("shape", [(8, 8, 8), (4, 16, 32), (15, 7, 8), (15, 7, 1)])
 def test_matvec_matches_oracle_stored_and_jvp(fh, torch, kind, shape):
     n = int(np.prod(shape))
     F = random_deformation(n, seed=5, scale=0.1, identity=omat.FINITE_STRAIN[kind]).reshape((9,) + shape)
@@ -209,7 +211,7 @@ def test_radix3_grid_solve_matches_oracle(fh, torch):
     assert np.abs(Fg - ref.F).max() < FIELD_TOL * np.abs(ref.F - Fbar.reshape(9, 1, 1, 1)).max()
 
 
-@pytest.mark.parametrize("shape", [(15, 21, 8), (27, 25, 2)])
+@pytest.mark.parametrize("shape", [(15, 21, 8), (27, 25, 2), (27, 25, 1)])
 def test_odd_grid_solve_matches_oracle(fh, torch, shape):
     """Odd x/y extents (the paper's grids are odd, Section 4.1.1): run-time FFT plans, no Nyquist index."""
     if shape[2] > 2:
@@ -318,13 +320,14 @@ def test_solve_is_deterministic(fh, torch):
     assert res[0][2] == res[1][2]
 
 
-def test_svk_square_inclusion_2d_matches_oracle(fh, torch):
-    """Section 4.1.1's St. Venant-Kirchhoff cell in the 2D mode (48 x 48 x 2): stiff square of side L/3
-    at a corner, simple shear 0.1, one increment, Newton tolerance 1e-5 and CG tolerance 1e-8 as in the
-    paper. The residual of every Newton iteration and the CG counts agree with the oracle."""
+@pytest.mark.parametrize("nz", [2, 1])
+def test_svk_square_inclusion_2d_matches_oracle(fh, torch, nz):
+    """Section 4.1.1's St. Venant-Kirchhoff cell in the 2D mode (48 x 48 x nz, z-invariant): stiff square
+    of side L/3 at a corner, simple shear 0.1, one increment, Newton tolerance 1e-5 and CG tolerance 1e-8
+    as in the paper. The residual of every Newton iteration and the CG counts agree with the oracle."""
     from rve_inputs import svk_square_config
 
-    phase, params, Fbar = svk_square_config(48, nz=2)
+    phase, params, Fbar = svk_square_config(48, nz=nz)
     Fg, pbar, stats, _, ref = _solve_both(fh, torch, phase, params, 2, Fbar, 1, 1e-5, cg_tol=1e-8)
     assert stats["n_newton"] == len(ref.newton_residuals) >= 2
     np.testing.assert_allclose(stats["newton_residuals"], ref.newton_residuals, rtol=1e-6)
@@ -363,3 +366,27 @@ def test_launch_accounting_books_idle_launches_apart(fh, torch, check_every):
         idle = prof["idle"][0]
         assert idle > 0 and idle % 8 == 0
         assert (idle // 8 + st["n_cg"]) % check_every == 0
+
+
+@pytest.mark.parametrize("kind", [2, 0])
+def test_plane_cell_one_voxel_thick_equals_two_layer_cell(fh, torch, kind):
+    """A z-invariant cell solved with nz = 1 and with nz = 2 (two identical layers): the second layer
+    only adds a zero Nyquist plane, so both give the same in-plane field, the same Pbar and the same
+    Newton iteration count (CG counts within one: the norms sum the layers in another order)."""
+    from rve_inputs import svk_square_config
+
+    res = []
+    for nz in (2, 1):
+        phase, params, Fbar = svk_square_config(45, nz=nz)
+        if kind == 0:
+            Fbar = np.zeros(9)
+            Fbar[1] = Fbar[3] = 0.01
+        with fh.Context(*phase.shape) as ctx:
+            F = torch.zeros((9,) + phase.shape, dtype=torch.float64, device="cuda")
+            pbar, st, _ = ctx.fft_homog_solve(fh.Material(kind, phase, params), Fbar, F, n_increments=1,
+                                              options=fh.default_options(newton_tol=1e-10))
+            res.append((host(F)[..., 0], pbar, st["n_newton"], st["cg_iterations"]))
+    (F2, p2, n2, c2), (F1, p1, n1, c1) = res
+    assert n1 == n2 and all(abs(a - b) <= 1 for a, b in zip(c1, c2))
+    assert np.abs(F1 - F2).max() < 1e-12
+    np.testing.assert_allclose(p1, p2, rtol=1e-12, atol=1e-14)

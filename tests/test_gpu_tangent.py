@@ -129,14 +129,14 @@ def test_simp_64_voigt_tangent_and_sensitivity_vs_finite_differences(fh):
         assert max(errs) < 1e-4, (max(errs), float(np.median(errs)))
 
 
-@pytest.mark.parametrize("n", [192, 199])
-def test_eshelby_2d_mode_matches_oracle_and_table1(fh, n):
-    """2D plane strain as a z-invariant n x n x 2 cell (Section 4.2.1, Table 1; the paper's grid is 199^2)."""
+@pytest.mark.parametrize("n,nz", [(192, 2), (199, 2), (199, 1)])
+def test_eshelby_2d_mode_matches_oracle_and_table1(fh, n, nz):
+    """2D plane strain as a z-invariant n x n x nz cell (Section 4.2.1, Table 1; the paper's grid is 199^2)."""
     import json
 
     from test_oracle_eshelby import GOLDEN, TABLE1_RTOL, dilute_estimate, eshelby_cell
 
-    phase, f = eshelby_cell(n, nz=2)
+    phase, f = eshelby_cell(n, nz=nz)
     params = np.array([[2.0, 1.0], [10.0, 5.0]])
     zero = np.zeros((9,) + phase.shape)
     C_ref = homogenize.tangent(phase, params, 0, zero, cg_tol=1e-12)

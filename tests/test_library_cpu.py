@@ -52,7 +52,7 @@ def test_default_options(lib):
     assert o.check_every == 16 and list(o.lengths) == [1.0, 1.0, 1.0]
 
 
-@pytest.mark.parametrize("shape", [(4, 4, 1), (4, 4, 5), (513, 4, 4), (4, 1024, 4), (4, 4, 10), (0, 4, 4),
+@pytest.mark.parametrize("shape", [(4, 4, 3), (4, 4, 5), (513, 4, 4), (4, 1024, 4), (4, 4, 10), (0, 4, 4),
                                    (4, 0, 4), (4, 4, 18), (4, 4, 512)])
 def test_create_rejects_unsupported_grids_without_touching_the_device(lib, shape):
     h = ctypes.c_void_p()
