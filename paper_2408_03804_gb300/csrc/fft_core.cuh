@@ -309,12 +309,15 @@ __device__ __forceinline__ void stockham_stage_rt(const double2* __restrict__ sr
 }
 
 // One stage of odd radix R (any R >= 5) as a direct DFT: with the inputs
-// twiddled, S_m = v_m + v_{R-m} and D_m = v_m - v_{R-m} (m = 1 .. (R-1)/2),
-// X_r = v_0 + sum_m S_m cos(2 pi r m / R) -+ i D_m sin(2 pi r m / R) (minus
-// sign forward). Two phases, each spread over all threads: one (butterfly, m)
-// pair per thread forms S_m and D_m and writes them back over the source
-// entries (each butterfly owns its R entries; the source buffer is dead after
-// the stage), then one (butterfly, r) output per thread.
+// twiddled, S_m = v_m + v_{R-m} and D_m = v_m - v_{R-m} (m = 1 .. (R-1)/2).
+// With P_r = sum_m S_m cos(2 pi r m / R) and Q_r = sum_m D_m sin(2 pi r m / R),
+// X_r = v_0 + P_r -+ i Q_r and X_{R-r} = v_0 + P_r +- i Q_r (upper signs
+// forward), so one pass over m gives a pair of outputs. Two phases, each
+// spread over all threads: one (butterfly, m) pair per thread forms S_m and
+// D_m and writes them back over the source entries (each butterfly owns its
+// R entries; the source buffer is dead after the stage), then one
+// (butterfly, r) per thread, r = 0 .. (R-1)/2, writes X_0 (r = 0) or the
+// pair X_r, X_{R-r}.
 template <bool INV, bool JFAST>
 __device__ __forceinline__ void stockham_stage_odd(double2* __restrict__ src, double2* __restrict__ dst,
                                                    const PencilLayout& lay, const double2* __restrict__ tw, int L,
@@ -341,33 +344,43 @@ __device__ __forceinline__ void stockham_stage_odd(double2* __restrict__ src, do
     s[(j + (R - m) * NB) * lay.j_stride] = csub(a, b);
   }
   __syncthreads();
-  // phase 2: outputs
-  for (int t = threadIdx.x; t < nq * NB * R; t += blockDim.x) {
-    const int r = t % R, qj = t / R;
+  // phase 2: X_0, or the pair X_r, X_{R-r}
+  const int H1 = H + 1;
+  for (int t = threadIdx.x; t < nq * NB * H1; t += blockDim.x) {
+    const int r = t % H1, qj = t / H1;
     const int q = pencil_of(JFAST ? qj / NB : qj % nq, lay);
     const int j = JFAST ? qj % NB : qj / nq;
     const double2* s = src + q * lay.q_stride;
     const double2 v0 = s[j * lay.j_stride];
-    double ar = v0.x, ai = v0.y;
-    int e = 0;
-    for (int m = 1; m <= H; ++m) {
-      const double2 sm = s[(j + m * NB) * lay.j_stride];
-      if (r == 0) {
+    const int base = (j / NS) * NS * R + j % NS;
+    double2* d = dst + q * lay.q_stride;
+    if (r == 0) {
+      double ar = v0.x, ai = v0.y;
+      for (int m = 1; m <= H; ++m) {
+        const double2 sm = s[(j + m * NB) * lay.j_stride];
         ar += sm.x;
         ai += sm.y;
-        continue;
       }
+      d[base * lay.j_stride] = make_double2(ar, ai);
+      continue;
+    }
+    double pr = 0.0, pi = 0.0, qr = 0.0, qi = 0.0;
+    int e = 0;
+    for (int m = 1; m <= H; ++m) {
       e += r;
       if (e >= R) e -= R;
       const double2 w = tw[e * NB];  // (cos, -sin) of 2 pi e / R
-      const double c = w.x, sn = INV ? w.y : -w.y;
+      const double2 sm = s[(j + m * NB) * lay.j_stride];
       const double2 dm = s[(j + (R - m) * NB) * lay.j_stride];
-      ar = fma(sm.x, c, fma(dm.y, sn, ar));
-      ai = fma(sm.y, c, fma(-dm.x, sn, ai));
+      pr = fma(sm.x, w.x, pr);
+      pi = fma(sm.y, w.x, pi);
+      qr = fma(dm.x, -w.y, qr);
+      qi = fma(dm.y, -w.y, qi);
     }
-    const int base = (j / NS) * NS * R + j % NS;
-    double2* d = dst + q * lay.q_stride;
-    d[(base + r * NS) * lay.j_stride] = make_double2(ar, ai);
+    // -i Q = (Q.y, -Q.x) forward, +i Q = (-Q.y, Q.x) inverse
+    const double sr = INV ? -qi : qi, si = INV ? qr : -qr;
+    d[(base + r * NS) * lay.j_stride] = make_double2(v0.x + pr + sr, v0.y + pi + si);
+    d[(base + (R - r) * NS) * lay.j_stride] = make_double2(v0.x + pr - sr, v0.y + pi - si);
   }
 }
 
@@ -455,6 +468,18 @@ __device__ __noinline__ double2* fft_pencils_rt(double2* a, double2* b, const Pe
                                                 const FftPlan p) {
   if (p.rader) return rader_pencils<INV, JFAST>(a, b, lay, tw, p);
   return run_stages_rt<INV, JFAST>(a, b, lay, tw, p.L, p.n, p.r);
+}
+
+// twiddles of the y (AX = 1) or x (AX = 0) axis into shared memory: the
+// compile-time table of L, or the run-time plan's table
+template <int L, int AX>
+__device__ __forceinline__ void stage_axis_twiddles(double2* dst, const double2* __restrict__ tw, const Grid& g) {
+  if constexpr (L > 0) {
+    stage_twiddles<L>(dst, tw, L);
+  } else {
+    const FftPlan& p = AX ? g.py : g.px;
+    for (int i = threadIdx.x; i < p.tw_len; i += blockDim.x) dst[i] = tw[p.tw_off + i];
+  }
 }
 
 // compile-time plan when L > 0, the run-time plan p otherwise

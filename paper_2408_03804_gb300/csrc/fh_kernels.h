@@ -34,6 +34,9 @@ struct CgScalars {
   int products;     // matrix-vector products whose result was used (it, plus one after a breakdown)
 };
 
+// launches of a CG loop queued after its convergence return at once
+__device__ __forceinline__ bool cg_done(const CgScalars* cg) { return cg != nullptr && cg->done != 0; }
+
 // per-cell pointers of a batched launch (device array, one entry per cell of a
 // group of equal grids); `stop` is the cell's skip flag for this launch
 struct CellView {
@@ -101,6 +104,14 @@ cudaError_t launch_inv_y(const Grid& g, const Tiling& t, double2* S, const doubl
                          cudaStream_t s);
 cudaError_t launch_inv_z(const Grid& g, const Tiling& t, int mode, const double2* S, double* out, const double* p,
                          double* partials, const double2* tw, const CgScalars* cg, cudaStream_t s);
+
+// the y and x passes of a plane cell (nz = 1; kernels_plane.cu), which the
+// launches above dispatch to
+cudaError_t setup_plane_kernels(const Grid& g);
+cudaError_t launch_plane_fwd_y(const Grid& g, double2* S, const double2* tw, const CgScalars* cg, cudaStream_t s);
+cudaError_t launch_plane_x_ghat(const Grid& g, double2* S, const double2* tw, double scale, const CgScalars* cg,
+                                cudaStream_t s);
+cudaError_t launch_plane_inv_y(const Grid& g, double2* S, const double2* tw, const CgScalars* cg, cudaStream_t s);
 
 cudaError_t launch_fwd_z_batch(const Grid& g, const Tiling& t, int mode, const CellView* cells, int n_cells,
                                const double2* tw, cudaStream_t s);

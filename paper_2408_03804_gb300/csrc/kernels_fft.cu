@@ -32,7 +32,6 @@
 
 namespace fh {
 
-__device__ __forceinline__ bool cg_done(const CgScalars* cg) { return cg != nullptr && cg->done != 0; }
 
 // ---------------------------------------------------------------------------
 // forward z pass: real-to-complex along z of LB consecutive z lines
@@ -90,15 +89,17 @@ __device__ __forceinline__ void fwd_z_body(int cta, Grid g, int LB, const double
     alpha = cg->alpha;
   }
   if constexpr (M == 0) {
-    // X_0 = 2 tau (the factor 2 every real-to-complex step of this pass
-    // carries); the j = z column is multiplied by xi_z = 0
+    // X_0 = tau, real (the plane y pass supplies the factor 2 of a
+    // real-to-complex step); the j = z columns, multiplied by xi_z = 0, are
+    // not read by the plane passes and are not written
     const long long v0 = (long long)cta * LB;
     for (int t = threadIdx.x; t < LB; t += blockDim.x) {
       const long long gi = v0 + t;
       double tau[9];
       z_pass_tau<MODE>(gi, n, src, p, x, K, alpha, beta, tau);
 #pragma unroll
-      for (int c = 0; c < 9; ++c) S[c * g.nspec + gi] = make_double2(c % 3 == 2 ? 0.0 : 2.0 * tau[c], 0.0);
+      for (int c = 0; c < 9; ++c)
+        if (c % 3 != 2) S[c * g.nspec + gi] = make_double2(tau[c], 0.0);
     }
   } else {
     extern __shared__ double2 smem[];
@@ -153,18 +154,6 @@ __device__ __forceinline__ void fwd_z_body(int cta, Grid g, int LB, const double
 // ---------------------------------------------------------------------------
 // forward y pass: row i, columns j = x, y, z along y; combine W_i
 // ---------------------------------------------------------------------------
-// twiddles of the y (AX = 1) or x (AX = 0) axis into shared memory: the
-// compile-time table of L, or the run-time plan's table
-template <int L, int AX>
-__device__ __forceinline__ void stage_axis_twiddles(double2* dst, const double2* __restrict__ tw, const Grid& g) {
-  if constexpr (L > 0) {
-    stage_twiddles<L>(dst, tw, L);
-  } else {
-    const FftPlan& p = AX ? g.py : g.px;
-    for (int i = threadIdx.x; i < p.tw_len; i += blockDim.x) dst[i] = tw[p.tw_off + i];
-  }
-}
-
 template <int L>
 __device__ __forceinline__ void fwd_y_body(int cta, Grid g, int BK, double2* __restrict__ S,
                                                    const double2* __restrict__ tw, const CgScalars* __restrict__ cg) {
@@ -648,6 +637,7 @@ Tiling choose_tiling(const Grid& g) {
 }
 
 size_t z_pass_smem(const Grid& g, const Tiling& t) {
+  if (g.nz == 1) return 0;  // identity along z: no staging
   const int M = g.nz / 2;
   return ((size_t)9 * t.lines_z * g.nz + M + M / 2 + 1) * sizeof(double2);
 }
@@ -710,6 +700,10 @@ static cudaError_t allow_smem(Kern k, size_t bytes) {
 
 cudaError_t setup_fft_kernels(const Grid& g, const Tiling& t) {
   cudaError_t e = cudaSuccess;
+  if (g.nz == 1) {
+    // plane cell: the z passes need no shared memory, the y and x passes are kernels_plane.cu's
+    return setup_plane_kernels(g);
+  }
   const size_t zs = z_pass_smem(g, t);
   const int M = g.nz / 2;
 #define ZCASE(V)                                                      \
@@ -779,6 +773,7 @@ cudaError_t launch_fwd_z(const Grid& g, const Tiling& t, int mode, const double*
 
 cudaError_t launch_fwd_y(const Grid& g, const Tiling& t, double2* S, const double2* tw, const CgScalars* cg,
                          cudaStream_t s) {
+  if (g.nz == 1) return launch_plane_fwd_y(g, S, tw, cg, s);
   const int NC = (g.nzh + t.bk_y - 1) / t.bk_y;
   const unsigned grid = (unsigned)((long long)g.nx * 3 * NC);
 #define YL(V)                                                                               \
@@ -793,6 +788,7 @@ cudaError_t launch_fwd_y(const Grid& g, const Tiling& t, double2* S, const doubl
 
 cudaError_t launch_x_ghat(const Grid& g, const Tiling& t, double2* S, const double2* tw, double scale,
                           const CgScalars* cg, cudaStream_t s) {
+  if (g.nz == 1) return launch_plane_x_ghat(g, S, tw, scale, cg, s);
   const int NC = (g.nzh + t.bk_x - 1) / t.bk_x;
   const unsigned grid = (unsigned)((long long)g.ny * NC);
 #define XL(V)                                                                                      \
@@ -807,6 +803,7 @@ cudaError_t launch_x_ghat(const Grid& g, const Tiling& t, double2* S, const doub
 
 cudaError_t launch_inv_y(const Grid& g, const Tiling& t, double2* S, const double2* tw, const CgScalars* cg,
                          cudaStream_t s) {
+  if (g.nz == 1) return launch_plane_inv_y(g, S, tw, cg, s);
   const int NC = (g.nzh + t.bk_y - 1) / t.bk_y;
   const unsigned grid = (unsigned)((long long)g.nx * 3 * NC);
 #define IYL(V)                                                                              \
