@@ -856,7 +856,10 @@ def run_ours(args, world, rank, local):
     shape = tuple(args.shape)
     phase, params, Fbar = neo_hookean_config(shape, seed=rank)
     n = phase.size
-    stream = torch.cuda.current_stream()
+    # a stream of our own, current for every torch op below: the library replays
+    # its CG chunks as CUDA graphs, which the legacy default stream cannot capture
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     ctx = fh.Context(*shape, stream=stream.cuda_stream)
     mat = fh.Material(fh.NEO_HOOKEAN, phase, params)
     F = torch.empty((9,) + shape, dtype=torch.float64, device=dev)

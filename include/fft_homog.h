@@ -97,6 +97,10 @@ extern "C" {
 #define FH_INIT_REFERENCE 0
 #define FH_INIT_GIVEN 1
 
+/* ---- how the kernels of a CG loop are launched (fh_options.launch_mode) ---- */
+#define FH_LAUNCH_GRAPH 0
+#define FH_LAUNCH_PLAIN 1
+
 typedef struct fh_ctx fh_ctx;
 
 typedef struct fh_material {
@@ -121,7 +125,12 @@ typedef struct fh_options {
   int init;             /* FH_INIT_REFERENCE or FH_INIT_GIVEN */
   int tangent_mode;     /* FH_TANGENT_STORED or FH_TANGENT_JVP */
   int check_every;      /* CG iterations queued between host convergence reads (>= 1) */
-  int reserved;
+  int launch_mode;      /* FH_LAUNCH_GRAPH: each chunk of check_every CG iterations is the replay
+                           of a CUDA graph captured on the context's stream (captured again when
+                           the material, the field pointer or the grid scale changes; plain
+                           launches on the legacy default stream, on a stream the caller is
+                           capturing and while fh_profile_enable timing is on); FH_LAUNCH_PLAIN:
+                           every kernel launched from the host. Results are identical. */
   double lengths[3];    /* box side lengths L_x, L_y, L_z (> 0) */
 } fh_options;
 
@@ -133,11 +142,13 @@ typedef struct fh_stats {
   double* newton_residuals;   /* host array: e after each Newton iteration, or NULL */
   int* cg_iterations;         /* host array: CG products of each Newton iteration, or NULL */
   double time_ms;             /* wall time of the call */
+  int cg_graph_replays;       /* chunks of CG iterations run as replays of a captured graph */
+  int cg_graph_captures;      /* graph captures the call needed (0 when the context's graphs were current) */
 } fh_stats;
 
 /* Fill *o with the defaults: newton_tol 1e-8, cg_tol 0 (= 1e-2 newton_tol),
  * max_newton 50, max_cg 5000, FH_INIT_REFERENCE, FH_TANGENT_STORED,
- * check_every 16, lengths (1, 1, 1). */
+ * check_every 16, FH_LAUNCH_GRAPH, lengths (1, 1, 1). */
 FH_API void fh_default_options(fh_options* o);
 
 /* Create a context for an nx x ny x nz grid whose work runs on cuda_stream

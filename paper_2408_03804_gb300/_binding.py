@@ -35,6 +35,9 @@ TANGENT_JVP = 1
 INIT_REFERENCE = 0
 INIT_GIVEN = 1
 
+LAUNCH_GRAPH = 0
+LAUNCH_PLAIN = 1
+
 _ERR_NAMES = {1: "FH_ERR_ARG", 2: "FH_ERR_CUDA", 3: "FH_ERR_NOT_CONVERGED", 4: "FH_ERR_NONPHYSICAL",
               5: "FH_ERR_TIMEOUT", 6: "FH_ERR_UNSUPPORTED"}
 
@@ -63,7 +66,7 @@ class FhMaterial(ctypes.Structure):
 
 class FhOptions(ctypes.Structure):
     _fields_ = [("newton_tol", c_double), ("cg_tol", c_double), ("max_newton", c_int), ("max_cg", c_int),
-                ("init", c_int), ("tangent_mode", c_int), ("check_every", c_int), ("reserved", c_int),
+                ("init", c_int), ("tangent_mode", c_int), ("check_every", c_int), ("launch_mode", c_int),
                 ("lengths", c_double * 3)]
 
 
@@ -75,7 +78,7 @@ class FhCell(ctypes.Structure):
 class FhStats(ctypes.Structure):
     _fields_ = [("n_newton", c_int), ("n_cg", c_int), ("capacity", c_int), ("n_recorded", c_int),
                 ("newton_residuals", POINTER(c_double)), ("cg_iterations", POINTER(c_int)),
-                ("time_ms", c_double)]
+                ("time_ms", c_double), ("cg_graph_replays", c_int), ("cg_graph_captures", c_int)]
 
 
 _lib = None
@@ -363,7 +366,8 @@ class Context:
                                     pbar.ctypes.data_as(POINTER(c_double)), ctypes.byref(st))
         _check(rc, allow=allow)
         stats = {"n_newton": st.n_newton, "n_cg": st.n_cg, "time_ms": st.time_ms,
-                 "newton_residuals": res[:st.n_recorded].tolist(), "cg_iterations": cgi[:st.n_recorded].tolist()}
+                 "newton_residuals": res[:st.n_recorded].tolist(), "cg_iterations": cgi[:st.n_recorded].tolist(),
+                 "cg_graph_replays": st.cg_graph_replays, "cg_graph_captures": st.cg_graph_captures}
         return pbar, stats, rc
 
 

@@ -65,6 +65,26 @@ struct ProfPair {
   cudaEvent_t a, b;  // null when events are off
 };
 
+// What a captured chunk of CG iterations depends on besides the context's own
+// buffers: a replay is valid while these are unchanged (compared bytewise;
+// zero-filled first so that padding compares equal)
+struct CgGraphKey {
+  Grid g;
+  Tiling t;
+  MatView mv;
+  const double* F;
+  double c_mv;
+  int stored, first, check_every, n_iz, n_upd;
+};
+
+// One chunk of check_every CG iterations captured as a CUDA graph, with the
+// class and iteration (0 .. check_every - 1) of each kernel it launches
+struct CgGraph {
+  CgGraphKey key;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<ProfPair> nodes;
+};
+
 struct fh_ctx {
   int dev = 0;
   // launch accounting (fh_profile_enable / fh_profile_read)
@@ -90,6 +110,12 @@ struct fh_ctx {
   double* params = nullptr;   // [256][2] Lame pairs, then [256][2] J2 (yield stress, hardening)
   double2* tw = nullptr;      // twiddle tables
   DevScalars* sc = nullptr;
+  // graph replay of the CG loop: chunk 0 starts a loop, chunk 1 continues it;
+  // off after a failed capture (e.g. the legacy default stream)
+  CgGraph cg_graph[2];
+  bool graphs_ok = true;
+  long long min_ctas = 0;     // CTAs per pass the default tiling aims for (two per SM)
+  long long graph_replays = 0, graph_captures = 0;
 };
 
 namespace {
@@ -216,11 +242,57 @@ int run_projection(fh_ctx* ctx, const Grid& g, int zmode, const double* src, dou
   return FH_OK;
 }
 
+// Capture `queue` (the launches of one chunk of CG iterations, tagged
+// 0 .. check_every - 1) into G. A stream that cannot be captured (the legacy
+// default stream) turns graph replay off for the context, and a stream the
+// caller is capturing gets plain launches; either way G.exec stays null and
+// the chunk runs as plain launches.
+template <class Queue>
+int capture_cg_chunk(fh_ctx* ctx, CgGraph& G, const CgGraphKey& key, Queue&& queue) {
+  cudaStream_t s = ctx->stream;
+  if (G.exec) {
+    cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+  }
+  G.nodes.clear();
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->graphs_ok = false;
+    return FH_OK;
+  }
+  if (st != cudaStreamCaptureStatusNone) return FH_OK;  // the caller is capturing: plain launches into its graph
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->graphs_ok = false;
+    return FH_OK;
+  }
+  const int rc = queue();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &graph);
+  G.nodes.swap(ctx->tagged);
+  ctx->tagged.clear();
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(FH_ERR_CUDA, "CG graph capture: %s", cudaGetErrorString(e));
+  const cudaError_t ei = cudaGraphInstantiate(&G.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    G.exec = nullptr;
+    return fail(FH_ERR_CUDA, "CG graph instantiation: %s", cudaGetErrorString(ei));
+  }
+  G.key = key;
+  ctx->graph_captures++;
+  return FH_OK;
+}
+
 // Conjugate gradients on G(K : d) = b (Alg. 1 inner solve). On entry ctx->r
 // holds b and ctx->partials the per-CTA sums of b . b from the inverse z pass
 // that produced it; on return ctx->x holds d and *host_cg the final scalars.
 int run_cg(fh_ctx* ctx, const Grid& g, const MatView& mv, const double* F_dev, bool stored, double cg_tol,
-           int max_cg, int check_every, CgScalars* host_cg) {
+           int max_cg, int check_every, bool plain, CgScalars* host_cg) {
   cudaStream_t s = ctx->stream;
   CgScalars* cg = &ctx->sc->cg;
   const int n_iz = (int)z_pass_ctas(g, ctx->tiling);
@@ -242,23 +314,62 @@ int run_cg(fh_ctx* ctx, const Grid& g, const MatView& mv, const double* F_dev, b
       }
     }
   } tag_reset{ctx};
-  while (true) {
-    for (int k = 0; k < check_every; ++k, ++launched) {
-      ctx->cg_tag = launched;
-      const int zmode = launched == 0 ? kZCgFirst : kZCg;
+  // queue CG iterations base .. base + count - 1, tagged base-relative
+  auto queue_iterations = [&](int base, int count, int tag0) -> int {
+    for (int k = 0; k < count; ++k) {
+      ctx->cg_tag = tag0 + k;
+      const int zmode = base + k == 0 ? kZCgFirst : kZCg;
+      int rc2;
       if (stored) {
-        if ((rc = run_projection(ctx, g, zmode, ctx->r, ctx->p, ctx->K, c_mv, kIZDot, ctx->y, ctx->p, cg, ctx->x)))
-          return rc;
+        if ((rc2 = run_projection(ctx, g, zmode, ctx->r, ctx->p, ctx->K, c_mv, kIZDot, ctx->y, ctx->p, cg, ctx->x)))
+          return rc2;
       } else {
         FH_CUDA(prof(ctx, kPJvp, [&] {
           return launch_jvp(g, mv, F_dev, ctx->r, ctx->p, ctx->x, ctx->P, zmode, cg, &ctx->sc->flags, s);
         }));
-        if ((rc = run_projection(ctx, g, kZDirect, ctx->P, nullptr, nullptr, c_mv, kIZDot, ctx->y, ctx->p, cg)))
-          return rc;
+        if ((rc2 = run_projection(ctx, g, kZDirect, ctx->P, nullptr, nullptr, c_mv, kIZDot, ctx->y, ctx->p, cg)))
+          return rc2;
       }
       FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_alpha(cg, ctx->partials, n_iz, s); }));
       FH_CUDA(prof(ctx, kPCgUpdate, [&] { return launch_cg_update(g, cg, ctx->r, ctx->y, ctx->partials, s); }));
       FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_beta(cg, ctx->partials, n_upd, s); }));
+    }
+    return FH_OK;
+  };
+  while (true) {
+    // Without per-launch timing, a chunk runs as a replay of a captured
+    // graph (one launch instead of about 8 * check_every); the graph is
+    // captured again only when what its kernels are given changes.
+    bool replayed = false;
+    if (!plain && !ctx->prof && ctx->graphs_ok) {
+      CgGraphKey key;
+      memset(&key, 0, sizeof key);
+      key.g = g;
+      key.t = ctx->tiling;
+      key.mv = mv;
+      key.F = stored ? nullptr : F_dev;  // only the jvp form reads F in the loop
+      key.c_mv = c_mv;
+      key.stored = stored;
+      key.first = launched == 0;
+      key.check_every = check_every;
+      key.n_iz = n_iz;
+      key.n_upd = n_upd;
+      CgGraph& G = ctx->cg_graph[key.first ? 0 : 1];
+      if (!G.exec || memcmp(&G.key, &key, sizeof key) != 0) {
+        if ((rc = capture_cg_chunk(ctx, G, key, [&] { return queue_iterations(launched, check_every, 0); })))
+          return rc;
+      }
+      if (G.exec) {
+        FH_CUDA(cudaGraphLaunch(G.exec, s));
+        ctx->graph_replays++;
+        for (const ProfPair& q : G.nodes) ctx->tagged.push_back(ProfPair{q.cls, launched + q.tag, nullptr, nullptr});
+        launched += check_every;
+        replayed = true;
+      }
+    }
+    if (!replayed) {
+      if ((rc = queue_iterations(launched, check_every, launched))) return rc;
+      launched += check_every;
     }
     ctx->cg_tag = -1;
     FH_CUDA(cudaMemcpyAsync(host_cg, cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
@@ -302,6 +413,7 @@ void fh_default_options(fh_options* o) {
   o->init = FH_INIT_REFERENCE;
   o->tangent_mode = FH_TANGENT_STORED;
   o->check_every = 16;
+  o->launch_mode = FH_LAUNCH_GRAPH;
   o->lengths[0] = o->lengths[1] = o->lengths[2] = 1.0;
 }
 
@@ -344,7 +456,11 @@ int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
   tw_len += g.px.tw_len;
   g.py = make_fft_plan(ny, tw_len);
   tw_len += g.py.tw_len;
-  c->tiling = choose_tiling(g);
+  // default tiles, smaller on small grids so that every pass keeps two CTAs per SM busy
+  int sms = 0;
+  FH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+  c->min_ctas = 2LL * sms;
+  c->tiling = choose_tiling(g, c->min_ctas);
   const size_t f9 = (size_t)9 * g.n * sizeof(double);
   long long np = 9LL * constitutive_ctas(g);
   np = std::max(np, (long long)nx * ny);  // z passes with one line per CTA (any autotuned tiling)
@@ -385,6 +501,8 @@ void fh_destroy(fh_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   prof_flush(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (CgGraph& G : c->cg_graph)
+    if (G.exec) cudaGraphExecDestroy(G.exec);
   cudaFree(c->S);
   cudaFree(c->x);
   cudaFree(c->r);
@@ -477,7 +595,8 @@ int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9], i
   if (opt_in) opt = *opt_in;
   else fh_default_options(&opt);
   if (n_increments < 1) return fail(FH_ERR_ARG, "n_increments must be >= 1");
-  if (!(opt.newton_tol > 0.0) || opt.max_newton < 1 || opt.max_cg < 0 || opt.check_every < 1)
+  if (!(opt.newton_tol > 0.0) || opt.max_newton < 1 || opt.max_cg < 0 || opt.check_every < 1 ||
+      (opt.launch_mode != FH_LAUNCH_GRAPH && opt.launch_mode != FH_LAUNCH_PLAIN))
     return fail(FH_ERR_ARG, "invalid options");
   if (opt.init != FH_INIT_REFERENCE && opt.init != FH_INIT_GIVEN) return fail(FH_ERR_ARG, "invalid init");
   if (opt.tangent_mode != FH_TANGENT_STORED && opt.tangent_mode != FH_TANGENT_JVP)
@@ -494,6 +613,7 @@ int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9], i
   if ((rc = upload_material(ctx, mat, &mv))) return rc;
   FH_CUDA(cudaMemsetAsync(&ctx->sc->flags, 0, sizeof(int), s));
   const bool stored = opt.tangent_mode == FH_TANGENT_STORED;
+  const long long replays0 = ctx->graph_replays, captures0 = ctx->graph_captures;
 
   // start tensor and load step (a1)
   double start[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -538,14 +658,15 @@ int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9], i
         return rc;
       // CG on G(K : dF) = b (a4, a5); scalars stay on the device
       CgScalars host_cg{};
-      if ((rc = run_cg(ctx, g, mv, F_dev, stored, cg_tol, opt.max_cg, opt.check_every, &host_cg))) return rc;
+      if ((rc = run_cg(ctx, g, mv, F_dev, stored, cg_tol, opt.max_cg, opt.check_every,
+                         opt.launch_mode == FH_LAUNCH_PLAIN, &host_cg))) return rc;
       // Newton update and convergence test (a6)
       FH_CUDA(prof(ctx, kPNewton, [&] { return launch_newton_update(g, F_dev, ctx->x, ctx->partials, s); }));
       FH_CUDA(prof(ctx, kPReduce, [&] { return launch_sum_partials(ctx->partials, n_nu, 1, ctx->sc->sums, s); }));
       double dd = 0.0;
       FH_CUDA(cudaMemcpyAsync(&dd, ctx->sc->sums, sizeof(double), cudaMemcpyDeviceToHost, s));
       FH_CUDA(cudaStreamSynchronize(s));
-        prof_flush(ctx);
+      prof_flush(ctx);
       const double e = std::sqrt(dd) / denom;
       if (stats && stats->newton_residuals && n_newton < stats->capacity) stats->newton_residuals[n_newton] = e;
       if (stats && stats->cg_iterations && n_newton < stats->capacity) stats->cg_iterations[n_newton] = host_cg.it;
@@ -581,12 +702,14 @@ int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9], i
     for (int c = 0; c < 9; ++c) Pbar_out[c] = sums[c] / N;
   }
   FH_CUDA(cudaStreamSynchronize(s));
-        prof_flush(ctx);
+  prof_flush(ctx);
   if (stats) {
     stats->n_newton = n_newton;
     stats->n_cg = n_cg;
     stats->n_recorded = stats->capacity < n_newton ? stats->capacity : n_newton;
     stats->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    stats->cg_graph_replays = (int)(ctx->graph_replays - replays0);
+    stats->cg_graph_captures = (int)(ctx->graph_captures - captures0);
   }
   return status;
 }
@@ -596,7 +719,9 @@ namespace {
 int options_or_default(const fh_options* in, fh_options* o) {
   if (in) *o = *in;
   else fh_default_options(o);
-  if (!(o->newton_tol > 0.0) || o->max_cg < 0 || o->check_every < 1) return fail(FH_ERR_ARG, "invalid options");
+  if (!(o->newton_tol > 0.0) || o->max_cg < 0 || o->check_every < 1 ||
+      (o->launch_mode != FH_LAUNCH_GRAPH && o->launch_mode != FH_LAUNCH_PLAIN))
+    return fail(FH_ERR_ARG, "invalid options");
   if (!lengths_ok(o->lengths)) return fail(FH_ERR_ARG, "box lengths must be positive");
   return FH_OK;
 }
@@ -610,7 +735,8 @@ int unit_response(fh_ctx* ctx, const Grid& g, const MatView& mv, int cd, double 
   int rc = run_projection(ctx, g, kZKApply, ctx->y, nullptr, ctx->K, -1.0 / (2.0 * (double)g.n), kIZRhs, ctx->r,
                           nullptr, nullptr);
   if (rc) return rc;
-  if ((rc = run_cg(ctx, g, mv, nullptr, true, cg_tol, opt.max_cg, opt.check_every, host_cg))) return rc;
+  if ((rc = run_cg(ctx, g, mv, nullptr, true, cg_tol, opt.max_cg, opt.check_every,
+                    opt.launch_mode == FH_LAUNCH_PLAIN, host_cg))) return rc;
   if (host_cg->done != 1)
     return fail(FH_ERR_NOT_CONVERGED, "tangent CG %s after %d products (column %d)",
                 host_cg->done == 2 ? "hit max_cg" : "broke down", host_cg->it, cd);
@@ -760,7 +886,7 @@ int fh_autotune(fh_ctx* ctx, int reps, double* best_ms, int chosen[3]) {
   DeviceGuard dg(ctx->dev);
   cudaStream_t s = ctx->stream;
   const Grid& g = ctx->g;
-  const Tiling base = choose_tiling(g);
+  const Tiling base = choose_tiling(g, ctx->min_ctas);
   std::vector<Tiling> cand;
   for (int fz : {1, 2, 4}) {
     for (int fy : {1, 2}) {

@@ -89,7 +89,9 @@ void fill_twiddles_of_length(double2* t, int L);
 // the tables of a run-time plan into t[p.tw_len] (host memory)
 void fill_plan_tables(double2* t, const FftPlan& p);
 
-Tiling choose_tiling(const Grid& g);
+// tiles of the five passes; smaller tiles where the default ones would leave
+// fewer than min_ctas CTAs in a pass (0: the default tiles)
+Tiling choose_tiling(const Grid& g, long long min_ctas = 0);
 size_t z_pass_smem(const Grid& g, const Tiling& t);
 long long z_pass_ctas(const Grid& g, const Tiling& t);
 

@@ -616,22 +616,32 @@ void fill_plan_tables(double2* t, const FftPlan& p) {
   }
 }
 
-Tiling choose_tiling(const Grid& g) {
+Tiling choose_tiling(const Grid& g, long long min_ctas) {
   Tiling t;
   const long long lines = (long long)g.nx * g.ny;
-  // z lines per CTA: the largest divisor of nx*ny not above 512 / nz
+  // z lines per CTA: the largest divisor of nx*ny not above 512 / nz that
+  // leaves at least min_ctas CTAs (one line per CTA if none does; a plane
+  // cell keeps its full tile: one voxel per line)
   int lb = 512 / g.nz;
   if (lb < 1) lb = 1;
   if (lb > lines) lb = (int)lines;
   while (lines % lb) --lb;
+  while (g.nz > 1 && lb > 1 && lines / lb < min_ctas) {
+    --lb;
+    while (lines % lb) --lb;
+  }
   t.lines_z = lb;
+  // kz columns per CTA of the y and x passes, likewise
+  auto chunks = [&](int bk) { return (long long)((g.nzh + bk - 1) / bk); };
   int by = 512 / g.ny;
   if (by < 1) by = 1;
   if (by > g.nzh) by = g.nzh;
+  while (by > 1 && 3LL * g.nx * chunks(by) < min_ctas) --by;
   t.bk_y = by;
   int bx = 256 / g.nx;
   if (bx < 1) bx = 1;
   if (bx > g.nzh) bx = g.nzh;
+  while (bx > 1 && (long long)g.ny * chunks(bx) < min_ctas) --bx;
   t.bk_x = bx;
   return t;
 }

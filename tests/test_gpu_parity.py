@@ -390,3 +390,38 @@ def test_plane_cell_one_voxel_thick_equals_two_layer_cell(fh, torch, kind):
     assert n1 == n2 and all(abs(a - b) <= 1 for a, b in zip(c1, c2))
     assert np.abs(F1 - F2).max() < 1e-12
     np.testing.assert_allclose(p1, p2, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("shape,kind,check_every", [((16, 16, 16), 0, 16), ((12, 10, 8), 1, 5), ((27, 25, 1), 2, 16)])
+def test_graph_replayed_cg_equals_plain_launches(fh, torch, shape, kind, check_every):
+    """Without per-launch timing each chunk of check_every CG iterations is the replay of a captured CUDA
+    graph; with timing on (fh_profile_enable), or with launch_mode FH_LAUNCH_PLAIN, the same kernels are
+    launched one by one. All give the same field bit for bit, the same iteration counts and the same
+    per-class launch counts."""
+    phase = centered_sphere(shape, 0.25) if shape[2] > 1 else _phase(shape, 4)
+    params = two_phase_table(1.5, 1.0, 10.0)
+    Fbar = shear_macro(0.02, finite=kind != 0)
+    res = []
+    stream = torch.cuda.Stream()  # graphs are not captured on the legacy default stream
+    with torch.cuda.stream(stream), fh.Context(*shape, stream=stream.cuda_stream) as ctx:
+        mat = fh.Material(kind, phase, params)
+        F = torch.empty((9,) + shape, dtype=torch.float64, device="cuda")
+        for timed, mode in ((False, fh.LAUNCH_GRAPH), (True, fh.LAUNCH_GRAPH), (False, fh.LAUNCH_PLAIN),
+                            (False, fh.LAUNCH_GRAPH)):
+            ctx.fh_profile_enable(timed)
+            F.zero_()
+            pbar, st, _ = ctx.fft_homog_solve(mat, Fbar, F, n_increments=2,
+                                              options=fh.default_options(newton_tol=1e-10, check_every=check_every,
+                                                                         launch_mode=mode))
+            counts = {k: v[0] for k, v in ctx.fh_profile_read().items()}
+            res.append((host(F), pbar, st["cg_iterations"], counts))
+            replayed = not timed and mode == fh.LAUNCH_GRAPH
+            assert (st["cg_graph_replays"] > 0) == replayed
+            if replayed:
+                # one replay per chunk of check_every iterations of every CG loop
+                assert st["cg_graph_replays"] == sum(max(1, -(-c // check_every)) for c in st["cg_iterations"])
+        # the second graph solve replays the graphs the first one captured
+        assert st["cg_graph_captures"] == 0
+    for F, pbar, cg, counts in res[1:]:
+        assert np.array_equal(F, res[0][0]) and np.array_equal(pbar, res[0][1])
+        assert cg == res[0][2] and counts == res[0][3]
