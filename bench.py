@@ -767,6 +767,78 @@ def run_examples(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_df64(args, world, rank, local):
+    """The double-float option of the CG matrix-vector product (FH_ARITH_DF64) on the 128^3 bench cell:
+    time-to-solve with each arithmetic (CUDA events, W warm-up and K timed solves each, alternating), the
+    per-kernel split of one profiled solve each, and how far the two solutions are apart (Pbar relative,
+    fluctuation field max-relative). Not the bench line: the method as stated is FP64 throughout."""
+    import torch
+
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    import paper_2408_03804_gb300 as fh
+    from paper_2408_03804_gb300 import build as fhbuild
+    from rve_inputs import neo_hookean_config
+
+    fhbuild.build()
+    fh.load()
+    dev = torch.device("cuda", local)
+    shape = tuple(args.shape)
+    phase, params, Fbar = neo_hookean_config(shape, seed=rank)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    res = {}
+    with fh.Context(*shape, stream=stream.cuda_stream) as ctx, ClockSampler(local) as clk:
+        mat = fh.Material(fh.NEO_HOOKEAN, phase, params)
+        F = {a: torch.empty((9,) + shape, dtype=torch.float64, device=dev) for a in (fh.ARITH_FP64, fh.ARITH_DF64)}
+        opts = {a: fh.default_options(newton_tol=NEWTON_TOL, matvec_arith=a) for a in F}
+        for _ in range(max(args.warmup, 1)):
+            for a in F:
+                ctx.fft_homog_solve(mat, Fbar, F[a], n_increments=N_INC, options=opts[a])
+        times = {a: [] for a in F}
+        stats = {}
+        for _ in range(args.steps):
+            for a in F:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pbar, st, _ = ctx.fft_homog_solve(mat, Fbar, F[a], n_increments=N_INC, options=opts[a])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times[a].append(e0.elapsed_time(e1) / 1e3)
+                stats[a] = (pbar, st)
+        prof = {}
+        for a in F:
+            ctx.fh_profile_enable(True)
+            ctx.fft_homog_solve(mat, Fbar, F[a], n_increments=N_INC, options=opts[a])
+            prof[a] = ctx.fh_profile_read()
+            ctx.fh_profile_enable(False)
+        fl = {a: F[a].cpu().numpy() - Fbar.reshape(9, 1, 1, 1) for a in F}
+    if rank != 0:
+        return
+    p64, pdf = stats[fh.ARITH_FP64][0], stats[fh.ARITH_DF64][0]
+    d = np.abs(fl[fh.ARITH_DF64] - fl[fh.ARITH_FP64]).max(axis=(1, 2, 3)) / np.maximum(
+        np.abs(fl[fh.ARITH_FP64]).max(axis=(1, 2, 3)), 1e-300)
+    names = {fh.ARITH_FP64: "fp64", fh.ARITH_DF64: "df64"}
+    out = {}
+    for a in F:
+        cls = {c: v for c, v in prof[a].items() if v[0] and c != "idle"}
+        cg_its = cls["fwd_z"][0] - stats[a][1]["n_newton"]
+        it_ms = sum(cls[c][1] / cls[c][0] for c in ("fwd_z", "fwd_y", "x_ghat", "inv_y", "inv_z", "cg_update"))
+        out[names[a]] = {"s": statistics.median(times[a]), "runs_s": times[a], "newton": stats[a][1]["n_newton"],
+                         "cg": stats[a][1]["n_cg"], "ms_per_cg_iteration": it_ms,
+                         "kernels_ms_per_launch": {c: v[1] / v[0] for c, v in cls.items()},
+                         "profiled_cg_products": cg_its}
+    line = {"metric": "128^3 neo-Hookean time-to-solve with the CG transforms in double-float (FH_ARITH_DF64) "
+                      "beside FP64", "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 1), "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": f"{shape[0]}x{shape[1]}x{shape[2]} neo-Hookean RSA spheres (seed 0), 5 "
+                                   "increments to shear 0.05, Newton tol 1e-8"},
+            "arith": out, "speedup": out["fp64"]["s"] / out["df64"]["s"],
+            "pbar_rel_diff": float(np.abs(pdf - p64).max() / np.abs(p64).max()),
+            "fluctuation_maxrel_diff": float(d.max()), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_differentiation(args, world, rank, local):
     """Config 4: the 64^3 SIMP cell (rho in [0.01, 1], E = rho^3, nu = 0.3). Each step computes the
     homogenized tangent (9 unit-response CG solves, fft_homog_tangent) and the sensitivity field
@@ -1027,6 +1099,8 @@ def main():
                     help="config 4: SIMP 64^3 tangent and sensitivities (not the bench line)")
     ap.add_argument("--examples", action="store_true",
                     help="time the paper's 2D examples (SVK square, J2 disks, Eshelby tangent); not the bench line")
+    ap.add_argument("--df64", action="store_true",
+                    help="the 128^3 solve with double-float CG transforms beside FP64 (an option; not the bench line)")
     ap.add_argument("--only", nargs="+", default=None,
                     choices=("svk_square", "svk_scaling", "j2_biaxial", "eshelby"),
                     help="with --examples: run only these examples (for launch lists)")
@@ -1050,6 +1124,9 @@ def main():
         return
     if args.differentiation:
         run_differentiation(args, world, rank, local)
+        return
+    if args.df64:
+        run_df64(args, world, rank, local)
         return
     run_ours(args, world, rank, local)
 

@@ -101,6 +101,20 @@ extern "C" {
 #define FH_LAUNCH_GRAPH 0
 #define FH_LAUNCH_PLAIN 1
 
+/* ---- arithmetic of the transforms in the CG matrix-vector product ----
+ * FH_ARITH_FP64  IEEE FP64 throughout (the default; the method as stated).
+ * FH_ARITH_DF64  an option, not the default: the five projection passes of
+ *                every CG product transform in double-float arithmetic
+ *                (each real number an unevaluated sum of two FP32 values,
+ *                about 48 significant bits, on the FP32 pipe, which issues
+ *                about 75 times faster than FP64 on GB300). K : p, the CG
+ *                vector updates and dot products, the Newton right-hand
+ *                side, residuals and stress stay FP64. Grids whose x and y
+ *                extents have compile-time plans and whose nz is even
+ *                (FH_ERR_UNSUPPORTED otherwise). */
+#define FH_ARITH_FP64 0
+#define FH_ARITH_DF64 1
+
 typedef struct fh_ctx fh_ctx;
 
 typedef struct fh_material {
@@ -132,6 +146,8 @@ typedef struct fh_options {
                            capturing and while fh_profile_enable timing is on); FH_LAUNCH_PLAIN:
                            every kernel launched from the host. Results are identical. */
   double lengths[3];    /* box side lengths L_x, L_y, L_z (> 0) */
+  int matvec_arith;     /* FH_ARITH_FP64 or FH_ARITH_DF64 */
+  int reserved;         /* 0 */
 } fh_options;
 
 typedef struct fh_stats {
@@ -148,7 +164,7 @@ typedef struct fh_stats {
 
 /* Fill *o with the defaults: newton_tol 1e-8, cg_tol 0 (= 1e-2 newton_tol),
  * max_newton 50, max_cg 5000, FH_INIT_REFERENCE, FH_TANGENT_STORED,
- * check_every 16, FH_LAUNCH_GRAPH, lengths (1, 1, 1). */
+ * check_every 16, FH_LAUNCH_GRAPH, lengths (1, 1, 1), FH_ARITH_FP64. */
 FH_API void fh_default_options(fh_options* o);
 
 /* Create a context for an nx x ny x nz grid whose work runs on cuda_stream
@@ -188,10 +204,12 @@ FH_API int fh_project(fh_ctx* ctx, const double* A_dev, double* out_dev, double 
 /* y = G(K : p), the CG matrix-vector product of the linearised Eq. 1.
  * With K_dev != NULL the stored packed tangent [45][N] is applied; with
  * K_dev == NULL, K : p is re-derived from F_dev and mat by AD (jvp form).
- *   p_dev in [9][N], y_dev out [9][N] (must not alias p_dev). */
+ *   p_dev in [9][N], y_dev out [9][N] (must not alias p_dev).
+ * arith: FH_ARITH_FP64, or FH_ARITH_DF64 for the transforms in double-float
+ * (FH_ERR_UNSUPPORTED on grids it does not cover, see FH_ARITH_DF64). */
 FH_API int fh_matvec(fh_ctx* ctx, const fh_material* mat, const double* F_dev,
               const double* K_dev, const double* p_dev, double* y_dev,
-              const double lengths[3]);
+              const double lengths[3], int arith);
 
 /* Solve the cell under the macroscopic tensor Fbar (Appendix A, Algorithm 1;
  * Listing 5's solve_microscale). The load goes from the start tensor to Fbar

@@ -38,6 +38,9 @@ INIT_GIVEN = 1
 LAUNCH_GRAPH = 0
 LAUNCH_PLAIN = 1
 
+ARITH_FP64 = 0
+ARITH_DF64 = 1
+
 _ERR_NAMES = {1: "FH_ERR_ARG", 2: "FH_ERR_CUDA", 3: "FH_ERR_NOT_CONVERGED", 4: "FH_ERR_NONPHYSICAL",
               5: "FH_ERR_TIMEOUT", 6: "FH_ERR_UNSUPPORTED"}
 
@@ -67,7 +70,7 @@ class FhMaterial(ctypes.Structure):
 class FhOptions(ctypes.Structure):
     _fields_ = [("newton_tol", c_double), ("cg_tol", c_double), ("max_newton", c_int), ("max_cg", c_int),
                 ("init", c_int), ("tangent_mode", c_int), ("check_every", c_int), ("launch_mode", c_int),
-                ("lengths", c_double * 3)]
+                ("lengths", c_double * 3), ("matvec_arith", c_int), ("reserved", c_int)]
 
 
 class FhCell(ctypes.Structure):
@@ -110,7 +113,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.fh_project.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(c_double)]
     lib.fh_project.restype = c_int
     lib.fh_matvec.argtypes = [c_void_p, POINTER(FhMaterial), c_void_p, c_void_p, c_void_p, c_void_p,
-                              POINTER(c_double)]
+                              POINTER(c_double), c_int]
     lib.fh_matvec.restype = c_int
     lib.fft_homog_solve.argtypes = [c_void_p, POINTER(FhMaterial), POINTER(c_double), c_int, POINTER(FhOptions),
                                     c_void_p, POINTER(c_double), POINTER(FhStats)]
@@ -306,10 +309,10 @@ class Context:
         La = _dvec(lengths, 3) if lengths is not None else (None, None)
         _check(load().fh_project(self._h, _ptr(A), _ptr(out), float(scale), La[1]))
 
-    def fh_matvec(self, p, y, K=None, mat: Material | None = None, F=None, lengths=None):
+    def fh_matvec(self, p, y, K=None, mat: Material | None = None, F=None, lengths=None, arith: int = ARITH_FP64):
         La = _dvec(lengths, 3) if lengths is not None else (None, None)
         _check(load().fh_matvec(self._h, mat.c if mat is not None else None, _ptr(F), _ptr(K), _ptr(p), _ptr(y),
-                                La[1]))
+                                La[1], int(arith)))
 
     def fh_autotune(self, reps: int = 3):
         """Time candidate tile shapes of the projection passes and keep the fastest.

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <vector>
 
+#include "df64.cuh"
 #include "fh_kernels.h"
 
 using namespace fh;
@@ -74,7 +75,7 @@ struct CgGraphKey {
   MatView mv;
   const double* F;
   double c_mv;
-  int stored, first, check_every, n_iz, n_upd;
+  int stored, first, check_every, n_iz, n_upd, df;
 };
 
 // One chunk of check_every CG iterations captured as a CUDA graph, with the
@@ -109,6 +110,7 @@ struct fh_ctx {
   long long n_partials = 0;
   double* params = nullptr;   // [256][2] Lame pairs, then [256][2] J2 (yield stress, hardening)
   double2* tw = nullptr;      // twiddle tables
+  dfc* tw_df = nullptr;       // the compile-time lengths' tables in double-float
   DevScalars* sc = nullptr;
   // graph replay of the CG loop: chunk 0 starts a loop, chunk 1 continues it;
   // off after a failed capture (e.g. the legacy default stream)
@@ -230,10 +232,22 @@ int upload_material(fh_ctx* ctx, const fh_material* m, MatView* mv) {
 }
 
 // G applied to src (tau = src, K : src, or the CG direction), result to out
+// (df: the transforms in double-float arithmetic, kernels_df64.cu)
 int run_projection(fh_ctx* ctx, const Grid& g, int zmode, const double* src, double* p, const double* K,
-                   double scale, int izmode, double* out, const double* pdot, CgScalars* cg, double* x = nullptr) {
+                   double scale, int izmode, double* out, const double* pdot, CgScalars* cg, double* x = nullptr,
+                   bool df = false) {
   const Tiling& t = ctx->tiling;
   cudaStream_t s = ctx->stream;
+  if (df) {
+    dfc* S = reinterpret_cast<dfc*>(ctx->S);
+    const dfc* tw = ctx->tw_df;
+    FH_CUDA(prof(ctx, kPFwdZ, [&] { return launch_fwd_z_df(g, t, zmode, src, p, x, K, cg, S, tw, s); }));
+    FH_CUDA(prof(ctx, kPFwdY, [&] { return launch_fwd_y_df(g, t, S, tw, cg, s); }));
+    FH_CUDA(prof(ctx, kPXGhat, [&] { return launch_x_ghat_df(g, t, S, tw, scale, cg, s); }));
+    FH_CUDA(prof(ctx, kPInvY, [&] { return launch_inv_y_df(g, t, S, tw, cg, s); }));
+    FH_CUDA(prof(ctx, kPInvZ, [&] { return launch_inv_z_df(g, t, izmode, S, out, pdot, ctx->partials, tw, cg, s); }));
+    return FH_OK;
+  }
   FH_CUDA(prof(ctx, kPFwdZ, [&] { return launch_fwd_z(g, t, zmode, src, p, x, K, cg, ctx->S, ctx->tw, s); }));
   FH_CUDA(prof(ctx, kPFwdY, [&] { return launch_fwd_y(g, t, ctx->S, ctx->tw, cg, s); }));
   FH_CUDA(prof(ctx, kPXGhat, [&] { return launch_x_ghat(g, t, ctx->S, ctx->tw, scale, cg, s); }));
@@ -292,7 +306,10 @@ int capture_cg_chunk(fh_ctx* ctx, CgGraph& G, const CgGraphKey& key, Queue&& que
 // holds b and ctx->partials the per-CTA sums of b . b from the inverse z pass
 // that produced it; on return ctx->x holds d and *host_cg the final scalars.
 int run_cg(fh_ctx* ctx, const Grid& g, const MatView& mv, const double* F_dev, bool stored, double cg_tol,
-           int max_cg, int check_every, bool plain, CgScalars* host_cg) {
+           const fh_options& opt, CgScalars* host_cg) {
+  const int max_cg = opt.max_cg, check_every = opt.check_every;
+  const bool plain = opt.launch_mode == FH_LAUNCH_PLAIN;
+  const bool df = opt.matvec_arith == FH_ARITH_DF64;
   cudaStream_t s = ctx->stream;
   CgScalars* cg = &ctx->sc->cg;
   const int n_iz = (int)z_pass_ctas(g, ctx->tiling);
@@ -321,13 +338,15 @@ int run_cg(fh_ctx* ctx, const Grid& g, const MatView& mv, const double* F_dev, b
       const int zmode = base + k == 0 ? kZCgFirst : kZCg;
       int rc2;
       if (stored) {
-        if ((rc2 = run_projection(ctx, g, zmode, ctx->r, ctx->p, ctx->K, c_mv, kIZDot, ctx->y, ctx->p, cg, ctx->x)))
+        if ((rc2 = run_projection(ctx, g, zmode, ctx->r, ctx->p, ctx->K, c_mv, kIZDot, ctx->y, ctx->p, cg, ctx->x,
+                                  df)))
           return rc2;
       } else {
         FH_CUDA(prof(ctx, kPJvp, [&] {
           return launch_jvp(g, mv, F_dev, ctx->r, ctx->p, ctx->x, ctx->P, zmode, cg, &ctx->sc->flags, s);
         }));
-        if ((rc2 = run_projection(ctx, g, kZDirect, ctx->P, nullptr, nullptr, c_mv, kIZDot, ctx->y, ctx->p, cg)))
+        if ((rc2 = run_projection(ctx, g, kZDirect, ctx->P, nullptr, nullptr, c_mv, kIZDot, ctx->y, ctx->p, cg,
+                                  nullptr, df)))
           return rc2;
       }
       FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_alpha(cg, ctx->partials, n_iz, s); }));
@@ -354,6 +373,7 @@ int run_cg(fh_ctx* ctx, const Grid& g, const MatView& mv, const double* F_dev, b
       key.check_every = check_every;
       key.n_iz = n_iz;
       key.n_upd = n_upd;
+      key.df = df;
       CgGraph& G = ctx->cg_graph[key.first ? 0 : 1];
       if (!G.exec || memcmp(&G.key, &key, sizeof key) != 0) {
         if ((rc = capture_cg_chunk(ctx, G, key, [&] { return queue_iterations(launched, check_every, 0); })))
@@ -414,6 +434,7 @@ void fh_default_options(fh_options* o) {
   o->tangent_mode = FH_TANGENT_STORED;
   o->check_every = 16;
   o->launch_mode = FH_LAUNCH_GRAPH;
+  o->matvec_arith = FH_ARITH_FP64;
   o->lengths[0] = o->lengths[1] = o->lengths[2] = 1.0;
 }
 
@@ -478,7 +499,8 @@ int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
       (e = cudaMalloc(&c->K, (size_t)45 * g.n * sizeof(double))) ||
       (e = cudaMalloc(&c->partials, (size_t)np * sizeof(double))) ||
       (e = cudaMalloc(&c->params, 1024 * sizeof(double))) ||
-      (e = cudaMalloc(&c->tw, tw_len * sizeof(double2))) || (e = cudaMalloc(&c->sc, sizeof(DevScalars)))) {
+      (e = cudaMalloc(&c->tw, tw_len * sizeof(double2))) || (e = cudaMalloc(&c->tw_df, kTwiddleTotal * sizeof(dfc))) ||
+      (e = cudaMalloc(&c->sc, sizeof(DevScalars)))) {
     fail(FH_ERR_CUDA, "fh_create: allocation failed: %s", cudaGetErrorString(e));
     return cleanup(FH_ERR_CUDA);
   }
@@ -486,7 +508,10 @@ int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
   fill_twiddle_table(tw.data());
   if (g.px.L) fill_plan_tables(tw.data() + g.px.tw_off, g.px);
   if (g.py.L) fill_plan_tables(tw.data() + g.py.tw_off, g.py);
+  std::vector<dfc> tw_df(kTwiddleTotal);
+  fill_twiddle_table_df(tw_df.data());
   if ((e = cudaMemcpy(c->tw, tw.data(), tw_len * sizeof(double2), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(c->tw_df, tw_df.data(), kTwiddleTotal * sizeof(dfc), cudaMemcpyHostToDevice)) ||
       (e = cudaMemset(c->sc, 0, sizeof(DevScalars))) || (e = setup_fft_kernels(g, c->tiling))) {
     fail(FH_ERR_CUDA, "fh_create: setup failed: %s", cudaGetErrorString(e));
     return cleanup(FH_ERR_CUDA);
@@ -513,6 +538,7 @@ void fh_destroy(fh_ctx* c) {
   cudaFree(c->partials);
   cudaFree(c->params);
   cudaFree(c->tw);
+  cudaFree(c->tw_df);
   cudaFree(c->sc);
   delete c;
 }
@@ -554,17 +580,21 @@ int fh_project(fh_ctx* ctx, const double* A_dev, double* out_dev, double scale, 
 }
 
 int fh_matvec(fh_ctx* ctx, const fh_material* mat, const double* F_dev, const double* K_dev, const double* p_dev,
-              double* y_dev, const double lengths[3]) {
+              double* y_dev, const double lengths[3], int arith) {
   g_err[0] = 0;
   if (!ctx || !p_dev || !y_dev) return fail(FH_ERR_ARG, "NULL argument");
   if (p_dev == y_dev) return fail(FH_ERR_ARG, "y must not alias p");
   if (!lengths_ok(lengths)) return fail(FH_ERR_ARG, "box lengths must be positive");
+  if (arith != FH_ARITH_FP64 && arith != FH_ARITH_DF64) return fail(FH_ERR_ARG, "invalid arith");
+  if (arith == FH_ARITH_DF64 && !df64_grid_ok(ctx->g))
+    return fail(FH_ERR_UNSUPPORTED, "FH_ARITH_DF64 needs x and y extents with compile-time plans and an even nz");
+  const bool df = arith == FH_ARITH_DF64;
   DeviceGuard dg(ctx->dev);
   const Grid g = grid_with_lengths(ctx, lengths);
   const double c = 1.0 / (2.0 * (double)g.n);
   int rc;
   if (K_dev) {
-    rc = run_projection(ctx, g, kZKApply, p_dev, nullptr, K_dev, c, kIZOut, y_dev, nullptr, nullptr);
+    rc = run_projection(ctx, g, kZKApply, p_dev, nullptr, K_dev, c, kIZOut, y_dev, nullptr, nullptr, nullptr, df);
     if (rc) return rc;
   } else {
     if (!F_dev) return fail(FH_ERR_ARG, "jvp form needs F");
@@ -573,7 +603,7 @@ int fh_matvec(fh_ctx* ctx, const fh_material* mat, const double* F_dev, const do
     if ((rc = upload_material(ctx, mat, &mv))) return rc;
     FH_CUDA(cudaMemsetAsync(&ctx->sc->flags, 0, sizeof(int), ctx->stream));
     FH_CUDA(prof(ctx, kPJvp, [&] { return launch_jvp(g, mv, F_dev, p_dev, nullptr, nullptr, ctx->P, kZKApply, nullptr, &ctx->sc->flags, ctx->stream); }));
-    rc = run_projection(ctx, g, kZDirect, ctx->P, nullptr, nullptr, c, kIZOut, y_dev, nullptr, nullptr);
+    rc = run_projection(ctx, g, kZDirect, ctx->P, nullptr, nullptr, c, kIZOut, y_dev, nullptr, nullptr, nullptr, df);
     if (rc) return rc;
     int flags = 0;
     if ((rc = read_flags(ctx, &flags))) return rc;
@@ -596,11 +626,14 @@ int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9], i
   else fh_default_options(&opt);
   if (n_increments < 1) return fail(FH_ERR_ARG, "n_increments must be >= 1");
   if (!(opt.newton_tol > 0.0) || opt.max_newton < 1 || opt.max_cg < 0 || opt.check_every < 1 ||
-      (opt.launch_mode != FH_LAUNCH_GRAPH && opt.launch_mode != FH_LAUNCH_PLAIN))
+      (opt.launch_mode != FH_LAUNCH_GRAPH && opt.launch_mode != FH_LAUNCH_PLAIN) ||
+      (opt.matvec_arith != FH_ARITH_FP64 && opt.matvec_arith != FH_ARITH_DF64))
     return fail(FH_ERR_ARG, "invalid options");
   if (opt.init != FH_INIT_REFERENCE && opt.init != FH_INIT_GIVEN) return fail(FH_ERR_ARG, "invalid init");
   if (opt.tangent_mode != FH_TANGENT_STORED && opt.tangent_mode != FH_TANGENT_JVP)
     return fail(FH_ERR_ARG, "invalid tangent_mode");
+  if (opt.matvec_arith == FH_ARITH_DF64 && !df64_grid_ok(ctx->g))
+    return fail(FH_ERR_UNSUPPORTED, "FH_ARITH_DF64 needs x and y extents with compile-time plans and an even nz");
   if (!lengths_ok(opt.lengths)) return fail(FH_ERR_ARG, "box lengths must be positive");
   for (int c = 0; c < 9; ++c)
     if (!std::isfinite(Fbar[c])) return fail(FH_ERR_ARG, "non-finite Fbar");
@@ -658,8 +691,7 @@ int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9], i
         return rc;
       // CG on G(K : dF) = b (a4, a5); scalars stay on the device
       CgScalars host_cg{};
-      if ((rc = run_cg(ctx, g, mv, F_dev, stored, cg_tol, opt.max_cg, opt.check_every,
-                         opt.launch_mode == FH_LAUNCH_PLAIN, &host_cg))) return rc;
+      if ((rc = run_cg(ctx, g, mv, F_dev, stored, cg_tol, opt, &host_cg))) return rc;
       // Newton update and convergence test (a6)
       FH_CUDA(prof(ctx, kPNewton, [&] { return launch_newton_update(g, F_dev, ctx->x, ctx->partials, s); }));
       FH_CUDA(prof(ctx, kPReduce, [&] { return launch_sum_partials(ctx->partials, n_nu, 1, ctx->sc->sums, s); }));
@@ -716,12 +748,15 @@ int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9], i
 
 namespace {
 
-int options_or_default(const fh_options* in, fh_options* o) {
+int options_or_default(const fh_ctx* ctx, const fh_options* in, fh_options* o) {
   if (in) *o = *in;
   else fh_default_options(o);
   if (!(o->newton_tol > 0.0) || o->max_cg < 0 || o->check_every < 1 ||
-      (o->launch_mode != FH_LAUNCH_GRAPH && o->launch_mode != FH_LAUNCH_PLAIN))
+      (o->launch_mode != FH_LAUNCH_GRAPH && o->launch_mode != FH_LAUNCH_PLAIN) ||
+      (o->matvec_arith != FH_ARITH_FP64 && o->matvec_arith != FH_ARITH_DF64))
     return fail(FH_ERR_ARG, "invalid options");
+  if (o->matvec_arith == FH_ARITH_DF64 && !df64_grid_ok(ctx->g))
+    return fail(FH_ERR_UNSUPPORTED, "FH_ARITH_DF64 needs x and y extents with compile-time plans and an even nz");
   if (!lengths_ok(o->lengths)) return fail(FH_ERR_ARG, "box lengths must be positive");
   return FH_OK;
 }
@@ -735,8 +770,7 @@ int unit_response(fh_ctx* ctx, const Grid& g, const MatView& mv, int cd, double 
   int rc = run_projection(ctx, g, kZKApply, ctx->y, nullptr, ctx->K, -1.0 / (2.0 * (double)g.n), kIZRhs, ctx->r,
                           nullptr, nullptr);
   if (rc) return rc;
-  if ((rc = run_cg(ctx, g, mv, nullptr, true, cg_tol, opt.max_cg, opt.check_every,
-                    opt.launch_mode == FH_LAUNCH_PLAIN, host_cg))) return rc;
+  if ((rc = run_cg(ctx, g, mv, nullptr, true, cg_tol, opt, host_cg))) return rc;
   if (host_cg->done != 1)
     return fail(FH_ERR_NOT_CONVERGED, "tangent CG %s after %d products (column %d)",
                 host_cg->done == 2 ? "hit max_cg" : "broke down", host_cg->it, cd);
@@ -754,7 +788,7 @@ int fft_homog_tangent(fh_ctx* ctx, const fh_material* mat, const double* F_dev, 
   if (mat->kind == FH_J2)
     return fail(FH_ERR_UNSUPPORTED, "the homogenized tangent is implemented for hyperelastic laws");
   fh_options opt;
-  if ((rc = options_or_default(opt_in, &opt))) return rc;
+  if ((rc = options_or_default(ctx, opt_in, &opt))) return rc;
   const double cg_tol = opt.cg_tol > 0.0 ? opt.cg_tol : 1e-2 * opt.newton_tol;
   DeviceGuard dg(ctx->dev);
   cudaStream_t s = ctx->stream;
@@ -791,7 +825,7 @@ int fft_homog_sensitivity(fh_ctx* ctx, const fh_material* mat, const fh_options*
   if (i < 0 || i > 2 || j < 0 || j > 2 || k < 0 || k > 2 || l < 0 || l > 2)
     return fail(FH_ERR_ARG, "tensor indices must be 0, 1 or 2");
   fh_options opt;
-  if ((rc = options_or_default(opt_in, &opt))) return rc;
+  if ((rc = options_or_default(ctx, opt_in, &opt))) return rc;
   const double cg_tol = opt.cg_tol > 0.0 ? opt.cg_tol : 1e-2 * opt.newton_tol;
   DeviceGuard dg(ctx->dev);
   cudaStream_t s = ctx->stream;
@@ -836,7 +870,7 @@ int fft_homog_stress_sensitivity(fh_ctx* ctx, const fh_material* mat, const doub
     return fail(FH_ERR_UNSUPPORTED, "stress sensitivities are implemented for hyperelastic and linear elastic laws");
   if (i < 0 || i > 2 || j < 0 || j > 2) return fail(FH_ERR_ARG, "tensor indices must be 0, 1 or 2");
   fh_options opt;
-  if ((rc = options_or_default(opt_in, &opt))) return rc;
+  if ((rc = options_or_default(ctx, opt_in, &opt))) return rc;
   const double cg_tol = opt.cg_tol > 0.0 ? opt.cg_tol : 1e-2 * opt.newton_tol;
   DeviceGuard dg(ctx->dev);
   cudaStream_t s = ctx->stream;

@@ -205,26 +205,27 @@ __device__ __forceinline__ int pencil_of(int qv, const PencilLayout& lay) {
 }
 
 // copy the twiddle table of length L (first n entries) to shared memory;
-// the caller synchronises before use
-template <int L>
-__device__ __forceinline__ void stage_twiddles(double2* dst, const double2* __restrict__ table, int n) {
+// the caller synchronises before use. The element type C is double2, or dfc
+// for the double-float transforms (same offsets, df64.cuh).
+template <int L, class C>
+__device__ __forceinline__ void stage_twiddles(C* dst, const C* __restrict__ table, int n) {
   constexpr int off = twiddle_offset(L);
-  const double2* src = table + off;
+  const C* src = table + off;
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
-template <int L, int R, int NS, bool INV, bool JFAST>
-__device__ __forceinline__ void stockham_stage(const double2* __restrict__ src, double2* __restrict__ dst,
-                                               const PencilLayout& lay, const double2* __restrict__ tw) {
+template <int L, int R, int NS, bool INV, bool JFAST, class C>
+__device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __restrict__ dst,
+                                               const PencilLayout& lay, const C* __restrict__ tw) {
   constexpr int NB = L / R;  // butterflies per pencil
   const int nq = (lay.np / lay.group) * lay.valid;
   const int total = nq * NB;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int q = pencil_of(JFAST ? t / NB : t % nq, lay);
     const int j = JFAST ? t % NB : t / nq;
-    const double2* s = src + q * lay.q_stride;
-    double2* d = dst + q * lay.q_stride;
-    double2 v[R];
+    const C* s = src + q * lay.q_stride;
+    C* d = dst + q * lay.q_stride;
+    C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = s[(j + r * NB) * lay.j_stride];
     if constexpr (NS > 1) {
@@ -232,7 +233,7 @@ __device__ __forceinline__ void stockham_stage(const double2* __restrict__ src, 
       constexpr int step = L / (NS * R);
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const double2 w = tw[r * k * step];
+        const C w = tw[r * k * step];
         v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
       }
     }
@@ -243,8 +244,8 @@ __device__ __forceinline__ void stockham_stage(const double2* __restrict__ src, 
   }
 }
 
-template <int L, bool INV, bool JFAST, int S, int NS>
-__device__ __forceinline__ double2* run_stages(double2* a, double2* b, const PencilLayout& lay, const double2* tw) {
+template <int L, bool INV, bool JFAST, int S, int NS, class C>
+__device__ __forceinline__ C* run_stages(C* a, C* b, const PencilLayout& lay, const C* tw) {
   if constexpr (S == Plan<L>::n) {
     return a;
   } else {
@@ -259,11 +260,10 @@ __device__ __forceinline__ double2* run_stages(double2* a, double2* b, const Pen
 // `tw` is the length-L twiddle table (in shared memory). Returns the buffer
 // holding the result. Synchronises the CTA before each stage and after the
 // last one.
-template <int L, bool INV, bool JFAST>
-__device__ __forceinline__ double2* fft_pencils(double2* a, double2* b, const PencilLayout& lay,
-                                                const double2* tw) {
+template <int L, bool INV, bool JFAST, class C>
+__device__ __forceinline__ C* fft_pencils(C* a, C* b, const PencilLayout& lay, const C* tw) {
   static_assert(L == 1 || Plan<L>::n > 0, "plan");
-  double2* out = run_stages<L, INV, JFAST, 0, 1>(a, b, lay, tw);
+  C* out = run_stages<L, INV, JFAST, 0, 1>(a, b, lay, tw);
   __syncthreads();
   return out;
 }
@@ -472,8 +472,8 @@ __device__ __noinline__ double2* fft_pencils_rt(double2* a, double2* b, const Pe
 
 // twiddles of the y (AX = 1) or x (AX = 0) axis into shared memory: the
 // compile-time table of L, or the run-time plan's table
-template <int L, int AX>
-__device__ __forceinline__ void stage_axis_twiddles(double2* dst, const double2* __restrict__ tw, const Grid& g) {
+template <int L, int AX, class C>
+__device__ __forceinline__ void stage_axis_twiddles(C* dst, const C* __restrict__ tw, const Grid& g) {
   if constexpr (L > 0) {
     stage_twiddles<L>(dst, tw, L);
   } else {

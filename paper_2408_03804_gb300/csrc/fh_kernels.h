@@ -115,6 +115,24 @@ cudaError_t launch_plane_x_ghat(const Grid& g, double2* S, const double2* tw, do
                                 cudaStream_t s);
 cudaError_t launch_plane_inv_y(const Grid& g, double2* S, const double2* tw, const CgScalars* cg, cudaStream_t s);
 
+// the same five passes with double-float transforms (kernels_df64.cu): grids
+// whose x and y extents have compile-time plans and whose nz is even; the
+// spectrum buffer and a double-float twiddle table (same offsets) as dfc
+struct dfc;
+bool df64_grid_ok(const Grid& g);
+void fill_twiddle_table_df(dfc* t);
+cudaError_t setup_df64_kernels(const Grid& g, const Tiling& t);
+cudaError_t launch_fwd_z_df(const Grid& g, const Tiling& t, int mode, const double* src, double* p, double* x,
+                            const double* K, const CgScalars* cg, dfc* S, const dfc* tw, cudaStream_t s);
+cudaError_t launch_fwd_y_df(const Grid& g, const Tiling& t, dfc* S, const dfc* tw, const CgScalars* cg,
+                            cudaStream_t s);
+cudaError_t launch_x_ghat_df(const Grid& g, const Tiling& t, dfc* S, const dfc* tw, double scale,
+                             const CgScalars* cg, cudaStream_t s);
+cudaError_t launch_inv_y_df(const Grid& g, const Tiling& t, dfc* S, const dfc* tw, const CgScalars* cg,
+                            cudaStream_t s);
+cudaError_t launch_inv_z_df(const Grid& g, const Tiling& t, int mode, const dfc* S, double* out, const double* p,
+                            double* partials, const dfc* tw, const CgScalars* cg, cudaStream_t s);
+
 cudaError_t launch_fwd_z_batch(const Grid& g, const Tiling& t, int mode, const CellView* cells, int n_cells,
                                const double2* tw, cudaStream_t s);
 cudaError_t launch_fwd_y_batch(const Grid& g, const Tiling& t, const CellView* cells, int n_cells,

@@ -1,382 +1,16 @@
-// The five passes of one application of the compatibility projection G of
-// Eq. 1 to a nine-component real field, with the stages of the CG
-// matrix-vector product y = G(K : p) fused into the first and last pass.
-//
-// Spectral layout: one complex buffer S[9][nx][ny][nzh] (nzh = nz/2 + 1) that
-// every pass updates in place. Ghat(xi)[Ahat] = v (x) xi with
-// v = Ahat xi / |xi|^2, a rank structure that removes a third of the 1D
-// transforms of the two outer passes:
-//
-//   z  (forward, real-to-complex): tau = K : p (or P), transform along z,
-//      multiply the j = z column by xi_z                         9 transforms
-//   y  (forward): transform the i-th row (j = x, y, z) along y, keep
-//      T_ix and form W_i = xi_y T_iy + T_iz                      9 transforms
-//   x  (forward + Ghat + inverse): transform T_ix, W_i along x,
-//      v_i = s (xi_x T_ix + W_i), s = c / |xi|^2 (0 at xi = 0),
-//      inverse-transform A_i = xi_x v_i and B_i = v_i along x   6 + 6 transforms
-//   y  (inverse): y_ix <- A_i, y_iy <- xi_y B_i, y_iz <- B_i,
-//      inverse transform along y, multiply y_iz by xi_z         9 transforms
-//   z  (inverse, complex-to-real): back to the real field, optionally the
-//      CG dot product p . y in the same pass                     9 transforms
-//
-// All transforms are unnormalised; the real-to-complex step skips its usual
-// factor 1/2, so the constant c carries 1 / (2 N) together with the caller's
-// scale. Each CTA owns a disjoint region of S in every pass, so in-place
-// updates are race free.
+// Kernels and launches of the five FP64 passes of the projection G (the pass
+// bodies and the description of the passes are in passes.cuh), the
+// batched-cell variants, and the host side of the transforms: twiddle
+// tables, run-time plans and tiles.
 #include <cmath>
 #include <cstdio>
 #include <vector>
 
 #include "fft_core.cuh"
 #include "fh_kernels.h"
+#include "passes.cuh"
 
 namespace fh {
-
-
-// ---------------------------------------------------------------------------
-// forward z pass: real-to-complex along z of LB consecutive z lines
-// ---------------------------------------------------------------------------
-// tau = K : p (or the source field) at voxel gi; the CG modes first advance
-// x and p of the previous iteration at this voxel
-template <int MODE>
-__device__ __forceinline__ void z_pass_tau(long long gi, long long n, const double* __restrict__ src,
-                                           double* __restrict__ p, double* __restrict__ x,
-                                           const double* __restrict__ K, double alpha, double beta, double tau[9]) {
-  if constexpr (MODE == kZDirect) {
-#pragma unroll
-    for (int c = 0; c < 9; ++c) tau[c] = src[c * n + gi];
-  } else {
-    double pv[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      if constexpr (MODE == kZKApply) {
-        pv[c] = src[c * n + gi];
-      } else if constexpr (MODE == kZCgFirst) {
-        pv[c] = src[c * n + gi];
-        p[c * n + gi] = pv[c];
-      } else {
-        // the previous iteration's x += alpha p, then p = r + beta p
-        const double po = p[c * n + gi];
-        x[c * n + gi] = fma(alpha, po, x[c * n + gi]);
-        pv[c] = fma(beta, po, src[c * n + gi]);
-        p[c * n + gi] = pv[c];
-      }
-    }
-    double k[45];
-#pragma unroll
-    for (int s = 0; s < 45; ++s) k[s] = K[s * n + gi];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      double acc = k[sym_slot(a, 0)] * pv[0];
-#pragma unroll
-      for (int b = 1; b < 9; ++b) acc = fma(k[sym_slot(a, b)], pv[b], acc);
-      tau[a] = acc;
-    }
-  }
-}
-
-// M = nz / 2; M = 0 is a cell one voxel thick along z (nz = 1), whose
-// transform along z is the identity
-template <int M, int MODE>
-__device__ __forceinline__ void fwd_z_body(int cta, Grid g, int LB, const double* __restrict__ src,
-                                                   double* __restrict__ p, double* __restrict__ x,
-                                                   const double* __restrict__ K, const CgScalars* __restrict__ cg,
-                                                   double2* __restrict__ S, const double2* __restrict__ tw) {
-  const long long n = g.n;
-  double beta = 0.0, alpha = 0.0;
-  if constexpr (MODE == kZCg) {
-    beta = cg->beta;
-    alpha = cg->alpha;
-  }
-  if constexpr (M == 0) {
-    // X_0 = tau, real (the plane y pass supplies the factor 2 of a
-    // real-to-complex step); the j = z columns, multiplied by xi_z = 0, are
-    // not read by the plane passes and are not written
-    const long long v0 = (long long)cta * LB;
-    for (int t = threadIdx.x; t < LB; t += blockDim.x) {
-      const long long gi = v0 + t;
-      double tau[9];
-      z_pass_tau<MODE>(gi, n, src, p, x, K, alpha, beta, tau);
-#pragma unroll
-      for (int c = 0; c < 9; ++c)
-        if (c % 3 != 2) S[c * g.nspec + gi] = make_double2(tau[c], 0.0);
-    }
-  } else {
-    extern __shared__ double2 smem[];
-    constexpr int NZ = 2 * M;
-    double2* bufA = smem;
-    double2* bufB = smem + 9 * LB * M;
-    double2* twM = bufB + 9 * LB * M;   // length-M table (half-length FFT)
-    double2* twN = twM + M;              // first M/2 + 1 entries of the length-NZ table (unpack)
-    stage_twiddles<M>(twM, tw, M);
-    stage_twiddles<NZ>(twN, tw, M / 2 + 1);
-    double* ra = reinterpret_cast<double*>(bufA);
-    const long long line0 = (long long)cta * LB;
-    const long long v0 = line0 * NZ;
-
-    for (int t = threadIdx.x; t < LB * NZ; t += blockDim.x) {
-      const long long gi = v0 + t;
-      const int line = t / NZ, z = t % NZ;
-      double tau[9];
-      z_pass_tau<MODE>(gi, n, src, p, x, K, alpha, beta, tau);
-#pragma unroll
-      for (int c = 0; c < 9; ++c) ra[(c * LB + line) * NZ + z] = tau[c];
-    }
-
-    double2* R = fft_pencils<M, false, true>(bufA, bufB, PencilLayout{9 * LB, M, 1, 1, 1}, twM);
-
-    // unpack the half-length transform Z of z_m = x_2m + i x_2m+1 into
-    // 2 X_k = (Z_k + conj Z_{M-k}) - i w^k (Z_k - conj Z_{M-k}), k = 0..M
-    constexpr int KH = M / 2 + 1;
-    for (int t = threadIdx.x; t < 9 * LB * KH; t += blockDim.x) {
-      const int q = t / KH, k = t % KH;
-      const int c = q / LB, line = q % LB;
-      const double2* Zq = R + q * M;
-      const double2 zk = Zq[k];
-      const double2 zm = Zq[k == 0 ? 0 : M - k];
-      const double2 e = make_double2(zk.x + zm.x, zk.y - zm.y);  // Z_k + conj Z_{M-k}
-      const double2 o = make_double2(zk.x - zm.x, zk.y + zm.y);  // Z_k - conj Z_{M-k}
-      const double2 wo = cmul(o, twN[k]);
-      const double2 tt = make_double2(wo.y, -wo.x);               // -i w^k o
-      double2 xk = cadd(e, tt);
-      double2 xm = make_double2(e.x - tt.x, tt.y - e.y);         // conj(e - tt)
-      double2* out = S + (long long)c * g.nspec + (line0 + line) * g.nzh;
-      if (c % 3 == 2) {
-        xk = cscale(xk, wave_int(k, NZ) * g.sz);
-        xm = cscale(xm, wave_int(M - k, NZ) * g.sz);
-      }
-      out[k] = xk;
-      if (M - k != k) out[M - k] = xm;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// forward y pass: row i, columns j = x, y, z along y; combine W_i
-// ---------------------------------------------------------------------------
-template <int L>
-__device__ __forceinline__ void fwd_y_body(int cta, Grid g, int BK, double2* __restrict__ S,
-                                                   const double2* __restrict__ tw, const CgScalars* __restrict__ cg) {
-  extern __shared__ double2 smem[];
-  const int Ln = L > 0 ? L : g.ny;
-  const int QS = Ln + 1;
-  const int np = 3 * BK;
-  double2* bufA = smem;
-  double2* bufB = smem + np * QS;
-  double2* twL = bufB + np * QS;
-  stage_axis_twiddles<L, 1>(twL, tw, g);
-  const int NC = (g.nzh + BK - 1) / BK;
-  int b = cta;
-  const int chunk = b % NC;
-  b /= NC;
-  const int i = b % 3;
-  const int x = b / 3;
-  const int kz0 = chunk * BK;
-  const int valid = min(BK, g.nzh - kz0);
-  for (int t = threadIdx.x; t < 3 * Ln * BK; t += blockDim.x) {
-    const int kzl = t % BK, rest = t / BK;
-    const int y = rest % Ln, f = rest / Ln;
-    const int kz = kz0 + kzl;
-    double2 v = make_double2(0.0, 0.0);
-    if (kz < g.nzh) v = S[(3 * i + f) * g.nspec + ((long long)x * Ln + y) * g.nzh + kz];
-    bufA[(f * BK + kzl) * QS + y] = v;
-  }
-  double2* R = fft_pencils_any<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL, g.py);
-  for (int t = threadIdx.x; t < Ln * BK; t += blockDim.x) {
-    const int kzl = t % BK, y = t / BK;
-    const int kz = kz0 + kzl;
-    if (kz >= g.nzh) continue;
-    const double xi_y = wave_int(y, Ln) * g.sy;
-    const double2 tx = R[(0 * BK + kzl) * QS + y];
-    const double2 ty = R[(1 * BK + kzl) * QS + y];
-    const double2 tz = R[(2 * BK + kzl) * QS + y];
-    const long long o = ((long long)x * Ln + y) * g.nzh + kz;
-    S[(3 * i + 0) * g.nspec + o] = tx;
-    S[(3 * i + 1) * g.nspec + o] = make_double2(fma(xi_y, ty.x, tz.x), fma(xi_y, ty.y, tz.y));
-  }
-}
-
-// ---------------------------------------------------------------------------
-// x pass: forward along x, Ghat, inverse along x
-// ---------------------------------------------------------------------------
-template <int L>
-__device__ __forceinline__ void x_ghat_body(int cta, Grid g, int BK, double2* __restrict__ S,
-                                                    const double2* __restrict__ tw, double scale,
-                                                    const CgScalars* __restrict__ cg) {
-  extern __shared__ double2 smem[];
-  const int Ln = L > 0 ? L : g.nx;
-  const int QS = Ln + 1;
-  const int np = 6 * BK;
-  double2* bufA = smem;
-  double2* bufB = smem + np * QS;
-  double2* twL = bufB + np * QS;
-  stage_axis_twiddles<L, 0>(twL, tw, g);
-  const int NC = (g.nzh + BK - 1) / BK;
-  const int chunk = cta % NC;
-  const int ky = cta / NC;
-  const int kz0 = chunk * BK;
-  const int valid = min(BK, g.nzh - kz0);
-  const long long row = (long long)g.ny * g.nzh;  // stride of x in S
-  for (int t = threadIdx.x; t < 6 * Ln * BK; t += blockDim.x) {
-    const int kzl = t % BK, rest = t / BK;
-    const int x = rest % Ln, f = rest / Ln;
-    const int kz = kz0 + kzl;
-    const int comp = 3 * (f >> 1) + (f & 1);
-    double2 v = make_double2(0.0, 0.0);
-    if (kz < g.nzh) v = S[comp * g.nspec + x * row + (long long)ky * g.nzh + kz];
-    bufA[(f * BK + kzl) * QS + x] = v;
-  }
-  double2* R = fft_pencils_any<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL, g.px);
-  const double xi_y = wave_int(ky, g.ny) * g.sy;
-  for (int t = threadIdx.x; t < Ln * BK; t += blockDim.x) {
-    const int kzl = t % BK, kx = t / BK;
-    const int kz = kz0 + kzl;
-    if (kzl >= valid) continue;
-    const double xi_x = wave_int(kx, Ln) * g.sx;
-    const double xi_z = wave_int(kz, g.nz) * g.sz;
-    const double d = fma(xi_x, xi_x, fma(xi_y, xi_y, xi_z * xi_z));
-    const double s = d > 0.0 ? scale / d : 0.0;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      double2* pa = R + ((2 * i) * BK + kzl) * QS + kx;
-      double2* pb = R + ((2 * i + 1) * BK + kzl) * QS + kx;
-      const double2 X = *pa, W = *pb;
-      const double2 v = make_double2(s * fma(xi_x, X.x, W.x), s * fma(xi_x, X.y, W.y));
-      *pa = cscale(v, xi_x);
-      *pb = v;
-    }
-  }
-  double2* other = (R == bufA) ? bufB : bufA;
-  double2* R2 = fft_pencils_any<L, true, true>(R, other, PencilLayout{np, QS, 1, BK, valid}, twL, g.px);
-  for (int t = threadIdx.x; t < 6 * Ln * BK; t += blockDim.x) {
-    const int kzl = t % BK, rest = t / BK;
-    const int x = rest % Ln, f = rest / Ln;
-    const int kz = kz0 + kzl;
-    if (kz >= g.nzh) continue;
-    const int comp = 3 * (f >> 1) + (f & 1);
-    S[comp * g.nspec + x * row + (long long)ky * g.nzh + kz] = R2[(f * BK + kzl) * QS + x];
-  }
-}
-
-// ---------------------------------------------------------------------------
-// inverse y pass: expand A_i, B_i to the three columns of row i
-// ---------------------------------------------------------------------------
-template <int L>
-__device__ __forceinline__ void inv_y_body(int cta, Grid g, int BK, double2* __restrict__ S,
-                                                   const double2* __restrict__ tw, const CgScalars* __restrict__ cg) {
-  extern __shared__ double2 smem[];
-  const int Ln = L > 0 ? L : g.ny;
-  const int QS = Ln + 1;
-  const int np = 3 * BK;
-  double2* bufA = smem;
-  double2* bufB = smem + np * QS;
-  double2* twL = bufB + np * QS;
-  stage_axis_twiddles<L, 1>(twL, tw, g);
-  const int NC = (g.nzh + BK - 1) / BK;
-  int b = cta;
-  const int chunk = b % NC;
-  b /= NC;
-  const int i = b % 3;
-  const int x = b / 3;
-  const int kz0 = chunk * BK;
-  const int valid = min(BK, g.nzh - kz0);
-  for (int t = threadIdx.x; t < 2 * Ln * BK; t += blockDim.x) {
-    const int kzl = t % BK, rest = t / BK;
-    const int y = rest % Ln, h = rest / Ln;
-    const int kz = kz0 + kzl;
-    double2 v = make_double2(0.0, 0.0);
-    if (kz < g.nzh) v = S[(3 * i + h) * g.nspec + ((long long)x * Ln + y) * g.nzh + kz];
-    if (h == 0) {
-      bufA[(0 * BK + kzl) * QS + y] = v;
-    } else {
-      bufA[(1 * BK + kzl) * QS + y] = cscale(v, wave_int(y, Ln) * g.sy);
-      bufA[(2 * BK + kzl) * QS + y] = v;
-    }
-  }
-  double2* R = fft_pencils_any<L, true, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL, g.py);
-  for (int t = threadIdx.x; t < Ln * BK; t += blockDim.x) {
-    const int kzl = t % BK, y = t / BK;
-    const int kz = kz0 + kzl;
-    if (kz >= g.nzh) continue;
-    const long long o = ((long long)x * Ln + y) * g.nzh + kz;
-    S[(3 * i + 0) * g.nspec + o] = R[(0 * BK + kzl) * QS + y];
-    S[(3 * i + 1) * g.nspec + o] = R[(1 * BK + kzl) * QS + y];
-    S[(3 * i + 2) * g.nspec + o] = cscale(R[(2 * BK + kzl) * QS + y], wave_int(kz, g.nz) * g.sz);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// inverse z pass: complex-to-real along z, optional dot-product epilogue
-// ---------------------------------------------------------------------------
-template <int M, int MODE>
-__device__ __forceinline__ void inv_z_body(int cta, Grid g, int LB, const double2* __restrict__ S,
-                                                   double* __restrict__ out, const double* __restrict__ p,
-                                                   double* __restrict__ partials, const double2* __restrict__ tw,
-                                                   const CgScalars* __restrict__ cg) {
-  __shared__ double red[32];
-  const long long line0 = (long long)cta * LB;
-  const long long n = g.n;
-  double acc = 0.0;
-  if constexpr (M == 0) {
-    // nz = 1: the real part of X_0 (complex-to-real semantics)
-    for (int t = threadIdx.x; t < LB; t += blockDim.x) {
-      const long long gi = line0 + t;
-#pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        const double yv = S[c * g.nspec + gi].x;
-        out[c * n + gi] = yv;
-        if constexpr (MODE == kIZDot) acc = fma(p[c * n + gi], yv, acc);
-        if constexpr (MODE == kIZRhs) acc = fma(yv, yv, acc);
-      }
-    }
-  } else {
-    extern __shared__ double2 smem[];
-    constexpr int NZ = 2 * M;
-    double2* bufA = smem;
-    double2* bufB = smem + 9 * LB * M;
-    double2* twM = bufB + 9 * LB * M;
-    double2* twN = twM + M;
-    stage_twiddles<M>(twM, tw, M);
-    stage_twiddles<NZ>(twN, tw, M / 2 + 1);
-    __syncthreads();
-    // pack Z_k = (X_k + conj X_{M-k}) + i w^-k (X_k - conj X_{M-k}); the
-    // imaginary parts of X_0 and X_M are dropped (complex-to-real semantics)
-    constexpr int KH = M / 2 + 1;
-    for (int t = threadIdx.x; t < 9 * LB * KH; t += blockDim.x) {
-      const int q = t / KH, k = t % KH;
-      const int c = q / LB, line = q % LB;
-      const double2* in = S + (long long)c * g.nspec + (line0 + line) * g.nzh;
-      double2 xk = in[k], xm = in[M - k];
-      if (k == 0) {
-        xk.y = 0.0;
-        xm.y = 0.0;
-      }
-      const double2 a = make_double2(xk.x + xm.x, xk.y - xm.y);
-      const double2 bb = make_double2(xk.x - xm.x, xk.y + xm.y);
-      const double2 bw = cmulc(bb, twN[k]);
-      const double2 u = make_double2(-bw.y, bw.x);  // i w^-k b
-      bufA[q * M + k] = cadd(a, u);
-      if (k != 0 && M - k != k) bufA[q * M + (M - k)] = make_double2(a.x - u.x, u.y - a.y);
-    }
-    double2* R = fft_pencils<M, true, true>(bufA, bufB, PencilLayout{9 * LB, M, 1, 1, 1}, twM);
-    const double* rr = reinterpret_cast<const double*>(R);
-    for (int t = threadIdx.x; t < LB * NZ; t += blockDim.x) {
-      const int line = t / NZ, z = t % NZ;
-      const long long gi = (line0 + line) * NZ + z;
-#pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        const double yv = rr[(c * LB + line) * NZ + z];
-        out[c * n + gi] = yv;
-        if constexpr (MODE == kIZDot) acc = fma(p[c * n + gi], yv, acc);
-        if constexpr (MODE == kIZRhs) acc = fma(yv, yv, acc);
-      }
-    }
-  }
-  if constexpr (MODE != kIZOut) {
-    const double s = block_sum(acc, red);
-    if (threadIdx.x == 0) partials[cta] = s;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // kernels: one cell (blockIdx.x = CTA of the pass) ...
@@ -660,49 +294,6 @@ static size_t y_smem_rt(const FftPlan& p, int bk, int fields) {
   return ((size_t)2 * fields * bk * (p.L + 1) + p.tw_len) * sizeof(double2);
 }
 
-#define FH_SWITCH_LEN(v, MACRO) \
-  switch (v) {                   \
-    MACRO(1)                     \
-    MACRO(2)                     \
-    MACRO(3)                     \
-    MACRO(4)                     \
-    MACRO(6)                     \
-    MACRO(8)                     \
-    MACRO(12)                    \
-    MACRO(16)                    \
-    MACRO(24)                    \
-    MACRO(32)                    \
-    MACRO(48)                    \
-    MACRO(64)                    \
-    MACRO(96)                    \
-    MACRO(128)                   \
-    MACRO(192)                   \
-    MACRO(256)                   \
-    default:                     \
-      return cudaErrorInvalidValue; \
-  }
-// half lengths of the real-to-complex axis (nz/2 <= 128; 0 for nz = 1)
-#define FH_SWITCH_HALF(v, MACRO) \
-  switch (v) {                   \
-    MACRO(0)                     \
-    MACRO(1)                     \
-    MACRO(2)                     \
-    MACRO(3)                     \
-    MACRO(4)                     \
-    MACRO(6)                     \
-    MACRO(8)                     \
-    MACRO(12)                    \
-    MACRO(16)                    \
-    MACRO(24)                    \
-    MACRO(32)                    \
-    MACRO(48)                    \
-    MACRO(64)                    \
-    MACRO(96)                    \
-    MACRO(128)                   \
-    default:                     \
-      return cudaErrorInvalidValue; \
-  }
-
 template <class Kern>
 static cudaError_t allow_smem(Kern k, size_t bytes) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -758,7 +349,8 @@ cudaError_t setup_fft_kernels(const Grid& g, const Tiling& t) {
     FH_SWITCH_LEN(g.nx, XCASE)
   }
 #undef XCASE
-  return cudaSuccess;
+  // the double-float kernels take the same tiles and shared memory
+  return setup_df64_kernels(g, t);
 }
 
 cudaError_t launch_fwd_z(const Grid& g, const Tiling& t, int mode, const double* src, double* p, double* x,

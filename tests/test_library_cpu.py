@@ -50,7 +50,8 @@ def test_default_options(lib):
     o = _binding.default_options()
     assert o.newton_tol == 1e-8 and o.cg_tol == 0.0 and o.max_newton == 50 and o.max_cg == 5000
     assert o.check_every == 16 and list(o.lengths) == [1.0, 1.0, 1.0]
-    assert o.launch_mode == _binding.LAUNCH_GRAPH
+    assert o.launch_mode == _binding.LAUNCH_GRAPH and o.matvec_arith == _binding.ARITH_FP64
+    assert ctypes.sizeof(_binding.FhOptions) == 72
 
 
 @pytest.mark.parametrize("shape", [(4, 4, 3), (4, 4, 5), (513, 4, 4), (4, 1024, 4), (4, 4, 10), (0, 4, 4),
