@@ -787,7 +787,18 @@ def run_df64(args, world, rank, local):
     phase, params, Fbar = neo_hookean_config(shape, seed=rank)
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
-    res = {}
+    if args.probe_newton:
+        # one Newton iteration with 16 double-float CG products (for ncu captures of those kernels)
+        with fh.Context(*shape, stream=stream.cuda_stream) as ctx:
+            F = torch.empty((9,) + shape, dtype=torch.float64, device=dev)
+            probe = fh.default_options(newton_tol=NEWTON_TOL, max_newton=1, max_cg=16, matvec_arith=fh.ARITH_DF64)
+            for _ in range(2):
+                ctx.fft_homog_solve(fh.Material(fh.NEO_HOOKEAN, phase, params), Fbar, F, n_increments=N_INC,
+                                    options=probe, allow=(fh.FH_ERR_NOT_CONVERGED,))
+            torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"probe_newton_df64": "ok", "shape": list(shape)}), flush=True)
+        return
     with fh.Context(*shape, stream=stream.cuda_stream) as ctx, ClockSampler(local) as clk:
         mat = fh.Material(fh.NEO_HOOKEAN, phase, params)
         F = {a: torch.empty((9,) + shape, dtype=torch.float64, device=dev) for a in (fh.ARITH_FP64, fh.ARITH_DF64)}

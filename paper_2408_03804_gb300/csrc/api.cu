@@ -111,6 +111,7 @@ struct fh_ctx {
   double* params = nullptr;   // [256][2] Lame pairs, then [256][2] J2 (yield stress, hardening)
   double2* tw = nullptr;      // twiddle tables
   dfc* tw_df = nullptr;       // the compile-time lengths' tables in double-float
+  df64* K_df = nullptr;       // double-float copy of a packed tangent [45][N] (allocated on first use)
   DevScalars* sc = nullptr;
   // graph replay of the CG loop: chunk 0 starts a loop, chunk 1 continues it;
   // off after a failed capture (e.g. the legacy default stream)
@@ -233,6 +234,15 @@ int upload_material(fh_ctx* ctx, const fh_material* m, MatView* mv) {
 
 // G applied to src (tau = src, K : src, or the CG direction), result to out
 // (df: the transforms in double-float arithmetic, kernels_df64.cu)
+// ctx->K_df = K in double-float (allocated on the first call: 360 bytes per voxel)
+int tangent_to_df64(fh_ctx* ctx, const Grid& g, const double* K) {
+  if (!ctx->K_df) FH_CUDA(cudaMalloc(&ctx->K_df, (size_t)45 * g.n * sizeof(df64)));
+  FH_CUDA(prof(ctx, kPConst, [&] { return launch_tangent_to_df64(g, K, ctx->K_df, ctx->stream); }));
+  return FH_OK;
+}
+
+// (df: the transforms in double-float arithmetic, kernels_df64.cu; a mode
+// that reads K then reads the double-float copy ctx->K_df instead)
 int run_projection(fh_ctx* ctx, const Grid& g, int zmode, const double* src, double* p, const double* K,
                    double scale, int izmode, double* out, const double* pdot, CgScalars* cg, double* x = nullptr,
                    bool df = false) {
@@ -241,7 +251,8 @@ int run_projection(fh_ctx* ctx, const Grid& g, int zmode, const double* src, dou
   if (df) {
     dfc* S = reinterpret_cast<dfc*>(ctx->S);
     const dfc* tw = ctx->tw_df;
-    FH_CUDA(prof(ctx, kPFwdZ, [&] { return launch_fwd_z_df(g, t, zmode, src, p, x, K, cg, S, tw, s); }));
+    const df64* Kd = K ? ctx->K_df : nullptr;
+    FH_CUDA(prof(ctx, kPFwdZ, [&] { return launch_fwd_z_df(g, t, zmode, src, p, x, Kd, cg, S, tw, s); }));
     FH_CUDA(prof(ctx, kPFwdY, [&] { return launch_fwd_y_df(g, t, S, tw, cg, s); }));
     FH_CUDA(prof(ctx, kPXGhat, [&] { return launch_x_ghat_df(g, t, S, tw, scale, cg, s); }));
     FH_CUDA(prof(ctx, kPInvY, [&] { return launch_inv_y_df(g, t, S, tw, cg, s); }));
@@ -310,6 +321,8 @@ int run_cg(fh_ctx* ctx, const Grid& g, const MatView& mv, const double* F_dev, b
   const int max_cg = opt.max_cg, check_every = opt.check_every;
   const bool plain = opt.launch_mode == FH_LAUNCH_PLAIN;
   const bool df = opt.matvec_arith == FH_ARITH_DF64;
+  int rc;
+  if (df && stored && (rc = tangent_to_df64(ctx, g, ctx->K))) return rc;
   cudaStream_t s = ctx->stream;
   CgScalars* cg = &ctx->sc->cg;
   const int n_iz = (int)z_pass_ctas(g, ctx->tiling);
@@ -318,7 +331,6 @@ int run_cg(fh_ctx* ctx, const Grid& g, const MatView& mv, const double* F_dev, b
   FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_init(cg, ctx->partials, n_iz, cg_tol, max_cg, s); }));
   FH_CUDA(cudaMemsetAsync(ctx->x, 0, (size_t)9 * g.n * sizeof(double), s));
   int launched = 0;
-  int rc;
   // every exit below clears the tag; launches of the loop are booked by prof_commit_cg
   struct TagReset {
     fh_ctx* c;
@@ -539,6 +551,7 @@ void fh_destroy(fh_ctx* c) {
   cudaFree(c->params);
   cudaFree(c->tw);
   cudaFree(c->tw_df);
+  cudaFree(c->K_df);
   cudaFree(c->sc);
   delete c;
 }
@@ -594,6 +607,7 @@ int fh_matvec(fh_ctx* ctx, const fh_material* mat, const double* F_dev, const do
   const double c = 1.0 / (2.0 * (double)g.n);
   int rc;
   if (K_dev) {
+    if (df && (rc = tangent_to_df64(ctx, g, K_dev))) return rc;
     rc = run_projection(ctx, g, kZKApply, p_dev, nullptr, K_dev, c, kIZOut, y_dev, nullptr, nullptr, nullptr, df);
     if (rc) return rc;
   } else {

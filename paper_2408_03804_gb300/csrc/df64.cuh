@@ -62,12 +62,53 @@ __device__ __forceinline__ df64 dd_fma(df64 a, df64 b, df64 c) {
   return fast_two_sum(s.hi, s.lo);
 }
 
-// conversions (the FP64 side does them: one rounding to float each way)
+// conversions through FP64 arithmetic (one rounding to float each way): for
+// constants and per-thread scalars
 __host__ __device__ __forceinline__ df64 to_df64(double x) {
   const float hi = (float)x;
   return df64{hi, (float)(x - (double)hi)};
 }
 __device__ __forceinline__ double to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+
+// Conversions of field values on the integer pipe (FP64 issue is the
+// scarce resource): split_double cuts the 52-bit significand of x after 23
+// bits (hi, exact) and turns the remaining 29 bits into lo, truncated to 24
+// significant bits, so that |x - hi - lo| < 2^-47 |x|. Values below the
+// smallest normal float (2^-126) become 0, and lo below it is dropped (an
+// absolute error under 2^-126); infinities and NaN map to hi.
+__device__ __forceinline__ df64 split_double(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff);  // biased by 1023
+  const unsigned long long m = b & 0xfffffffffffffull;
+  if (e == 0x7ff) return df64{__uint_as_float(sign | 0x7f800000u | (unsigned)(m >> 29)), 0.f};
+  const int ef = e - 1023 + 127;  // float exponent field of hi
+  if (ef <= 0) return df64{__uint_as_float(sign), 0.f};
+  if (ef >= 255) return df64{__uint_as_float(sign | 0x7f800000u), 0.f};
+  const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)(m >> 29));
+  const unsigned rem = (unsigned)(m & 0x1fffffffu);  // weight 2^(e - 1023 - 52) each
+  if (rem == 0) return df64{hi, 0.f};
+  const int top = 31 - __clz(rem);           // highest set bit of the 29-bit remainder
+  const int el = ef - 52 + top;               // float exponent field of lo
+  if (el <= 0) return df64{hi, 0.f};
+  const unsigned frac = top >= 23 ? (rem >> (top - 23)) : (rem << (23 - top));
+  return df64{hi, __uint_as_float(sign | ((unsigned)el << 23) | (frac & 0x7fffffu))};
+}
+
+// (double)f for a normal float or zero by bit operations (denormals give 0)
+__device__ __forceinline__ double float_bits_to_double(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned ef = (u >> 23) & 0xffu;
+  if (ef == 0) return __longlong_as_double((long long)sign);
+  if (ef == 0xffu)
+    return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | ((unsigned long long)(u & 0x7fffffu) << 29)));
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)(ef + 1023 - 127) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+// hi + lo with one FP64 addition
+__device__ __forceinline__ double join_df64(df64 a) { return float_bits_to_double(a.hi) + float_bits_to_double(a.lo); }
 
 // ---- complex df64 -----------------------------------------------------------
 __device__ __forceinline__ dfc cadd(dfc a, dfc b) { return dfc{dd_add(a.re, b.re), dd_add(a.im, b.im)}; }

@@ -119,11 +119,14 @@ cudaError_t launch_plane_inv_y(const Grid& g, double2* S, const double2* tw, con
 // whose x and y extents have compile-time plans and whose nz is even; the
 // spectrum buffer and a double-float twiddle table (same offsets) as dfc
 struct dfc;
+struct df64;
 bool df64_grid_ok(const Grid& g);
+// K_df = the packed tangent [45][N] in double-float
+cudaError_t launch_tangent_to_df64(const Grid& g, const double* K, df64* K_df, cudaStream_t s);
 void fill_twiddle_table_df(dfc* t);
 cudaError_t setup_df64_kernels(const Grid& g, const Tiling& t);
 cudaError_t launch_fwd_z_df(const Grid& g, const Tiling& t, int mode, const double* src, double* p, double* x,
-                            const double* K, const CgScalars* cg, dfc* S, const dfc* tw, cudaStream_t s);
+                            const df64* K, const CgScalars* cg, dfc* S, const dfc* tw, cudaStream_t s);
 cudaError_t launch_fwd_y_df(const Grid& g, const Tiling& t, dfc* S, const dfc* tw, const CgScalars* cg,
                             cudaStream_t s);
 cudaError_t launch_x_ghat_df(const Grid& g, const Tiling& t, dfc* S, const dfc* tw, double scale,

@@ -16,7 +16,7 @@ namespace {
 template <int M, int MODE>
 __global__ void __launch_bounds__(kThreads) k_fwd_z_df(Grid g, int LB, const double* __restrict__ src,
                                                       double* __restrict__ p, double* __restrict__ x,
-                                                      const double* __restrict__ K, const CgScalars* __restrict__ cg,
+                                                      const df64* __restrict__ K, const CgScalars* __restrict__ cg,
                                                       dfc* __restrict__ S, const dfc* __restrict__ tw) {
   if (cg_done(cg)) return;
   fwd_z_body<M, MODE>(blockIdx.x, g, LB, src, p, x, K, cg, S, tw);
@@ -109,8 +109,27 @@ cudaError_t setup_df64_kernels(const Grid& g, const Tiling& t) {
   return cudaSuccess;
 }
 
+// the packed tangent [45][N] in double-float (K_df[i] from K[i])
+__global__ void __launch_bounds__(kThreads) k_tangent_to_df64(const double* __restrict__ K, df64* __restrict__ K_df,
+                                                             long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    K_df[i] = split_double(K[i]);
+}
+
+cudaError_t launch_tangent_to_df64(const Grid& g, const double* K, df64* K_df, cudaStream_t s) {
+  const long long count = 45LL * g.n;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long blocks = (count + kThreads - 1) / kThreads;
+  if (blocks > 8LL * sms) blocks = 8LL * sms;
+  k_tangent_to_df64<<<(unsigned)blocks, kThreads, 0, s>>>(K, K_df, count);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fwd_z_df(const Grid& g, const Tiling& t, int mode, const double* src, double* p, double* x,
-                            const double* K, const CgScalars* cg, dfc* S, const dfc* tw, cudaStream_t s) {
+                            const df64* K, const CgScalars* cg, dfc* S, const dfc* tw, cudaStream_t s) {
   const size_t smem = z_pass_smem(g, t);
   const unsigned grid = (unsigned)z_pass_ctas(g, t);
   const int M = g.nz / 2;

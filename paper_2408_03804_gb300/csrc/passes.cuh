@@ -78,12 +78,12 @@ __device__ __forceinline__ void czero(dfc& a) { a = dfc{df64{0.f, 0.f}, df64{0.f
 
 // the real sequence packed two per complex entry (a real-to-complex step)
 __device__ __forceinline__ void store_real(double2* buf, int i, double v) { reinterpret_cast<double*>(buf)[i] = v; }
-__device__ __forceinline__ void store_real(dfc* buf, int i, double v) { reinterpret_cast<df64*>(buf)[i] = to_df64(v); }
+__device__ __forceinline__ void store_real(dfc* buf, int i, df64 v) { reinterpret_cast<df64*>(buf)[i] = v; }
 __device__ __forceinline__ double load_real(const double2* buf, int i) {
   return reinterpret_cast<const double*>(buf)[i];
 }
 __device__ __forceinline__ double load_real(const dfc* buf, int i) {
-  return to_double(reinterpret_cast<const df64*>(buf)[i]);
+  return join_df64(reinterpret_cast<const df64*>(buf)[i]);
 }
 
 // s = c / |xi|^2, 0 at xi = 0
@@ -147,39 +147,51 @@ __device__ __forceinline__ C* pencils(C* a, C* b, const PencilLayout& lay, const
 // forward z pass: real-to-complex along z of LB consecutive z lines
 // ---------------------------------------------------------------------------
 // tau = K : p (or the source field) at voxel gi; the CG modes first advance
-// x and p of the previous iteration at this voxel
-template <int MODE>
+// x and p of the previous iteration at this voxel (FP64 in both forms). R is
+// the real type of tau and of the packed tangent K: double, or df64 for the
+// double-float passes, which read a double-float copy of K and form K : p
+// with double-float fused multiply-adds.
+__device__ __forceinline__ double real_from(double v, double*) { return v; }
+__device__ __forceinline__ df64 real_from(double v, df64*) { return split_double(v); }
+__device__ __forceinline__ double real_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ df64 real_fma(df64 a, df64 b, df64 c) { return dd_fma(a, b, c); }
+__device__ __forceinline__ double real_mul(double a, double b) { return a * b; }
+__device__ __forceinline__ df64 real_mul(df64 a, df64 b) { return dd_mul(a, b); }
+
+template <int MODE, class R>
 __device__ __forceinline__ void z_pass_tau(long long gi, long long n, const double* __restrict__ src,
                                            double* __restrict__ p, double* __restrict__ x,
-                                           const double* __restrict__ K, double alpha, double beta, double tau[9]) {
+                                           const R* __restrict__ K, double alpha, double beta, R tau[9]) {
   if constexpr (MODE == kZDirect) {
 #pragma unroll
-    for (int c = 0; c < 9; ++c) tau[c] = src[c * n + gi];
+    for (int c = 0; c < 9; ++c) tau[c] = real_from(src[c * n + gi], (R*)nullptr);
   } else {
-    double pv[9];
+    R pv[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
+      double v;
       if constexpr (MODE == kZKApply) {
-        pv[c] = src[c * n + gi];
+        v = src[c * n + gi];
       } else if constexpr (MODE == kZCgFirst) {
-        pv[c] = src[c * n + gi];
-        p[c * n + gi] = pv[c];
+        v = src[c * n + gi];
+        p[c * n + gi] = v;
       } else {
         // the previous iteration's x += alpha p, then p = r + beta p
         const double po = p[c * n + gi];
         x[c * n + gi] = fma(alpha, po, x[c * n + gi]);
-        pv[c] = fma(beta, po, src[c * n + gi]);
-        p[c * n + gi] = pv[c];
+        v = fma(beta, po, src[c * n + gi]);
+        p[c * n + gi] = v;
       }
+      pv[c] = real_from(v, (R*)nullptr);
     }
-    double k[45];
+    R k[45];
 #pragma unroll
     for (int s = 0; s < 45; ++s) k[s] = K[s * n + gi];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      double acc = k[sym_slot(a, 0)] * pv[0];
+      R acc = real_mul(k[sym_slot(a, 0)], pv[0]);
 #pragma unroll
-      for (int b = 1; b < 9; ++b) acc = fma(k[sym_slot(a, b)], pv[b], acc);
+      for (int b = 1; b < 9; ++b) acc = real_fma(k[sym_slot(a, b)], pv[b], acc);
       tau[a] = acc;
     }
   }
@@ -190,8 +202,9 @@ __device__ __forceinline__ void z_pass_tau(long long gi, long long n, const doub
 template <int M, int MODE, class C>
 __device__ __forceinline__ void fwd_z_body(int cta, Grid g, int LB, const double* __restrict__ src,
                                            double* __restrict__ p, double* __restrict__ x,
-                                           const double* __restrict__ K, const CgScalars* __restrict__ cg,
-                                           C* __restrict__ S, const C* __restrict__ tw) {
+                                           const typename RealOf<C>::type* __restrict__ K,
+                                           const CgScalars* __restrict__ cg, C* __restrict__ S,
+                                           const C* __restrict__ tw) {
   using R = typename RealOf<C>::type;
   const long long n = g.n;
   double beta = 0.0, alpha = 0.0;
@@ -227,7 +240,7 @@ __device__ __forceinline__ void fwd_z_body(int cta, Grid g, int LB, const double
     for (int t = threadIdx.x; t < LB * NZ; t += blockDim.x) {
       const long long gi = v0 + t;
       const int line = t / NZ, z = t % NZ;
-      double tau[9];
+      R tau[9];
       z_pass_tau<MODE>(gi, n, src, p, x, K, alpha, beta, tau);
 #pragma unroll
       for (int c = 0; c < 9; ++c) store_real(bufA, (c * LB + line) * NZ + z, tau[c]);
