@@ -128,7 +128,7 @@ def cg_iteration_bytes(nx, ny, nz):
 
 
 # sources of the projection and CG kernels whose DRAM traffic profiles/ncu_traffic.json records
-TRAFFIC_SOURCES = ("kernels_fft.cu", "fft_core.cuh", "fh_common.cuh", "fh_kernels.h")
+TRAFFIC_SOURCES = ("kernels_fft.cu", "passes.cuh", "fft_core.cuh", "fh_common.cuh", "fh_kernels.h")
 
 
 def kernel_source_hash() -> str:
