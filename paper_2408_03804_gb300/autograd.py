@@ -11,6 +11,12 @@ voxel field with the incoming gradient and nothing else.
                                     as a differentiable function of a voxel
                                     density rho (through the modulus scale
                                     s(rho) held in ``mat.scale``).
+``homogenized_stress_of_density(rho, ...)``
+                                    Pbar of a (finite-strain or linear) cell
+                                    under a fixed Fbar as a differentiable
+                                    function of the voxel density; backward
+                                    contracts the incoming 9-gradient with
+                                    fft_homog_stress_sensitivity's fields.
 """
 
 from __future__ import annotations
@@ -76,4 +82,42 @@ def homogenized_modulus(rho: torch.Tensor, cell: Context, mat: Material, ijkl, d
                                      options if options is not None else default_options(cg_tol=1e-12))
 
 
-__all__ = ["homogenized_stress", "homogenized_modulus"]
+class _HomogenizedStressOfDensity(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rho, cell, mat, Fbar, F, dscale, n_increments, options, adjoint_options):
+        fb = Fbar.detach().to("cpu", torch.float64).reshape(9).numpy() if torch.is_tensor(Fbar) else Fbar
+        pbar, _, _ = cell.fft_homog_solve(mat, fb, F, n_increments=n_increments, options=options)
+        ctx.cell, ctx.mat, ctx.F, ctx.dscale, ctx.aopt = cell, mat, F, dscale, adjoint_options
+        return torch.as_tensor(pbar, dtype=torch.float64, device=rho.device)
+
+    @staticmethod
+    def backward(ctx, grad):
+        # sum_ab g_ab dPbar_ab/drho: one adjoint (unit-response) solve per entry the gradient touches
+        g = grad.detach().to("cpu", torch.float64).reshape(9).numpy()
+        field = torch.empty(tuple(ctx.cell.shape), dtype=torch.float64, device="cuda")
+        out = torch.zeros_like(field)
+        for ab in range(9):
+            if g[ab] == 0.0:
+                continue
+            ctx.cell.fft_homog_stress_sensitivity(ctx.mat, ctx.F, (ab // 3, ab % 3), ctx.dscale, field, ctx.aopt)
+            out.add_(field, alpha=float(g[ab]))
+        return out, None, None, None, None, None, None, None, None
+
+
+def homogenized_stress_of_density(rho: torch.Tensor, cell: Context, mat: Material, Fbar, F: torch.Tensor,
+                                  dscale: torch.Tensor, n_increments: int = 1, options: FhOptions | None = None,
+                                  adjoint_options: FhOptions | None = None) -> torch.Tensor:
+    """Pbar (9 entries) of the cell under Fbar, differentiable in the voxel density rho.
+
+    ``mat.scale`` must hold s(rho) and ``dscale`` ds/drho (CUDA float64 fields of the grid shape); F is the
+    caller's CUDA float64 field [9, nx, ny, nz], left at the converged state by forward and read there by
+    backward (it must not change in between). The gradient is sum_ab g_ab dPbar_ab/drho, each term from
+    fft_homog_stress_sensitivity (the adjoint of the linearised equilibrium is a unit response, since the
+    tangent has major symmetry).
+    """
+    return _HomogenizedStressOfDensity.apply(rho, cell, mat, Fbar, F, dscale, n_increments, options,
+                                             adjoint_options if adjoint_options is not None
+                                             else default_options(cg_tol=1e-12))
+
+
+__all__ = ["homogenized_stress", "homogenized_modulus", "homogenized_stress_of_density"]

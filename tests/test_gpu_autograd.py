@@ -5,7 +5,10 @@
   converged state (1e-8 relative), and central finite differences of two
   solves (step 1e-6, relative 1e-5);
 * Cbar_1212(rho) of a SIMP cell: the gradient with respect to the voxel
-  density equals the oracle's sensitivity field (1e-8 max-relative).
+  density equals the oracle's sensitivity field (1e-8 max-relative);
+* Pbar(rho) of a finite-strain SIMP cell under a fixed Fbar: the gradient of
+  w . Pbar equals sum_ab w_ab of the oracle's stress sensitivity fields
+  (1e-8 max-relative) and central differences of two solves at a voxel.
 """
 
 import numpy as np
@@ -82,3 +85,43 @@ def test_modulus_gradient_is_sensitivity_field(fh):
     np.testing.assert_allclose(float(c), C_ref[1, 1], rtol=1e-9)
     ref = homogenize.sensitivity(phase, params, scale, dscale, 1, 1, cg_tol=1e-13)
     assert field_maxrel(grad[None], ref[None]) < 1e-8
+
+
+def test_stress_of_density_gradient_is_weighted_stress_sensitivity(fh):
+    import torch
+
+    from paper_2408_03804_gb300.autograd import homogenized_stress_of_density
+
+    n = 12
+    rho = 0.35 + 0.65 * simp_config(n, seed=4)[2]
+    scale, dscale = rho ** 3, 3.0 * rho ** 2
+    phase = np.zeros((n, n, n), np.uint8)
+    params = np.array([[1.5, 1.0]])
+    Fbar = shear_macro(0.05, finite=True)
+    w = np.random.default_rng(2).uniform(-1, 1, 9)
+    opts = fh.default_options(newton_tol=1e-12, cg_tol=1e-13)
+    with fh.Context(n, n, n) as cell:
+        mat = fh.Material(fh.NEO_HOOKEAN, phase, params, scale=dev(scale))
+        F = torch.zeros((9, n, n, n), dtype=torch.float64, device="cuda")
+        r = torch.tensor(rho, dtype=torch.float64, device="cuda", requires_grad=True)
+        pbar = homogenized_stress_of_density(r, cell, mat, Fbar, F, dev(dscale), options=opts,
+                                             adjoint_options=fh.default_options(cg_tol=1e-13))
+        (pbar * torch.as_tensor(w, device="cuda")).sum().backward()
+        grad = host(r.grad)
+        ref = sum(w[ab] * homogenize.stress_sensitivity(phase, params, 1, host(F), scale, dscale, ab, cg_tol=1e-13)
+                  for ab in range(9))
+        assert field_maxrel(grad[None], ref[None]) < 1e-8
+
+        def wpbar(rr):
+            Fs = torch.zeros_like(F)
+            p, _, _ = cell.fft_homog_solve(fh.Material(fh.NEO_HOOKEAN, phase, params, scale=dev(rr ** 3)), Fbar,
+                                           Fs, options=opts)
+            return float(w @ p)
+
+        v = (3, 7, 1)
+        h = 1e-4
+        rp, rm = rho.copy(), rho.copy()
+        rp[v] += h
+        rm[v] -= h
+        fd = (wpbar(rp) - wpbar(rm)) / (2 * h)
+        assert abs(fd - grad[v]) <= 1e-5 * abs(grad[v]) + 1e-7 * np.abs(grad).max()
