@@ -38,7 +38,10 @@ GAMMA = 0.05
 METRIC = "time-to-solve @1e-8 residual (128³ neo-Hookean); CG matvec GB/s vs HBM peak"
 WORKLOAD = ("neo-Hookean 128^3, RSA spheres r~U[4,10] vox, f=0.30, contrast 10 (mu=1, lambda=1.5), "
             "Fbar=I+0.05 e_x(x)e_y in 5 increments, Newton tol 1e-8, CG tol 1e-10, FP64")
-L2_NOTE = "working set ~1.6 GB per solve (inputs larger than L2), no explicit flush"
+def l2_note(shape) -> str:
+    """The working set of one CG iteration (fields, packed tangent, spectrum: about 0.8 KB per voxel)."""
+    gb = 810.0 * shape[0] * shape[1] * shape[2] / 1e9
+    return f"working set ~{gb:.1f} GB per solve (inputs larger than L2), no explicit flush"
 HBM_PEAK_FALLBACK = 6694.5
 # FP64 issue rate from unit counts and clock (152 SMs x 2 FP64 FMA lanes per
 # clock x 2.07 GHz), used only when the live DFMA probe cannot run
@@ -334,7 +337,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [N_GRID] * 3, "l2": L2_NOTE},
+        "config": {"workload": WORKLOAD, "grid": [N_GRID] * 3, "l2": l2_note([N_GRID] * 3)},
         "extrapolated": True,
         "cpu_baseline": {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle", "extrapolated": True,
                          "sample": f"extrapolated from a sample: per step one Newton iteration at 128^3 with 3 CG "
@@ -1073,7 +1076,7 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if shape == (N_GRID,) * 3 else WORKLOAD.replace("128^3", "x".join(map(str, shape))),
-                   "grid": list(shape), "l2": L2_NOTE},
+                   "grid": list(shape), "l2": l2_note(shape)},
         "replicas": world,
         "timing": "CUDA events around the K solves, no per-launch events inside the timed region",
         "result": {"newton_iterations": st["n_newton"], "cg_iterations": st["n_cg"], "pbar": pbar.tolist()},
