@@ -512,6 +512,23 @@ def run_batch(args, world, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         t_batch = max_over_ranks(world, e0.elapsed_time(e1) / 1e3 / args.steps, torch.device("cuda", local))
+        df = None
+        if args.df64:
+            # the same batch with double-float CG products (an option; the line's value stays FP64)
+            opts_df = fh.default_options(newton_tol=NEWTON_TOL, check_every=8, matvec_arith=fh.ARITH_DF64)
+            for _ in range(max(args.warmup, 1)):
+                b.fft_homog_solve_batched(fh.LINEAR_ELASTIC, params, Ebar, options=opts_df)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                pb_df, st_df, nw_df, cg_df, rc_df = b.fft_homog_solve_batched(fh.LINEAR_ELASTIC, params, Ebar,
+                                                                             options=opts_df)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_df = max_over_ranks(world, e0.elapsed_time(e1) / 1e3 / args.steps, torch.device("cuda", local))
+            df = {"batched_df64_s": t_df, "speedup_vs_fp64_batched": t_batch / t_df, "rc": int(rc_df),
+                  "newton_iterations": int(nw_df.sum()), "cg_iterations": int(cg_df.sum()),
+                  "max_rel_diff_pbar_vs_fp64": float(np.abs(pb_df - pbar).max() / np.abs(pbar).max())}
         b.close()
         # the same cells one after another with the single-cell solver (one context per grid)
         ctxs = {}
@@ -563,6 +580,8 @@ def run_batch(args, world, rank, local):
         "fp64_floor_frac_sequential": floor_s / t_seq, "max_speedup_at_fp64_floor": t_seq / floor_s,
         "fp64_lane_ops": ops, "fp64_probe_lane_ops_per_s": fp64["lane_ops_per_s"],
     }
+    if df is not None:
+        line["df64_option"] = df
     print(json.dumps(line), flush=True)
 
 
@@ -1114,7 +1133,8 @@ def main():
     ap.add_argument("--examples", action="store_true",
                     help="time the paper's 2D examples (SVK square, J2 disks, Eshelby tangent); not the bench line")
     ap.add_argument("--df64", action="store_true",
-                    help="the 128^3 solve with double-float CG transforms beside FP64 (an option; not the bench line)")
+                    help="the 128^3 solve with double-float CG transforms beside FP64 (an option; not the bench "
+                         "line); with --batch, the batch also with double-float CG products")
     ap.add_argument("--only", nargs="+", default=None,
                     choices=("svk_square", "svk_scaling", "j2_biaxial", "eshelby"),
                     help="with --examples: run only these examples (for launch lists)")

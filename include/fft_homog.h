@@ -315,7 +315,9 @@ FH_API void fh_batch_destroy(fh_batch* batch);
  * (FH_OK, FH_ERR_NOT_CONVERGED or FH_ERR_NONPHYSICAL), newton_out[i] and
  * cg_out[i] (iteration totals). Returns FH_OK when every cell converged,
  * else the first failing cell's status; FH_ERR_UNSUPPORTED for FH_J2 (no
- * per-cell history). */
+ * per-cell history). opt->matvec_arith = FH_ARITH_DF64 runs every cell's CG
+ * products with double-float transforms (each cell's tangent buffer then
+ * holds its double-float copy during CG). */
 FH_API int fft_homog_solve_batched(fh_batch* batch, int kind, int n_phase, const double* params,
                                    const double Fbar[9], int n_increments, const fh_options* opt,
                                    double* Pbar_out, int* status_out, int* newton_out, int* cg_out);

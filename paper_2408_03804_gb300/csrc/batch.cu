@@ -22,6 +22,7 @@
 #include <map>
 #include <vector>
 
+#include "df64.cuh"
 #include "fh_kernels.h"
 
 using namespace fh;
@@ -78,6 +79,7 @@ struct SolveParams {
   double start[9], dfbar[9];
   double newton_tol, cg_tol;
   int n_inc, max_newton, max_cg, check_every, kind;
+  int df;  // CG products with double-float transforms (FH_ARITH_DF64)
   bool operator==(const SolveParams& o) const { return std::memcmp(this, &o, sizeof(*this)) == 0; }
 };
 
@@ -162,6 +164,7 @@ struct fh_batch {
   int* flags = nullptr;            // device [n_cells]
   double* params = nullptr;        // device [256][2]
   double2* tw = nullptr;
+  dfc* tw_df = nullptr;            // the same tables in double-float
   cudaGraphExec_t chunk = nullptr;  // one Newton tick and check_every CG iterations of every group
   SolveParams chunk_params;         // the parameters chunk was captured with (valid while chunk != nullptr)
 };
@@ -212,6 +215,8 @@ int launch_replay(fh_batch* b, const SolveParams& sp) {
     FB_CUDA(launch_x_ghat_batch(G.g, G.t, G.views_rhs, n, b->tw, -1.0 / (2.0 * (double)G.g.n), s));
     FB_CUDA(launch_inv_y_batch(G.g, G.t, G.views_rhs, n, b->tw, s));
     FB_CUDA(launch_inv_z_batch(G.g, G.t, kIZRhs, G.views_rhs, n, b->tw, s));
+    // the fresh tangents in double-float, in place, for the double-float CG products
+    if (sp.df) FB_CUDA(launch_tangent_to_df64_batch(G.g, G.states_rhs, n, s));
     FB_CUDA(launch_cg_init_batch(G.states_rhs, n, G.n_iz, sp.cg_tol, sp.max_cg, s));
     FB_CUDA(launch_fill_batch(G.g, G.states_rhs, n, 1, zero9, 0, s));
   }
@@ -219,11 +224,19 @@ int launch_replay(fh_batch* b, const SolveParams& sp) {
     for (Group& G : b->groups) {
       const int n = (int)G.cells.size();
       const double c_mv = 1.0 / (2.0 * (double)G.g.n);
-      FB_CUDA(launch_fwd_z_batch(G.g, G.t, kZCg, G.views_cg, n, b->tw, s));
-      FB_CUDA(launch_fwd_y_batch(G.g, G.t, G.views_cg, n, b->tw, s));
-      FB_CUDA(launch_x_ghat_batch(G.g, G.t, G.views_cg, n, b->tw, c_mv, s));
-      FB_CUDA(launch_inv_y_batch(G.g, G.t, G.views_cg, n, b->tw, s));
-      FB_CUDA(launch_inv_z_batch(G.g, G.t, kIZDot, G.views_cg, n, b->tw, s));
+      if (sp.df) {
+        FB_CUDA(launch_fwd_z_batch_df(G.g, G.t, kZCg, G.views_cg, n, b->tw_df, s));
+        FB_CUDA(launch_fwd_y_batch_df(G.g, G.t, G.views_cg, n, b->tw_df, s));
+        FB_CUDA(launch_x_ghat_batch_df(G.g, G.t, G.views_cg, n, b->tw_df, c_mv, s));
+        FB_CUDA(launch_inv_y_batch_df(G.g, G.t, G.views_cg, n, b->tw_df, s));
+        FB_CUDA(launch_inv_z_batch_df(G.g, G.t, G.views_cg, n, b->tw_df, s));
+      } else {
+        FB_CUDA(launch_fwd_z_batch(G.g, G.t, kZCg, G.views_cg, n, b->tw, s));
+        FB_CUDA(launch_fwd_y_batch(G.g, G.t, G.views_cg, n, b->tw, s));
+        FB_CUDA(launch_x_ghat_batch(G.g, G.t, G.views_cg, n, b->tw, c_mv, s));
+        FB_CUDA(launch_inv_y_batch(G.g, G.t, G.views_cg, n, b->tw, s));
+        FB_CUDA(launch_inv_z_batch(G.g, G.t, kIZDot, G.views_cg, n, b->tw, s));
+      }
       FB_CUDA(launch_cg_alpha_batch(G.states, n, G.n_iz, s));
       FB_CUDA(launch_cg_update_batch(G.g, G.states, n, s));
       FB_CUDA(launch_cg_beta_batch(G.states, n, G.n_pw, s));
@@ -285,11 +298,15 @@ int fh_batch_create(fh_batch** out, const fh_cell* cells, int n_cells, void* cud
   int rc;
   if ((rc = dalloc(b, &b->cg, sizeof(CgScalars) * n_cells)) || (rc = dalloc(b, &b->sums, 16 * sizeof(double) * n_cells)) ||
       (rc = dalloc(b, &b->ctl, sizeof(CellCtl) * n_cells)) || (rc = dalloc(b, &b->flags, sizeof(int) * n_cells)) ||
-      (rc = dalloc(b, &b->params, 512 * sizeof(double))) || (rc = dalloc(b, &b->tw, kTwiddleTotal * sizeof(double2))))
+      (rc = dalloc(b, &b->params, 512 * sizeof(double))) || (rc = dalloc(b, &b->tw, kTwiddleTotal * sizeof(double2))) ||
+      (rc = dalloc(b, &b->tw_df, kTwiddleTotal * sizeof(dfc))))
     return cleanup(rc);
   std::vector<double2> tw(kTwiddleTotal);
   fill_twiddle_table(tw.data());
-  if (cudaMemcpy(b->tw, tw.data(), kTwiddleTotal * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
+  std::vector<dfc> tw_df(kTwiddleTotal);
+  fill_twiddle_table_df(tw_df.data());
+  if (cudaMemcpy(b->tw, tw.data(), kTwiddleTotal * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->tw_df, tw_df.data(), kTwiddleTotal * sizeof(dfc), cudaMemcpyHostToDevice) != cudaSuccess)
     return cleanup(bfail(FH_ERR_CUDA, "twiddle upload failed"));
   // group the cells by grid shape
   std::map<long long, int> key_to_group;
@@ -389,7 +406,8 @@ int fft_homog_solve_batched(fh_batch* b, int kind, int n_phase, const double* pa
   fh_options opt;
   if (opt_in) opt = *opt_in;
   else fh_default_options(&opt);
-  if (!(opt.newton_tol > 0.0) || opt.max_newton < 1 || opt.max_cg < 0 || opt.check_every < 1)
+  if (!(opt.newton_tol > 0.0) || opt.max_newton < 1 || opt.max_cg < 0 || opt.check_every < 1 ||
+      (opt.matvec_arith != FH_ARITH_FP64 && opt.matvec_arith != FH_ARITH_DF64))
     return bfail(FH_ERR_ARG, "invalid options");
   if (opt.init != FH_INIT_REFERENCE) return bfail(FH_ERR_UNSUPPORTED, "batched solves start from the reference state");
   if (opt.tangent_mode != FH_TANGENT_STORED) return bfail(FH_ERR_UNSUPPORTED, "batched solves store the tangent");
@@ -418,6 +436,7 @@ int fft_homog_solve_batched(fh_batch* b, int kind, int n_phase, const double* pa
   sp.max_cg = opt.max_cg;
   sp.check_every = opt.check_every;
   sp.kind = kind;
+  sp.df = opt.matvec_arith == FH_ARITH_DF64;  // every batched grid has compile-time plans and an even nz
   // every cell at its first load increment, CG idle (done = 1), flags clear
   {
     std::vector<CellCtl> c0(nc);

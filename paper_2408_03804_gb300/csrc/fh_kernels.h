@@ -136,6 +136,21 @@ cudaError_t launch_inv_y_df(const Grid& g, const Tiling& t, dfc* S, const dfc* t
 cudaError_t launch_inv_z_df(const Grid& g, const Tiling& t, int mode, const dfc* S, double* out, const double* p,
                             double* partials, const dfc* tw, const CgScalars* cg, cudaStream_t s);
 
+// batched double-float CG passes (kZCg / kZCgFirst forward, kIZDot inverse)
+// over cells whose spectrum and tangent buffers hold double-float data; the
+// tangents are converted in place for the cells not masked by newton_done
+cudaError_t launch_tangent_to_df64_batch(const Grid& g, const CellState* cells, int n_cells, cudaStream_t s);
+cudaError_t launch_fwd_z_batch_df(const Grid& g, const Tiling& t, int mode, const CellView* cells, int n_cells,
+                                  const dfc* tw, cudaStream_t s);
+cudaError_t launch_fwd_y_batch_df(const Grid& g, const Tiling& t, const CellView* cells, int n_cells,
+                                  const dfc* tw, cudaStream_t s);
+cudaError_t launch_x_ghat_batch_df(const Grid& g, const Tiling& t, const CellView* cells, int n_cells,
+                                   const dfc* tw, double scale, cudaStream_t s);
+cudaError_t launch_inv_y_batch_df(const Grid& g, const Tiling& t, const CellView* cells, int n_cells,
+                                  const dfc* tw, cudaStream_t s);
+cudaError_t launch_inv_z_batch_df(const Grid& g, const Tiling& t, const CellView* cells, int n_cells,
+                                  const dfc* tw, cudaStream_t s);
+
 cudaError_t launch_fwd_z_batch(const Grid& g, const Tiling& t, int mode, const CellView* cells, int n_cells,
                                const double2* tw, cudaStream_t s);
 cudaError_t launch_fwd_y_batch(const Grid& g, const Tiling& t, const CellView* cells, int n_cells,

@@ -150,3 +150,26 @@ def test_df64_full_size_bench_cell_matches_fp64_solve(fh, torch):
     assert all(abs(a - b) <= 2 for a, b in zip(sdf["cg_iterations"], s64["cg_iterations"]))
     np.testing.assert_allclose(pdf, p64, rtol=PBAR_TOL, atol=PBAR_TOL * np.abs(p64).max())
     assert field_maxrel(Fdf - Fbar.reshape(9, 1, 1, 1), F64 - Fbar.reshape(9, 1, 1, 1)) < FIELD_TOL
+
+
+def test_df64_batched_cells_match_oracle_and_single_cell_df64_solves(fh, torch):
+    """A batch of uneven neo-Hookean cells with double-float CG products: each cell against the oracle
+    (the parity bars, same Newton counts) and against the single-cell double-float solve (1e-12)."""
+    shapes = [(16, 16, 16), (12, 12, 24), (8, 8, 8), (16, 16, 16)]
+    cells = [(random_spheres(shape, seed=20 + k, r_min=1.5, r_max=3.0), None) for k, shape in enumerate(shapes)]
+    params = two_phase_table(1.5, 1.0, 10.0)
+    Fbar = shear_macro(0.05, finite=True)
+    opts = fh.default_options(newton_tol=1e-10, check_every=4, matvec_arith=fh.ARITH_DF64)
+    with fh.Batch(cells) as b:
+        pbar, status, newton, cg, rc = b.fft_homog_solve_batched(fh.NEO_HOOKEAN, params, Fbar, options=opts)
+        F_batch = [F.cpu().numpy() for F in b.F]
+    assert rc == fh.FH_OK and np.all(status == 0)
+    for i, (phase, _) in enumerate(cells):
+        ref = osolver.solve(phase, params, 1, Fbar, newton_tol=1e-10)
+        assert newton[i] == len(ref.newton_residuals)
+        np.testing.assert_allclose(pbar[i], ref.Pbar, rtol=PBAR_TOL, atol=PBAR_TOL * np.abs(ref.Pbar).max())
+        assert np.abs(F_batch[i] - ref.F).max() < FIELD_TOL * np.abs(ref.F - Fbar.reshape(9, 1, 1, 1)).max()
+        F1, p1, st1 = _solve(fh, torch, phase, params, 1, Fbar, 1, 1e-10, fh.ARITH_DF64)
+        np.testing.assert_allclose(pbar[i], p1, rtol=1e-12, atol=1e-14)
+        assert np.abs(F_batch[i] - F1).max() <= 1e-12 * np.abs(F1 - Fbar.reshape(9, 1, 1, 1)).max()
+        assert abs(cg[i] - st1["n_cg"]) <= 2 * newton[i]
