@@ -355,6 +355,17 @@ FH_API int fh_profile_read(fh_ctx* ctx, long long counts[FH_PROF_NCLASS], double
 FH_API int fh_probe_fp64(int ctas_per_sm, int chains, long long iters, void* cuda_stream, double* ms_out,
                          double* lane_ops_out);
 
+/* The double-float conversions of FH_ARITH_DF64, for checking (no
+ * counterpart in the paper): for each of the n device doubles in_dev, hi_dev
+ * and lo_dev (device floats, NULL to skip) get the split the double-float
+ * kernels make of it (hi: the significand cut after 23 bits; lo: the rest
+ * truncated to 24 significant bits; |x - hi - lo| < max(2^-47 |x|, 2^-125);
+ * 0 below the smallest normal float), and out_dev (device doubles) hi + lo joined back
+ * with one FP64 addition. n >= 0; out_dev may equal in_dev. Runs on
+ * cuda_stream and returns when done. */
+FH_API int fh_df64_roundtrip(const double* in_dev, float* hi_dev, float* lo_dev, double* out_dev, long long n,
+                             void* cuda_stream);
+
 /* ---- projection without device allocation ----
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory, such as a plug-in inside an application that

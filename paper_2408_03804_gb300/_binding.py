@@ -47,7 +47,7 @@ _ERR_NAMES = {1: "FH_ERR_ARG", 2: "FH_ERR_CUDA", 3: "FH_ERR_NOT_CONVERGED", 4: "
 # every symbol include/fft_homog.h declares
 EXPORTS = ["fh_default_options", "fh_create", "fh_destroy", "fh_last_error_string", "fh_constitutive",
            "fh_project", "fh_matvec", "fft_homog_solve", "fh_profile_enable", "fh_profile_read", "fh_project_static", "fft_homog_tangent", "fft_homog_sensitivity", "fft_homog_stress_sensitivity",
-           "fh_batch_create", "fh_batch_destroy", "fft_homog_solve_batched", "fh_autotune", "fh_probe_fp64",
+           "fh_batch_create", "fh_batch_destroy", "fft_homog_solve_batched", "fh_autotune", "fh_probe_fp64", "fh_df64_roundtrip",
            "fh_fno_param_count", "fh_fno_create", "fh_fno_destroy", "fh_fno_set_params", "fh_fno_forward",
            "fh_fno_loss_grad", "fh_fno_adam", "fh_fno_make_target", "fh_fno_warm_start", "fh_fno_test_skip_mma"]
 
@@ -146,6 +146,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.fh_autotune.restype = c_int
     lib.fh_probe_fp64.argtypes = [c_int, c_int, ctypes.c_longlong, c_void_p, POINTER(c_double), POINTER(c_double)]
     lib.fh_probe_fp64.restype = c_int
+    lib.fh_df64_roundtrip.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_longlong, c_void_p]
+    lib.fh_df64_roundtrip.restype = c_int
     lib.fh_fno_param_count.argtypes = []
     lib.fh_fno_param_count.restype = ctypes.c_longlong
     lib.fh_fno_create.argtypes = [POINTER(c_void_p), c_int, c_int, c_int, c_int, c_int, c_void_p]
@@ -218,6 +220,20 @@ def fh_project_static(A, out, scale: float = 1.0, lengths=None, stream=None):
     nx, ny, nz = A.shape[1:]
     La = _dvec(lengths, 3) if lengths is not None else (None, None)
     return _check(load().fh_project_static(_ptr(A), _ptr(out), nx, ny, nz, float(scale), La[1], c_void_p(stream)))
+
+
+def fh_df64_roundtrip(x, hi=None, lo=None, out=None, stream=None):
+    """The double-float split of a CUDA float64 tensor x as the FH_ARITH_DF64 kernels make it:
+    (hi, lo) float32 tensors and hi + lo joined back to float64 (returned as (hi, lo, out))."""
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    hi = torch.empty(x.shape, dtype=torch.float32, device=x.device) if hi is None else hi
+    lo = torch.empty(x.shape, dtype=torch.float32, device=x.device) if lo is None else lo
+    out = torch.empty_like(x) if out is None else out
+    _check(load().fh_df64_roundtrip(_ptr(x), _ptr(hi), _ptr(lo), _ptr(out), int(x.numel()), c_void_p(stream)))
+    return hi, lo, out
 
 
 def fh_probe_fp64(ctas_per_sm: int = 4, chains: int = 8, iters: int = 1 << 18, stream=None):

@@ -74,8 +74,8 @@ __device__ __forceinline__ double to_double(df64 a) { return (double)a.hi + (dou
 // scarce resource): split_double cuts the 52-bit significand of x after 23
 // bits (hi, exact) and turns the remaining 29 bits into lo, truncated to 24
 // significant bits, so that |x - hi - lo| < 2^-47 |x|. Values below the
-// smallest normal float (2^-126) become 0, and lo below it is dropped (an
-// absolute error under 2^-126); infinities and NaN map to hi.
+// smallest normal float (2^-126) become 0, and a lo below it is dropped (an
+// absolute error under 2^-125); infinities and NaN map to hi.
 __device__ __forceinline__ df64 split_double(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;

@@ -4,6 +4,7 @@
 // the element type dfc; K : p, the CG updates and the p . y dot product stay
 // FP64. Grids whose x and y extents have compile-time plans and whose nz is
 // even only.
+#include <algorithm>
 #include <cmath>
 
 #include "fft_df64.cuh"
@@ -99,6 +100,16 @@ __global__ void __launch_bounds__(kThreads) k_tangent_to_df64_b(const CellState*
        i += (long long)gridDim.x * blockDim.x) {
     const double v = c.K[i];
     out[i] = split_double(v);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_df64_roundtrip(const double* __restrict__ in, float* __restrict__ hi,
+                                                            float* __restrict__ lo, double* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const df64 v = split_double(in[i]);
+    if (hi) hi[i] = v.hi;
+    if (lo) lo[i] = v.lo;
+    out[i] = join_df64(v);
   }
 }
 
@@ -346,3 +357,25 @@ cudaError_t launch_inv_z_batch_df(const Grid& g, const Tiling& t, const CellView
 }
 
 }  // namespace fh
+
+extern "C" void fh_internal_set_error(const char* msg);
+
+extern "C" int fh_df64_roundtrip(const double* in_dev, float* hi_dev, float* lo_dev, double* out_dev, long long n,
+                                 void* cuda_stream) {
+  fh_internal_set_error("");
+  if (n < 0 || (n > 0 && (!in_dev || !out_dev))) {
+    fh_internal_set_error("fh_df64_roundtrip: n < 0 or NULL in/out");
+    return FH_ERR_ARG;
+  }
+  if (n == 0) return FH_OK;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const long long blocks = std::min<long long>((n + fh::kThreads - 1) / fh::kThreads, 4096);
+  fh::k_df64_roundtrip<<<(unsigned)blocks, fh::kThreads, 0, s>>>(in_dev, hi_dev, lo_dev, out_dev, n);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    fh_internal_set_error(cudaGetErrorString(e));
+    return FH_ERR_CUDA;
+  }
+  return FH_OK;
+}

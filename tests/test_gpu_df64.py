@@ -173,3 +173,32 @@ def test_df64_batched_cells_match_oracle_and_single_cell_df64_solves(fh, torch):
         np.testing.assert_allclose(pbar[i], p1, rtol=1e-12, atol=1e-14)
         assert np.abs(F_batch[i] - F1).max() <= 1e-12 * np.abs(F1 - Fbar.reshape(9, 1, 1, 1)).max()
         assert abs(cg[i] - st1["n_cg"]) <= 2 * newton[i]
+
+
+def test_df64_split_and_join_of_field_values(fh, torch):
+    """The conversions the double-float kernels apply to FP64 field values: hi is x with its significand
+    cut after 23 bits (exact), lo the rest truncated to 24 significant bits, |x - hi - lo| < 2^-47 |x|
+    (or below 2^-125 where lo would fall below the smallest normal float),
+    hi + lo joined back with one FP64 addition; values below the smallest normal float give 0 and values
+    beyond the float range give an infinite hi."""
+    rng = np.random.default_rng(7)
+    x = np.concatenate([
+        np.array([0.0, -0.0, 1.0, -1.0, np.pi, -np.e, 2.0 ** -126, 2.0 ** -125 * 3, 1e-30, -3e-38, 1e300, -1e39]),
+        rng.standard_normal(4000) * 10.0 ** rng.uniform(-30, 30, 4000),
+    ])
+    hi, lo, out = fh.fh_df64_roundtrip(dev(x))
+    hi, lo, out = (host(t) for t in (hi, lo, out))
+    # expected hi: the double's bit pattern with the low 29 significand bits cleared, as a float32
+    bits = x.view(np.uint64) & ~np.uint64((1 << 29) - 1)
+    hi_ref = bits.view(np.float64).astype(np.float32)
+    normal = (np.abs(x) >= 2.0 ** -126) & (np.abs(x) < 2.0 ** 128)
+    assert np.array_equal(hi[normal], hi_ref[normal])
+    # relative 2^-47, or (a lo below the smallest normal float is dropped) absolute 2^-125
+    err = np.abs(x[normal] - (hi[normal].astype(np.float64) + lo[normal]))
+    assert np.all(err <= np.maximum(2.0 ** -47 * np.abs(x[normal]), 2.0 ** -125))
+    assert np.all(lo[normal] * np.sign(x[normal]) >= 0)  # truncation: lo has the sign of x (or is 0)
+    np.testing.assert_array_equal(out, hi.astype(np.float64) + lo.astype(np.float64))
+    tiny = np.abs(x) < 2.0 ** -126
+    assert np.all(hi[tiny] == 0) and np.all(lo[tiny] == 0)
+    huge = np.abs(x) >= 2.0 ** 128
+    assert np.all(np.isinf(hi[huge])) and np.all(np.sign(hi[huge]) == np.sign(x[huge]))
