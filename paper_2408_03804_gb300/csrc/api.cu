@@ -249,6 +249,7 @@ int run_projection(fh_ctx* ctx, const Grid& g, int zmode, const double* src, dou
   const Tiling& t = ctx->tiling;
   cudaStream_t s = ctx->stream;
   if (df) {
+    const Tiling t = df_tiles(ctx->tiling);
     dfc* S = reinterpret_cast<dfc*>(ctx->S);
     const dfc* tw = ctx->tw_df;
     const df64* Kd = K ? ctx->K_df : nullptr;
@@ -325,10 +326,13 @@ int run_cg(fh_ctx* ctx, const Grid& g, const MatView& mv, const double* F_dev, b
   if (df && stored && (rc = tangent_to_df64(ctx, g, ctx->K))) return rc;
   cudaStream_t s = ctx->stream;
   CgScalars* cg = &ctx->sc->cg;
-  const int n_iz = (int)z_pass_ctas(g, ctx->tiling);
+  // partial sums of the inverse z pass: the right-hand side's came from the FP64 tiles,
+  // the CG products' from the tiles of their arithmetic
+  const int n_iz_rhs = (int)z_pass_ctas(g, ctx->tiling);
+  const int n_iz = (int)z_pass_ctas(g, df ? df_tiles(ctx->tiling) : ctx->tiling);
   const int n_upd = (int)cg_update_ctas(g);
   const double c_mv = 1.0 / (2.0 * (double)g.n);
-  FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_init(cg, ctx->partials, n_iz, cg_tol, max_cg, s); }));
+  FH_CUDA(prof(ctx, kPCgScalar, [&] { return launch_cg_init(cg, ctx->partials, n_iz_rhs, cg_tol, max_cg, s); }));
   FH_CUDA(cudaMemsetAsync(ctx->x, 0, (size_t)9 * g.n * sizeof(double), s));
   int launched = 0;
   // every exit below clears the tag; launches of the loop are booked by prof_commit_cg

@@ -225,11 +225,12 @@ int launch_replay(fh_batch* b, const SolveParams& sp) {
       const int n = (int)G.cells.size();
       const double c_mv = 1.0 / (2.0 * (double)G.g.n);
       if (sp.df) {
-        FB_CUDA(launch_fwd_z_batch_df(G.g, G.t, kZCg, G.views_cg, n, b->tw_df, s));
-        FB_CUDA(launch_fwd_y_batch_df(G.g, G.t, G.views_cg, n, b->tw_df, s));
-        FB_CUDA(launch_x_ghat_batch_df(G.g, G.t, G.views_cg, n, b->tw_df, c_mv, s));
-        FB_CUDA(launch_inv_y_batch_df(G.g, G.t, G.views_cg, n, b->tw_df, s));
-        FB_CUDA(launch_inv_z_batch_df(G.g, G.t, G.views_cg, n, b->tw_df, s));
+        const Tiling td = df_tiles(G.t);
+        FB_CUDA(launch_fwd_z_batch_df(G.g, td, kZCg, G.views_cg, n, b->tw_df, s));
+        FB_CUDA(launch_fwd_y_batch_df(G.g, td, G.views_cg, n, b->tw_df, s));
+        FB_CUDA(launch_x_ghat_batch_df(G.g, td, G.views_cg, n, b->tw_df, c_mv, s));
+        FB_CUDA(launch_inv_y_batch_df(G.g, td, G.views_cg, n, b->tw_df, s));
+        FB_CUDA(launch_inv_z_batch_df(G.g, td, G.views_cg, n, b->tw_df, s));
       } else {
         FB_CUDA(launch_fwd_z_batch(G.g, G.t, kZCg, G.views_cg, n, b->tw, s));
         FB_CUDA(launch_fwd_y_batch(G.g, G.t, G.views_cg, n, b->tw, s));
@@ -237,7 +238,7 @@ int launch_replay(fh_batch* b, const SolveParams& sp) {
         FB_CUDA(launch_inv_y_batch(G.g, G.t, G.views_cg, n, b->tw, s));
         FB_CUDA(launch_inv_z_batch(G.g, G.t, kIZDot, G.views_cg, n, b->tw, s));
       }
-      FB_CUDA(launch_cg_alpha_batch(G.states, n, G.n_iz, s));
+      FB_CUDA(launch_cg_alpha_batch(G.states, n, sp.df ? (int)z_pass_ctas(G.g, df_tiles(G.t)) : G.n_iz, s));
       FB_CUDA(launch_cg_update_batch(G.g, G.states, n, s));
       FB_CUDA(launch_cg_beta_batch(G.states, n, G.n_pw, s));
     }

@@ -72,10 +72,18 @@ struct CellState {
 };
 
 struct Tiling {
-  int lines_z;   // z lines per CTA in the z passes
-  int bk_y;      // kz columns per CTA in the y passes
-  int bk_x;      // kz columns per CTA in the x pass
+  int lines_z;     // z lines per CTA in the z passes
+  int bk_y;        // kz columns per CTA in the y passes
+  int bk_x;        // kz columns per CTA in the x pass
+  int lines_z_df;  // z lines per CTA in the double-float z passes (half the shared memory of lines_z)
 };
+
+// the tiles of the double-float passes: lines_z_df z lines per CTA
+inline Tiling df_tiles(const Tiling& t) {
+  Tiling d = t;
+  d.lines_z = t.lines_z_df > 0 ? t.lines_z_df : t.lines_z;
+  return d;
+}
 
 // the twiddle tables of every supported length, w_L^m = exp(-2 pi i m / L) at
 // twiddle_offset(L) + m, into t[kTwiddleTotal] (host memory)

@@ -143,7 +143,7 @@ void fill_twiddle_table_df(dfc* t) {
 cudaError_t setup_df64_kernels(const Grid& g, const Tiling& t) {
   if (!df64_grid_ok(g)) return cudaSuccess;
   cudaError_t e = cudaSuccess;
-  const size_t zs = z_pass_smem(g, t);
+  const size_t zs = z_pass_smem(g, df_tiles(t));
   const int M = g.nz / 2;
 #define ZCASE(V)                                                       \
   case V:                                                              \

@@ -265,6 +265,11 @@ Tiling choose_tiling(const Grid& g, long long min_ctas) {
     while (lines % lb) --lb;
   }
   t.lines_z = lb;
+  // the double-float z passes stream the tangent with fewer registers free
+  // for loads in flight: half the lines per CTA, for more resident CTAs
+  int ld = lb / 2 > 0 ? lb / 2 : 1;
+  while (lines % ld) --ld;
+  t.lines_z_df = ld;
   // kz columns per CTA of the y and x passes, likewise
   auto chunks = [&](int bk) { return (long long)((g.nzh + bk - 1) / bk); };
   int by = 512 / g.ny;
