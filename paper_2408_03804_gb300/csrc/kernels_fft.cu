@@ -265,10 +265,15 @@ Tiling choose_tiling(const Grid& g, long long min_ctas) {
     while (lines % lb) --lb;
   }
   t.lines_z = lb;
-  // the double-float z passes stream the tangent with fewer registers free
-  // for loads in flight: half the lines per CTA, for more resident CTAs
-  int ld = lb / 2 > 0 ? lb / 2 : 1;
-  while (lines % ld) --ld;
+  // the double-float z passes on long z lines: half the lines per CTA (half
+  // the shared memory, more resident CTAs to stream the tangent); measured
+  // faster at 128^3 (4 -> 2 lines), slower at one line per CTA (256^3) and on
+  // the short lines of the batched grids, which keep lines_z
+  int ld = lb;
+  if (g.nz >= 128 && lb >= 4) {
+    ld = lb / 2;
+    while (lines % ld) --ld;
+  }
   t.lines_z_df = ld;
   // kz columns per CTA of the y and x passes, likewise
   auto chunks = [&](int bk) { return (long long)((g.nzh + bk - 1) / bk); };
