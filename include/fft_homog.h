@@ -109,9 +109,7 @@ extern "C" {
  *                about 48 significant bits, on the FP32 pipe, which issues
  *                about 75 times faster than FP64 on GB300). K : p, the CG
  *                vector updates and dot products, the Newton right-hand
- *                side, residuals and stress stay FP64. Grids whose x and y
- *                extents have compile-time plans and whose nz is even
- *                (FH_ERR_UNSUPPORTED otherwise). */
+ *                side, residuals and stress stay FP64. Every grid. */
 #define FH_ARITH_FP64 0
 #define FH_ARITH_DF64 1
 
@@ -205,8 +203,7 @@ FH_API int fh_project(fh_ctx* ctx, const double* A_dev, double* out_dev, double 
  * With K_dev != NULL the stored packed tangent [45][N] is applied; with
  * K_dev == NULL, K : p is re-derived from F_dev and mat by AD (jvp form).
  *   p_dev in [9][N], y_dev out [9][N] (must not alias p_dev).
- * arith: FH_ARITH_FP64, or FH_ARITH_DF64 for the transforms in double-float
- * (FH_ERR_UNSUPPORTED on grids it does not cover, see FH_ARITH_DF64). */
+ * arith: FH_ARITH_FP64, or FH_ARITH_DF64 for the transforms in double-float. */
 FH_API int fh_matvec(fh_ctx* ctx, const fh_material* mat, const double* F_dev,
               const double* K_dev, const double* p_dev, double* y_dev,
               const double lengths[3], int arith);

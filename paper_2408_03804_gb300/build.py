@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB_NAME = "libfft_homog.so"
-SOURCES = ["kernels_fft.cu", "kernels_df64.cu", "kernels_plane.cu", "kernels_pointwise.cu", "api.cu", "project_static.cu", "batch.cu", "fno.cu", "probe.cu"]
+SOURCES = ["kernels_fft.cu", "kernels_df64.cu", "kernels_df64_yx.cu", "kernels_df64_batch.cu", "kernels_plane.cu", "kernels_pointwise.cu", "api.cu", "project_static.cu", "batch.cu", "fno.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-fvisibility=hidden"]

@@ -515,7 +515,7 @@ int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
       (e = cudaMalloc(&c->K, (size_t)45 * g.n * sizeof(double))) ||
       (e = cudaMalloc(&c->partials, (size_t)np * sizeof(double))) ||
       (e = cudaMalloc(&c->params, 1024 * sizeof(double))) ||
-      (e = cudaMalloc(&c->tw, tw_len * sizeof(double2))) || (e = cudaMalloc(&c->tw_df, kTwiddleTotal * sizeof(dfc))) ||
+      (e = cudaMalloc(&c->tw, tw_len * sizeof(double2))) || (e = cudaMalloc(&c->tw_df, tw_len * sizeof(dfc))) ||
       (e = cudaMalloc(&c->sc, sizeof(DevScalars)))) {
     fail(FH_ERR_CUDA, "fh_create: allocation failed: %s", cudaGetErrorString(e));
     return cleanup(FH_ERR_CUDA);
@@ -524,10 +524,10 @@ int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
   fill_twiddle_table(tw.data());
   if (g.px.L) fill_plan_tables(tw.data() + g.px.tw_off, g.px);
   if (g.py.L) fill_plan_tables(tw.data() + g.py.tw_off, g.py);
-  std::vector<dfc> tw_df(kTwiddleTotal);
-  fill_twiddle_table_df(tw_df.data());
+  std::vector<dfc> tw_df(tw_len);
+  twiddles_to_df64(tw.data(), tw_df.data(), tw_len);
   if ((e = cudaMemcpy(c->tw, tw.data(), tw_len * sizeof(double2), cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(c->tw_df, tw_df.data(), kTwiddleTotal * sizeof(dfc), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(c->tw_df, tw_df.data(), tw_len * sizeof(dfc), cudaMemcpyHostToDevice)) ||
       (e = cudaMemset(c->sc, 0, sizeof(DevScalars))) || (e = setup_fft_kernels(g, c->tiling))) {
     fail(FH_ERR_CUDA, "fh_create: setup failed: %s", cudaGetErrorString(e));
     return cleanup(FH_ERR_CUDA);
@@ -603,8 +603,6 @@ int fh_matvec(fh_ctx* ctx, const fh_material* mat, const double* F_dev, const do
   if (p_dev == y_dev) return fail(FH_ERR_ARG, "y must not alias p");
   if (!lengths_ok(lengths)) return fail(FH_ERR_ARG, "box lengths must be positive");
   if (arith != FH_ARITH_FP64 && arith != FH_ARITH_DF64) return fail(FH_ERR_ARG, "invalid arith");
-  if (arith == FH_ARITH_DF64 && !df64_grid_ok(ctx->g))
-    return fail(FH_ERR_UNSUPPORTED, "FH_ARITH_DF64 needs x and y extents with compile-time plans and an even nz");
   const bool df = arith == FH_ARITH_DF64;
   DeviceGuard dg(ctx->dev);
   const Grid g = grid_with_lengths(ctx, lengths);
@@ -650,8 +648,6 @@ int fft_homog_solve(fh_ctx* ctx, const fh_material* mat, const double Fbar[9], i
   if (opt.init != FH_INIT_REFERENCE && opt.init != FH_INIT_GIVEN) return fail(FH_ERR_ARG, "invalid init");
   if (opt.tangent_mode != FH_TANGENT_STORED && opt.tangent_mode != FH_TANGENT_JVP)
     return fail(FH_ERR_ARG, "invalid tangent_mode");
-  if (opt.matvec_arith == FH_ARITH_DF64 && !df64_grid_ok(ctx->g))
-    return fail(FH_ERR_UNSUPPORTED, "FH_ARITH_DF64 needs x and y extents with compile-time plans and an even nz");
   if (!lengths_ok(opt.lengths)) return fail(FH_ERR_ARG, "box lengths must be positive");
   for (int c = 0; c < 9; ++c)
     if (!std::isfinite(Fbar[c])) return fail(FH_ERR_ARG, "non-finite Fbar");
@@ -773,8 +769,6 @@ int options_or_default(const fh_ctx* ctx, const fh_options* in, fh_options* o) {
       (o->launch_mode != FH_LAUNCH_GRAPH && o->launch_mode != FH_LAUNCH_PLAIN) ||
       (o->matvec_arith != FH_ARITH_FP64 && o->matvec_arith != FH_ARITH_DF64))
     return fail(FH_ERR_ARG, "invalid options");
-  if (o->matvec_arith == FH_ARITH_DF64 && !df64_grid_ok(ctx->g))
-    return fail(FH_ERR_UNSUPPORTED, "FH_ARITH_DF64 needs x and y extents with compile-time plans and an even nz");
   if (!lengths_ok(o->lengths)) return fail(FH_ERR_ARG, "box lengths must be positive");
   return FH_OK;
 }

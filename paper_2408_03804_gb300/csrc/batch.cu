@@ -305,7 +305,7 @@ int fh_batch_create(fh_batch** out, const fh_cell* cells, int n_cells, void* cud
   std::vector<double2> tw(kTwiddleTotal);
   fill_twiddle_table(tw.data());
   std::vector<dfc> tw_df(kTwiddleTotal);
-  fill_twiddle_table_df(tw_df.data());
+  twiddles_to_df64(tw.data(), tw_df.data(), kTwiddleTotal);
   if (cudaMemcpy(b->tw, tw.data(), kTwiddleTotal * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->tw_df, tw_df.data(), kTwiddleTotal * sizeof(dfc), cudaMemcpyHostToDevice) != cudaSuccess)
     return cleanup(bfail(FH_ERR_CUDA, "twiddle upload failed"));

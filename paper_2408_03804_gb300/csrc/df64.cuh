@@ -24,6 +24,7 @@ struct df64 {
 struct __align__(16) dfc {
   df64 re, im;
 };
+static_assert(sizeof(dfc) == sizeof(double2), "a double-float entry takes the place of an FP64 one");
 
 __device__ __forceinline__ df64 two_sum(float a, float b) {
   const float s = a + b;
@@ -123,6 +124,14 @@ __device__ __forceinline__ dfc cmulc(dfc a, dfc w) {
 }
 __device__ __forceinline__ dfc cscale(dfc a, df64 s) { return dfc{dd_mul(a.re, s), dd_mul(a.im, s)}; }
 __device__ __forceinline__ dfc cscale(dfc a, double s) { return cscale(a, to_df64(s)); }
+
+// s a + b, zero, the parts of a twiddle (cos, -sin), a Rader permutation entry (two indices)
+__device__ __forceinline__ dfc caxpy(df64 s, dfc a, dfc b) { return dfc{dd_fma(s, a.re, b.re), dd_fma(s, a.im, b.im)}; }
+__device__ __forceinline__ void czero(dfc& a) { a = dfc{df64{0.f, 0.f}, df64{0.f, 0.f}}; }
+__device__ __forceinline__ df64 tw_cos(dfc w) { return w.re; }
+__device__ __forceinline__ df64 tw_sin(dfc w) { return dd_neg(w.im); }
+__device__ __forceinline__ int perm_first(dfc w) { return (int)w.re.hi; }
+__device__ __forceinline__ int perm_second(dfc w) { return (int)w.im.hi; }
 
 template <bool INV>
 __device__ __forceinline__ dfc mul_mi(dfc a) {

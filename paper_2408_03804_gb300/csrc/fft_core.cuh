@@ -31,6 +31,18 @@ __device__ __forceinline__ double2 mul_mi(double2 a) {
   return INV ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
 }
 
+// scalar helpers shared with the double-float element type (df64.cuh has the
+// dfc overloads): s a + b, zero, the cosine and minus-sine parts of a twiddle
+// (cos, -sin), and the index pair stored in a Rader permutation entry
+__device__ __forceinline__ double2 caxpy(double s, double2 a, double2 b) {
+  return make_double2(fma(s, a.x, b.x), fma(s, a.y, b.y));
+}
+__device__ __forceinline__ void czero(double2& a) { a = make_double2(0.0, 0.0); }
+__device__ __forceinline__ double tw_cos(double2 w) { return w.x; }
+__device__ __forceinline__ double tw_sin(double2 w) { return -w.y; }
+__device__ __forceinline__ int perm_first(double2 w) { return (int)w.x; }
+__device__ __forceinline__ int perm_second(double2 w) { return (int)w.y; }
+
 template <bool INV>
 __device__ __forceinline__ void dft2(double2* v) {
   const double2 a = v[0], b = v[1];
@@ -277,9 +289,9 @@ __device__ __forceinline__ C* fft_pencils(C* a, C* b, const PencilLayout& lay, c
 // the p-point roots of a direct stage are entries of the same table
 // (w_p^e = w_L^(e L / p)).
 
-template <int R, bool INV, bool JFAST>
-__device__ __forceinline__ void stockham_stage_rt(const double2* __restrict__ src, double2* __restrict__ dst,
-                                                  const PencilLayout& lay, const double2* __restrict__ tw, int L,
+template <int R, bool INV, bool JFAST, class C>
+__device__ __forceinline__ void stockham_stage_rt(const C* __restrict__ src, C* __restrict__ dst,
+                                                  const PencilLayout& lay, const C* __restrict__ tw, int L,
                                                   int NS) {
   const int NB = L / R;
   const int nq = (lay.np / lay.group) * lay.valid;
@@ -288,16 +300,16 @@ __device__ __forceinline__ void stockham_stage_rt(const double2* __restrict__ sr
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int q = pencil_of(JFAST ? t / NB : t % nq, lay);
     const int j = JFAST ? t % NB : t / nq;
-    const double2* s = src + q * lay.q_stride;
-    double2* d = dst + q * lay.q_stride;
-    double2 v[R];
+    const C* s = src + q * lay.q_stride;
+    C* d = dst + q * lay.q_stride;
+    C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = s[(j + r * NB) * lay.j_stride];
     const int k = j % NS;
     if (NS > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const double2 w = tw[r * k * step];
+        const C w = tw[r * k * step];
         v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
       }
     }
@@ -318,10 +330,9 @@ __device__ __forceinline__ void stockham_stage_rt(const double2* __restrict__ sr
 // R entries; the source buffer is dead after the stage), then one
 // (butterfly, r) per thread, r = 0 .. (R-1)/2, writes X_0 (r = 0) or the
 // pair X_r, X_{R-r}.
-template <bool INV, bool JFAST>
-__device__ __forceinline__ void stockham_stage_odd(double2* __restrict__ src, double2* __restrict__ dst,
-                                                   const PencilLayout& lay, const double2* __restrict__ tw, int L,
-                                                   int R, int NS) {
+template <bool INV, bool JFAST, class C>
+__device__ __forceinline__ void stockham_stage_odd(C* __restrict__ src, C* __restrict__ dst, const PencilLayout& lay,
+                                                   const C* __restrict__ tw, int L, int R, int NS) {
   const int NB = L / R;
   const int nq = (lay.np / lay.group) * lay.valid;
   const int step = L / (NS * R);
@@ -331,12 +342,12 @@ __device__ __forceinline__ void stockham_stage_odd(double2* __restrict__ src, do
     const int m = 1 + t % H, qj = t / H;
     const int q = pencil_of(JFAST ? qj / NB : qj % nq, lay);
     const int j = JFAST ? qj % NB : qj / nq;
-    double2* s = src + q * lay.q_stride;
-    double2 a = s[(j + m * NB) * lay.j_stride];
-    double2 b = s[(j + (R - m) * NB) * lay.j_stride];
+    C* s = src + q * lay.q_stride;
+    C a = s[(j + m * NB) * lay.j_stride];
+    C b = s[(j + (R - m) * NB) * lay.j_stride];
     if (NS > 1) {
       const int k = j % NS;
-      const double2 wa = tw[m * k * step], wb = tw[(R - m) * k * step];
+      const C wa = tw[m * k * step], wb = tw[(R - m) * k * step];
       a = INV ? cmulc(a, wa) : cmul(a, wa);
       b = INV ? cmulc(b, wb) : cmul(b, wb);
     }
@@ -350,45 +361,39 @@ __device__ __forceinline__ void stockham_stage_odd(double2* __restrict__ src, do
     const int r = t % H1, qj = t / H1;
     const int q = pencil_of(JFAST ? qj / NB : qj % nq, lay);
     const int j = JFAST ? qj % NB : qj / nq;
-    const double2* s = src + q * lay.q_stride;
-    const double2 v0 = s[j * lay.j_stride];
+    const C* s = src + q * lay.q_stride;
+    const C v0 = s[j * lay.j_stride];
     const int base = (j / NS) * NS * R + j % NS;
-    double2* d = dst + q * lay.q_stride;
+    C* d = dst + q * lay.q_stride;
     if (r == 0) {
-      double ar = v0.x, ai = v0.y;
-      for (int m = 1; m <= H; ++m) {
-        const double2 sm = s[(j + m * NB) * lay.j_stride];
-        ar += sm.x;
-        ai += sm.y;
-      }
-      d[base * lay.j_stride] = make_double2(ar, ai);
+      C acc = v0;
+      for (int m = 1; m <= H; ++m) acc = cadd(acc, s[(j + m * NB) * lay.j_stride]);
+      d[base * lay.j_stride] = acc;
       continue;
     }
-    double pr = 0.0, pi = 0.0, qr = 0.0, qi = 0.0;
+    C P, Q;
+    czero(P);
+    czero(Q);
     int e = 0;
     for (int m = 1; m <= H; ++m) {
       e += r;
       if (e >= R) e -= R;
-      const double2 w = tw[e * NB];  // (cos, -sin) of 2 pi e / R
-      const double2 sm = s[(j + m * NB) * lay.j_stride];
-      const double2 dm = s[(j + (R - m) * NB) * lay.j_stride];
-      pr = fma(sm.x, w.x, pr);
-      pi = fma(sm.y, w.x, pi);
-      qr = fma(dm.x, -w.y, qr);
-      qi = fma(dm.y, -w.y, qi);
+      const C w = tw[e * NB];  // (cos, -sin) of 2 pi e / R
+      P = caxpy(tw_cos(w), s[(j + m * NB) * lay.j_stride], P);
+      Q = caxpy(tw_sin(w), s[(j + (R - m) * NB) * lay.j_stride], Q);
     }
-    // -i Q = (Q.y, -Q.x) forward, +i Q = (-Q.y, Q.x) inverse
-    const double sr = INV ? -qi : qi, si = INV ? qr : -qr;
-    d[(base + r * NS) * lay.j_stride] = make_double2(v0.x + pr + sr, v0.y + pi + si);
-    d[(base + (R - r) * NS) * lay.j_stride] = make_double2(v0.x + pr - sr, v0.y + pi - si);
+    // -i Q forward, +i Q inverse
+    const C e0 = cadd(v0, P), iq = mul_mi<INV>(Q);
+    d[(base + r * NS) * lay.j_stride] = cadd(e0, iq);
+    d[(base + (R - r) * NS) * lay.j_stride] = csub(e0, iq);
   }
 }
 
 // The stages `r[0..n)` of a run-time plan of length L over the pencils of a
 // (partner b); returns the buffer holding the result.
-template <bool INV, bool JFAST>
-__device__ __forceinline__ double2* run_stages_rt(double2* a, double2* b, const PencilLayout& lay,
-                                                  const double2* tw, int L, int n, const int* r) {
+template <bool INV, bool JFAST, class C>
+__device__ __forceinline__ C* run_stages_rt(C* a, C* b, const PencilLayout& lay, const C* tw, int L, int n,
+                                            const int* r) {
   int NS = 1;
   for (int st = 0; st < n; ++st) {
     const int R = r[st];
@@ -401,7 +406,7 @@ __device__ __forceinline__ double2* run_stages_rt(double2* a, double2* b, const 
       case 16: stockham_stage_rt<16, INV, JFAST>(a, b, lay, tw, L, NS); break;
       default: stockham_stage_odd<INV, JFAST>(a, b, lay, tw, L, R, NS); break;
     }
-    double2* t = a;
+    C* t = a;
     a = b;
     b = t;
     NS *= R;
@@ -418,13 +423,12 @@ __device__ __forceinline__ double2* run_stages_rt(double2* a, double2* b, const 
 // length-M twiddles, Bhat forward, Bhat inverse, then (g^r, g^-r) as
 // doubles. Each pencil keeps v_0 in slot 0 of both buffers and runs the
 // inner transforms on slots 1..M; slot L (the pencil's padding) holds X_0.
-template <bool INV, bool JFAST>
-__device__ __forceinline__ double2* rader_pencils(double2* a, double2* b, const PencilLayout& lay,
-                                                  const double2* tab, const FftPlan& p) {
+template <bool INV, bool JFAST, class C>
+__device__ __forceinline__ C* rader_pencils(C* a, C* b, const PencilLayout& lay, const C* tab, const FftPlan& p) {
   const int L = p.L, M = L - 1;
-  const double2* itw = tab;
-  const double2* bhat = tab + (INV ? 2 : 1) * M;
-  const double2* perm = tab + 3 * M;
+  const C* itw = tab;
+  const C* bhat = tab + (INV ? 2 : 1) * M;
+  const C* perm = tab + 3 * M;
   const int nq = (lay.np / lay.group) * lay.valid;
   const int js = lay.j_stride;
   __syncthreads();
@@ -432,40 +436,39 @@ __device__ __forceinline__ double2* rader_pencils(double2* a, double2* b, const 
   for (int t = threadIdx.x; t < nq * L; t += blockDim.x) {
     const int q = pencil_of(JFAST ? t / L : t % nq, lay);
     const int e = JFAST ? t % L : t / nq;
-    const double2* s = a + q * lay.q_stride;
-    double2* d = b + q * lay.q_stride;
-    d[e * js] = e == 0 ? s[0] : s[(int)perm[e - 1].x * js];
+    const C* s = a + q * lay.q_stride;
+    C* d = b + q * lay.q_stride;
+    d[e * js] = e == 0 ? s[0] : s[perm_first(perm[e - 1]) * js];
   }
-  double2* C = run_stages_rt<false, JFAST>(b + js, a + js, lay, itw, M, p.in_n, p.in_r) - js;
+  C* Cv = run_stages_rt<false, JFAST>(b + js, a + js, lay, itw, M, p.in_n, p.in_r) - js;
   // Ahat * Bhat; X_0 = v_0 + Ahat_0 into slot L
   for (int t = threadIdx.x; t < nq * M; t += blockDim.x) {
     const int q = pencil_of(JFAST ? t / M : t % nq, lay);
     const int k = JFAST ? t % M : t / nq;
-    double2* c = C + q * lay.q_stride;
-    const double2 ah = c[(1 + k) * js];
+    C* c = Cv + q * lay.q_stride;
+    const C ah = c[(1 + k) * js];
     if (k == 0) c[L * js] = cadd(c[0], ah);
-    c[(1 + k) * js] = make_double2(ah.x * bhat[k].x - ah.y * bhat[k].y, ah.x * bhat[k].y + ah.y * bhat[k].x);
+    c[(1 + k) * js] = cmul(ah, bhat[k]);
   }
-  double2* D = (C == a) ? b : a;
-  double2* E = run_stages_rt<true, JFAST>(C + js, D + js, lay, itw, M, p.in_n, p.in_r) - js;
-  double2* O = (E == a) ? b : a;
-  // X_{g^-k} = v_0 + c_k, X_0 from slot L of C
+  C* D = (Cv == a) ? b : a;
+  C* E = run_stages_rt<true, JFAST>(Cv + js, D + js, lay, itw, M, p.in_n, p.in_r) - js;
+  C* O = (E == a) ? b : a;
+  // X_{g^-k} = v_0 + c_k, X_0 from slot L of Cv
   for (int t = threadIdx.x; t < nq * L; t += blockDim.x) {
     const int q = pencil_of(JFAST ? t / L : t % nq, lay);
     const int e = JFAST ? t % L : t / nq;
-    const double2* ee = E + q * lay.q_stride;
-    double2* o = O + q * lay.q_stride;
-    if (e == 0) o[0] = C[q * lay.q_stride + L * js];
-    else o[(int)perm[e - 1].y * js] = cadd(ee[0], ee[e * js]);
+    const C* ee = E + q * lay.q_stride;
+    C* o = O + q * lay.q_stride;
+    if (e == 0) o[0] = Cv[q * lay.q_stride + L * js];
+    else o[perm_second(perm[e - 1]) * js] = cadd(ee[0], ee[e * js]);
   }
   __syncthreads();
   return O;
 }
 
 // Transform all pencils of `a` with a run-time plan (see fft_pencils).
-template <bool INV, bool JFAST>
-__device__ __noinline__ double2* fft_pencils_rt(double2* a, double2* b, const PencilLayout lay, const double2* tw,
-                                                const FftPlan p) {
+template <bool INV, bool JFAST, class C>
+__device__ __noinline__ C* fft_pencils_rt(C* a, C* b, const PencilLayout lay, const C* tw, const FftPlan p) {
   if (p.rader) return rader_pencils<INV, JFAST>(a, b, lay, tw, p);
   return run_stages_rt<INV, JFAST>(a, b, lay, tw, p.L, p.n, p.r);
 }
@@ -483,9 +486,8 @@ __device__ __forceinline__ void stage_axis_twiddles(C* dst, const C* __restrict_
 }
 
 // compile-time plan when L > 0, the run-time plan p otherwise
-template <int L, bool INV, bool JFAST>
-__device__ __forceinline__ double2* fft_pencils_any(double2* a, double2* b, const PencilLayout& lay,
-                                                    const double2* tw, const FftPlan& p) {
+template <int L, bool INV, bool JFAST, class C>
+__device__ __forceinline__ C* fft_pencils_any(C* a, C* b, const PencilLayout& lay, const C* tw, const FftPlan& p) {
   if constexpr (L > 0) return fft_pencils<L, INV, JFAST>(a, b, lay, tw);
   else return fft_pencils_rt<INV, JFAST>(a, b, lay, tw, p);
 }

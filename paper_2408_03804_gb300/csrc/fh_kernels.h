@@ -101,6 +101,11 @@ void fill_plan_tables(double2* t, const FftPlan& p);
 // fewer than min_ctas CTAs in a pass (0: the default tiles)
 Tiling choose_tiling(const Grid& g, long long min_ctas = 0);
 size_t z_pass_smem(const Grid& g, const Tiling& t);
+// shared memory of a y or x pass CTA: `fields` x bk pencils of a compile-time
+// length L, or of a run-time plan (whose tables may exceed L entries); the
+// same for FP64 and double-float entries (16 bytes each)
+size_t y_smem(int L, int bk, int fields);
+size_t y_smem_rt(const FftPlan& p, int bk, int fields);
 long long z_pass_ctas(const Grid& g, const Tiling& t);
 
 cudaError_t setup_fft_kernels(const Grid& g, const Tiling& t);
@@ -122,17 +127,24 @@ cudaError_t launch_plane_fwd_y(const Grid& g, double2* S, const double2* tw, con
 cudaError_t launch_plane_x_ghat(const Grid& g, double2* S, const double2* tw, double scale, const CgScalars* cg,
                                 cudaStream_t s);
 cudaError_t launch_plane_inv_y(const Grid& g, double2* S, const double2* tw, const CgScalars* cg, cudaStream_t s);
-
-// the same five passes with double-float transforms (kernels_df64.cu): grids
-// whose x and y extents have compile-time plans and whose nz is even; the
-// spectrum buffer and a double-float twiddle table (same offsets) as dfc
 struct dfc;
+// ... with double-float transforms (setup_plane_kernels prepares both)
+cudaError_t launch_plane_fwd_y(const Grid& g, dfc* S, const dfc* tw, const CgScalars* cg, cudaStream_t s);
+cudaError_t launch_plane_x_ghat(const Grid& g, dfc* S, const dfc* tw, double scale, const CgScalars* cg,
+                                cudaStream_t s);
+cudaError_t launch_plane_inv_y(const Grid& g, dfc* S, const dfc* tw, const CgScalars* cg, cudaStream_t s);
+
+// the same five passes with double-float transforms (kernels_df64.cu; plane
+// cells dispatch to kernels_plane.cu): the spectrum buffer and a double-float
+// copy of the twiddle table (same offsets, run-time plan tables included) as dfc
 struct df64;
-bool df64_grid_ok(const Grid& g);
 // K_df = the packed tangent [45][N] in double-float
 cudaError_t launch_tangent_to_df64(const Grid& g, const double* K, df64* K_df, cudaStream_t s);
-void fill_twiddle_table_df(dfc* t);
+// the n entries of an FP64 twiddle table (with any run-time plan tables) in double-float
+void twiddles_to_df64(const double2* src, dfc* dst, int n);
 cudaError_t setup_df64_kernels(const Grid& g, const Tiling& t);
+cudaError_t setup_df64_yx_kernels(const Grid& g, const Tiling& t);     // kernels_df64_yx.cu
+cudaError_t setup_df64_batch_kernels(const Grid& g, const Tiling& t);  // kernels_df64_batch.cu
 cudaError_t launch_fwd_z_df(const Grid& g, const Tiling& t, int mode, const double* src, double* p, double* x,
                             const df64* K, const CgScalars* cg, dfc* S, const dfc* tw, cudaStream_t s);
 cudaError_t launch_fwd_y_df(const Grid& g, const Tiling& t, dfc* S, const dfc* tw, const CgScalars* cg,

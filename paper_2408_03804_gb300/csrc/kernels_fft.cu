@@ -296,11 +296,11 @@ size_t z_pass_smem(const Grid& g, const Tiling& t) {
   return ((size_t)9 * t.lines_z * g.nz + M + M / 2 + 1) * sizeof(double2);
 }
 long long z_pass_ctas(const Grid& g, const Tiling& t) { return (long long)g.nx * g.ny / t.lines_z; }
-static size_t y_smem(int L, int bk, int fields) {
+size_t y_smem(int L, int bk, int fields) {
   return ((size_t)2 * fields * bk * (L + 1) + L) * sizeof(double2);
 }
 // shared memory of a pass along an axis with a run-time plan (its tables may exceed L entries)
-static size_t y_smem_rt(const FftPlan& p, int bk, int fields) {
+size_t y_smem_rt(const FftPlan& p, int bk, int fields) {
   return ((size_t)2 * fields * bk * (p.L + 1) + p.tw_len) * sizeof(double2);
 }
 

@@ -29,7 +29,8 @@
 // (double-float, kernels_df64.cu). K : p, the CG updates and the dot
 // products work on the FP64 fields in both; the double-float form converts
 // tau to double-float in the z pass and the result back in the inverse z
-// pass. Lengths with run-time plans (L = 0) exist for double2 only.
+// pass. Both element types cover every grid: compile-time plans (L > 0),
+// run-time plans (L = 0) and plane cells (M = 0).
 #pragma once
 
 #include "df64.cuh"
@@ -57,11 +58,6 @@ __device__ __forceinline__ df64 to_real(double x, dfc*) { return to_df64(x); }
 __device__ __forceinline__ double wave_real(int k, double sc) { return k * sc; }
 __device__ __forceinline__ df64 wave_real(int k, df64 sc) { return dd_mul(df64{(float)k, 0.f}, sc); }
 
-// s a + b
-__device__ __forceinline__ double2 caxpy(double s, double2 a, double2 b) {
-  return make_double2(fma(s, a.x, b.x), fma(s, a.y, b.y));
-}
-__device__ __forceinline__ dfc caxpy(df64 s, dfc a, dfc b) { return dfc{dd_fma(s, a.re, b.re), dd_fma(s, a.im, b.im)}; }
 
 // a + conj(b), a - conj(b), conj(a), a with its imaginary part dropped
 __device__ __forceinline__ double2 cadd_conj(double2 a, double2 b) { return make_double2(a.x + b.x, a.y - b.y); }
@@ -73,10 +69,14 @@ __device__ __forceinline__ dfc csub_conj(dfc a, dfc b) { return dfc{dd_sub(a.re,
 __device__ __forceinline__ dfc cconj(dfc a) { return dfc{a.re, dd_neg(a.im)}; }
 __device__ __forceinline__ dfc creal(dfc a) { return dfc{a.re, df64{0.f, 0.f}}; }
 
-__device__ __forceinline__ void czero(double2& a) { a = make_double2(0.0, 0.0); }
-__device__ __forceinline__ void czero(dfc& a) { a = dfc{df64{0.f, 0.f}, df64{0.f, 0.f}}; }
 
 // the real sequence packed two per complex entry (a real-to-complex step)
+// a real value as a complex entry, and the real part of an entry as a double
+__device__ __forceinline__ double2 cfrom_real(double v) { return make_double2(v, 0.0); }
+__device__ __forceinline__ dfc cfrom_real(df64 v) { return dfc{v, df64{0.f, 0.f}}; }
+__device__ __forceinline__ double creal_double(double2 a) { return a.x; }
+__device__ __forceinline__ double creal_double(dfc a) { return join_df64(a.re); }
+
 __device__ __forceinline__ void store_real(double2* buf, int i, double v) { reinterpret_cast<double*>(buf)[i] = v; }
 __device__ __forceinline__ void store_real(dfc* buf, int i, df64 v) { reinterpret_cast<df64*>(buf)[i] = v; }
 __device__ __forceinline__ double load_real(const double2* buf, int i) {
@@ -106,13 +106,6 @@ template <class C>
 __device__ __forceinline__ C* pass_smem() {
   extern __shared__ __align__(16) unsigned char fh_pass_smem[];
   return reinterpret_cast<C*>(fh_pass_smem);
-}
-
-// compile-time plan when L > 0, the run-time plan p otherwise (double2 only)
-template <int L, bool INV, bool JFAST, class C>
-__device__ __forceinline__ C* pencils(C* a, C* b, const PencilLayout& lay, const C* tw, const FftPlan& p) {
-  if constexpr (L > 0) return fft_pencils<L, INV, JFAST>(a, b, lay, tw);
-  else return fft_pencils_rt<INV, JFAST>(a, b, lay, tw, p);
 }
 
 // dispatch on the lengths with compile-time plans: the x and y extents, and
@@ -198,7 +191,7 @@ __device__ __forceinline__ void z_pass_tau(long long gi, long long n, const doub
 }
 
 // M = nz / 2; M = 0 is a cell one voxel thick along z (nz = 1), whose
-// transform along z is the identity (FP64 only)
+// transform along z is the identity
 template <int M, int MODE, class C>
 __device__ __forceinline__ void fwd_z_body(int cta, Grid g, int LB, const double* __restrict__ src,
                                            double* __restrict__ p, double* __restrict__ x,
@@ -219,11 +212,11 @@ __device__ __forceinline__ void fwd_z_body(int cta, Grid g, int LB, const double
     const long long v0 = (long long)cta * LB;
     for (int t = threadIdx.x; t < LB; t += blockDim.x) {
       const long long gi = v0 + t;
-      double tau[9];
+      R tau[9];
       z_pass_tau<MODE>(gi, n, src, p, x, K, alpha, beta, tau);
 #pragma unroll
       for (int c = 0; c < 9; ++c)
-        if (c % 3 != 2) S[c * g.nspec + gi] = make_double2(tau[c], 0.0);
+        if (c % 3 != 2) S[c * g.nspec + gi] = cfrom_real(tau[c]);
     }
   } else {
     C* smem = pass_smem<C>();
@@ -292,7 +285,7 @@ __device__ __forceinline__ void inv_z_body(int cta, Grid g, int LB, const C* __r
       const long long gi = line0 + t;
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        const double yv = S[c * g.nspec + gi].x;
+        const double yv = creal_double(S[c * g.nspec + gi]);
         out[c * n + gi] = yv;
         if constexpr (MODE == kIZDot) acc = fma(p[c * n + gi], yv, acc);
         if constexpr (MODE == kIZRhs) acc = fma(yv, yv, acc);
@@ -376,7 +369,7 @@ __device__ __forceinline__ void fwd_y_body(int cta, Grid g, int BK, C* __restric
     if (kz < g.nzh) v = S[(3 * i + f) * g.nspec + ((long long)x * Ln + y) * g.nzh + kz];
     bufA[(f * BK + kzl) * QS + y] = v;
   }
-  C* Ry = pencils<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL, g.py);
+  C* Ry = fft_pencils_any<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL, g.py);
   const R rsy = to_real(g.sy, (C*)nullptr);
   for (int t = threadIdx.x; t < Ln * BK; t += blockDim.x) {
     const int kzl = t % BK, y = t / BK;
@@ -423,7 +416,7 @@ __device__ __forceinline__ void x_ghat_body(int cta, Grid g, int BK, C* __restri
     if (kz < g.nzh) v = S[comp * g.nspec + x * row + (long long)ky * g.nzh + kz];
     bufA[(f * BK + kzl) * QS + x] = v;
   }
-  C* Rx = pencils<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL, g.px);
+  C* Rx = fft_pencils_any<L, false, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL, g.px);
   const R rsx = to_real(g.sx, (C*)nullptr), rsz = to_real(g.sz, (C*)nullptr);
   const R rc = to_real(scale, (C*)nullptr);
   const R xi_y = wave_real(wave_int(ky, g.ny), to_real(g.sy, (C*)nullptr));
@@ -444,7 +437,7 @@ __device__ __forceinline__ void x_ghat_body(int cta, Grid g, int BK, C* __restri
     }
   }
   C* other = (Rx == bufA) ? bufB : bufA;
-  const C* R2 = pencils<L, true, true>(Rx, other, PencilLayout{np, QS, 1, BK, valid}, twL, g.px);
+  const C* R2 = fft_pencils_any<L, true, true>(Rx, other, PencilLayout{np, QS, 1, BK, valid}, twL, g.px);
   for (int t = threadIdx.x; t < 6 * Ln * BK; t += blockDim.x) {
     const int kzl = t % BK, rest = t / BK;
     const int x = rest % Ln, f = rest / Ln;
@@ -493,7 +486,7 @@ __device__ __forceinline__ void inv_y_body(int cta, Grid g, int BK, C* __restric
       bufA[(2 * BK + kzl) * QS + y] = v;
     }
   }
-  const C* Ry = pencils<L, true, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL, g.py);
+  const C* Ry = fft_pencils_any<L, true, true>(bufA, bufB, PencilLayout{np, QS, 1, BK, valid}, twL, g.py);
   for (int t = threadIdx.x; t < Ln * BK; t += blockDim.x) {
     const int kzl = t % BK, y = t / BK;
     const int kz = kz0 + kzl;

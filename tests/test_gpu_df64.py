@@ -121,16 +121,24 @@ def test_df64_tangent_matches_oracle(fh, torch):
     assert np.abs(C - C_ref).max() < PBAR_TOL * np.abs(C_ref).max()
 
 
-@pytest.mark.parametrize("shape", [(199, 8, 2), (16, 16, 1), (12, 10, 8)])
-def test_df64_rejects_grids_without_compile_time_plans(fh, torch, shape):
-    phase = np.zeros(shape, np.uint8)
+@pytest.mark.parametrize("shape,kind", [((27, 25, 1), 2), ((15, 21, 8), 1), ((37, 12, 4), 1), ((45, 45, 1), 0),
+                                        ((199, 6, 2), 2)])
+def test_df64_on_run_time_plans_and_plane_cells_matches_oracle(fh, torch, shape, kind):
+    """The double-float transforms on every kind of axis: odd lengths (direct odd-radix stages), primes
+    from 37 on (Rader's algorithm) and plane cells (nz = 1), against the oracle."""
+    if shape[2] > 2:
+        phase = random_spheres(shape, seed=sum(shape), r_min=1.5, r_max=3.0)
+    else:  # z-invariant cell
+        phase = np.ascontiguousarray(np.repeat(
+            (np.random.default_rng(sum(shape)).random(shape[:2] + (1,)) < 0.3).astype(np.uint8), shape[2], axis=2))
     params = two_phase_table(1.5, 1.0, 10.0)
-    with fh.Context(*shape) as ctx:
-        F = torch.zeros((9,) + shape, dtype=torch.float64, device="cuda")
-        opts = fh.default_options(matvec_arith=fh.ARITH_DF64)
-        _, _, rc = ctx.fft_homog_solve(fh.Material(1, phase, params), shear_macro(0.01, finite=True), F,
-                                      options=opts, allow=(fh.FH_ERR_UNSUPPORTED,))
-    assert rc == fh.FH_ERR_UNSUPPORTED
+    Fbar = shear_macro(0.05, finite=kind != 0)
+    Fg, pbar, st = _solve(fh, torch, phase, params, kind, Fbar, 2, 1e-10, fh.ARITH_DF64)
+    ref = osolver.solve(phase, params, kind, Fbar, n_increments=2, newton_tol=1e-10)
+    assert st["n_newton"] == len(ref.newton_residuals)
+    assert all(abs(a - b) <= 2 for a, b in zip(st["cg_iterations"], ref.cg_iterations))
+    np.testing.assert_allclose(pbar, ref.Pbar, rtol=PBAR_TOL, atol=PBAR_TOL * np.abs(ref.Pbar).max())
+    assert np.abs(Fg - ref.F).max() < FIELD_TOL * np.abs(ref.F - Fbar.reshape(9, 1, 1, 1)).max()
 
 
 def test_df64_full_size_bench_cell_matches_fp64_solve(fh, torch):
