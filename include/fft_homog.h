@@ -107,9 +107,11 @@ extern "C" {
  *                every CG product transform in double-float arithmetic
  *                (each real number an unevaluated sum of two FP32 values,
  *                about 48 significant bits, on the FP32 pipe, which issues
- *                about 75 times faster than FP64 on GB300). K : p, the CG
- *                vector updates and dot products, the Newton right-hand
- *                side, residuals and stress stay FP64. Every grid. */
+ *                about 75 times faster than FP64 on GB300), and K : p is
+ *                formed in double-float from a double-float copy of the
+ *                packed tangent. The CG vector updates and dot products,
+ *                the Newton right-hand side, residuals and stress stay
+ *                FP64. Every grid. */
 #define FH_ARITH_FP64 0
 #define FH_ARITH_DF64 1
 

@@ -63,13 +63,12 @@ __device__ __forceinline__ df64 dd_fma(df64 a, df64 b, df64 c) {
   return fast_two_sum(s.hi, s.lo);
 }
 
-// conversions through FP64 arithmetic (one rounding to float each way): for
+// conversion through FP64 arithmetic (one rounding to float each way): for
 // constants and per-thread scalars
 __host__ __device__ __forceinline__ df64 to_df64(double x) {
   const float hi = (float)x;
   return df64{hi, (float)(x - (double)hi)};
 }
-__device__ __forceinline__ double to_double(df64 a) { return (double)a.hi + (double)a.lo; }
 
 // Conversions of field values on the integer pipe (FP64 issue is the
 // scarce resource): split_double cuts the 52-bit significand of x after 23

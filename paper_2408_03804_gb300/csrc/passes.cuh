@@ -26,10 +26,11 @@
 //
 // The bodies are templates over the element type C of the spectrum and of
 // the shared-memory pencils: double2 (IEEE FP64, kernels_fft.cu) or dfc
-// (double-float, kernels_df64.cu). K : p, the CG updates and the dot
-// products work on the FP64 fields in both; the double-float form converts
-// tau to double-float in the z pass and the result back in the inverse z
-// pass. Both element types cover every grid: compile-time plans (L > 0),
+// (double-float, kernels_df64.cu). The CG updates and the dot products
+// work on the FP64 fields in both; the double-float form converts p (or the
+// source field) to double-float in the z pass, forms K : p from a
+// double-float copy of the tangent, and converts the result back in the
+// inverse z pass. Both element types cover every grid: compile-time plans (L > 0),
 // run-time plans (L = 0) and plane cells (M = 0).
 #pragma once
 

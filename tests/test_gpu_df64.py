@@ -1,8 +1,9 @@
 """The double-float option of the CG matrix-vector product (FH_ARITH_DF64).
 
 The five projection passes of every CG product transform in double-float
-arithmetic (pairs of FP32 values, about 48 significant bits); K : p, the CG
-updates and dot products, the Newton right-hand side and residuals stay FP64.
+arithmetic (pairs of FP32 values, about 48 significant bits) and K : p is
+formed in double-float; the CG updates and dot products, the Newton
+right-hand side and residuals stay FP64.
 The method's results must not move beyond the parity bars: against the CPU
 oracle, 1e-9 relative on the homogenized stress and tangent and 1e-8
 max-relative on the voxel fields, with the same Newton iteration counts.
