@@ -134,12 +134,22 @@ def cg_iteration_bytes(nx, ny, nz):
 TRAFFIC_SOURCES = ("kernels_fft.cu", "passes.cuh", "fft_core.cuh", "fh_common.cuh", "fh_kernels.h")
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments and with whitespace collapsed: what the compiler sees."""
+    import re
+
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash() -> str:
+    """Hash of the code (comments and layout excluded) of the passes whose traffic was captured."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2408_03804_gb300", "csrc")
     for f in TRAFFIC_SOURCES:
-        with open(os.path.join(csrc, f), "rb") as fh_:
-            h.update(fh_.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh_:
+            h.update(_code_only(fh_.read()).encode())
     return h.hexdigest()[:16]
 
 
