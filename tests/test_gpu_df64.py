@@ -211,3 +211,24 @@ def test_df64_split_and_join_of_field_values(fh, torch):
     assert np.all(hi[tiny] == 0) and np.all(lo[tiny] == 0)
     huge = np.abs(x) >= 2.0 ** 128
     assert np.all(np.isinf(hi[huge])) and np.all(np.sign(hi[huge]) == np.sign(x[huge]))
+
+
+@pytest.mark.parametrize("shape", [(16, 8, 12), (15, 7, 1)])
+def test_df64_anisotropic_box_matches_oracle(fh, torch, shape):
+    """Box side lengths (1, 2, 0.5): the double-float wave vectors k / L_a against the oracle."""
+    lengths = (1.0, 2.0, 0.5)
+    phase = (np.random.default_rng(11).random(shape) < 0.3).astype(np.uint8)
+    if shape[2] == 1:
+        lengths = (1.0, 2.0, 1.0)
+    params = two_phase_table(1.5, 1.0, 10.0)
+    Fbar = shear_macro(0.05, finite=True)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream), fh.Context(*shape, stream=stream.cuda_stream) as ctx:
+        F = torch.zeros((9,) + shape, dtype=torch.float64, device="cuda")
+        opts = fh.default_options(newton_tol=1e-10, matvec_arith=fh.ARITH_DF64, lengths=lengths)
+        pbar, st, _ = ctx.fft_homog_solve(fh.Material(1, phase, params), Fbar, F, n_increments=2, options=opts)
+        Fg = host(F)
+    ref = osolver.solve(phase, params, 1, Fbar, n_increments=2, newton_tol=1e-10, lengths=lengths)
+    assert st["n_newton"] == len(ref.newton_residuals)
+    np.testing.assert_allclose(pbar, ref.Pbar, rtol=PBAR_TOL, atol=PBAR_TOL * np.abs(ref.Pbar).max())
+    assert np.abs(Fg - ref.F).max() < FIELD_TOL * np.abs(ref.F - Fbar.reshape(9, 1, 1, 1)).max()
