@@ -141,9 +141,16 @@ def test_matvec_matches_oracle_stored_and_jvp(fh, torch, kind, shape):
         y2 = torch.empty_like(pd)
         ctx.fh_matvec(pd, y1, K=K)
         ctx.fh_matvec(pd, y2, mat=mat, F=Fd)
+        # the double-float option in both forms (stored K converted by the library, jvp)
+        y3 = torch.empty_like(pd)
+        y4 = torch.empty_like(pd)
+        ctx.fh_matvec(pd, y3, K=K, arith=fh.ARITH_DF64)
+        ctx.fh_matvec(pd, y4, mat=mat, F=Fd, arith=fh.ARITH_DF64)
     scale = np.abs(ref).max()
     assert np.abs(host(y1) - ref).max() < OP_TOL * 10 * scale
     assert np.abs(host(y2) - ref).max() < OP_TOL * 10 * scale
+    assert np.abs(host(y3) - ref).max() < 1e-12 * scale
+    assert np.abs(host(y4) - ref).max() < 1e-12 * scale
 
 
 # ---------------------------------------------------------------------------
