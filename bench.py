@@ -73,13 +73,16 @@ def algorithmic_work(cls: str, nx: int, ny: int, nz: int):
 
 
 # FP64 lane operations (DADD, DMUL, DFMA each one) per launch, counted from the
-# kernels' code: complex length-L transform per point = FP64_FFT_OPS[L]
-# compile-time plans of the library (radix of each stage) and FP64 operations per point of an R-point
-# butterfly; a stage after the first adds 4 (R-1)/R per point for its twiddle multiplications
+# kernels' code: complex length-L transform per point = FP64_FFT_OPS[L], from the
+# compile-time plans of the library (radix of each stage) and the FP64 operations per point of
+# an R-point butterfly: BUTTERFLY_OPS for the first stage (no twiddles), TWIDDLED_OPS for the
+# later ones (radix 2^P: P layers of 6-FMA butterflies with the twiddles in the tangent form,
+# 3 P per point; radix 3: two tangent-form products of 4 operations and the radix-3 butterfly)
 FFT_PLANS = {1: (), 2: (2,), 3: (3,), 4: (4,), 6: (2, 3), 8: (8,), 12: (4, 3), 16: (16,), 24: (8, 3),
              32: (8, 4), 48: (16, 3), 64: (8, 8), 96: (8, 4, 3), 128: (16, 8), 192: (16, 4, 3), 256: (16, 16)}
-BUTTERFLY_OPS = {2: 2.0, 3: 4.0, 4: 4.0, 8: 6.5, 16: 10.0}
-FP64_FFT_OPS = {L: sum(BUTTERFLY_OPS[r] + (4.0 * (r - 1) / r if k else 0.0) for k, r in enumerate(plan))
+BUTTERFLY_OPS = {2: 2.0, 3: 4.0, 4: 4.0, 8: 6.5, 16: 9.0}
+TWIDDLED_OPS = {2: 3.0, 3: 4.0 + 8.0 / 3.0, 4: 6.0, 8: 9.0, 16: 12.0}
+FP64_FFT_OPS = {L: sum((TWIDDLED_OPS if k else BUTTERFLY_OPS)[r] for k, r in enumerate(plan))
                 for L, plan in FFT_PLANS.items()}
 
 

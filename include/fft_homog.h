@@ -371,8 +371,8 @@ FH_API int fh_df64_roundtrip(const double* in_dev, float* hi_dev, float* lo_dev,
  * owns the GPU's memory, or a loop that must not allocate once it runs. It
  * computes exactly what fh_project computes (out = scale * G(A)), with the
  * same kernels, but needs no fh_ctx: its scratch is a static device array of
- * 9 * 32768 complex doubles (4.5 MiB) plus the twiddle tables (892 complex
- * doubles, about 14 KiB), which every GPU that loads this library holds until
+ * 9 * 32768 complex doubles (4.5 MiB) plus the twiddle tables (1784 complex
+ * doubles, about 28 KiB), which every GPU that loads this library holds until
  * the process exits.
  *   A_dev, out_dev  device [9][nx][ny][nz] fields (out may equal A)
  *   nx, ny, nz      extents as for fh_create, nx*ny*nz <= 32768;

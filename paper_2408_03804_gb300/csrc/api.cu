@@ -488,7 +488,7 @@ int fh_create(fh_ctx** out, int nx, int ny, int nz, void* cuda_stream) {
   g.sx = g.sy = g.sz = 1.0;
   // lengths without a compile-time plan get a run-time plan and their own
   // twiddle table after the tables of the compile-time lengths
-  int tw_len = kTwiddleTotal;
+  int tw_len = kTwiddleTables;
   g.px = make_fft_plan(nx, tw_len);
   tw_len += g.px.tw_len;
   g.py = make_fft_plan(ny, tw_len);

@@ -299,15 +299,15 @@ int fh_batch_create(fh_batch** out, const fh_cell* cells, int n_cells, void* cud
   int rc;
   if ((rc = dalloc(b, &b->cg, sizeof(CgScalars) * n_cells)) || (rc = dalloc(b, &b->sums, 16 * sizeof(double) * n_cells)) ||
       (rc = dalloc(b, &b->ctl, sizeof(CellCtl) * n_cells)) || (rc = dalloc(b, &b->flags, sizeof(int) * n_cells)) ||
-      (rc = dalloc(b, &b->params, 512 * sizeof(double))) || (rc = dalloc(b, &b->tw, kTwiddleTotal * sizeof(double2))) ||
-      (rc = dalloc(b, &b->tw_df, kTwiddleTotal * sizeof(dfc))))
+      (rc = dalloc(b, &b->params, 512 * sizeof(double))) || (rc = dalloc(b, &b->tw, kTwiddleTables * sizeof(double2))) ||
+      (rc = dalloc(b, &b->tw_df, kTwiddleTables * sizeof(dfc))))
     return cleanup(rc);
-  std::vector<double2> tw(kTwiddleTotal);
+  std::vector<double2> tw(kTwiddleTables);
   fill_twiddle_table(tw.data());
-  std::vector<dfc> tw_df(kTwiddleTotal);
-  twiddles_to_df64(tw.data(), tw_df.data(), kTwiddleTotal);
-  if (cudaMemcpy(b->tw, tw.data(), kTwiddleTotal * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->tw_df, tw_df.data(), kTwiddleTotal * sizeof(dfc), cudaMemcpyHostToDevice) != cudaSuccess)
+  std::vector<dfc> tw_df(kTwiddleTables);
+  twiddles_to_df64(tw.data(), tw_df.data(), kTwiddleTables);
+  if (cudaMemcpy(b->tw, tw.data(), kTwiddleTables * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->tw_df, tw_df.data(), kTwiddleTables * sizeof(dfc), cudaMemcpyHostToDevice) != cudaSuccess)
     return cleanup(bfail(FH_ERR_CUDA, "twiddle upload failed"));
   // group the cells by grid shape
   std::map<long long, int> key_to_group;

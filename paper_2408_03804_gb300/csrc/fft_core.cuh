@@ -10,11 +10,17 @@
 // needs no twiddles. Twiddles w_L^m = exp(-2 pi i m / L) come from a table that
 // each CTA first copies from global to shared memory (reading them through the
 // texture path throttled the FP64 kernels); the inverse uses their conjugates.
+// In FP64 the twiddled stages read them in a tangent form and fold them into
+// their butterflies (6 FMAs per radix-2 butterfly, see below).
 //
 // The plans minimise FP64 instructions (FP64 issue is the bound of this path):
 // 32 = 8x4, 64 = 8x8, 128 = 16x8, 256 = 16x16, smaller powers of two in one
 // stage; lengths 3 * 2^a end with a radix-3 stage (48 = 16x3, 96 = 8x4x3).
+// Per complex point a length-128 transform takes 18 FP64 operations (144 for
+// the radix-16 butterfly, 72 for a twiddled radix-8 one).
 #pragma once
+
+#include <cstring>
 
 #include "fh_common.cuh"
 
@@ -24,27 +30,28 @@ constexpr double kC8 = 0.70710678118654752440;   // cos(pi/4)
 constexpr double kS3 = 0.86602540378443864676;   // sin(pi/3)
 constexpr double kC16 = 0.92387953251128675613;  // cos(pi/8)
 constexpr double kS16 = 0.38268343236508977173;  // sin(pi/8)
+constexpr double kT16 = 0.41421356237309504880;  // tan(pi/8) = sqrt(2) - 1
 
 // multiply by -i (forward, INV = false) or +i (inverse)
 template <bool INV>
-__device__ __forceinline__ double2 mul_mi(double2 a) {
+__host__ __device__ __forceinline__ double2 mul_mi(double2 a) {
   return INV ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
 }
 
 // scalar helpers shared with the double-float element type (df64.cuh has the
 // dfc overloads): s a + b, zero, the cosine and minus-sine parts of a twiddle
 // (cos, -sin), and the index pair stored in a Rader permutation entry
-__device__ __forceinline__ double2 caxpy(double s, double2 a, double2 b) {
+__host__ __device__ __forceinline__ double2 caxpy(double s, double2 a, double2 b) {
   return make_double2(fma(s, a.x, b.x), fma(s, a.y, b.y));
 }
-__device__ __forceinline__ void czero(double2& a) { a = make_double2(0.0, 0.0); }
+__host__ __device__ __forceinline__ void czero(double2& a) { a = make_double2(0.0, 0.0); }
 __device__ __forceinline__ double tw_cos(double2 w) { return w.x; }
 __device__ __forceinline__ double tw_sin(double2 w) { return -w.y; }
 __device__ __forceinline__ int perm_first(double2 w) { return (int)w.x; }
 __device__ __forceinline__ int perm_second(double2 w) { return (int)w.y; }
 
 template <bool INV>
-__device__ __forceinline__ void dft2(double2* v) {
+__host__ __device__ __forceinline__ void dft2(double2* v) {
   const double2 a = v[0], b = v[1];
   v[0] = cadd(a, b);
   v[1] = csub(a, b);
@@ -53,7 +60,7 @@ __device__ __forceinline__ void dft2(double2* v) {
 // X0 = a + b + c, X1,2 = a - (b + c)/2 -+ i sin(pi/3) (b - c) (forward; signs
 // of the sine term swap for the inverse)
 template <bool INV>
-__device__ __forceinline__ void dft3(double2* v) {
+__host__ __device__ __forceinline__ void dft3(double2* v) {
   const double2 a = v[0];
   const double2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
   const double2 m = make_double2(fma(-0.5, t1.x, a.x), fma(-0.5, t1.y, a.y));
@@ -64,7 +71,7 @@ __device__ __forceinline__ void dft3(double2* v) {
 }
 
 template <bool INV>
-__device__ __forceinline__ void dft4(double2& v0, double2& v1, double2& v2, double2& v3) {
+__host__ __device__ __forceinline__ void dft4(double2& v0, double2& v1, double2& v2, double2& v3) {
   const double2 t0 = cadd(v0, v2), t1 = csub(v0, v2);
   const double2 t2 = cadd(v1, v3), t3 = mul_mi<INV>(csub(v1, v3));
   v0 = cadd(t0, t2);
@@ -74,13 +81,13 @@ __device__ __forceinline__ void dft4(double2& v0, double2& v1, double2& v2, doub
 }
 
 template <bool INV>
-__device__ __forceinline__ void dft4(double2* v) {
+__host__ __device__ __forceinline__ void dft4(double2* v) {
   dft4<INV>(v[0], v[1], v[2], v[3]);
 }
 
 // e + w8^1 o and e - w8^1 o, fused (w8 = exp(-+ 2 pi i / 8))
 template <bool INV>
-__device__ __forceinline__ void bfly_w8_1(double2& e, double2& o) {
+__host__ __device__ __forceinline__ void bfly_w8_1(double2& e, double2& o) {
   // forward: o (1 - i)/sqrt2 = ((x + y) + i (y - x))/sqrt2 ; inverse: ((x - y) + i (x + y))/sqrt2
   const double s = INV ? o.x - o.y : o.x + o.y;
   const double t = INV ? o.x + o.y : o.y - o.x;
@@ -90,7 +97,7 @@ __device__ __forceinline__ void bfly_w8_1(double2& e, double2& o) {
 }
 // e + w8^3 o and e - w8^3 o
 template <bool INV>
-__device__ __forceinline__ void bfly_w8_3(double2& e, double2& o) {
+__host__ __device__ __forceinline__ void bfly_w8_3(double2& e, double2& o) {
   // forward: o (-1 - i)/sqrt2 = ((y - x) - i (x + y))/sqrt2 ; inverse: (-(x + y) + i (x - y))/sqrt2
   const double s = INV ? -(o.x + o.y) : o.y - o.x;
   const double t = INV ? o.x - o.y : -(o.x + o.y);
@@ -100,7 +107,7 @@ __device__ __forceinline__ void bfly_w8_3(double2& e, double2& o) {
 }
 
 template <bool INV>
-__device__ __forceinline__ void dft8(double2* v) {
+__host__ __device__ __forceinline__ void dft8(double2* v) {
   double2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
   double2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
   dft4<INV>(e0, e1, e2, e3);
@@ -118,27 +125,32 @@ __device__ __forceinline__ void dft8(double2* v) {
   v[7] = o3;
 }
 
-// multiply by w16^m (forward exp(-2 pi i m/16), inverse its conjugate), m in 1..9
-template <bool INV, int M>
-__device__ __forceinline__ double2 rot16(double2 a) {
-  constexpr double sg = INV ? 1.0 : -1.0;  // sign of the imaginary part of the twiddle
-  if constexpr (M == 4) {
-    return mul_mi<INV>(a);
-  } else if constexpr (M == 2 || M == 6) {
-    // w = (c, sg c) for M = 2 ; (-c, sg c) for M = 6
-    constexpr double wr = (M == 2) ? kC8 : -kC8;
-    constexpr double wi = sg * kC8;
-    return make_double2(fma(a.x, wr, -a.y * wi), fma(a.x, wi, a.y * wr));
-  } else {
-    constexpr double wr = (M == 1) ? kC16 : (M == 3) ? kS16 : -kC16;  // M = 9: cos(9pi/8) = -c16
-    constexpr double wi = sg * ((M == 1) ? kS16 : (M == 3) ? kC16 : -kS16);
-    return make_double2(fma(a.x, wr, -a.y * wi), fma(a.x, wi, a.y * wr));
-  }
+// a (1 + i sg), a (-1 + i sg) and a (1 + i sg t16), with sg = -1 forward and
+// +1 inverse (the sign of the imaginary part of w16^1) and t16 = tan(pi/8)
+template <bool INV>
+__host__ __device__ __forceinline__ double2 mul_1pi(double2 a) {
+  return INV ? make_double2(a.x - a.y, a.y + a.x) : make_double2(a.x + a.y, a.y - a.x);
+}
+template <bool INV>
+__host__ __device__ __forceinline__ double2 mul_m1pi(double2 a) {
+  return INV ? make_double2(-a.x - a.y, a.x - a.y) : make_double2(a.y - a.x, -a.y - a.x);
+}
+template <bool INV>
+__host__ __device__ __forceinline__ double2 mul_1pit(double2 a) {
+  return INV ? make_double2(fma(-kT16, a.y, a.x), fma(kT16, a.x, a.y))
+             : make_double2(fma(kT16, a.y, a.x), fma(-kT16, a.x, a.y));
 }
 
+// 16 = 4 x 4: DFT-4 over the stride-4 inputs (column k1 of a[j] from inputs
+// j + 4 n1), the twiddles w16^(j k1), DFT-4 across j. The twiddles of a
+// column are written as a common real factor times values of the form
+// 1 + i sg, -1 + i sg or (1 +- i sg t16) times a power of i: w16^1, w16^3 and
+// w16^9 all equal c16 times such a value, w16^2 and w16^6 c8 times one. The
+// factor then enters the DFT-4 as the multiplier of an FMA, so a twiddled
+// column costs 22 (20 for k1 = 2) FP64 operations instead of 28 (24); the
+// whole transform 144 instead of 160.
 template <bool INV>
-__device__ __forceinline__ void dft16(double2* v) {
-  // 16 = 4 x 4: DFT-4 over stride-4 inputs, twiddles w16^(j k1), DFT-4 across
+__host__ __device__ __forceinline__ void dft16(double2* v) {
   double2 a[4][4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -148,28 +160,50 @@ __device__ __forceinline__ void dft16(double2* v) {
     a[j][3] = v[j + 12];
     dft4<INV>(a[j][0], a[j][1], a[j][2], a[j][3]);
   }
-  a[1][1] = rot16<INV, 1>(a[1][1]);
-  a[1][2] = rot16<INV, 2>(a[1][2]);
-  a[1][3] = rot16<INV, 3>(a[1][3]);
-  a[2][1] = rot16<INV, 2>(a[2][1]);
-  a[2][2] = rot16<INV, 4>(a[2][2]);
-  a[2][3] = rot16<INV, 6>(a[2][3]);
-  a[3][1] = rot16<INV, 3>(a[3][1]);
-  a[3][2] = rot16<INV, 6>(a[3][2]);
-  a[3][3] = rot16<INV, 9>(a[3][3]);
-#pragma unroll
-  for (int k1 = 0; k1 < 4; ++k1) {
-    double2 b0 = a[0][k1], b1 = a[1][k1], b2 = a[2][k1], b3 = a[3][k1];
+  {  // k1 = 0: no twiddles
+    double2 b0 = a[0][0], b1 = a[1][0], b2 = a[2][0], b3 = a[3][0];
     dft4<INV>(b0, b1, b2, b3);
-    v[k1] = b0;
-    v[k1 + 4] = b1;
-    v[k1 + 8] = b2;
-    v[k1 + 12] = b3;
+    v[0] = b0;
+    v[4] = b1;
+    v[8] = b2;
+    v[12] = b3;
+  }
+  {  // k1 = 1: w^1 = c16 (1 + i sg t16), w^2 = c8 (1 + i sg), w^3 = c16 i sg (1 - i sg t16)
+    const double2 u1 = mul_1pit<INV>(a[1][1]);
+    const double2 u3 = mul_mi<INV>(mul_1pit<!INV>(a[3][1]));
+    const double2 s2 = mul_1pi<INV>(a[2][1]);
+    const double2 t0 = caxpy(kC8, s2, a[0][1]), t1 = caxpy(-kC8, s2, a[0][1]);
+    const double2 p = cadd(u1, u3), d = mul_mi<INV>(csub(u1, u3));
+    v[1] = caxpy(kC16, p, t0);
+    v[9] = caxpy(-kC16, p, t0);
+    v[5] = caxpy(kC16, d, t1);
+    v[13] = caxpy(-kC16, d, t1);
+  }
+  {  // k1 = 2: w^2 = c8 (1 + i sg), w^4 = i sg, w^6 = c8 (-1 + i sg)
+    const double2 b2 = mul_mi<INV>(a[2][2]);
+    const double2 t0 = cadd(a[0][2], b2), t1 = csub(a[0][2], b2);
+    const double2 s1 = mul_1pi<INV>(a[1][2]), s3 = mul_m1pi<INV>(a[3][2]);
+    const double2 p = cadd(s1, s3), d = mul_mi<INV>(csub(s1, s3));
+    v[2] = caxpy(kC8, p, t0);
+    v[10] = caxpy(-kC8, p, t0);
+    v[6] = caxpy(kC8, d, t1);
+    v[14] = caxpy(-kC8, d, t1);
+  }
+  {  // k1 = 3: w^3 = c16 i sg (1 - i sg t16), w^6 = c8 (-1 + i sg), w^9 = -c16 (1 + i sg t16)
+    const double2 u1 = mul_mi<INV>(mul_1pit<!INV>(a[1][3]));
+    const double2 z3 = mul_1pit<INV>(a[3][3]);  // b3 = -c16 z3
+    const double2 s2 = mul_m1pi<INV>(a[2][3]);
+    const double2 t0 = caxpy(kC8, s2, a[0][3]), t1 = caxpy(-kC8, s2, a[0][3]);
+    const double2 p = csub(u1, z3), d = mul_mi<INV>(cadd(u1, z3));
+    v[3] = caxpy(kC16, p, t0);
+    v[11] = caxpy(-kC16, p, t0);
+    v[7] = caxpy(kC16, d, t1);
+    v[15] = caxpy(-kC16, d, t1);
   }
 }
 
 template <int R, bool INV>
-__device__ __forceinline__ void dft_r(double2* v) {
+__host__ __device__ __forceinline__ void dft_r(double2* v) {
   if constexpr (R == 2) dft2<INV>(v);
   else if constexpr (R == 3) dft3<INV>(v);
   else if constexpr (R == 4) dft4<INV>(v);
@@ -226,6 +260,162 @@ __device__ __forceinline__ void stage_twiddles(C* dst, const C* __restrict__ tab
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
+// ---- twiddled stages in the tangent form (FP64) ------------------------------
+// A root of unity is stored as w = i^Q rho (1 + i tau) with |tau| <= 1: the
+// tangent form of the twiddled FFT stages (the table at kTwiddleTotal +
+// twiddle_offset(L) holds (rho, tau) of w_L^m; Q follows from m and L). Then
+// x + w b and x - w b take 6 FMAs, u = b (1 + i tau) and x +- rho i^Q u, where
+// the power of i only swaps the parts of u and flips the signs of rho (integer
+// operations); the usual complex product and two additions take 8. This is
+// the FMA butterfly of S. Goedecker, SIAM J. Sci. Comput. 18 (1997) 1605.
+
+template <class C>
+struct IsFp64Complex {
+  static constexpr bool value = false;
+};
+template <>
+struct IsFp64Complex<double2> {
+  static constexpr bool value = true;
+};
+
+// the table of the FFT stages of length L: the tangent form for FP64, the
+// (cos, -sin) form for double-float elements
+template <int L, class C>
+__device__ __forceinline__ void stage_fft_twiddles(C* dst, const C* __restrict__ table, int n) {
+  constexpr int off = (IsFp64Complex<C>::value ? kTwiddleTotal : 0) + twiddle_offset(L);
+  const C* src = table + off;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// x with its sign bit flipped when f is 1
+__host__ __device__ __forceinline__ double flip_sign(double x, unsigned f) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(x) ^ ((unsigned long long)f << 63)));
+#else
+  unsigned long long b;
+  memcpy(&b, &x, sizeof b);
+  b ^= (unsigned long long)f << 63;
+  memcpy(&x, &b, sizeof b);
+  return x;
+#endif
+}
+
+// w = i^Q rho (1 + i tau) as the multipliers of the butterfly: the real and
+// imaginary parts of w b are rx p_x and ry p_y, (p_x, p_y) = u or u swapped
+struct TanTw {
+  double rx, ry, tau;
+  bool swap;
+};
+
+// w_L^m (its conjugate for the inverse) from the tangent table t: with qr the
+// nearest quarter turn of 2 pi m / L (halves rounded up), w_L^m = (-i)^qr
+// rho (1 + i tau); the conjugate is i^qr rho (1 - i tau)
+template <int L, bool INV>
+__host__ __device__ __forceinline__ TanTw tan_twiddle(const double2* __restrict__ t, int m) {
+  const double2 e = t[m];
+  const int qr = (8 * m + L) / (2 * L);
+  const unsigned Q = (unsigned)(INV ? qr : -qr) & 3u;
+  // i^Q u: Q = 0 (u_x, u_y), 1 (-u_y, u_x), 2 (-u_x, -u_y), 3 (u_y, -u_x)
+  return TanTw{flip_sign(e.x, ((Q + 1u) >> 1) & 1u), flip_sign(e.x, Q >> 1), INV ? -e.y : e.y, (Q & 1u) != 0};
+}
+
+// x + w b into x, x - w b into b (6 FMAs)
+__host__ __device__ __forceinline__ void bfly_tan(double2& x, double2& b, const TanTw& w) {
+  const double ux = fma(-w.tau, b.y, b.x), uy = fma(w.tau, b.x, b.y);
+  const double px = w.swap ? uy : ux, py = w.swap ? ux : uy;
+  const double2 a = x;
+  x = make_double2(fma(w.rx, px, a.x), fma(w.ry, py, a.y));
+  b = make_double2(fma(-w.rx, px, a.x), fma(-w.ry, py, a.y));
+}
+
+// w b (2 FMAs and 2 products)
+__host__ __device__ __forceinline__ double2 mul_tan(double2 b, const TanTw& w) {
+  const double ux = fma(-w.tau, b.y, b.x), uy = fma(w.tau, b.x, b.y);
+  return make_double2(w.rx * (w.swap ? uy : ux), w.ry * (w.swap ? ux : uy));
+}
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+__host__ __device__ constexpr int bit_reverse(int r, int bits) {
+  return bits == 0 ? 0 : ((r & 1) << (bits - 1)) | bit_reverse(r >> 1, bits - 1);
+}
+
+// layer LAYER of dft_pow2_twiddled, from the pair offset S on (every index a
+// compile-time constant, so the R values stay in registers)
+template <int L, int R, bool INV, int LAYER, int S>
+__host__ __device__ __forceinline__ void tw_layer(double2 (&a)[R], const double2* __restrict__ t, int m1) {
+  constexpr int half = 1 << (LAYER - 1);
+  if constexpr (S < half) {
+    const TanTw w = tan_twiddle<L, INV>(t, m1 * (R >> LAYER) + S * (L >> LAYER));
+    if constexpr (S < R) bfly_tan(a[S], a[S + half], w);
+    if constexpr (2 * half + S < R) bfly_tan(a[2 * half + S], a[3 * half + S], w);
+    if constexpr (4 * half + S < R) bfly_tan(a[4 * half + S], a[5 * half + S], w);
+    if constexpr (6 * half + S < R) bfly_tan(a[6 * half + S], a[7 * half + S], w);
+    if constexpr (8 * half + S < R) bfly_tan(a[8 * half + S], a[9 * half + S], w);
+    if constexpr (10 * half + S < R) bfly_tan(a[10 * half + S], a[11 * half + S], w);
+    if constexpr (12 * half + S < R) bfly_tan(a[12 * half + S], a[13 * half + S], w);
+    if constexpr (14 * half + S < R) bfly_tan(a[14 * half + S], a[15 * half + S], w);
+    tw_layer<L, R, INV, LAYER, S + 1>(a, t, m1);
+  }
+}
+
+template <int L, int R, bool INV, int LAYER>
+__host__ __device__ __forceinline__ void tw_layers(double2 (&a)[R], const double2* __restrict__ t, int m1) {
+  if constexpr ((1 << LAYER) <= R) {
+    tw_layer<L, R, INV, LAYER, 0>(a, t, m1);
+    tw_layers<L, R, INV, LAYER + 1>(a, t, m1);
+  }
+}
+
+template <int R, int P, int I>
+__host__ __device__ __forceinline__ void load_bit_reversed(double2 (&a)[R], const double2* v) {
+  if constexpr (I < R) {
+    constexpr int src = bit_reverse(I, P);
+    a[I] = v[src];
+    load_bit_reversed<R, P, I + 1>(a, v);
+  }
+}
+
+// Y_s = sum_r v_r omega^r w_R^(r s), omega = w_L^m1, R = 2^P <= 16, in place:
+// the DFT of a twiddled radix-R stage as P layers of radix-2 decimation in
+// time on the bit-reversed inputs. Layer l combines pairs half = 2^(l-1)
+// apart with the twiddle omega^(R / 2^l) w_(2^l)^s = w_L^(m1 R / 2^l + s L / 2^l)
+// for the pair's offset s in its group; 3 P R FP64 operations (72 for R = 8
+// against 80 for seven complex products and the radix-8 butterfly).
+template <int L, int R, bool INV>
+__host__ __device__ __forceinline__ void dft_pow2_twiddled(double2* v, const double2* __restrict__ t, int m1) {
+  constexpr int P = ilog2(R);
+  static_assert((1 << P) == R && R <= 16 && L % R == 0, "radix 2^P <= 16 dividing L");
+  double2 a[R];
+  load_bit_reversed<R, P, 0>(a, v);
+  tw_layers<L, R, INV, 1>(a, t, m1);
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = a[r];
+}
+
+// the butterfly of a stage with sub-transform size NS > 1 of a compile-time
+// plan: v_r times w_L^(r m1), then the R-point DFT. FP64 elements use the
+// tangent table (radix 2^P as above; radix 3 by two products in the tangent
+// form); double-float elements the (cos, -sin) table.
+template <int L, int R, bool INV, class C>
+__device__ __forceinline__ void twiddled_butterfly(C* v, const C* __restrict__ tw, int m1) {
+  if constexpr (IsFp64Complex<C>::value) {
+    if constexpr (R == 3) {
+      v[1] = mul_tan(v[1], tan_twiddle<L, INV>(tw, m1));
+      v[2] = mul_tan(v[2], tan_twiddle<L, INV>(tw, 2 * m1));
+      dft3<INV>(v);
+    } else {
+      dft_pow2_twiddled<L, R, INV>(v, tw, m1);
+    }
+  } else {
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      const C w = tw[r * m1];
+      v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+    }
+    dft_r<R, INV>(v);
+  }
+}
+
 template <int L, int R, int NS, bool INV, bool JFAST, class C>
 __device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __restrict__ dst,
                                                const PencilLayout& lay, const C* __restrict__ tw) {
@@ -241,15 +431,11 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __r
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = s[(j + r * NB) * lay.j_stride];
     if constexpr (NS > 1) {
-      const int k = j % NS;
       constexpr int step = L / (NS * R);
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        const C w = tw[r * k * step];
-        v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
-      }
+      twiddled_butterfly<L, R, INV>(v, tw, (j % NS) * step);
+    } else {
+      dft_r<R, INV>(v);
     }
-    dft_r<R, INV>(v);
     const int base = (j / NS) * NS * R + (j % NS);
 #pragma unroll
     for (int r = 0; r < R; ++r) d[(base + r * NS) * lay.j_stride] = v[r];
@@ -269,7 +455,8 @@ __device__ __forceinline__ C* run_stages(C* a, C* b, const PencilLayout& lay, co
 }
 
 // Transform all pencils of `a` (length L). Uses `b` as the ping-pong partner;
-// `tw` is the length-L twiddle table (in shared memory). Returns the buffer
+// `tw` is the length-L table of the FFT stages (stage_fft_twiddles: the
+// tangent form for FP64) in shared memory. Returns the buffer
 // holding the result. Synchronises the CTA before each stage and after the
 // last one.
 template <int L, bool INV, bool JFAST, class C>
@@ -478,7 +665,7 @@ __device__ __noinline__ C* fft_pencils_rt(C* a, C* b, const PencilLayout lay, co
 template <int L, int AX, class C>
 __device__ __forceinline__ void stage_axis_twiddles(C* dst, const C* __restrict__ tw, const Grid& g) {
   if constexpr (L > 0) {
-    stage_twiddles<L>(dst, tw, L);
+    stage_fft_twiddles<L>(dst, tw, L);
   } else {
     const FftPlan& p = AX ? g.py : g.px;
     for (int i = threadIdx.x; i < p.tw_len; i += blockDim.x) dst[i] = tw[p.tw_off + i];

@@ -29,18 +29,23 @@ __host__ __device__ constexpr int twiddle_offset(int L) {
   return off;
 }
 constexpr int kTwiddleTotal = twiddle_offset(kMaxN) + kMaxN;
+// Every length has two tables: w_L^m as (cos, -sin) at twiddle_offset(L) + m,
+// and the same roots in the tangent form of the twiddled FFT stages
+// (fft_core.cuh) at kTwiddleTotal + twiddle_offset(L) + m. Run-time plans put
+// their tables after both (from kTwiddleTables on).
+constexpr int kTwiddleTables = 2 * kTwiddleTotal;
 
 // ---------------------------------------------------------------------------
 // complex helpers (double2 = re, im)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 // a * w with w a unit twiddle: 2 DMUL + 2 DFMA
-__device__ __forceinline__ double2 cmul(double2 a, double2 w) {
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 w) {
   return make_double2(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
 }
 // a * conj(w)
-__device__ __forceinline__ double2 cmulc(double2 a, double2 w) {
+__host__ __device__ __forceinline__ double2 cmulc(double2 a, double2 w) {
   return make_double2(fma(a.x, w.x, a.y * w.y), fma(a.y, w.x, -a.x * w.y));
 }
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }

@@ -85,9 +85,12 @@ inline Tiling df_tiles(const Tiling& t) {
   return d;
 }
 
-// the twiddle tables of every supported length, w_L^m = exp(-2 pi i m / L) at
-// twiddle_offset(L) + m, into t[kTwiddleTotal] (host memory)
+// the twiddle tables of every supported length into t[kTwiddleTables] (host
+// memory): w_L^m = exp(-2 pi i m / L) at twiddle_offset(L) + m, its tangent
+// form at kTwiddleTotal + twiddle_offset(L) + m
 void fill_twiddle_table(double2* t);
+// the tangent form (rho, tau) of w_L^m for m < L into t[L] (host memory)
+void fill_tangent_twiddles_of_length(double2* t, int L);
 
 // run-time plan of a length without a compile-time plan (L = 0 when it has
 // one); its tables (tw_len entries) go to offset tw_off of the context's table

@@ -93,24 +93,36 @@ __global__ void __launch_bounds__(kThreads) k_inv_z_b(Grid g, int LB, const Cell
 // host side: twiddle tables, tiling, dispatch on the compile-time lengths
 // ---------------------------------------------------------------------------
 void fill_twiddle_table(double2* t) {
-  const long double two_pi = 6.283185307179586476925286766559005768L;
-  for (int i = 0; i < kTwiddleTotal; ++i) t[i] = make_double2(0.0, 0.0);
+  for (int i = 0; i < kTwiddleTables; ++i) t[i] = make_double2(0.0, 0.0);
   for (int L = 1; L <= kMaxN; ++L) {
     if (!fft_length_ok(L)) continue;
-    for (int m = 0; m < L; ++m) {
-      double c, s;
-      if ((4 * m) % L == 0) {
-        // exact values at multiples of pi/2
-        const int q = (4 * m) / L;
-        c = (q == 0) ? 1.0 : (q == 2) ? -1.0 : 0.0;
-        s = (q == 1) ? -1.0 : (q == 3) ? 1.0 : 0.0;
-      } else {
-        const long double a = two_pi * (long double)m / (long double)L;
-        c = (double)cosl(a);
-        s = (double)-sinl(a);
-      }
-      t[twiddle_offset(L) + m] = make_double2(c, s);
+    fill_twiddles_of_length(t + twiddle_offset(L), L);
+    fill_tangent_twiddles_of_length(t + kTwiddleTotal + twiddle_offset(L), L);
+  }
+}
+
+// w_L^m = i^Q rho (1 + i tau) with qr the nearest quarter turn of 2 pi m / L
+// (halves rounded up), Q = -qr mod 4 (computed again by the kernels from m and
+// L), phi = 2 pi m / L - qr pi / 2 in [-pi/4, pi/4), rho = cos phi,
+// tau = -tan phi; entry m holds (rho, tau)
+void fill_tangent_twiddles_of_length(double2* t, int L) {
+  const long double half_pi = 1.570796326794896619231321691639751442L;
+  for (int m = 0; m < L; ++m) {
+    const int qr = (8 * m + L) / (2 * L);
+    const int n4 = 4 * m - qr * L;  // phi = (pi / 2) n4 / L, |n4| <= L / 2
+    double rho, tau;
+    if (n4 == 0) {
+      rho = 1.0;
+      tau = 0.0;
+    } else if (2 * n4 == L || 2 * n4 == -L) {
+      rho = (double)sqrtl(0.5L);
+      tau = n4 > 0 ? -1.0 : 1.0;
+    } else {
+      const long double phi = half_pi * (long double)n4 / (long double)L;
+      rho = (double)cosl(phi);
+      tau = (double)-tanl(phi);
     }
+    t[m] = make_double2(rho, tau);
   }
 }
 

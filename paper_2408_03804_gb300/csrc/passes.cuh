@@ -226,7 +226,7 @@ __device__ __forceinline__ void fwd_z_body(int cta, Grid g, int LB, const double
     C* bufB = smem + 9 * LB * M;
     C* twM = bufB + 9 * LB * M;  // length-M table (half-length FFT)
     C* twN = twM + M;            // first M/2 + 1 entries of the length-NZ table (unpack)
-    stage_twiddles<M>(twM, tw, M);
+    stage_fft_twiddles<M>(twM, tw, M);
     stage_twiddles<NZ>(twN, tw, M / 2 + 1);
     const long long line0 = (long long)cta * LB;
     const long long v0 = line0 * NZ;
@@ -299,7 +299,7 @@ __device__ __forceinline__ void inv_z_body(int cta, Grid g, int LB, const C* __r
     C* bufB = smem + 9 * LB * M;
     C* twM = bufB + 9 * LB * M;
     C* twN = twM + M;
-    stage_twiddles<M>(twM, tw, M);
+    stage_fft_twiddles<M>(twM, tw, M);
     stage_twiddles<NZ>(twN, tw, M / 2 + 1);
     __syncthreads();
     // pack Z_k = (X_k + conj X_{M-k}) + i w^-k (X_k - conj X_{M-k}); the

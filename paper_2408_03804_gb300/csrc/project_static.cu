@@ -24,8 +24,8 @@ constexpr long long kStaticMaxVoxels = 32768;
 constexpr long long kStaticSpectrum = 9 * kStaticMaxVoxels;
 
 static __device__ __align__(256) double2 g_static_spectrum[kStaticSpectrum];
-static __device__ __align__(256) double2 g_static_twiddles[kTwiddleTotal];
-static_assert(kTwiddleTotal == 892, "the header states the size of the static twiddle tables");
+static __device__ __align__(256) double2 g_static_twiddles[kTwiddleTables];
+static_assert(kTwiddleTables == 1784, "the header states the size of the static twiddle tables");
 
 namespace {
 
@@ -53,9 +53,9 @@ int static_setup(int dev, cudaStream_t s, double2** spectrum, double2** twiddles
   e = cudaMemcpyAsync(&head, *twiddles, sizeof(double2), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess && !(head.x == 1.0 && head.y == 0.0)) {
-    std::vector<double2> tw(kTwiddleTotal);
+    std::vector<double2> tw(kTwiddleTables);
     fill_twiddle_table(tw.data());
-    e = cudaMemcpyAsync(*twiddles, tw.data(), kTwiddleTotal * sizeof(double2), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(*twiddles, tw.data(), kTwiddleTables * sizeof(double2), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
   if (e != cudaSuccess) {

@@ -4,8 +4,9 @@ Every cell of a batch runs Algorithm 1 with its own Newton and CG state;
 passes are launched per group of equal grids and the CG iterations run as a
 captured CUDA graph. The tests compare each cell with the oracle's solve of
 that cell, and with the single-cell GPU solve (fft_homog_solve): the same
-kernels in the same order, so the results agree to rounding of the fixed
-reduction order (they are bit-identical in practice).
+pass bodies in the same order, but the single-cell contexts tile small grids
+finer, so their dot products sum the same terms in another order; the two
+fields agree to a few units of rounding (5e-14 of the field's maximum).
 """
 
 import numpy as np
@@ -44,7 +45,7 @@ def test_batch_of_uneven_linear_cells_matches_oracle_and_single_solves(fh):
             F1 = torch.zeros((9,) + phase.shape, dtype=torch.float64, device="cuda")
             p1, st1, _ = ctx.fft_homog_solve(fh.Material(0, phase, params, scale=scale), Ebar, F1, options=opts)
         np.testing.assert_allclose(pbar[i], p1, rtol=1e-14, atol=1e-18)
-        assert np.abs(F_batch[i] - F1.cpu().numpy()).max() <= 1e-14 * np.abs(F_batch[i]).max()
+        assert np.abs(F_batch[i] - F1.cpu().numpy()).max() <= 5e-14 * np.abs(F_batch[i]).max()
         assert cg[i] == st1["n_cg"]
 
 
