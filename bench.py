@@ -90,7 +90,7 @@ def fp64_ops(cls: str, nx: int, ny: int, nz: int):
     n = nx * ny * nz
     h = nx * ny * (nz // 2 + 1)
     m = nz // 2
-    r2c = 9 * (FP64_FFT_OPS[m] * m + 12 * (m // 2 + 1)) * nx * ny  # half-length FFT + unpack
+    r2c = 9 * (FP64_FFT_OPS[m] * m + 10 * (m // 2 + 1)) * nx * ny  # half-length FFT + unpack (tangent-form pairs)
     if cls == "fwd_z":
         return 99 * n + r2c + 3 * 4 * (m // 2 + 1) * nx * ny
     if cls == "fwd_y":

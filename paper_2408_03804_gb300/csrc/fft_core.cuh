@@ -334,6 +334,26 @@ __host__ __device__ __forceinline__ double2 mul_tan(double2 b, const TanTw& w) {
   return make_double2(w.rx * (w.swap ? uy : ux), w.ry * (w.swap ? ux : uy));
 }
 
+// The pair steps of the real-to-complex transform along z (passes.cuh) in the
+// tangent form, w = w_NZ^k: unpack (x_k, x_{M-k}) = (e + t, conj(e - t)) with
+// t = -i w o, and pack (z_k, z_{M-k}) = (a + u, conj(a - u)) with u = i conj(w) b
+// (wc: the conjugate's multipliers). 6 FMAs each against a complex product and
+// two complex additions (8).
+__host__ __device__ __forceinline__ void unpack_pair_tan(double2 e, double2 o, const TanTw& w, double2& xk,
+                                                         double2& xm) {
+  const double ux = fma(-w.tau, o.y, o.x), uy = fma(w.tau, o.x, o.y);
+  const double px = w.swap ? uy : ux, py = w.swap ? ux : uy;  // w o = (rx px, ry py)
+  xk = make_double2(fma(w.ry, py, e.x), fma(-w.rx, px, e.y));
+  xm = make_double2(fma(-w.ry, py, e.x), fma(-w.rx, px, -e.y));
+}
+__host__ __device__ __forceinline__ void pack_pair_tan(double2 a, double2 b, const TanTw& wc, double2& zk,
+                                                       double2& zm) {
+  const double ux = fma(-wc.tau, b.y, b.x), uy = fma(wc.tau, b.x, b.y);
+  const double px = wc.swap ? uy : ux, py = wc.swap ? ux : uy;  // conj(w) b = (rx px, ry py)
+  zk = make_double2(fma(-wc.ry, py, a.x), fma(wc.rx, px, a.y));
+  zm = make_double2(fma(wc.ry, py, a.x), fma(wc.rx, px, -a.y));
+}
+
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 __host__ __device__ constexpr int bit_reverse(int r, int bits) {
   return bits == 0 ? 0 : ((r & 1) << (bits - 1)) | bit_reverse(r >> 1, bits - 1);

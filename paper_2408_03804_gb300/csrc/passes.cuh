@@ -225,9 +225,9 @@ __device__ __forceinline__ void fwd_z_body(int cta, Grid g, int LB, const double
     C* bufA = smem;
     C* bufB = smem + 9 * LB * M;
     C* twM = bufB + 9 * LB * M;  // length-M table (half-length FFT)
-    C* twN = twM + M;            // first M/2 + 1 entries of the length-NZ table (unpack)
+    C* twN = twM + M;            // first M/2 + 1 entries of the length-NZ table (unpack; tangent form in FP64)
     stage_fft_twiddles<M>(twM, tw, M);
-    stage_twiddles<NZ>(twN, tw, M / 2 + 1);
+    stage_fft_twiddles<NZ>(twN, tw, M / 2 + 1);
     const long long line0 = (long long)cta * LB;
     const long long v0 = line0 * NZ;
 
@@ -254,9 +254,14 @@ __device__ __forceinline__ void fwd_z_body(int cta, Grid g, int LB, const double
       const C zm = Zq[k == 0 ? 0 : M - k];
       const C e = cadd_conj(zk, zm);
       const C o = csub_conj(zk, zm);
-      const C tt = mul_mi<false>(cmul(o, twN[k]));  // -i w^k o
-      C xk = cadd(e, tt);
-      C xm = cconj(csub(e, tt));
+      C xk, xm;
+      if constexpr (IsFp64Complex<C>::value) {
+        unpack_pair_tan(e, o, tan_twiddle<NZ, false>(twN, k), xk, xm);
+      } else {
+        const C tt = mul_mi<false>(cmul(o, twN[k]));  // -i w^k o
+        xk = cadd(e, tt);
+        xm = cconj(csub(e, tt));
+      }
       C* out = S + (long long)c * g.nspec + (line0 + line) * g.nzh;
       if (c % 3 == 2) {
         xk = cscale(xk, wave_real(wave_int(k, NZ), rsz));
@@ -300,7 +305,7 @@ __device__ __forceinline__ void inv_z_body(int cta, Grid g, int LB, const C* __r
     C* twM = bufB + 9 * LB * M;
     C* twN = twM + M;
     stage_fft_twiddles<M>(twM, tw, M);
-    stage_twiddles<NZ>(twN, tw, M / 2 + 1);
+    stage_fft_twiddles<NZ>(twN, tw, M / 2 + 1);
     __syncthreads();
     // pack Z_k = (X_k + conj X_{M-k}) + i w^-k (X_k - conj X_{M-k}); the
     // imaginary parts of X_0 and X_M are dropped (complex-to-real semantics)
@@ -315,9 +320,16 @@ __device__ __forceinline__ void inv_z_body(int cta, Grid g, int LB, const C* __r
         xm = creal(xm);
       }
       const C a = cadd_conj(xk, xm);
-      const C u = mul_mi<true>(cmulc(csub_conj(xk, xm), twN[k]));  // i w^-k b
-      bufA[q * M + k] = cadd(a, u);
-      if (k != 0 && M - k != k) bufA[q * M + (M - k)] = cconj(csub(a, u));
+      C zk, zm;
+      if constexpr (IsFp64Complex<C>::value) {
+        pack_pair_tan(a, csub_conj(xk, xm), tan_twiddle<NZ, true>(twN, k), zk, zm);
+      } else {
+        const C u = mul_mi<true>(cmulc(csub_conj(xk, xm), twN[k]));  // i w^-k b
+        zk = cadd(a, u);
+        zm = cconj(csub(a, u));
+      }
+      bufA[q * M + k] = zk;
+      if (k != 0 && M - k != k) bufA[q * M + (M - k)] = zm;
     }
     const C* Rz = fft_pencils<M, true, true>(bufA, bufB, PencilLayout{9 * LB, M, 1, 1, 1}, twM);
     for (int t = threadIdx.x; t < LB * NZ; t += blockDim.x) {
