@@ -267,7 +267,7 @@ __device__ __forceinline__ void stage_twiddles(C* dst, const C* __restrict__ tab
 // x + w b and x - w b take 6 FMAs, u = b (1 + i tau) and x +- rho i^Q u, where
 // the power of i only swaps the parts of u and flips the signs of rho (integer
 // operations); the usual complex product and two additions take 8. This is
-// the FMA butterfly of S. Goedecker, SIAM J. Sci. Comput. 18 (1997) 1605.
+// the FMA butterfly of S. Goedecker (SIAM J. Sci. Comput. 18, 1997).
 
 template <class C>
 struct IsFp64Complex {
