@@ -79,7 +79,7 @@ def algorithmic_work(cls: str, nx: int, ny: int, nz: int):
 # later ones (radix 2^P: P layers of 6-FMA butterflies with the twiddles in the tangent form,
 # 3 P per point; radix 3: two tangent-form products of 4 operations and the radix-3 butterfly)
 FFT_PLANS = {1: (), 2: (2,), 3: (3,), 4: (4,), 6: (2, 3), 8: (8,), 12: (4, 3), 16: (16,), 24: (8, 3),
-             32: (8, 4), 48: (16, 3), 64: (8, 8), 96: (8, 4, 3), 128: (16, 8), 192: (16, 4, 3), 256: (16, 16)}
+             32: (8, 4), 48: (16, 3), 64: (8, 8), 96: (8, 4, 3), 128: (16, 8), 192: (16, 4, 3), 256: (16, 4, 4)}
 BUTTERFLY_OPS = {2: 2.0, 3: 4.0, 4: 4.0, 8: 6.5, 16: 9.0}
 TWIDDLED_OPS = {2: 3.0, 3: 4.0 + 8.0 / 3.0, 4: 6.0, 8: 9.0, 16: 12.0}
 FP64_FFT_OPS = {L: sum((TWIDDLED_OPS if k else BUTTERFLY_OPS)[r] for k, r in enumerate(plan))

@@ -14,8 +14,9 @@
 // their butterflies (6 FMAs per radix-2 butterfly, see below).
 //
 // The plans minimise FP64 instructions (FP64 issue is the bound of this path):
-// 32 = 8x4, 64 = 8x8, 128 = 16x8, 256 = 16x16, smaller powers of two in one
-// stage; lengths 3 * 2^a end with a radix-3 stage (48 = 16x3, 96 = 8x4x3).
+// 32 = 8x4, 64 = 8x8, 128 = 16x8, 256 = 16x16 (16x4x4 in FP64), smaller powers
+// of two in one stage; lengths 3 * 2^a end with a radix-3 stage (48 = 16x3,
+// 96 = 8x4x3).
 // Per complex point a length-128 transform takes 18 FP64 operations (144 for
 // the radix-16 butterfly, 72 for a twiddled radix-8 one).
 #pragma once
@@ -230,6 +231,17 @@ template <> struct Plan<96>  { static constexpr int n = 3; static constexpr int 
 template <> struct Plan<128> { static constexpr int n = 2; static constexpr int r[3] = {16, 8, 1}; };
 template <> struct Plan<192> { static constexpr int n = 3; static constexpr int r[3] = {16, 4, 3}; };
 template <> struct Plan<256> { static constexpr int n = 2; static constexpr int r[3] = {16, 16, 1}; };
+
+// the plan of an element type: FP64 transforms of length 256 run 16 x 4 x 4,
+// the same FP64 operations as 16 x 16 in the tangent form (9 + 6 + 6 per
+// point) without the registers of a twiddled radix-16 butterfly, which spilled
+template <int L, class C>
+struct PlanFor : Plan<L> {};
+template <>
+struct PlanFor<256, double2> {
+  static constexpr int n = 3;
+  static constexpr int r[3] = {16, 4, 4};
+};
 
 // Pencil addressing inside a shared buffer: element j of pencil q lives at
 // q_stride * q + j_stride * j (in double2 units). Pencils come in groups of
@@ -464,10 +476,10 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __r
 
 template <int L, bool INV, bool JFAST, int S, int NS, class C>
 __device__ __forceinline__ C* run_stages(C* a, C* b, const PencilLayout& lay, const C* tw) {
-  if constexpr (S == Plan<L>::n) {
+  if constexpr (S == PlanFor<L, C>::n) {
     return a;
   } else {
-    constexpr int R = Plan<L>::r[S];
+    constexpr int R = PlanFor<L, C>::r[S];
     __syncthreads();
     stockham_stage<L, R, NS, INV, JFAST>(a, b, lay, tw);
     return run_stages<L, INV, JFAST, S + 1, NS * R>(b, a, lay, tw);
