@@ -354,6 +354,19 @@ FH_API int fh_profile_read(fh_ctx* ctx, long long counts[FH_PROF_NCLASS], double
 FH_API int fh_probe_fp64(int ctas_per_sm, int chains, long long iters, void* cuda_stream, double* ms_out,
                          double* lane_ops_out);
 
+/* The twiddle tables of the compile-time FFT plans (the transforms of Eq. 1),
+ * for checking on the host (no counterpart in the paper; touches no device).
+ * out receives 2 * count doubles: count complex entries, count = 2 * T where
+ * T = 892 is the total length of the tables of all lengths L in {1, 2, 3, 4, 6,
+ * 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256}, stored back to back in that
+ * order. Entry o(L) + m (o(L) the sum of the shorter lengths) is w_L^m =
+ * exp(-2 pi i m / L) as (cos, -sin); entry T + o(L) + m the same root in the
+ * tangent form (rho, tau) of the FP64 stages: with qr = floor((8 m + L) / (2 L))
+ * (the nearest quarter turn), w_L^m = (-i)^qr rho (1 + i tau), |tau| <= 1.
+ * Returns count (and writes nothing) when out is NULL or capacity (in complex
+ * entries) is below count; otherwise writes the tables and returns count. */
+FH_API int fh_twiddle_tables(double* out, int capacity);
+
 /* The double-float conversions of FH_ARITH_DF64, for checking (no
  * counterpart in the paper): for each of the n device doubles in_dev, hi_dev
  * and lo_dev (device floats, NULL to skip) get the split the double-float

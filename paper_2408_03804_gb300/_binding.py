@@ -47,7 +47,7 @@ _ERR_NAMES = {1: "FH_ERR_ARG", 2: "FH_ERR_CUDA", 3: "FH_ERR_NOT_CONVERGED", 4: "
 # every symbol include/fft_homog.h declares
 EXPORTS = ["fh_default_options", "fh_create", "fh_destroy", "fh_last_error_string", "fh_constitutive",
            "fh_project", "fh_matvec", "fft_homog_solve", "fh_profile_enable", "fh_profile_read", "fh_project_static", "fft_homog_tangent", "fft_homog_sensitivity", "fft_homog_stress_sensitivity",
-           "fh_batch_create", "fh_batch_destroy", "fft_homog_solve_batched", "fh_autotune", "fh_probe_fp64", "fh_df64_roundtrip",
+           "fh_batch_create", "fh_batch_destroy", "fft_homog_solve_batched", "fh_autotune", "fh_probe_fp64", "fh_df64_roundtrip", "fh_twiddle_tables",
            "fh_fno_param_count", "fh_fno_create", "fh_fno_destroy", "fh_fno_set_params", "fh_fno_forward",
            "fh_fno_loss_grad", "fh_fno_adam", "fh_fno_make_target", "fh_fno_warm_start", "fh_fno_test_skip_mma"]
 
@@ -148,6 +148,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.fh_probe_fp64.restype = c_int
     lib.fh_df64_roundtrip.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_longlong, c_void_p]
     lib.fh_df64_roundtrip.restype = c_int
+    lib.fh_twiddle_tables.argtypes = [POINTER(c_double), c_int]
+    lib.fh_twiddle_tables.restype = c_int
     lib.fh_fno_param_count.argtypes = []
     lib.fh_fno_param_count.restype = ctypes.c_longlong
     lib.fh_fno_create.argtypes = [POINTER(c_void_p), c_int, c_int, c_int, c_int, c_int, c_void_p]
@@ -234,6 +236,18 @@ def fh_df64_roundtrip(x, hi=None, lo=None, out=None, stream=None):
     out = torch.empty_like(x) if out is None else out
     _check(load().fh_df64_roundtrip(_ptr(x), _ptr(hi), _ptr(lo), _ptr(out), int(x.numel()), c_void_p(stream)))
     return hi, lo, out
+
+
+def fh_twiddle_tables():
+    """The library's twiddle tables (host only): a complex numpy array of 2 T entries, w_L^m as
+    (cos, -sin) at offset(L) + m and its tangent form (rho, tau) at T + offset(L) + m."""
+    lib = load()
+    n = lib.fh_twiddle_tables(None, 0)
+    buf = (c_double * (2 * n))()
+    if lib.fh_twiddle_tables(buf, n) != n:
+        raise FhError(FH_ERR_ARG, "fh_twiddle_tables: unexpected size")
+    a = np.frombuffer(buf, dtype=np.float64).copy().reshape(n, 2)
+    return a[:, 0] + 1j * a[:, 1]
 
 
 def fh_probe_fp64(ctas_per_sm: int = 4, chains: int = 8, iters: int = 1 << 18, stream=None):

@@ -1005,6 +1005,18 @@ int fh_profile_enable(fh_ctx* ctx, int enable) {
   return FH_OK;
 }
 
+int fh_twiddle_tables(double* out, int capacity) {
+  g_err[0] = 0;
+  if (!out || capacity < kTwiddleTables) return kTwiddleTables;
+  std::vector<double2> t(kTwiddleTables);
+  fill_twiddle_table(t.data());
+  for (int i = 0; i < kTwiddleTables; ++i) {
+    out[2 * i] = t[i].x;
+    out[2 * i + 1] = t[i].y;
+  }
+  return kTwiddleTables;
+}
+
 int fh_profile_read(fh_ctx* ctx, long long counts[FH_PROF_NCLASS], double ms[FH_PROF_NCLASS]) {
   g_err[0] = 0;
   if (!ctx) return fail(FH_ERR_ARG, "context is NULL");
