@@ -26,28 +26,28 @@ struct __align__(16) dfc {
 };
 static_assert(sizeof(dfc) == sizeof(double2), "a double-float entry takes the place of an FP64 one");
 
-__device__ __forceinline__ df64 two_sum(float a, float b) {
+__host__ __device__ __forceinline__ df64 two_sum(float a, float b) {
   const float s = a + b;
   const float bb = s - a;
   return df64{s, (a - (s - bb)) + (b - bb)};
 }
 
-__device__ __forceinline__ df64 fast_two_sum(float a, float b) {
+__host__ __device__ __forceinline__ df64 fast_two_sum(float a, float b) {
   const float s = a + b;
   return df64{s, b - (s - a)};
 }
 
-__device__ __forceinline__ df64 dd_add(df64 a, df64 b) {
+__host__ __device__ __forceinline__ df64 dd_add(df64 a, df64 b) {
   df64 s = two_sum(a.hi, b.hi);
   s.lo += a.lo + b.lo;
   return fast_two_sum(s.hi, s.lo);
 }
 
-__device__ __forceinline__ df64 dd_neg(df64 a) { return df64{-a.hi, -a.lo}; }
+__host__ __device__ __forceinline__ df64 dd_neg(df64 a) { return df64{-a.hi, -a.lo}; }
 
-__device__ __forceinline__ df64 dd_sub(df64 a, df64 b) { return dd_add(a, dd_neg(b)); }
+__host__ __device__ __forceinline__ df64 dd_sub(df64 a, df64 b) { return dd_add(a, dd_neg(b)); }
 
-__device__ __forceinline__ df64 dd_mul(df64 a, df64 b) {
+__host__ __device__ __forceinline__ df64 dd_mul(df64 a, df64 b) {
   const float p = a.hi * b.hi;
   float e = fmaf(a.hi, b.hi, -p);
   e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
@@ -55,7 +55,7 @@ __device__ __forceinline__ df64 dd_mul(df64 a, df64 b) {
 }
 
 // a * b + c with a single renormalisation
-__device__ __forceinline__ df64 dd_fma(df64 a, df64 b, df64 c) {
+__host__ __device__ __forceinline__ df64 dd_fma(df64 a, df64 b, df64 c) {
   const float p = a.hi * b.hi;
   float e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p)));
   df64 s = two_sum(p, c.hi);
@@ -111,29 +111,29 @@ __device__ __forceinline__ double float_bits_to_double(float f) {
 __device__ __forceinline__ double join_df64(df64 a) { return float_bits_to_double(a.hi) + float_bits_to_double(a.lo); }
 
 // ---- complex df64 -----------------------------------------------------------
-__device__ __forceinline__ dfc cadd(dfc a, dfc b) { return dfc{dd_add(a.re, b.re), dd_add(a.im, b.im)}; }
-__device__ __forceinline__ dfc csub(dfc a, dfc b) { return dfc{dd_sub(a.re, b.re), dd_sub(a.im, b.im)}; }
+__host__ __device__ __forceinline__ dfc cadd(dfc a, dfc b) { return dfc{dd_add(a.re, b.re), dd_add(a.im, b.im)}; }
+__host__ __device__ __forceinline__ dfc csub(dfc a, dfc b) { return dfc{dd_sub(a.re, b.re), dd_sub(a.im, b.im)}; }
 // a * w
-__device__ __forceinline__ dfc cmul(dfc a, dfc w) {
+__host__ __device__ __forceinline__ dfc cmul(dfc a, dfc w) {
   return dfc{dd_fma(a.re, w.re, dd_neg(dd_mul(a.im, w.im))), dd_fma(a.re, w.im, dd_mul(a.im, w.re))};
 }
 // a * conj(w)
-__device__ __forceinline__ dfc cmulc(dfc a, dfc w) {
+__host__ __device__ __forceinline__ dfc cmulc(dfc a, dfc w) {
   return dfc{dd_fma(a.re, w.re, dd_mul(a.im, w.im)), dd_fma(a.im, w.re, dd_neg(dd_mul(a.re, w.im)))};
 }
-__device__ __forceinline__ dfc cscale(dfc a, df64 s) { return dfc{dd_mul(a.re, s), dd_mul(a.im, s)}; }
-__device__ __forceinline__ dfc cscale(dfc a, double s) { return cscale(a, to_df64(s)); }
+__host__ __device__ __forceinline__ dfc cscale(dfc a, df64 s) { return dfc{dd_mul(a.re, s), dd_mul(a.im, s)}; }
+__host__ __device__ __forceinline__ dfc cscale(dfc a, double s) { return cscale(a, to_df64(s)); }
 
 // s a + b, zero, the parts of a twiddle (cos, -sin), a Rader permutation entry (two indices)
-__device__ __forceinline__ dfc caxpy(df64 s, dfc a, dfc b) { return dfc{dd_fma(s, a.re, b.re), dd_fma(s, a.im, b.im)}; }
-__device__ __forceinline__ void czero(dfc& a) { a = dfc{df64{0.f, 0.f}, df64{0.f, 0.f}}; }
-__device__ __forceinline__ df64 tw_cos(dfc w) { return w.re; }
-__device__ __forceinline__ df64 tw_sin(dfc w) { return dd_neg(w.im); }
-__device__ __forceinline__ int perm_first(dfc w) { return (int)w.re.hi; }
-__device__ __forceinline__ int perm_second(dfc w) { return (int)w.im.hi; }
+__host__ __device__ __forceinline__ dfc caxpy(df64 s, dfc a, dfc b) { return dfc{dd_fma(s, a.re, b.re), dd_fma(s, a.im, b.im)}; }
+__host__ __device__ __forceinline__ void czero(dfc& a) { a = dfc{df64{0.f, 0.f}, df64{0.f, 0.f}}; }
+__host__ __device__ __forceinline__ df64 tw_cos(dfc w) { return w.re; }
+__host__ __device__ __forceinline__ df64 tw_sin(dfc w) { return dd_neg(w.im); }
+__host__ __device__ __forceinline__ int perm_first(dfc w) { return (int)w.re.hi; }
+__host__ __device__ __forceinline__ int perm_second(dfc w) { return (int)w.im.hi; }
 
 template <bool INV>
-__device__ __forceinline__ dfc mul_mi(dfc a) {
+__host__ __device__ __forceinline__ dfc mul_mi(dfc a) {
   return INV ? dfc{dd_neg(a.im), a.re} : dfc{a.im, dd_neg(a.re)};
 }
 

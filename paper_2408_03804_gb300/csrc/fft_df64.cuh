@@ -9,10 +9,10 @@
 
 namespace fh {
 
-__device__ __forceinline__ df64 dd_half(df64 a) { return df64{0.5f * a.hi, 0.5f * a.lo}; }  // exact
+__host__ __device__ __forceinline__ df64 dd_half(df64 a) { return df64{0.5f * a.hi, 0.5f * a.lo}; }  // exact
 
 template <bool INV>
-__device__ __forceinline__ void dft2(dfc* v) {
+__host__ __device__ __forceinline__ void dft2(dfc* v) {
   const dfc a = v[0], b = v[1];
   v[0] = cadd(a, b);
   v[1] = csub(a, b);
@@ -20,7 +20,7 @@ __device__ __forceinline__ void dft2(dfc* v) {
 
 // X0 = a + t1, X1,2 = a - t1/2 +- sin(pi/3) (-+ i t2), t1 = b + c, t2 = b - c
 template <bool INV>
-__device__ __forceinline__ void dft3(dfc* v) {
+__host__ __device__ __forceinline__ void dft3(dfc* v) {
   const dfc a = v[0];
   const dfc t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
   const dfc m = csub(a, dfc{dd_half(t1.re), dd_half(t1.im)});
@@ -31,7 +31,7 @@ __device__ __forceinline__ void dft3(dfc* v) {
 }
 
 template <bool INV>
-__device__ __forceinline__ void dft4(dfc& v0, dfc& v1, dfc& v2, dfc& v3) {
+__host__ __device__ __forceinline__ void dft4(dfc& v0, dfc& v1, dfc& v2, dfc& v3) {
   const dfc t0 = cadd(v0, v2), t1 = csub(v0, v2);
   const dfc t2 = cadd(v1, v3), t3 = mul_mi<INV>(csub(v1, v3));
   v0 = cadd(t0, t2);
@@ -41,13 +41,13 @@ __device__ __forceinline__ void dft4(dfc& v0, dfc& v1, dfc& v2, dfc& v3) {
 }
 
 template <bool INV>
-__device__ __forceinline__ void dft4(dfc* v) {
+__host__ __device__ __forceinline__ void dft4(dfc* v) {
   dft4<INV>(v[0], v[1], v[2], v[3]);
 }
 
 // o times w8^m for m = 1, 3 (w8 = exp(-+ 2 pi i / 8)): (s + i t) cos(pi/4)
 template <bool INV, int M>
-__device__ __forceinline__ dfc rot8(dfc o) {
+__host__ __device__ __forceinline__ dfc rot8(dfc o) {
   df64 s, t;
   if constexpr (M == 1) {
     s = INV ? dd_sub(o.re, o.im) : dd_add(o.re, o.im);
@@ -61,7 +61,7 @@ __device__ __forceinline__ dfc rot8(dfc o) {
 }
 
 template <bool INV>
-__device__ __forceinline__ void dft8(dfc* v) {
+__host__ __device__ __forceinline__ void dft8(dfc* v) {
   dfc e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
   dfc o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
   dft4<INV>(e0, e1, e2, e3);
@@ -81,7 +81,7 @@ __device__ __forceinline__ void dft8(dfc* v) {
 
 // multiply by w16^m (forward exp(-2 pi i m/16), inverse its conjugate), m in 1..9
 template <bool INV, int M>
-__device__ __forceinline__ dfc rot16(dfc a) {
+__host__ __device__ __forceinline__ dfc rot16(dfc a) {
   if constexpr (M == 4) {
     return mul_mi<INV>(a);
   } else if constexpr (M == 2) {
@@ -97,7 +97,7 @@ __device__ __forceinline__ dfc rot16(dfc a) {
 }
 
 template <bool INV>
-__device__ __forceinline__ void dft16(dfc* v) {
+__host__ __device__ __forceinline__ void dft16(dfc* v) {
   // 16 = 4 x 4: DFT-4 over stride-4 inputs, twiddles w16^(j k1), DFT-4 across
   dfc a[4][4];
 #pragma unroll
@@ -129,7 +129,7 @@ __device__ __forceinline__ void dft16(dfc* v) {
 }
 
 template <int R, bool INV>
-__device__ __forceinline__ void dft_r(dfc* v) {
+__host__ __device__ __forceinline__ void dft_r(dfc* v) {
   if constexpr (R == 2) dft2<INV>(v);
   else if constexpr (R == 3) dft3<INV>(v);
   else if constexpr (R == 4) dft4<INV>(v);

@@ -6,7 +6,9 @@ in the tangent form (rho, tau) of the FP64 stages, w = (-i)^qr rho (1 + i tau)
 with qr the nearest quarter turn. The butterflies themselves are
 host-and-device code: tests/host_fft_check.cu compiles them for the host and
 compares every twiddled stage, the radix-16 butterfly and the real-to-complex
-pair steps with a direct DFT in long double.
+pair steps with a direct DFT in long double; tests/host_df64_check.cu does the
+same for the double-float arithmetic and butterflies of the FH_ARITH_DF64
+option against the error bounds of df64.cuh.
 """
 
 import os
@@ -77,25 +79,48 @@ def test_tangent_form_gives_each_root(tables):
         np.testing.assert_array_equal(tau[exact], 0.0)
 
 
-def test_fp64_butterflies_match_a_direct_dft_on_the_host(tables, tmp_path):
+def _host_program(name, tmp_path):
+    """Compile tests/<name>.cu (host code only) with nvcc; returns the executable."""
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not found")
-    exe = tmp_path / "host_fft_check"
-    src = os.path.join(ROOT, "tests", "host_fft_check.cu")
+    exe = tmp_path / name
+    src = os.path.join(ROOT, "tests", name + ".cu")
     r = subprocess.run([nvcc, "-std=c++17", "--expt-relaxed-constexpr", "-O2", "-o", str(exe), src],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-2000:]
+    return exe
+
+
+def _results(stdout):
+    out = {}
+    for line in stdout.splitlines():
+        name, err = line.rsplit(" ", 1)
+        out[name] = float(err)
+    return out
+
+
+def test_fp64_butterflies_match_a_direct_dft_on_the_host(tables, tmp_path):
+    exe = _host_program("host_fft_check", tmp_path)
     t, total = tables
     table_file = tmp_path / "tables.bin"
     np.stack([t.real, t.imag], axis=1).astype(np.float64).tofile(table_file)
     r = subprocess.run([str(exe), str(table_file), str(total)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
-    worst = {}
-    for line in r.stdout.splitlines():
-        name, err = line.rsplit(" ", 1)
-        worst[name] = float(err)
+    worst = _results(r.stdout)
     assert len(worst) >= 40
     # relative to the largest output; rounding of a few operations per point
     bad = {k: v for k, v in worst.items() if not v <= 1e-15}
+    assert not bad, bad
+
+
+def test_double_float_arithmetic_and_butterflies_within_their_bounds_on_the_host(tmp_path):
+    exe = _host_program("host_df64_check", tmp_path)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
+    ratio = _results(r.stdout)
+    # each line: worst error / its bound (dd_add 4 eps (|a| + |b|), products 4 eps |a b|, an R-point
+    # butterfly 4 eps R max(|re| + |im|), eps = 2^-47)
+    assert {"dd_add", "dd_mul", "dd_fma", "dfc_dft16_fwd", "dfc_dft16_inv", "dfc_twiddle_products"} <= set(ratio)
+    bad = {k: v for k, v in ratio.items() if not v <= 1.0}
     assert not bad, bad
